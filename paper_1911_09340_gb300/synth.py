@@ -1,0 +1,495 @@
+"""Seeded synthetic drift-chamber events for the seed scan.
+
+This module makes INPUTS only: the chamber's wires, the hits an electron leaves in it, and the
+seed-lattice specification of every turn partition.  It holds no step of the scan itself.  The
+detector response is simulated from the closed-form helix of a charged particle in a uniform axial
+field (or, for the tabulated field, scipy's DOP853 integrator) and a vectorised golden-section
+minimiser.  The RK4 recording, the closest-state search, the virtual-plane refinement, the RSS, the
+argmin and the classification live only in the CUDA library and, independently, in the oracle.
+
+Units: metres, MeV/c, tesla.  KAPPA = 299.792458 MeV/c per (T m), so a track of transverse momentum
+pT curls with radius R = pT / (KAPPA |q| B).  The electron charge is q = -1 and B points along +z
+(the paper's downstream direction, Sec. 1).
+
+Shapes follow the paper's workload (Sec. 1 and Sec. 3.1-3.3): an 18-sense-layer cylindrical drift
+chamber between about 50 and 84 cm with alternating stereo wires, a 1 T solenoid field, multi-turn
+electrons near 105 MeV/c, 150 um drift smearing, fewer than 250 fired wires, and a few times 10^4 to
+2^18 seeds per turn partition laid out on a Cartesian lattice around the expected seed.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Optional
+
+import numpy as np
+
+KAPPA = 299.792458          # MeV/c per (T m)
+ROOT_SEED = 20191120        # SeedSequence root of every synthetic workload
+
+# ----------------------------------------------------------------------------------------------
+# Chamber
+# ----------------------------------------------------------------------------------------------
+
+
+@dataclasses.dataclass
+class Chamber:
+    """Sense wires of the synthetic cylindrical drift chamber.
+
+    Layer l (0..17) has radius 0.50 + l*0.34/17 m and 300 wires at azimuth
+    2*pi*(k + 0.5*[l odd])/300.  Each wire is the axial wire rotated about its radial vector by the
+    stereo angle (+4 deg on even layers, -4 deg on odd ones), as the paper's CDC tilts its wires
+    (Sec. 1).  A wire is stored as its midpoint ``a`` (at z = 0) and unit direction ``u``; it spans
+    |z| <= half_length.
+    """
+    n_layers: int
+    wires_per_layer: int
+    radii: np.ndarray          # [n_layers]
+    stereo: np.ndarray         # [n_layers] radians
+    half_length: float
+    a: np.ndarray              # [3, N] midpoints
+    u: np.ndarray              # [3, N] unit directions
+    layer: np.ndarray          # [N] int
+    phi: np.ndarray            # [N] azimuth of the midpoint
+
+    @property
+    def n_wires(self) -> int:
+        return self.a.shape[1]
+
+
+def make_chamber(n_layers: int = 18, r_inner: float = 0.50, r_outer: float = 0.84,
+                 wires_per_layer: int = 300, stereo_deg: float = 4.0,
+                 half_length: float = 0.75) -> Chamber:
+    radii = r_inner + np.arange(n_layers) * (r_outer - r_inner) / (n_layers - 1)
+    stereo = np.where(np.arange(n_layers) % 2 == 0, 1.0, -1.0) * math.radians(stereo_deg)
+    lay = np.repeat(np.arange(n_layers), wires_per_layer)
+    k = np.tile(np.arange(wires_per_layer), n_layers)
+    phi = 2.0 * np.pi * (k + 0.5 * (lay % 2)) / wires_per_layer
+    r = radii[lay]
+    al = stereo[lay]
+    a = np.stack([r * np.cos(phi), r * np.sin(phi), np.zeros_like(r)])
+    u = np.stack([-np.sin(al) * np.sin(phi), np.sin(al) * np.cos(phi), np.cos(al)])
+    return Chamber(n_layers, wires_per_layer, radii, stereo, half_length, a, u, lay, phi)
+
+
+# ----------------------------------------------------------------------------------------------
+# Field description (input to both sides; the table IS the field model for the table case)
+# ----------------------------------------------------------------------------------------------
+
+
+@dataclasses.dataclass
+class Field:
+    """kind 0: uniform field ``b``.  kind 1: trilinear table [3][nz][ny][nx] on a regular grid with
+    ``origin`` (x, y, z of node 0) and isotropic ``spacing``."""
+    kind: int
+    b: tuple = (0.0, 0.0, 1.0)
+    table: Optional[np.ndarray] = None      # float32 [3, nz, ny, nx]
+    origin: tuple = (0.0, 0.0, 0.0)
+    spacing: float = 0.0
+
+    @property
+    def shape(self):
+        return (0, 0, 0) if self.table is None else self.table.shape[1:]
+
+
+def uniform_field(bz: float = 1.0) -> Field:
+    return Field(kind=0, b=(0.0, 0.0, float(bz)))
+
+
+def solenoid_model(x, y, z, b0=1.0, alpha=0.05, length=0.75):
+    """Harmonic (curl- and divergence-free) solenoid model: B_z = B0[1 - alpha(z^2 - rho^2/2)/L^2],
+    B_rho = B0 alpha z rho / L^2.  Gives a 5% axial drop at the chamber ends and a few-% radial rise."""
+    bz = b0 * (1.0 - alpha * (z * z - 0.5 * (x * x + y * y)) / (length * length))
+    g = b0 * alpha * z / (length * length)
+    return g * x, g * y, bz
+
+
+def table_field(spacing: float = 0.005, xy_half: float = 0.90, z_half: float = 0.80,
+                b0: float = 1.0, alpha: float = 0.05, length: float = 0.75) -> Field:
+    """Tabulate ``solenoid_model`` on a Cartesian grid (float32), covering |x|,|y| <= xy_half and
+    |z| <= z_half."""
+    nx = int(round(2 * xy_half / spacing)) + 1
+    nz = int(round(2 * z_half / spacing)) + 1
+    xs = -xy_half + spacing * np.arange(nx)
+    zs = -z_half + spacing * np.arange(nz)
+    tab = np.empty((3, nz, nx, nx), dtype=np.float32)
+    X, Y = np.meshgrid(xs, xs, indexing="xy")      # [ny, nx]
+    for iz, zz in enumerate(zs):
+        bx, by, bz = solenoid_model(X, Y, zz, b0, alpha, length)
+        tab[0, iz] = bx
+        tab[1, iz] = by
+        tab[2, iz] = bz
+    return Field(kind=1, b=(0.0, 0.0, b0), table=tab,
+                 origin=(-xy_half, -xy_half, -z_half), spacing=spacing)
+
+
+# ----------------------------------------------------------------------------------------------
+# Truth trajectories (detector simulation only)
+# ----------------------------------------------------------------------------------------------
+
+
+def helix_points(vertex, pt, phi0, pz, q, bz, s):
+    """Closed-form helix in a uniform field B = (0, 0, bz) at arc lengths ``s``.
+
+    Returns positions [3, n] and momenta [3, n].  Solves dx/ds = p/P0, dp/ds = (KAPPA q/P0) p x B."""
+    s = np.asarray(s, dtype=np.float64)
+    P0 = math.hypot(pt, pz)
+    w = KAPPA * q * bz / P0
+    th = phi0 - w * s
+    if abs(w) < 1e-15:
+        x = vertex[0] + (pt / P0) * math.cos(phi0) * s
+        y = vertex[1] + (pt / P0) * math.sin(phi0) * s
+    else:
+        x = vertex[0] - (pt / P0) * (np.sin(th) - math.sin(phi0)) / w
+        y = vertex[1] + (pt / P0) * (np.cos(th) - math.cos(phi0)) / w
+    z = vertex[2] + (pz / P0) * s
+    pos = np.stack([x, y, z])
+    mom = np.stack([pt * np.cos(th), pt * np.sin(th), np.full_like(s, pz)])
+    return pos, mom
+
+
+class _DenseTrack:
+    """Truth trajectory in a tabulated (non-uniform) field, from scipy's DOP853 with dense output.
+    Used only to simulate hits for the table-field workload."""
+
+    def __init__(self, field: Field, vertex, mom, q, s_max, model_kwargs=None):
+        from scipy.integrate import solve_ivp
+        P0 = float(np.linalg.norm(mom))
+        kw = model_kwargs or {}
+
+        def rhs(_s, y):
+            bx, by, bz = solenoid_model(y[0], y[1], y[2], **kw)
+            c = KAPPA * q / P0
+            return [y[3] / P0, y[4] / P0, y[5] / P0,
+                    c * (y[4] * bz - y[5] * by),
+                    c * (y[5] * bx - y[3] * bz),
+                    c * (y[3] * by - y[4] * bx)]
+        y0 = [vertex[0], vertex[1], vertex[2], mom[0], mom[1], mom[2]]
+        self.sol = solve_ivp(rhs, (0.0, s_max), y0, method="DOP853", rtol=1e-11, atol=1e-13,
+                             dense_output=True)
+        self.s_max = s_max
+
+    def __call__(self, s):
+        y = self.sol.sol(np.clip(np.asarray(s, dtype=np.float64), 0.0, self.s_max))
+        return y[:3], y[3:]
+
+
+def _dist_to_wires(pos, a, u):
+    """Distance of points pos[3, n] to lines (a[3, n], u[3, n]) and the line parameter of the foot."""
+    d = pos - a
+    t = (d * u).sum(0)
+    perp = d - t * u
+    return np.sqrt((perp * perp).sum(0)), t
+
+
+def _golden_min(fun, lo, hi, iters=60):
+    """Vectorised golden-section minimisation of fun(s[n]) -> [n] on brackets [lo, hi]."""
+    g = (math.sqrt(5.0) - 1.0) / 2.0
+    a = lo.copy()
+    b = hi.copy()
+    c = b - g * (b - a)
+    d = a + g * (b - a)
+    fc = fun(c)
+    fd = fun(d)
+    for _ in range(iters):
+        left = fc < fd
+        b = np.where(left, d, b)
+        a = np.where(left, a, c)
+        newc = b - g * (b - a)
+        newd = a + g * (b - a)
+        # reuse one interior evaluation per side
+        c2 = np.where(left, newc, d)
+        d2 = np.where(left, c, newd)
+        fc2 = np.where(left, np.nan, fd)
+        fd2 = np.where(left, fc, np.nan)
+        c, d = c2, d2
+        need_c = np.isnan(fc2)
+        need_d = np.isnan(fd2)
+        fc2[need_c] = fun(c)[need_c]
+        fd2[need_d] = fun(d)[need_d]
+        fc, fd = fc2, fd2
+    s = 0.5 * (a + b)
+    return s, fun(s)
+
+
+# ----------------------------------------------------------------------------------------------
+# Events
+# ----------------------------------------------------------------------------------------------
+
+
+@dataclasses.dataclass
+class LatticeSpec:
+    """Cartesian seed lattice of one turn partition.
+
+    Dimensions, slowest to fastest: vertex z0, transverse-momentum azimuth phi, p_z, p_T.  Node i of
+    a dimension with n nodes sits at centre + half_width*(2i/(n-1) - 1).  The seed vertex (x, y) is
+    fixed at ``vxy``.  This plays the role of the paper's seed ranges from prior knowledge (Sec. 2.1,
+    Sec. 3.1)."""
+    vxy: tuple
+    centre: tuple          # (z0, phi, pz, pt)
+    half_width: tuple      # (z0, phi, pz, pt)
+    counts: tuple          # (n_z0, n_phi, n_pz, n_pt)
+    charge: int = -1
+
+    @property
+    def n_seeds(self) -> int:
+        return int(np.prod(self.counts))
+
+
+@dataclasses.dataclass
+class Event:
+    vertex: np.ndarray           # [3]
+    pt: float
+    phi0: float
+    pz: float
+    q: int
+    n_turns: int
+    s_turn: float                # arc length of one helix turn (uniform field; nominal for table)
+    # hits in CSR order (sorted by wire id, stable)
+    wire_ids: np.ndarray         # [W] int32 ascending, chamber wire index of each hit wire
+    wires: np.ndarray            # [6, W] float64: a (3) then u (3)
+    hit_offsets: np.ndarray      # [W+1] int32
+    drift: np.ndarray            # [H] float64
+    hit_turn: np.ndarray         # [H] int32 truth turn of each hit, -1 = noise
+    hit_dtrue: np.ndarray        # [H] float64 true DCA (noise: nan)
+    partitions: List[LatticeSpec]
+    n_steps: List[int]           # RK4 steps per partition
+
+    @property
+    def n_hits(self) -> int:
+        return int(self.drift.shape[0])
+
+    @property
+    def n_wires(self) -> int:
+        return int(self.wire_ids.shape[0])
+
+    @property
+    def p(self) -> float:
+        return math.hypot(self.pt, self.pz)
+
+
+def _signal_hits(ch: Chamber, track, s_total, rng, max_dca=8e-3, sigma=150e-6, ds=1e-3):
+    """All (wire, pass) local minima of the truth-trajectory distance to a wire under ``max_dca``,
+    with the foot of the perpendicular inside the wire's extent.  Returns (wire, s_pca, dtrue, r)."""
+    s = np.arange(0.0, s_total + 0.5 * ds, ds)
+    pos, _ = track(s)
+    rho = np.hypot(pos[0], pos[1])
+    phi = np.arctan2(pos[1], pos[0])
+    wl, sl = [], []
+    W = ch.wires_per_layer
+    for l in range(ch.n_layers):
+        r_l = ch.radii[l]
+        tan_al = math.tan(ch.stereo[l])
+        sel = np.nonzero(np.abs(rho - r_l) < max_dca + 0.004 + 0.0015)[0]
+        if sel.size == 0:
+            continue
+        zz = pos[2, sel]
+        # azimuth of the wire's crossing point at height z is phi_k + atan(z tan(alpha)/r)
+        kf = (phi[sel] - np.arctan(zz * tan_al / r_l)) * W / (2 * np.pi) - 0.5 * (l % 2)
+        k0 = np.round(kf).astype(np.int64)
+        for dk in range(-2, 3):
+            k = np.mod(k0 + dk, W)
+            wid = l * W + k
+            d, _ = _dist_to_wires(pos[:, sel], ch.a[:, wid], ch.u[:, wid])
+            ok = d < max_dca + 1.5e-3
+            wl.append(wid[ok])
+            sl.append(sel[ok])
+    if not wl:
+        return (np.zeros(0, np.int64),) + (np.zeros(0),) * 3
+    wid = np.concatenate(wl)
+    sidx = np.concatenate(sl)
+    # unique (wire, sample) then runs of consecutive samples per wire = passes
+    key = np.unique(wid * (len(s) + 1) + sidx)
+    wid = key // (len(s) + 1)
+    sidx = key % (len(s) + 1)
+    new_run = np.ones(len(key), bool)
+    new_run[1:] = (wid[1:] != wid[:-1]) | (sidx[1:] != sidx[:-1] + 1)
+    run_id = np.cumsum(new_run) - 1
+    n_runs = run_id[-1] + 1
+    d_all, _ = _dist_to_wires(pos[:, sidx], ch.a[:, wid], ch.u[:, wid])
+    # argmin sample of every run
+    order = np.lexsort((d_all, run_id))
+    first = np.ones(len(order), bool)
+    first[1:] = run_id[order[1:]] != run_id[order[:-1]]
+    best = order[first]
+    run_w = wid[best]
+    s_best = s[sidx[best]]
+    lo = np.maximum(s_best - 1.5 * ds, 0.0)
+    hi = np.minimum(s_best + 1.5 * ds, s_total)
+    aw = ch.a[:, run_w]
+    uw = ch.u[:, run_w]
+
+    def dist_at(sv):
+        p_, _ = track(sv)
+        return _dist_to_wires(p_, aw, uw)[0]
+    s_pca, dtrue = _golden_min(dist_at, lo, hi)
+    p_pca, _ = track(s_pca)
+    _, tfoot = _dist_to_wires(p_pca, aw, uw)
+    zfoot = tfoot * uw[2]
+    ok = (dtrue < max_dca) & (np.abs(zfoot) <= ch.half_length)
+    run_w, s_pca, dtrue = run_w[ok], s_pca[ok], dtrue[ok]
+    assert n_runs >= len(run_w)
+    r = np.maximum(0.0, dtrue + rng.normal(0.0, sigma, size=dtrue.shape))
+    return run_w, s_pca, dtrue, r
+
+
+def _assemble(ch: Chamber, w_sig, s_sig, d_sig, r_sig, s_turn, n_turns, noise_frac, rng):
+    n_sig = len(w_sig)
+    order = np.argsort(s_sig, kind="stable")
+    w_sig, s_sig, d_sig, r_sig = w_sig[order], s_sig[order], d_sig[order], r_sig[order]
+    turn = np.minimum(np.floor(s_sig / s_turn).astype(np.int32), n_turns - 1)
+    n_noise = int(round(noise_frac * n_sig))
+    w_n = rng.integers(0, ch.n_wires, size=n_noise)
+    r_n = rng.uniform(0.0, 8e-3, size=n_noise)
+    w_all = np.concatenate([w_sig, w_n]).astype(np.int64)
+    r_all = np.concatenate([r_sig, r_n])
+    t_all = np.concatenate([turn, -np.ones(n_noise, np.int32)])
+    d_all = np.concatenate([d_sig, np.full(n_noise, np.nan)])
+    o = np.argsort(w_all, kind="stable")
+    w_all, r_all, t_all, d_all = w_all[o], r_all[o], t_all[o], d_all[o]
+    wire_ids, counts = np.unique(w_all, return_counts=True)
+    offs = np.zeros(len(wire_ids) + 1, np.int32)
+    offs[1:] = np.cumsum(counts)
+    wires = np.concatenate([ch.a[:, wire_ids], ch.u[:, wire_ids]], axis=0)
+    return wire_ids.astype(np.int32), wires, offs, r_all, t_all, d_all
+
+
+def partition_lattices(track, s_turn, q, n_turns, counts, rng,
+                       half_width=(0.02, 0.04, 3.0, 6.4)) -> List[LatticeSpec]:
+    """Lattice spec of each turn partition k: the truth seed is the trajectory state at the start of
+    turn k (arc length k*s_turn; in a uniform field the same x, y as the vertex with z advanced); the
+    lattice centre is truth + U(-1/2, 1/2)*spacing per dimension so that the truth is off-node."""
+    out = []
+    for k in range(n_turns):
+        pos, mom = track(np.array([k * s_turn]))
+        pos, mom = pos[:, 0], mom[:, 0]
+        truth = (float(pos[2]), math.atan2(mom[1], mom[0]), float(mom[2]), math.hypot(mom[0], mom[1]))
+        cen = []
+        for d in range(4):
+            sp = 2.0 * half_width[d] / max(counts[d] - 1, 1)
+            cen.append(truth[d] + rng.uniform(-0.5, 0.5) * sp)
+        out.append(LatticeSpec(vxy=(float(pos[0]), float(pos[1])), centre=tuple(cen),
+                               half_width=tuple(half_width), counts=tuple(counts), charge=q))
+    return out
+
+
+def steps_for(spec: LatticeSpec, bz: float = 1.0, h: float = 1e-3, margin: float = 1.02) -> int:
+    """RK4 steps of one turn partition: one helix turn's arc length at the lattice centre
+    (2*pi*P0/(KAPPA*|q|*B)), plus a 2% margin."""
+    pz, pt = spec.centre[2], spec.centre[3]
+    P0 = math.hypot(pt, pz)
+    return int(math.ceil(margin * 2.0 * math.pi * P0 / (KAPPA * abs(spec.charge) * bz) / h))
+
+
+def make_event_fixed(ch: Chamber, rng, p=104.0, pitch_deg=80.0, vertex=(0.03, 0.0, -0.40),
+                     phi0=0.3, q=-1, bz=1.0, n_turns=2, counts=(8, 8, 8, 8), noise_frac=0.0,
+                     h=1e-3, sigma=150e-6) -> Event:
+    """One electron of momentum p at ``pitch_deg`` to +z (the single-event FP64 workload)."""
+    al = math.radians(pitch_deg)
+    pt, pz = p * math.sin(al), p * math.cos(al)
+    return _make_event(ch, rng, np.array(vertex, float), pt, phi0, pz, q, bz, n_turns, counts,
+                       noise_frac, h, sigma=sigma)
+
+
+def _make_event(ch, rng, vertex, pt, phi0, pz, q, bz, n_turns, counts, noise_frac, h, field=None,
+                sigma=150e-6):
+    P0 = math.hypot(pt, pz)
+    s_turn = 2.0 * math.pi * P0 / (KAPPA * abs(q) * bz)
+    s_total = n_turns * s_turn
+    if field is None or field.kind == 0:
+        def track(sv):
+            return helix_points(vertex, pt, phi0, pz, q, bz, sv)
+    else:
+        mom = np.array([pt * math.cos(phi0), pt * math.sin(phi0), pz])
+        track = _DenseTrack(field, vertex, mom, q, s_total)
+    w, s_pca, dtrue, r = _signal_hits(ch, track, s_total, rng, sigma=sigma)
+    wire_ids, wires, offs, drift, turn, dt = _assemble(ch, w, s_pca, dtrue, r, s_turn, n_turns,
+                                                       noise_frac, rng)
+    parts = partition_lattices(track, s_turn, q, n_turns, counts, rng)
+    margin = 1.02 if field is None or field.kind == 0 else 1.08
+    return Event(vertex=vertex, pt=pt, phi0=phi0, pz=pz, q=q, n_turns=n_turns, s_turn=s_turn,
+                 wire_ids=wire_ids, wires=wires, hit_offsets=offs, drift=drift, hit_turn=turn,
+                 hit_dtrue=dt, partitions=parts,
+                 n_steps=[steps_for(sp, bz, h, margin) for sp in parts])
+
+
+def make_event_random(ch: Chamber, rng, p_range=(100.0, 105.0), turns=(2, 5), counts=(16, 16, 32, 32),
+                      hits_window=(60, 250), noise_frac=0.10, q=-1, bz=1.0, h=1e-3,
+                      field: Optional[Field] = None, p_sampler=None, max_tries=200) -> Event:
+    """One multi-turn event of the 1000-event workload.
+
+    Vertex: one of 17 disks (z = -0.40 + 0.05 d m, d = 0..16) of 10 cm radius, uniform on the disk.
+    Turns N_t uniform in ``turns``; p uniform in ``p_range`` (or from ``p_sampler``).  Pitch: p_z is
+    derived so that N_t turns span U(0.6, 0.95) of the chamber length in front of the vertex (a 40-70
+    degree pitch cannot fit 2-5 turns in a 1.5 m chamber; this keeps the chamber and the turn count).
+    Events whose number of signal fired wires falls outside ``hits_window`` are redrawn (the paper's
+    preselection counts fired wires, Sec. 3.3); 10% noise hits are then added on top."""
+    for _ in range(max_tries):
+        n_t = int(rng.integers(turns[0], turns[1] + 1))
+        p = float(p_sampler(rng)) if p_sampler is not None else float(rng.uniform(*p_range))
+        d = int(rng.integers(0, 17))
+        zv = -0.40 + 0.05 * d
+        rr = 0.10 * math.sqrt(rng.uniform())
+        ang = rng.uniform(0.0, 2.0 * math.pi)
+        vertex = np.array([rr * math.cos(ang), rr * math.sin(ang), zv])
+        frac = rng.uniform(0.6, 0.95)
+        dz_turn = frac * (ch.half_length - zv) / n_t
+        pz = dz_turn * KAPPA * abs(q) * bz / (2.0 * math.pi)
+        if pz >= p:
+            continue
+        pt = math.sqrt(p * p - pz * pz)
+        phi0 = rng.uniform(0.0, 2.0 * math.pi)
+        ev = _make_event(ch, rng, vertex, pt, phi0, pz, q, bz, n_t, counts, noise_frac, h, field)
+        n_fired = len(np.unique(ev.wire_ids[np.repeat(np.arange(ev.n_wires), np.diff(ev.hit_offsets))]
+                                [ev.hit_turn >= 0]))
+        if hits_window[0] <= n_fired <= hits_window[1]:
+            return ev
+    raise RuntimeError("could not draw an event inside the hit window")
+
+
+def dio_momentum_sampler(rng):
+    """Half of the events p ~ U(50, 105); half with E = E_end - (E_end - 90) u^(1/6), the endpoint
+    shape proportional to (E_end - E)^5 (E_end = 104.97 MeV, p ~ E for an electron)."""
+    e_end = 104.97
+    if rng.uniform() < 0.5:
+        return rng.uniform(50.0, 105.0)
+    return e_end - (e_end - 90.0) * rng.uniform() ** (1.0 / 6.0)
+
+
+# ----------------------------------------------------------------------------------------------
+# Named workloads
+# ----------------------------------------------------------------------------------------------
+
+def workload_rng(config: int, event: int = 0) -> np.random.Generator:
+    ss = np.random.SeedSequence([ROOT_SEED, config, event])
+    return np.random.default_rng(ss)
+
+
+def single_event_fp64(chamber: Optional[Chamber] = None) -> Event:
+    """One 104 MeV/c electron, 80 deg to +z, two turns, 1 T, no noise, 8^4 seeds per turn."""
+    ch = chamber or make_chamber()
+    return make_event_fixed(ch, workload_rng(1, 0))
+
+
+def multi_turn_event(i: int, chamber: Optional[Chamber] = None, counts=(16, 16, 32, 32)) -> Event:
+    """Event i of the 1000-event FP32 workload: 2-5 turns, p ~ U(100, 105) MeV/c, 17 vertex disks,
+    60-250 hits plus 10% noise, 2^18 seeds per turn partition (16 x 16 x 32 x 32)."""
+    ch = chamber or make_chamber()
+    return make_event_random(ch, workload_rng(2, i), counts=counts)
+
+
+def table_field_event(i: int, field: Field, chamber: Optional[Chamber] = None,
+                      counts=(16, 16, 32, 32)) -> Event:
+    """Event i of the non-uniform-field workload: p from the DIO-shaped sampler, field from the
+    tabulated solenoid model (hits are simulated on the analytic model)."""
+    ch = chamber or make_chamber()
+    return make_event_random(ch, workload_rng(3, i), counts=counts, field=field,
+                             p_sampler=dio_momentum_sampler)
+
+
+def unmasked_wire_count(ev: Event, mask: np.ndarray) -> int:
+    cnt = 0
+    for w in range(ev.n_wires):
+        if np.any(mask[ev.hit_offsets[w]:ev.hit_offsets[w + 1]] == 0):
+            cnt += 1
+    return cnt
