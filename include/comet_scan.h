@@ -1,0 +1,207 @@
+/*
+ * comet_scan.h -- C ABI of the GB300 (sm_103a) brute-force seed scan for multi-turn electron
+ * reconstruction in a cylindrical drift chamber (arXiv:1911.09340, Sec. 2).
+ *
+ * The scan of one turn partition is five calls on one CUDA stream, with no host synchronisation
+ * between them:
+ *
+ *   comet_scan_lattice    seeds from the prior ranges of the seed components        (Sec. 2.1, 3.1)
+ *   comet_scan_propagate  track recording: extrapolate every seed, record its states (Algorithm 1)
+ *   comet_scan_dca        DCA of every (seed, wire) and the capped per-seed RSS      (Algorithm 2, Eq. 1)
+ *   comet_scan_select     the seeds of lowest RSS                                     (Sec. 2.1)
+ *   comet_scan_classify   classify the selected seed's hits; mask them for the next   (Sec. 2.1, 3.1)
+ *                         turn partition
+ *
+ * Conventions shared by every call
+ *   - Units: metres, MeV/c, tesla.  Equations of motion in arc length s, with P0 = |p| of the seed
+ *     and KAPPA = 299.792458 MeV/c per (T m):  dx/ds = p / P0,  dp/ds = (KAPPA q / P0) p x B(x).
+ *   - Every array pointer is a DEVICE pointer owned by the caller (for example a torch tensor), unless
+ *     stated otherwise; the library never frees it.  Element type "T" is float for COMET_F32 and
+ *     double for COMET_F64.  Arrays are dense and C-ordered; "SoA [6][S]" means component-major
+ *     (row c holds component c of every seed), the seed index running fastest.
+ *   - Every call is asynchronous on `stream` (a cudaStream_t; NULL is the legacy default stream) and
+ *     returns once its kernels are enqueued.  Arguments are validated on the host before anything is
+ *     launched; an invalid argument returns COMET_ERR_INVALID_ARG and launches nothing.  A failed
+ *     launch returns COMET_ERR_CUDA.  No call aborts, throws or prints.  comet_last_error() returns
+ *     a message for the last non-OK status of the calling thread.
+ *   - The library allocates device memory only inside a comet_ctx: a status word at creation, and
+ *     comet_scan_select's per-block partial results lazily on first need (grown when a larger S or
+ *     k needs more), kept until comet_ctx_destroy.  A comet_scan_select call that grows the scratch
+ *     synchronises the device and calls cudaMalloc; make the largest such call once before
+ *     capturing a stream.
+ */
+#ifndef COMET_SCAN_H
+#define COMET_SCAN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *comet_stream; /* a cudaStream_t */
+typedef struct comet_ctx comet_ctx;
+
+typedef enum {
+    COMET_OK = 0,
+    COMET_ERR_INVALID_ARG = 1,
+    COMET_ERR_CUDA = 2,
+    COMET_ERR_NO_MEMORY = 3,
+    COMET_ERR_UNSUPPORTED = 5
+} comet_status;
+
+typedef enum { COMET_F32 = 0, COMET_F64 = 1 } comet_dtype;
+
+/* Magnetic field (Sec. 2.2.1: the field "in the grid format" is copied to the device).
+ *   kind 0: uniform field b (tesla).
+ *   kind 1: trilinear interpolation of a float32 DEVICE table [3][nz][ny][nx] (component, z, y, x)
+ *           whose node (ix, iy, iz) sits at origin + spacing * (ix, iy, iz).  A coordinate outside
+ *           the grid is clamped to its edge.  The same float32 table serves both dtypes. */
+typedef struct {
+    int32_t kind;
+    double b[3];
+    const void *table;
+    int32_t nx, ny, nz;
+    double origin[3];
+    double spacing;
+} comet_field;
+
+/* Scan parameters.
+ *   h         RK4 step (m), > 0.  The paper's extrapolator is an adaptive RKN (Sec. 2.1); here the
+ *             step is fixed.
+ *   n_steps   RK4 steps per turn partition, >= 1.
+ *   stride    record every stride-th state, >= 1; state 0 (the seed) is always recorded, so
+ *             n_rec = n_steps / stride + 1 states per seed.
+ *   lambda    the cutoff of Eq. 1 (m), > 0.
+ *   tol       virtual-plane distance below which the DCA refinement stops (m), > 0
+ *             (Algorithm 2's TOLERANCE).
+ *   max_iter  maximum refinement steps per (seed, wire), >= 0.
+ *   zmin, zmax, rmax  target region: recording stops after the first recorded state with
+ *             z < zmin, z > zmax or x^2 + y^2 > rmax^2 (Algorithm 1's loop condition). */
+typedef struct {
+    double h;
+    int32_t n_steps;
+    int32_t stride;
+    double lambda;
+    double tol;
+    int32_t max_iter;
+    double zmin, zmax, rmax;
+} comet_scan_params;
+
+/* Cartesian seed lattice (Sec. 2.1: seeds are combined from grids over the prior ranges of each
+ * seed component).  Dimensions, slowest to fastest: vertex z0, transverse-momentum azimuth phi,
+ * p_z, p_T.  Node i of a dimension with n nodes sits at centre + half_width * (2i/(n-1) - 1) (the
+ * centre alone when n = 1).  Seed = (vx, vy, z0, pT cos phi, pT sin phi, pz), of charge `charge`
+ * (units of e; -1 for the electron, +1 for the positron of the paper's Sec. 5.1 outlook). */
+typedef struct {
+    double vx, vy;
+    double centre[4];
+    double half_width[4];
+    int32_t counts[4];
+    int32_t charge;
+} comet_lattice;
+
+/* ---- context ----------------------------------------------------------------------------------
+ * comet_ctx_create: binds a context to CUDA device `device` (>= 0) and returns it in *out.  It
+ * allocates one 256-byte device status word (zeroed).  comet_ctx_destroy synchronises the device,
+ * frees the context's device memory and the context; NULL is a no-op.  A context may be used from
+ * one host thread at a time.
+ * comet_ctx_status: synchronises the device and copies the status word to *flags (host pointer):
+ *   bit 0  a kernel's wait for a shared-memory bulk copy exceeded its time limit (2 s); the kernel
+ *          then re-read the data with plain loads, so its results are still valid;
+ *   bit 1  comet_scan_classify was given a seed index outside [0, S); its hit_class was zeroed.
+ * comet_last_error: message of the calling thread's last non-OK status (static storage). */
+comet_status comet_ctx_create(int device, comet_ctx **out);
+void comet_ctx_destroy(comet_ctx *ctx);
+comet_status comet_ctx_status(comet_ctx *ctx, int32_t *flags);
+const char *comet_last_error(void);
+
+/* ---- a1: seed lattice -------------------------------------------------------------------------
+ * Writes the S = counts[0]*counts[1]*counts[2]*counts[3] seeds of `lat` to seeds (SoA [6][S], T)
+ * and, if charge_out is not NULL, lat->charge to charge_out ([S] int8).  Computed in double and
+ * rounded to T.  S must equal the product of the counts and the charge must fit int8 (else
+ * COMET_ERR_INVALID_ARG).  Paper: Sec. 2.1 (grid of seeds over prior ranges), Sec. 3.1. */
+comet_status comet_scan_lattice(comet_ctx *ctx, comet_dtype dtype, const comet_lattice *lat,
+                                void *seeds, int8_t *charge_out, int64_t S, comet_stream stream);
+
+/* ---- a2/a3: track recording (Algorithm 1, Sec. 2.2.1) ------------------------------------------
+ *   seeds    SoA [6][S] T: (x, y, z, px, py, pz) of each seed.
+ *   charge   [S] int8: particle charge in units of e (the electron is -1); 0 gives a straight line.
+ *   points   out, SoA [6][n_rec][S] T: recorded state k of seed s is points[c][k][s].  Entries past
+ *            n_valid[s] are left unwritten.
+ *   n_valid  out, [S] int32: number of recorded states of each seed (1 .. n_rec).
+ * One thread extrapolates one seed with fixed-step RK4.  The FP32 path carries each state component
+ * as an unevaluated float pair (a compensated sum), so that 6,500 steps stay within a few um of FP64;
+ * the recorded value is the leading float. */
+comet_status comet_scan_propagate(comet_ctx *ctx, comet_dtype dtype, const comet_field *field,
+                                  const comet_scan_params *params, const void *seeds,
+                                  const int8_t *charge, int64_t S, void *points, int32_t *n_valid,
+                                  comet_stream stream);
+
+/* ---- a4-a6: DCA finding and RSS (Algorithm 2, Eq. 1, Sec. 2.2.2) --------------------------------
+ *   points, n_valid, charge, S   as written by comet_scan_propagate with the same params.
+ *   wires        SoA [6][ldw] T: (a_x, a_y, a_z, u_x, u_y, u_z) of wire i in column i: a point on
+ *                the wire and its unit direction.  ldw >= W is the row stride in elements.
+ *   W            number of wires (>= 0).  W = 0 gives rss = 0 and n_in = 0.
+ *   hit_offsets  [W+1] int32 CSR: the hits of wire i are hit_offsets[i] .. hit_offsets[i+1]-1;
+ *                hit_offsets[0] = 0, non-decreasing.
+ *   drift        [H] T: drift distance r of each hit (H = hit_offsets[W]).
+ *   hit_mask     [H] uint8: non-zero marks a hit classified by an earlier turn partition; it is
+ *                ignored here, and a wire whose hits are all masked leaves the sum.
+ *   rss          out, [S] T: RSS = sum over wires with an unmasked hit of d_i^2, where
+ *                d_i = min(min_j |D_i - r_ij|, lambda) and D_i is the DCA of the track to wire i
+ *                (Eq. 1; the left and right hits of drift r sit at +-r across the wire, so
+ *                min(d^L, d^R) = |D - r|).  Accumulated in double, summed in ascending wire order.
+ *   n_in         out, [S] int32: wires whose capped residual is below lambda.
+ *   dca_out      optional out, [W][S] T (NULL to skip): D_i of every (wire, seed).  Requesting it
+ *                computes the exact DCA of every wire; without it, a wire the track never comes
+ *                within (max drift + lambda + half a recording interval) of is known to contribute
+ *                lambda^2 and is not refined.
+ *   n_unconverged optional, device [1] int32 (NULL to skip): incremented by the number of
+ *                (seed, wire) refinements that reached max_iter or met a track parallel to the wire.
+ *                The caller zeroes it.
+ * D_i: start from the recorded state closest to the wire line (ties: lowest index), then step along
+ * the track by -d/|n| with one RK4 step, where n is the part of the unit direction perpendicular to
+ * the wire and d the distance to the plane that contains the wire axis with normal n, until
+ * |d| < tol (Algorithm 2's loop; the Newton step length is the reading of "the distance").
+ * The closest recorded state is found exactly by a bounded search over the recorded states (recorded
+ * states one recording interval apart are at most that arc length apart). */
+comet_status comet_scan_dca(comet_ctx *ctx, comet_dtype dtype, const comet_field *field,
+                            const comet_scan_params *params, const void *points,
+                            const int32_t *n_valid, const int8_t *charge, int64_t S,
+                            const void *wires, int32_t W, int32_t ldw, const int32_t *hit_offsets,
+                            const void *drift, const uint8_t *hit_mask, void *rss, int32_t *n_in,
+                            void *dca_out, int32_t *n_unconverged, comet_stream stream);
+
+/* ---- a7: selection (Sec. 2.1; top-k for Sec. 3.1's "10 seeds at each side") ------------------
+ *   rss      [S] T.
+ *   k        1 .. 64, and k <= S.
+ *   idx_out  out, [k] int64: the seeds of the k lowest RSS in ascending order; equal RSS ordered by
+ *            seed index; NaN sorts after every number.
+ *   rss_out  out, [k] T (may be NULL).
+ * Uses the context's device scratch (allocated on first use). */
+comet_status comet_scan_select(comet_ctx *ctx, comet_dtype dtype, const void *rss, int64_t S,
+                               int32_t k, int64_t *idx_out, void *rss_out, comet_stream stream);
+
+/* ---- a8/a9: classification (Sec. 2.1) and the mask of the next turn partition (Sec. 3.1) -------
+ *   points, n_valid, charge, S, wires, W, ldw, hit_offsets, drift  as for comet_scan_dca.
+ *   seed_index  device [1] int64: the seed to classify (for example idx_out of comet_scan_select);
+ *               read on the device, so no host synchronisation is needed.  Must be in [0, S).
+ *   hit_mask    [H] uint8, read; when update_mask != 0 the classified hits are OR-ed into it.
+ *   hit_class   out, [H] uint8: 1 for the closest unmasked hit of each wire whose |D - r| is below
+ *               lambda (ties: lowest hit index), 0 otherwise.
+ *   dca_wire    optional out, [W] T (NULL to skip): the selected seed's DCA to every wire.
+ * The closest recorded state is found by exhaustive search here. */
+comet_status comet_scan_classify(comet_ctx *ctx, comet_dtype dtype, const comet_field *field,
+                                 const comet_scan_params *params, const void *points,
+                                 const int32_t *n_valid, const int8_t *charge, int64_t S,
+                                 const int64_t *seed_index, const void *wires, int32_t W,
+                                 int32_t ldw, const int32_t *hit_offsets, const void *drift,
+                                 uint8_t *hit_mask, uint8_t *hit_class, void *dca_wire,
+                                 int32_t update_mask, comet_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* COMET_SCAN_H */

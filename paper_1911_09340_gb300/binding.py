@@ -1,0 +1,255 @@
+"""Thin Python binding of the C ABI in include/comet_scan.h.
+
+Argument marshalling only: every function takes torch CUDA tensors, checks their dtype, device and
+contiguity, and passes raw device pointers to the library function of the same name, on the current
+torch stream.  There is no CPU path: if the shared library is missing the import-time loader raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import os
+import threading
+from typing import Optional
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libcomet_scan.so")
+
+COMET_OK = 0
+COMET_F32 = 0
+COMET_F64 = 1
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "NO_MEMORY", 5: "UNSUPPORTED"}
+
+
+class CometError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class _Field(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("b", C.c_double * 3), ("table", C.c_void_p),
+                ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+                ("origin", C.c_double * 3), ("spacing", C.c_double)]
+
+
+class _Params(C.Structure):
+    _fields_ = [("h", C.c_double), ("n_steps", C.c_int32), ("stride", C.c_int32),
+                ("lam", C.c_double), ("tol", C.c_double), ("max_iter", C.c_int32),
+                ("zmin", C.c_double), ("zmax", C.c_double), ("rmax", C.c_double)]
+
+
+class _Lattice(C.Structure):
+    _fields_ = [("vx", C.c_double), ("vy", C.c_double), ("centre", C.c_double * 4),
+                ("half_width", C.c_double * 4), ("counts", C.c_int32 * 4), ("charge", C.c_int32)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+# (name, argtypes) of every exported entry point
+_vp, _i32, _i64 = C.c_void_p, C.c_int32, C.c_int64
+SIGNATURES = {
+    "comet_ctx_create": [C.c_int, C.POINTER(C.c_void_p)],
+    "comet_ctx_destroy": [_vp],
+    "comet_ctx_status": [_vp, C.POINTER(C.c_int32)],
+    "comet_last_error": [],
+    "comet_scan_lattice": [_vp, C.c_int, C.POINTER(_Lattice), _vp, _vp, _i64, _vp],
+    "comet_scan_propagate": [_vp, C.c_int, C.POINTER(_Field), C.POINTER(_Params), _vp, _vp, _i64,
+                             _vp, _vp, _vp],
+    "comet_scan_dca": [_vp, C.c_int, C.POINTER(_Field), C.POINTER(_Params), _vp, _vp, _vp, _i64,
+                       _vp, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
+    "comet_scan_select": [_vp, C.c_int, _vp, _i64, _i32, _vp, _vp, _vp],
+    "comet_scan_classify": [_vp, C.c_int, C.POINTER(_Field), C.POINTER(_Params), _vp, _vp, _vp,
+                            _i64, _vp, _vp, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _i32, _vp],
+}
+
+
+def lib():
+    """The loaded library (built by ``paper_1911_09340_gb300.build``).  Raises if it is absent."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(f"{LIB_PATH} is missing: build it with "
+                                  "`python -c 'import __graft_entry__ as g; g.build()'`")
+            L = C.CDLL(LIB_PATH)
+            for name, args in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = None if name == "comet_ctx_destroy" else (
+                    C.c_char_p if name == "comet_last_error" else C.c_int)
+            _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != COMET_OK:
+        raise CometError(status, lib().comet_last_error().decode())
+
+
+def _dtype_code(t: torch.Tensor) -> int:
+    if t.dtype == torch.float32:
+        return COMET_F32
+    if t.dtype == torch.float64:
+        return COMET_F64
+    raise TypeError(f"expected float32 or float64, got {t.dtype}")
+
+
+def _ptr(t: Optional[torch.Tensor], dtype=None) -> Optional[int]:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"expected {dtype}, got {t.dtype}")
+    return t.data_ptr()
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+@dataclasses.dataclass
+class ScanParams:
+    """Mirror of comet_scan_params (see include/comet_scan.h)."""
+    h: float = 1e-3
+    n_steps: int = 2200
+    stride: int = 1
+    lam: float = 1e-2
+    tol: float = 1e-12
+    max_iter: int = 16
+    zmin: float = -0.80
+    zmax: float = 0.80
+    rmax: float = 0.90
+
+    @property
+    def n_rec(self) -> int:
+        return self.n_steps // self.stride + 1
+
+    def c(self) -> _Params:
+        return _Params(self.h, self.n_steps, self.stride, self.lam, self.tol, self.max_iter,
+                       self.zmin, self.zmax, self.rmax)
+
+
+class DeviceField:
+    """Mirror of comet_field.  ``table`` (if given) is copied to the device as float32."""
+
+    def __init__(self, kind: int = 0, b=(0.0, 0.0, 1.0), table=None, origin=(0.0, 0.0, 0.0),
+                 spacing: float = 0.0, device="cuda"):
+        self.kind = kind
+        self.b = tuple(float(x) for x in b)
+        self.table = None
+        self.origin = tuple(float(x) for x in origin)
+        self.spacing = float(spacing)
+        if kind == 1:
+            t = torch.as_tensor(table)
+            self.table = t.to(device=device, dtype=torch.float32).contiguous()
+
+    @classmethod
+    def from_synth(cls, f, device="cuda"):
+        return cls(f.kind, f.b, f.table, f.origin, f.spacing, device)
+
+    def c(self) -> _Field:
+        if self.kind == 0:
+            return _Field(0, (C.c_double * 3)(*self.b), None, 0, 0, 0, (C.c_double * 3)(0, 0, 0), 0.0)
+        nz, ny, nx = self.table.shape[1:]
+        return _Field(1, (C.c_double * 3)(*self.b), self.table.data_ptr(), nx, ny, nz,
+                      (C.c_double * 3)(*self.origin), self.spacing)
+
+
+class Context:
+    """Owns a comet_ctx bound to one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        h = C.c_void_p()
+        _check(lib().comet_ctx_create(int(device), C.byref(h)))
+        self.handle = h
+        self.device = device
+
+    def status(self) -> int:
+        v = C.c_int32(0)
+        _check(lib().comet_ctx_status(self.handle, C.byref(v)))
+        return v.value
+
+    def close(self):
+        if self.handle:
+            lib().comet_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def lattice_struct(spec) -> _Lattice:
+    return _Lattice(float(spec.vxy[0]), float(spec.vxy[1]), (C.c_double * 4)(*spec.centre),
+                    (C.c_double * 4)(*spec.half_width), (C.c_int32 * 4)(*spec.counts),
+                    int(spec.charge))
+
+
+def comet_scan_lattice(ctx: Context, spec, seeds: torch.Tensor, charge: Optional[torch.Tensor] = None,
+                       stream=None):
+    lat = lattice_struct(spec)
+    _check(lib().comet_scan_lattice(ctx.handle, _dtype_code(seeds), C.byref(lat), _ptr(seeds),
+                                    _ptr(charge, torch.int8), seeds.shape[-1], _stream(stream)))
+
+
+def comet_scan_propagate(ctx: Context, field: DeviceField, params: ScanParams, seeds, charge,
+                         points, n_valid, stream=None):
+    dt = _dtype_code(seeds)
+    S = seeds.shape[-1]
+    f, p = field.c(), params.c()
+    _check(lib().comet_scan_propagate(ctx.handle, dt, C.byref(f), C.byref(p), _ptr(seeds),
+                                      _ptr(charge, torch.int8), S, _ptr(points, seeds.dtype),
+                                      _ptr(n_valid, torch.int32), _stream(stream)))
+
+
+def comet_scan_dca(ctx: Context, field: DeviceField, params: ScanParams, points, n_valid, charge,
+                   wires, hit_offsets, drift, hit_mask, rss, n_in, dca_out=None, n_unconverged=None,
+                   n_wires: Optional[int] = None, stream=None):
+    """``wires`` is [6][ldw]; the first ``n_wires`` columns (default: all) are the wires."""
+    dt = _dtype_code(points)
+    S = n_valid.shape[0]
+    ldw = wires.shape[-1]
+    W = ldw if n_wires is None else int(n_wires)
+    f, p = field.c(), params.c()
+    _check(lib().comet_scan_dca(ctx.handle, dt, C.byref(f), C.byref(p), _ptr(points),
+                                _ptr(n_valid, torch.int32), _ptr(charge, torch.int8), S,
+                                _ptr(wires, points.dtype), W, ldw, _ptr(hit_offsets, torch.int32),
+                                _ptr(drift, points.dtype), _ptr(hit_mask, torch.uint8),
+                                _ptr(rss, points.dtype), _ptr(n_in, torch.int32),
+                                _ptr(dca_out, points.dtype), _ptr(n_unconverged, torch.int32),
+                                _stream(stream)))
+
+
+def comet_scan_select(ctx: Context, rss, k: int, idx_out, rss_out=None, stream=None):
+    _check(lib().comet_scan_select(ctx.handle, _dtype_code(rss), _ptr(rss), rss.shape[0], int(k),
+                                   _ptr(idx_out, torch.int64), _ptr(rss_out, rss.dtype),
+                                   _stream(stream)))
+
+
+def comet_scan_classify(ctx: Context, field: DeviceField, params: ScanParams, points, n_valid,
+                        charge, seed_index, wires, hit_offsets, drift, hit_mask, hit_class,
+                        dca_wire=None, update_mask: bool = False, n_wires: Optional[int] = None,
+                        stream=None):
+    dt = _dtype_code(points)
+    S = n_valid.shape[0]
+    ldw = wires.shape[-1]
+    W = ldw if n_wires is None else int(n_wires)
+    f, p = field.c(), params.c()
+    _check(lib().comet_scan_classify(ctx.handle, dt, C.byref(f), C.byref(p), _ptr(points),
+                                     _ptr(n_valid, torch.int32), _ptr(charge, torch.int8), S,
+                                     _ptr(seed_index, torch.int64), _ptr(wires, points.dtype), W,
+                                     ldw, _ptr(hit_offsets, torch.int32), _ptr(drift, points.dtype),
+                                     _ptr(hit_mask, torch.uint8), _ptr(hit_class, torch.uint8),
+                                     _ptr(dca_wire, points.dtype), int(bool(update_mask)),
+                                     _stream(stream)))

@@ -1,0 +1,381 @@
+// C ABI of the seed scan (declared and documented in include/comet_scan.h): argument validation on
+// the host, the context's lazily allocated device scratch, and dispatch to the kernel launchers.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "comet_scan.h"
+#include "internal.h"
+
+struct comet_ctx {
+    int device;
+    void *scratch = nullptr;     // comet_scan_select's per-block partial results
+    size_t scratch_bytes = 0;
+    int32_t *status = nullptr;   // device status word (bit 0: bulk-copy timeout, bit 1: bad seed index)
+};
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+comet_status fail(comet_status st, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+comet_status cuda_fail(cudaError_t e, const char *where)
+{
+    return fail(COMET_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+// Makes ctx->device current for the scope of a call and restores the caller's device afterwards.
+struct DeviceGuard {
+    int prev = -1;
+    cudaError_t err = cudaSuccess;
+    explicit DeviceGuard(int dev)
+    {
+        err = cudaGetDevice(&prev);
+        if (err == cudaSuccess && prev != dev) err = cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+size_t esize(comet_dtype dt) { return dt == COMET_F32 ? sizeof(float) : sizeof(double); }
+
+bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+comet_status check_dtype(comet_dtype dt)
+{
+    if (dt != COMET_F32 && dt != COMET_F64) return fail(COMET_ERR_INVALID_ARG, "dtype must be COMET_F32 or COMET_F64");
+    return COMET_OK;
+}
+
+comet_status check_field(const comet_field *f)
+{
+    if (!f) return fail(COMET_ERR_INVALID_ARG, "field is NULL");
+    if (f->kind == 0) {
+        for (int i = 0; i < 3; ++i)
+            if (!std::isfinite(f->b[i])) return fail(COMET_ERR_INVALID_ARG, "field.b must be finite");
+        return COMET_OK;
+    }
+    if (f->kind != 1) return fail(COMET_ERR_INVALID_ARG, "field.kind must be 0 (uniform) or 1 (table)");
+    if (!f->table) return fail(COMET_ERR_INVALID_ARG, "field.table is NULL");
+    if (!aligned(f->table, 4)) return fail(COMET_ERR_INVALID_ARG, "field.table must be 4-byte aligned");
+    if (f->nx < 2 || f->ny < 2 || f->nz < 2) return fail(COMET_ERR_INVALID_ARG, "field table needs >= 2 nodes per axis");
+    if (!(f->spacing > 0.0) || !std::isfinite(f->spacing)) return fail(COMET_ERR_INVALID_ARG, "field.spacing must be > 0");
+    for (int i = 0; i < 3; ++i)
+        if (!std::isfinite(f->origin[i])) return fail(COMET_ERR_INVALID_ARG, "field.origin must be finite");
+    if ((double)f->nx * f->ny * f->nz * 3.0 > 9.0e18) return fail(COMET_ERR_INVALID_ARG, "field table too large");
+    return COMET_OK;
+}
+
+comet_status check_params(const comet_scan_params *p, bool need_hits)
+{
+    if (!p) return fail(COMET_ERR_INVALID_ARG, "params is NULL");
+    if (!(p->h > 0.0) || !std::isfinite(p->h)) return fail(COMET_ERR_INVALID_ARG, "params.h must be > 0");
+    if (p->n_steps < 1) return fail(COMET_ERR_INVALID_ARG, "params.n_steps must be >= 1");
+    if (p->stride < 1) return fail(COMET_ERR_INVALID_ARG, "params.stride must be >= 1");
+    if (std::isnan(p->zmin) || std::isnan(p->zmax) || std::isnan(p->rmax))
+        return fail(COMET_ERR_INVALID_ARG, "params target region must not be NaN");
+    if (need_hits) {
+        if (!(p->lambda > 0.0) || !std::isfinite(p->lambda)) return fail(COMET_ERR_INVALID_ARG, "params.lambda must be > 0");
+        if (!(p->tol > 0.0) || !std::isfinite(p->tol)) return fail(COMET_ERR_INVALID_ARG, "params.tol must be > 0");
+        if (p->max_iter < 0) return fail(COMET_ERR_INVALID_ARG, "params.max_iter must be >= 0");
+    }
+    return COMET_OK;
+}
+
+comet_status check_hits(comet_dtype dt, const void *wires, int32_t W, int32_t ldw,
+                        const int32_t *offs, const void *drift, const void *mask)
+{
+    if (W < 0) return fail(COMET_ERR_INVALID_ARG, "W must be >= 0");
+    if (W == 0) return COMET_OK;
+    if (ldw < W) return fail(COMET_ERR_INVALID_ARG, "ldw must be >= W");
+    if (!wires || !offs || !drift || !mask) return fail(COMET_ERR_INVALID_ARG, "wires, hit_offsets, drift and hit_mask are required when W > 0");
+    if (!aligned(wires, esize(dt)) || !aligned(drift, esize(dt)) || !aligned(offs, 4))
+        return fail(COMET_ERR_INVALID_ARG, "wires/drift/hit_offsets are misaligned for their element type");
+    return COMET_OK;
+}
+
+#define CHECK(expr)                                                                                \
+    do {                                                                                           \
+        comet_status _s = (expr);                                                                  \
+        if (_s != COMET_OK) return _s;                                                             \
+    } while (0)
+
+int n_rec_of(const comet_scan_params *p) { return p->n_steps / p->stride + 1; }
+
+} // namespace
+
+extern "C" {
+
+const char *comet_last_error(void) { return g_err; }
+
+comet_status comet_ctx_create(int device, comet_ctx **out)
+{
+    if (!out) return fail(COMET_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+    if (device < 0 || device >= n) return fail(COMET_ERR_INVALID_ARG, "device %d out of range (%d devices)", device, n);
+    DeviceGuard g(device);
+    if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+    comet_ctx *c = new (std::nothrow) comet_ctx;
+    if (!c) return fail(COMET_ERR_NO_MEMORY, "host allocation failed");
+    c->device = device;
+    e = cudaMalloc(&c->status, 256);
+    if (e != cudaSuccess) {
+        delete c;
+        return e == cudaErrorMemoryAllocation ? fail(COMET_ERR_NO_MEMORY, "cudaMalloc(status)") : cuda_fail(e, "cudaMalloc(status)");
+    }
+    e = cudaMemset(c->status, 0, 256);
+    if (e != cudaSuccess) {
+        cudaFree(c->status);
+        delete c;
+        return cuda_fail(e, "cudaMemset(status)");
+    }
+    *out = c;
+    return COMET_OK;
+}
+
+void comet_ctx_destroy(comet_ctx *ctx)
+{
+    if (!ctx) return;
+    {
+        DeviceGuard g(ctx->device);
+        cudaDeviceSynchronize();
+        if (ctx->scratch) cudaFree(ctx->scratch);
+        if (ctx->status) cudaFree(ctx->status);
+    }
+    delete ctx;
+}
+
+comet_status comet_ctx_status(comet_ctx *ctx, int32_t *flags)
+{
+    if (!ctx || !flags) return fail(COMET_ERR_INVALID_ARG, "ctx and flags are required");
+    DeviceGuard g(ctx->device);
+    if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+    e = cudaMemcpy(flags, ctx->status, sizeof(int32_t), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(status)");
+    return COMET_OK;
+}
+
+comet_status comet_scan_lattice(comet_ctx *ctx, comet_dtype dtype, const comet_lattice *lat,
+                                void *seeds, int8_t *charge_out, int64_t S, comet_stream stream)
+{
+    if (!ctx) return fail(COMET_ERR_INVALID_ARG, "ctx is NULL");
+    CHECK(check_dtype(dtype));
+    if (!lat) return fail(COMET_ERR_INVALID_ARG, "lattice is NULL");
+    int64_t prod = 1;
+    for (int d = 0; d < 4; ++d) {
+        if (lat->counts[d] < 1) return fail(COMET_ERR_INVALID_ARG, "lattice.counts must be >= 1");
+        prod *= lat->counts[d];
+        if (prod > (int64_t)1 << 40) return fail(COMET_ERR_INVALID_ARG, "lattice too large");
+        if (!std::isfinite(lat->centre[d]) || !std::isfinite(lat->half_width[d]))
+            return fail(COMET_ERR_INVALID_ARG, "lattice centre/half_width must be finite");
+    }
+    if (S != prod) return fail(COMET_ERR_INVALID_ARG, "S (%lld) != product of lattice counts (%lld)", (long long)S, (long long)prod);
+    if (!seeds || !aligned(seeds, esize(dtype))) return fail(COMET_ERR_INVALID_ARG, "seeds is NULL or misaligned");
+    if (lat->charge < -128 || lat->charge > 127) return fail(COMET_ERR_INVALID_ARG, "lattice.charge must fit int8");
+    DeviceGuard g(ctx->device);
+    if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+    comet::LatArgs a;
+    a.vx = lat->vx;
+    a.vy = lat->vy;
+    for (int d = 0; d < 4; ++d) {
+        a.centre[d] = lat->centre[d];
+        a.half_width[d] = lat->half_width[d];
+        a.counts[d] = lat->counts[d];
+    }
+    a.charge = lat->charge;
+    a.charge_out = charge_out;
+    cudaError_t e = comet::launch_lattice(dtype, a, seeds, S, (cudaStream_t)stream);
+    return e == cudaSuccess ? COMET_OK : cuda_fail(e, "lattice launch");
+}
+
+comet_status comet_scan_propagate(comet_ctx *ctx, comet_dtype dtype, const comet_field *field,
+                                  const comet_scan_params *params, const void *seeds,
+                                  const int8_t *charge, int64_t S, void *points, int32_t *n_valid,
+                                  comet_stream stream)
+{
+    if (!ctx) return fail(COMET_ERR_INVALID_ARG, "ctx is NULL");
+    CHECK(check_dtype(dtype));
+    CHECK(check_field(field));
+    CHECK(check_params(params, false));
+    if (S < 0) return fail(COMET_ERR_INVALID_ARG, "S must be >= 0");
+    if (S == 0) return COMET_OK;
+    if (!seeds || !charge || !points || !n_valid) return fail(COMET_ERR_INVALID_ARG, "seeds, charge, points and n_valid are required");
+    if (!aligned(seeds, esize(dtype)) || !aligned(points, esize(dtype)) || !aligned(n_valid, 4))
+        return fail(COMET_ERR_INVALID_ARG, "seeds/points/n_valid misaligned for their element type");
+    DeviceGuard g(ctx->device);
+    if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+    comet::PropArgs a;
+    a.seeds = seeds;
+    a.charge = charge;
+    a.S = S;
+    a.points = points;
+    a.n_valid = n_valid;
+    a.h = params->h;
+    a.zmin = params->zmin;
+    a.zmax = params->zmax;
+    a.rmax = params->rmax;
+    a.n_steps = params->n_steps;
+    a.stride = params->stride;
+    a.n_rec = n_rec_of(params);
+    cudaError_t e = comet::launch_propagate(dtype, *field, a, (cudaStream_t)stream);
+    return e == cudaSuccess ? COMET_OK : cuda_fail(e, "propagate launch");
+}
+
+comet_status comet_scan_dca(comet_ctx *ctx, comet_dtype dtype, const comet_field *field,
+                            const comet_scan_params *params, const void *points,
+                            const int32_t *n_valid, const int8_t *charge, int64_t S,
+                            const void *wires, int32_t W, int32_t ldw, const int32_t *hit_offsets,
+                            const void *drift, const uint8_t *hit_mask, void *rss, int32_t *n_in,
+                            void *dca_out, int32_t *n_unconverged, comet_stream stream)
+{
+    if (!ctx) return fail(COMET_ERR_INVALID_ARG, "ctx is NULL");
+    CHECK(check_dtype(dtype));
+    CHECK(check_field(field));
+    CHECK(check_params(params, true));
+    if (S < 0) return fail(COMET_ERR_INVALID_ARG, "S must be >= 0");
+    CHECK(check_hits(dtype, wires, W, ldw, hit_offsets, drift, hit_mask));
+    if (S == 0) return COMET_OK;
+    if (!points || !n_valid || !charge || !rss || !n_in) return fail(COMET_ERR_INVALID_ARG, "points, n_valid, charge, rss and n_in are required");
+    if (!aligned(points, esize(dtype)) || !aligned(rss, esize(dtype)) || !aligned(n_valid, 4) ||
+        !aligned(n_in, 4) || (dca_out && !aligned(dca_out, esize(dtype))) ||
+        (n_unconverged && !aligned(n_unconverged, 4)))
+        return fail(COMET_ERR_INVALID_ARG, "an array is misaligned for its element type");
+    DeviceGuard g(ctx->device);
+    if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+    comet::DcaArgs a;
+    a.points = points;
+    a.n_valid = n_valid;
+    a.charge = charge;
+    a.S = S;
+    a.n_rec = n_rec_of(params);
+    a.wires = wires;
+    a.W = W;
+    a.ldw = W > 0 ? ldw : 0;
+    a.offs = hit_offsets;
+    a.drift = drift;
+    a.mask = hit_mask;
+    a.rss = rss;
+    a.n_in = n_in;
+    a.dca_out = W > 0 ? dca_out : nullptr;
+    a.n_unconv = n_unconverged;
+    a.status = ctx->status;
+    a.lambda = params->lambda;
+    a.tol = params->tol;
+    a.max_iter = params->max_iter;
+    const int n1max = comet::dca_n1max(dtype);
+    a.G = (a.n_rec + n1max - 1) / n1max;
+    if (a.G < 1) a.G = 1;
+    // consecutive recorded states are at most stride*h apart along the track (|dx/ds| = |p|/P0 = 1
+    // up to rounding); the margins cover the rounding of the distances in the working precision
+    const double h_rec = params->h * params->stride;
+    const double margin = dtype == COMET_F32 ? 4e-6 : 1e-9;
+    a.R1 = (a.G / 2) * h_rec * (1.0 + 1e-4) + margin;
+    a.half_rec = 0.5 * h_rec * (1.0 + 1e-4) + margin;
+    a.exact_all = dca_out != nullptr;
+    cudaError_t e = comet::launch_dca(dtype, *field, a, (cudaStream_t)stream);
+    return e == cudaSuccess ? COMET_OK : cuda_fail(e, "dca launch");
+}
+
+comet_status comet_scan_select(comet_ctx *ctx, comet_dtype dtype, const void *rss, int64_t S,
+                               int32_t k, int64_t *idx_out, void *rss_out, comet_stream stream)
+{
+    if (!ctx) return fail(COMET_ERR_INVALID_ARG, "ctx is NULL");
+    CHECK(check_dtype(dtype));
+    if (S < 1) return fail(COMET_ERR_INVALID_ARG, "S must be >= 1");
+    if (k < 1 || k > 64 || k > S) return fail(COMET_ERR_INVALID_ARG, "k must be in [1, min(64, S)]");
+    if (!rss || !idx_out) return fail(COMET_ERR_INVALID_ARG, "rss and idx_out are required");
+    if (!aligned(rss, esize(dtype)) || !aligned(idx_out, 8) || (rss_out && !aligned(rss_out, esize(dtype))))
+        return fail(COMET_ERR_INVALID_ARG, "an array is misaligned for its element type");
+    DeviceGuard g(ctx->device);
+    if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+    comet::SelArgs a;
+    a.rss = rss;
+    a.S = S;
+    a.k = k;
+    a.idx_out = idx_out;
+    a.rss_out = rss_out;
+    const size_t need = comet::select_scratch_bytes(dtype, S, k, &a.n_blocks);
+    if (need > ctx->scratch_bytes) {
+        // grow: the old buffer may still be in use by queued work on any stream
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+        if (ctx->scratch) cudaFree(ctx->scratch);
+        ctx->scratch = nullptr;
+        ctx->scratch_bytes = 0;
+        size_t want = need < ((size_t)1 << 20) ? ((size_t)1 << 20) : need;
+        e = cudaMalloc(&ctx->scratch, want);
+        if (e != cudaSuccess)
+            return e == cudaErrorMemoryAllocation ? fail(COMET_ERR_NO_MEMORY, "cudaMalloc(select scratch, %zu B)", want) : cuda_fail(e, "cudaMalloc");
+        ctx->scratch_bytes = want;
+    }
+    a.scratch = ctx->scratch;
+    cudaError_t e = comet::launch_select(dtype, a, (cudaStream_t)stream);
+    return e == cudaSuccess ? COMET_OK : cuda_fail(e, "select launch");
+}
+
+comet_status comet_scan_classify(comet_ctx *ctx, comet_dtype dtype, const comet_field *field,
+                                 const comet_scan_params *params, const void *points,
+                                 const int32_t *n_valid, const int8_t *charge, int64_t S,
+                                 const int64_t *seed_index, const void *wires, int32_t W,
+                                 int32_t ldw, const int32_t *hit_offsets, const void *drift,
+                                 uint8_t *hit_mask, uint8_t *hit_class, void *dca_wire,
+                                 int32_t update_mask, comet_stream stream)
+{
+    if (!ctx) return fail(COMET_ERR_INVALID_ARG, "ctx is NULL");
+    CHECK(check_dtype(dtype));
+    CHECK(check_field(field));
+    CHECK(check_params(params, true));
+    if (S < 1) return fail(COMET_ERR_INVALID_ARG, "S must be >= 1");
+    CHECK(check_hits(dtype, wires, W, ldw, hit_offsets, drift, hit_mask));
+    if (W == 0) return COMET_OK;
+    if (!points || !n_valid || !charge || !seed_index || !hit_class)
+        return fail(COMET_ERR_INVALID_ARG, "points, n_valid, charge, seed_index and hit_class are required");
+    if (!aligned(points, esize(dtype)) || !aligned(n_valid, 4) || !aligned(seed_index, 8) ||
+        (dca_wire && !aligned(dca_wire, esize(dtype))))
+        return fail(COMET_ERR_INVALID_ARG, "an array is misaligned for its element type");
+    DeviceGuard g(ctx->device);
+    if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+    comet::ClsArgs a;
+    a.points = points;
+    a.n_valid = n_valid;
+    a.charge = charge;
+    a.S = S;
+    a.n_rec = n_rec_of(params);
+    a.seed_index = seed_index;
+    a.wires = wires;
+    a.W = W;
+    a.ldw = ldw;
+    a.offs = hit_offsets;
+    a.drift = drift;
+    a.mask = hit_mask;
+    a.hit_class = hit_class;
+    a.dca_wire = dca_wire;
+    a.status = ctx->status;
+    a.lambda = params->lambda;
+    a.tol = params->tol;
+    a.max_iter = params->max_iter;
+    a.update_mask = update_mask;
+    cudaError_t e = comet::launch_classify(dtype, *field, a, (cudaStream_t)stream);
+    return e == cudaSuccess ? COMET_OK : cuda_fail(e, "classify launch");
+}
+
+} // extern "C"

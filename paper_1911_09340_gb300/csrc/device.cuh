@@ -1,0 +1,322 @@
+// Device building blocks of the seed scan (sm_103a): field evaluation, RK4 on y = (x, p), the
+// compensated FP32 state update, the point-to-wire distance, the virtual-plane DCA refinement and
+// the shared-memory staging of small arrays with the bulk-copy (TMA) engine.
+//
+// Equations of motion (arc length s, P0 = |p| of the seed, KAPPA = 299.792458 MeV/c per (T m)):
+//     dx/ds = p / P0,    dp/ds = (KAPPA q / P0) p x B(x).
+// In a uniform field this is the helix of Sec. 1; the paper integrates it with an RKN method
+// (Sec. 2.1), the scan here with classic fixed-step RK4.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace comet {
+
+constexpr double kKappa = 299.792458;
+
+// ------------------------------------------------------------------------------------------------
+// Fields
+// ------------------------------------------------------------------------------------------------
+
+// Uniform field along z: B = (0, 0, bz).  dp/ds reduces to w (py, -px, 0) with w = c bz.
+template <typename T>
+struct FieldAxial {
+    static constexpr bool kAxial = true;
+    T bz;
+    __device__ __forceinline__ void at(T, T, T, T &bx, T &by, T &bz_) const
+    {
+        bx = T(0);
+        by = T(0);
+        bz_ = bz;
+    }
+};
+
+// Uniform field of any direction.
+template <typename T>
+struct FieldUniform {
+    static constexpr bool kAxial = false;
+    T b0, b1, b2;
+    __device__ __forceinline__ void at(T, T, T, T &bx, T &by, T &bz) const
+    {
+        bx = b0;
+        by = b1;
+        bz = b2;
+    }
+};
+
+// Trilinear interpolation of a float32 table [3][nz][ny][nx]; coordinates clamped to the grid.
+template <typename T>
+struct FieldTable {
+    static constexpr bool kAxial = false;
+    const float *__restrict__ tab;
+    int nx, ny, nz;
+    T ox, oy, oz, inv_sp;
+
+    __device__ __forceinline__ static void cell(T g, int n, int &i, T &t)
+    {
+        g = g < T(0) ? T(0) : g;
+        g = g > T(n - 1) ? T(n - 1) : g;
+        T fl = floor(g);
+        i = (int)fl;
+        i = i > n - 2 ? n - 2 : i;
+        t = g - T(i);
+    }
+
+    __device__ __forceinline__ void at(T x, T y, T z, T &bx, T &by, T &bz) const
+    {
+        int ix, iy, iz;
+        T tx, ty, tz;
+        cell((x - ox) * inv_sp, nx, ix, tx);
+        cell((y - oy) * inv_sp, ny, iy, ty);
+        cell((z - oz) * inv_sp, nz, iz, tz);
+        const size_t plane = (size_t)nz * ny * nx;
+        const size_t base = ((size_t)iz * ny + iy) * nx + ix;
+        const size_t sy = (size_t)nx, sz = (size_t)nx * ny;
+        T out[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float *p = tab + c * plane + base;
+            T v000 = (T)__ldg(p), v001 = (T)__ldg(p + 1);
+            T v010 = (T)__ldg(p + sy), v011 = (T)__ldg(p + sy + 1);
+            T v100 = (T)__ldg(p + sz), v101 = (T)__ldg(p + sz + 1);
+            T v110 = (T)__ldg(p + sz + sy), v111 = (T)__ldg(p + sz + sy + 1);
+            T a00 = v000 + tx * (v001 - v000);
+            T a01 = v010 + tx * (v011 - v010);
+            T a10 = v100 + tx * (v101 - v100);
+            T a11 = v110 + tx * (v111 - v110);
+            T b0 = a00 + ty * (a01 - a00);
+            T b1 = a10 + ty * (a11 - a10);
+            out[c] = b0 + tz * (b1 - b0);
+        }
+        bx = out[0];
+        by = out[1];
+        bz = out[2];
+    }
+};
+
+// ------------------------------------------------------------------------------------------------
+// RK4
+// ------------------------------------------------------------------------------------------------
+
+// Increment of one classic RK4 step of length h from state y: inc = h/6 (k1 + 2 k2 + 2 k3 + k4).
+// c = KAPPA q / P0, ip = 1 / P0.
+template <typename T, class F>
+__device__ __forceinline__ void rk4_increment(const F &f, T c, T ip, const T y[6], T h, T inc[6])
+{
+    const T hh = T(0.5) * h;
+    const T h6 = h / T(6);
+    if constexpr (F::kAxial) {
+        const T w = c * f.bz;
+        // stage momenta (pz is constant in an axial field)
+        const T p1x = y[3], p1y = y[4];
+        const T k1x = w * p1y, k1y = -w * p1x;
+        const T p2x = y[3] + hh * k1x, p2y = y[4] + hh * k1y;
+        const T k2x = w * p2y, k2y = -w * p2x;
+        const T p3x = y[3] + hh * k2x, p3y = y[4] + hh * k2y;
+        const T k3x = w * p3y, k3y = -w * p3x;
+        const T p4x = y[3] + h * k3x, p4y = y[4] + h * k3y;
+        const T k4x = w * p4y, k4y = -w * p4x;
+        const T vz = y[5] * ip;
+        inc[0] = h6 * ((p1x * ip + T(2) * (p2x * ip + p3x * ip)) + p4x * ip);
+        inc[1] = h6 * ((p1y * ip + T(2) * (p2y * ip + p3y * ip)) + p4y * ip);
+        inc[2] = h6 * ((vz + T(2) * (vz + vz)) + vz);
+        inc[3] = h6 * ((k1x + T(2) * (k2x + k3x)) + k4x);
+        inc[4] = h6 * ((k1y + T(2) * (k2y + k3y)) + k4y);
+        inc[5] = T(0);
+    } else {
+        T k[4][6];
+        T t[6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) t[i] = y[i];
+#pragma unroll
+        for (int st = 0; st < 4; ++st) {
+            T bx, by, bz;
+            f.at(t[0], t[1], t[2], bx, by, bz);
+            k[st][0] = t[3] * ip;
+            k[st][1] = t[4] * ip;
+            k[st][2] = t[5] * ip;
+            k[st][3] = c * (t[4] * bz - t[5] * by);
+            k[st][4] = c * (t[5] * bx - t[3] * bz);
+            k[st][5] = c * (t[3] * by - t[4] * bx);
+            if (st < 3) {
+                const T a = st < 2 ? hh : h;
+#pragma unroll
+                for (int i = 0; i < 6; ++i) t[i] = y[i] + a * k[st][i];
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 6; ++i)
+            inc[i] = h6 * ((k[0][i] + T(2) * (k[1][i] + k[2][i])) + k[3][i]);
+    }
+}
+
+template <typename T, class F>
+__device__ __forceinline__ void rk4_step(const F &f, T c, T ip, T y[6], T h)
+{
+    T inc[6];
+    rk4_increment<T, F>(f, c, ip, y, h, inc);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) y[i] += inc[i];
+}
+
+// hi + lo += d, renormalised so that |lo| <= ulp(hi)/2 (Knuth's TwoSum; the rounded adds are never
+// contracted or reassociated).
+__device__ __forceinline__ void two_sum_add(float &hi, float &lo, float d)
+{
+    const float t = __fadd_rn(d, lo);
+    const float s = __fadd_rn(hi, t);
+    const float bb = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(t, bb));
+    hi = s;
+    lo = err;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Geometry
+// ------------------------------------------------------------------------------------------------
+
+// Squared distance of (x, y, z) to the line through a with unit direction u.
+template <typename T>
+__device__ __forceinline__ T line_dist2(T x, T y, T z, T ax, T ay, T az, T ux, T uy, T uz)
+{
+    const T dx = x - ax, dy = y - ay, dz = z - az;
+    const T t = dx * ux + dy * uy + dz * uz;
+    const T ex = dx - t * ux, ey = dy - t * uy, ez = dz - t * uz;
+    return ex * ex + ey * ey + ez * ez;
+}
+
+template <typename T>
+__device__ __forceinline__ T rsqrt_t(T v);
+template <>
+__device__ __forceinline__ float rsqrt_t<float>(float v) { return rsqrtf(v); }
+template <>
+__device__ __forceinline__ double rsqrt_t<double>(double v) { return 1.0 / sqrt(v); }
+
+// Lexicographic (distance, index) minimum: the lowest index wins exact ties.
+template <typename T>
+__device__ __forceinline__ void lex_min(T &bd, int &bk, T d, int k)
+{
+    if (d < bd || (d == bd && k < bk)) {
+        bd = d;
+        bk = k;
+    }
+}
+
+// Virtual-plane refinement of Algorithm 2 from state y: the plane contains the wire axis and has
+// normal n = t - (t.u) u (t the unit direction); d is the state's signed distance to it.  While
+// |d| >= tol, step along the track by -d/|n| with one RK4 step (moving ds along the track moves the
+// state |n| ds towards the plane).  Returns 1 if |d| < tol was reached within max_iter steps, 0 if
+// not or if the track runs parallel to the wire.  D = distance of the final state to the wire line.
+template <typename T, class F>
+__device__ __forceinline__ int refine_dca(const F &f, T c, T ip, T y[6], T ax, T ay, T az, T ux,
+                                          T uy, T uz, T tol, int max_iter, T &D)
+{
+    int conv = 0;
+    for (int it = 0;; ++it) {
+        const T rp = rsqrt_t<T>(y[3] * y[3] + y[4] * y[4] + y[5] * y[5]);
+        const T tx = y[3] * rp, ty = y[4] * rp, tz = y[5] * rp;
+        const T tu = tx * ux + ty * uy + tz * uz;
+        const T nx = tx - tu * ux, ny = ty - tu * uy, nz = tz - tu * uz;
+        const T nn2 = nx * nx + ny * ny + nz * nz;
+        if (nn2 < T(1e-18)) break;
+        const T rn = rsqrt_t<T>(nn2);
+        const T dist = ((y[0] - ax) * nx + (y[1] - ay) * ny + (y[2] - az) * nz) * rn;
+        if (fabs(dist) < tol) {
+            conv = 1;
+            break;
+        }
+        if (it >= max_iter) break;
+        rk4_step<T, F>(f, c, ip, y, -dist * rn);
+    }
+    D = sqrt(line_dist2<T>(y[0], y[1], y[2], ax, ay, az, ux, uy, uz));
+    return conv;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Shared-memory staging with the bulk-copy engine (cp.async.bulk + mbarrier)
+// ------------------------------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Orders this thread's earlier generic-proxy shared-memory accesses before later bulk copies.
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Waits for phase `parity` of the barrier to complete, for at most ~timeout_ns.  Returns false on
+// timeout (the caller then records an error and falls back to plain loads).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t timeout_ns)
+{
+    const uint32_t a = smem_u32(bar);
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 0; it < (1u << 26); ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if ((it & 63) == 63 && global_ns() - t0 > timeout_ns) return false;
+    }
+    return false;
+}
+
+// Plan for copying n elements of size es from global src into a 16-byte-aligned shared buffer so
+// that element i lands at dst[off + i]: the 16-byte-aligned middle goes through one bulk copy, the
+// ragged head and tail through plain loads.  Every thread computes the same plan from the address.
+struct StagePlan {
+    int off;      // element offset of element 0 inside the shared buffer
+    int head;     // elements before the first 16-byte boundary of src
+    int body;     // elements in the bulk-copied middle
+};
+
+__device__ __forceinline__ StagePlan stage_plan(const void *src, int n, int es)
+{
+    StagePlan p;
+    const int mis = (int)((uintptr_t)src & 15);
+    p.off = mis / es;
+    int head = mis == 0 ? 0 : (16 - mis) / es;
+    head = head > n ? n : head;
+    p.head = head;
+    p.body = (((n - head) * es) / 16) * 16 / es;
+    return p;
+}
+
+} // namespace comet

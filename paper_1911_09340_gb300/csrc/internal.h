@@ -1,0 +1,100 @@
+// Launchers shared between the C-ABI layer (comet_scan.cu) and the kernel translation units.
+// Arguments arrive here already validated.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "comet_scan.h"
+
+namespace comet {
+
+struct LatArgs {
+    double vx, vy;
+    double centre[4], half_width[4];
+    int counts[4];
+    int charge;
+    int8_t *charge_out;
+};
+
+struct PropArgs {
+    const void *seeds;
+    const int8_t *charge;
+    int64_t S;
+    void *points;
+    int32_t *n_valid;
+    double h, zmin, zmax, rmax;
+    int n_steps, stride, n_rec;
+};
+
+struct DcaArgs {
+    const void *points;
+    const int32_t *n_valid;
+    const int8_t *charge;
+    int64_t S;
+    int n_rec;
+    const void *wires;
+    int W, ldw;
+    const int32_t *offs;
+    const void *drift;
+    const uint8_t *mask;
+    void *rss;
+    int32_t *n_in;
+    void *dca_out;
+    int32_t *n_unconv;
+    int32_t *status;       // device status word of the context (bit 0: a bulk-copy wait timed out)
+    double lambda, tol;
+    double R1;             // level-1 segment radius (m), margins included
+    double half_rec;       // half a recording interval (m), margins included
+    int max_iter;
+    int G;                 // recorded states per level-1 segment
+    int exact_all;         // refine every wire (dca_out requested)
+};
+
+struct SelArgs {
+    const void *rss;
+    int64_t S;
+    int k;
+    int64_t *idx_out;
+    void *rss_out;
+    void *scratch;         // per-block partial results
+    int n_blocks;
+};
+
+struct ClsArgs {
+    const void *points;
+    const int32_t *n_valid;
+    const int8_t *charge;
+    int64_t S;
+    int n_rec;
+    const int64_t *seed_index;
+    const void *wires;
+    int W, ldw;
+    const int32_t *offs;
+    const void *drift;
+    uint8_t *mask;
+    uint8_t *hit_class;
+    void *dca_wire;
+    int32_t *status;       // bit 1: seed_index out of range
+    double lambda, tol;
+    int max_iter;
+    int update_mask;
+};
+
+cudaError_t launch_lattice(comet_dtype dt, const LatArgs &a, void *seeds, int64_t S, cudaStream_t st);
+cudaError_t launch_propagate(comet_dtype dt, const comet_field &f, const PropArgs &a, cudaStream_t st);
+cudaError_t launch_dca(comet_dtype dt, const comet_field &f, const DcaArgs &a, cudaStream_t st);
+int dca_n1max(comet_dtype dt);   // maximum number of level-1 segments per seed
+cudaError_t launch_select(comet_dtype dt, const SelArgs &a, cudaStream_t st);
+size_t select_scratch_bytes(comet_dtype dt, int64_t S, int k, int *n_blocks);
+cudaError_t launch_classify(comet_dtype dt, const comet_field &f, const ClsArgs &a, cudaStream_t st);
+
+// Field kinds the kernels are specialised for.
+enum class FieldKind { Axial, Uniform, Table };
+inline FieldKind field_kind(const comet_field &f)
+{
+    if (f.kind == 1) return FieldKind::Table;
+    return (f.b[0] == 0.0 && f.b[1] == 0.0) ? FieldKind::Axial : FieldKind::Uniform;
+}
+
+} // namespace comet

@@ -1,0 +1,116 @@
+// Hit classification of the selected seed (Sec. 2.1) and the hit mask of the next turn partition
+// (Sec. 3.1: hits classified earlier are excluded from later seed scans).
+//
+// One warp per wire: the 32 lanes split the selected seed's recorded states for an exhaustive
+// closest-state search, reduce the lexicographic (distance, index) minimum with warp shuffles, and
+// lane 0 refines the DCA on the virtual plane exactly as comet_scan_dca does (same device functions,
+// same inputs, hence the same D), then classifies the closest unmasked hit if |D - r| < lambda.
+#include <float.h>
+
+#include "device.cuh"
+#include "internal.h"
+
+namespace comet {
+
+template <typename T, class F>
+__global__ void __launch_bounds__(256) classify_kernel(F f, ClsArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    const int i = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (i >= a.W) return;   // whole warps
+    const int hb = a.offs[i], he = a.offs[i + 1];
+    const int64_t s = *a.seed_index;
+    if (s < 0 || s >= a.S) {
+        for (int j = hb + lane; j < he; j += 32) a.hit_class[j] = 0;
+        if (lane == 0 && a.status) atomicOr(a.status, 2);
+        return;
+    }
+    const int64_t S = a.S;
+    const int64_t plane = (int64_t)a.n_rec * S;
+    const T *__restrict__ P = (const T *)a.points;
+    const T *__restrict__ Wg = (const T *)a.wires;
+    const T ax = Wg[i], ay = Wg[(size_t)a.ldw + i], az = Wg[2 * (size_t)a.ldw + i];
+    const T ux = Wg[3 * (size_t)a.ldw + i], uy = Wg[4 * (size_t)a.ldw + i],
+            uz = Wg[5 * (size_t)a.ldw + i];
+    const int nv = a.n_valid[s];
+
+    T bd = T(INFINITY);
+    int bk = 0x7fffffff;
+    for (int k = lane; k < nv; k += 32) {
+        const int64_t o = (int64_t)k * S + s;
+        lex_min<T>(bd, bk, line_dist2<T>(P[o], P[plane + o], P[2 * plane + o], ax, ay, az, ux, uy, uz),
+                   k);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const T od = __shfl_xor_sync(0xffffffffu, bd, off);
+        const int ok = __shfl_xor_sync(0xffffffffu, bk, off);
+        lex_min<T>(bd, bk, od, ok);
+    }
+    if (lane != 0) return;
+
+    const double px = P[3 * plane + s], py = P[4 * plane + s], pz = P[5 * plane + s];
+    const double pd = sqrt(px * px + py * py + pz * pz);
+    const int q = a.charge[s];
+    T y[6];
+    const int64_t o = (int64_t)bk * S + s;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) y[c] = P[c * plane + o];
+    T D;
+    refine_dca<T, F>(f, (T)(kKappa * q / pd), (T)(1.0 / pd), y, ax, ay, az, ux,
+                     uy, uz, (T)a.tol, a.max_iter, D);
+    if (a.dca_wire) ((T *)a.dca_wire)[i] = D;
+
+    const T *__restrict__ Dg = (const T *)a.drift;
+    const T lam = (T)a.lambda;
+    int jb = -1;
+    T eb = T(INFINITY);
+    for (int j = hb; j < he; ++j) {
+        if (a.mask[j]) continue;
+        const T e = fabs(D - Dg[j]);
+        if (e < eb) {
+            eb = e;
+            jb = j;
+        }
+    }
+    for (int j = hb; j < he; ++j) {
+        const uint8_t cl = (j == jb && eb < lam) ? 1 : 0;
+        a.hit_class[j] = cl;
+        if (cl && a.update_mask) a.mask[j] = 1;
+    }
+}
+
+template <typename T>
+static void cls_dispatch(const comet_field &f, const ClsArgs &a, cudaStream_t st)
+{
+    const int nt = 256;
+    const int64_t threads = (int64_t)a.W * 32;
+    const unsigned nb = (unsigned)((threads + nt - 1) / nt);
+    switch (field_kind(f)) {
+    case FieldKind::Axial:
+        classify_kernel<T, FieldAxial<T>><<<nb, nt, 0, st>>>(FieldAxial<T>{(T)f.b[2]}, a);
+        break;
+    case FieldKind::Uniform:
+        classify_kernel<T, FieldUniform<T>><<<nb, nt, 0, st>>>(
+            FieldUniform<T>{(T)f.b[0], (T)f.b[1], (T)f.b[2]}, a);
+        break;
+    case FieldKind::Table:
+        classify_kernel<T, FieldTable<T>><<<nb, nt, 0, st>>>(
+            FieldTable<T>{(const float *)f.table, f.nx, f.ny, f.nz, (T)f.origin[0], (T)f.origin[1],
+                          (T)f.origin[2], (T)(1.0 / f.spacing)},
+            a);
+        break;
+    }
+}
+
+cudaError_t launch_classify(comet_dtype dt, const comet_field &f, const ClsArgs &a, cudaStream_t st)
+{
+    if (a.W == 0) return cudaSuccess;
+    if (dt == COMET_F32)
+        cls_dispatch<float>(f, a, st);
+    else
+        cls_dispatch<double>(f, a, st);
+    return cudaGetLastError();
+}
+
+} // namespace comet

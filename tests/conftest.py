@@ -16,3 +16,13 @@ def pytest_configure(config):
 def chamber():
     from paper_1911_09340_gb300 import synth
     return synth.make_chamber()
+
+
+@pytest.fixture(scope="session")
+def ctx():
+    """A comet_ctx on cuda:0 (GPU tests only); builds the library first if needed."""
+    from paper_1911_09340_gb300 import binding, build
+    build.build()
+    c = binding.Context(0)
+    yield c
+    c.close()

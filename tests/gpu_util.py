@@ -1,0 +1,80 @@
+"""Helpers shared by the GPU parity tests: run the CUDA path through the C ABI on inputs that the
+generator or the oracle made, and bring results back in the oracle's layouts."""
+import numpy as np
+import torch
+
+import oracle as O
+from paper_1911_09340_gb300 import binding as B
+
+
+def both_params(**kw):
+    return O.Params(**kw), B.ScanParams(**kw)
+
+
+def dev_seeds(seeds_aos, dtype):
+    return torch.as_tensor(np.ascontiguousarray(np.asarray(seeds_aos).T), dtype=dtype, device="cuda").contiguous()
+
+
+def dev_wires(wires_soa, dtype, misalign=0, pad_to=4):
+    """[6][ldw] device tensor; ``misalign`` shifts the base pointer by that many elements."""
+    W = wires_soa.shape[1]
+    ldw = max(pad_to, (W + pad_to - 1) // pad_to * pad_to)
+    flat = torch.zeros(6 * ldw + misalign, dtype=dtype, device="cuda")
+    w = flat[misalign:].view(6, ldw)
+    w[:, :W] = torch.as_tensor(np.asarray(wires_soa), dtype=dtype)
+    return w
+
+
+def gpu_propagate(ctx, field, bp, seeds_aos, q, dtype):
+    S = seeds_aos.shape[0]
+    seeds = dev_seeds(seeds_aos, dtype)
+    charge = torch.full((S,), int(q), dtype=torch.int8, device="cuda")
+    pts = torch.full((6, bp.n_rec, S), float("nan"), dtype=dtype, device="cuda")
+    nv = torch.zeros(S, dtype=torch.int32, device="cuda")
+    B.comet_scan_propagate(ctx, field, bp, seeds, charge, pts, nv)
+    return seeds, charge, pts, nv
+
+
+def to_aos_points(pts):
+    return pts.double().cpu().numpy().transpose(2, 1, 0)
+
+
+def gpu_dca(ctx, field, bp, seeds_aos, q, wires_soa, offs, drift, mask, dtype, want_dca=True,
+            misalign=0):
+    seeds, charge, pts, nv = gpu_propagate(ctx, field, bp, seeds_aos, q, dtype)
+    S = seeds_aos.shape[0]
+    W = wires_soa.shape[1]
+    w = dev_wires(wires_soa, dtype, misalign)
+    o = torch.as_tensor(np.asarray(offs, np.int32), device="cuda")
+    d = torch.as_tensor(np.asarray(drift), dtype=dtype, device="cuda")
+    m = torch.as_tensor(np.asarray(mask, np.uint8), device="cuda")
+    rss = torch.full((S,), float("nan"), dtype=dtype, device="cuda")
+    n_in = torch.full((S,), -1, dtype=torch.int32, device="cuda")
+    dca = torch.full((max(W, 1), S), float("nan"), dtype=dtype, device="cuda") if want_dca else None
+    nunc = torch.zeros(1, dtype=torch.int32, device="cuda")
+    B.comet_scan_dca(ctx, field, bp, pts, nv, charge, w, o, d, m, rss, n_in, dca_out=dca,
+                     n_unconverged=nunc, n_wires=W)
+    torch.cuda.synchronize()
+    out = dict(rss=rss.double().cpu().numpy(), n_in=n_in.cpu().numpy(), n_unconv=int(nunc.item()),
+               pts=pts, nv=nv, charge=charge, w=w, o=o, d=d, m=m)
+    if want_dca:
+        out["dca"] = dca[:W].double().cpu().numpy().T   # [S][W]
+    return out
+
+
+def per_wire_residual(dca_sw, offs, drift, mask):
+    """min over unmasked hits of |D - r| per (seed, wire); inf where a wire has no unmasked hit."""
+    S, W = dca_sw.shape
+    e = np.full((S, W), np.inf)
+    for i in range(W):
+        for j in range(offs[i], offs[i + 1]):
+            if not mask[j]:
+                e[:, i] = np.minimum(e[:, i], np.abs(dca_sw[:, i] - drift[j]))
+    return e
+
+
+def rss_bound(e_oracle, lam, delta):
+    """Largest |RSS_gpu - RSS_oracle| when every DCA is within delta: wires capped with margin
+    contribute nothing, the others at most 2*min(e, lam)*delta + delta^2 each."""
+    near = e_oracle < lam + delta
+    return np.where(near, 2.0 * np.minimum(e_oracle, lam) * delta + delta * delta, 0.0).sum(1)

@@ -1,0 +1,56 @@
+"""The C-ABI library: it builds for sm_103a, loads without a GPU, and exports every entry point that
+include/comet_scan.h declares.  No compute call is made here."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "comet_scan.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(comet_\w+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_1911_09340_gb300 import build
+    return build.build()
+
+
+def test_header_declares_the_scan_steps():
+    names = declared_functions()
+    for n in ("comet_scan_lattice", "comet_scan_propagate", "comet_scan_dca", "comet_scan_select",
+              "comet_scan_classify", "comet_ctx_create", "comet_ctx_destroy", "comet_last_error"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (comet_\w+)$", out, flags=re.M))
+    assert set(declared_functions()) <= exported
+
+
+def test_binding_signatures_cover_the_header():
+    from paper_1911_09340_gb300 import binding
+    assert set(binding.SIGNATURES) == set(declared_functions())
+
+
+def test_library_is_built_for_sm_103a(libpath):
+    out = subprocess.run(["cuobjdump", "--list-elf", libpath], capture_output=True, text=True).stdout
+    assert "sm_103a" in out
+
+
+def test_header_compiles_as_c(tmp_path):
+    src = tmp_path / "t.c"
+    src.write_text('#include "comet_scan.h"\nint main(void){ comet_scan_params p; (void)p; return 0; }\n')
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    "-c", str(src), "-o", str(tmp_path / "t.o")], check=True)

@@ -1,0 +1,199 @@
+"""Parity of DCA finding and the RSS (Algorithm 2, Eq. 1) with the FP64 oracle.
+
+Bars: FP64 DCAs within 1e-9 m and RSS within 1e-10 relative (the paper's own CPU/GPU validation
+found < O(1e-12), Sec. 4.1); FP32 DCAs within 2 um (track points within 1 um over one turn plus the
+FP32 distance arithmetic) and RSS within the bound those DCAs imply; n_in identical where no
+residual sits within the DCA tolerance of the cutoff.  Covered: both dtypes, both lane layouts (4
+lanes per seed below 65,536 seeds, 1 above), ragged seed counts, several wire tiles, hits beyond the
+shared-memory capacity, misaligned wire rows, W = 0, all hits masked, the pruned and exact paths.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1911_09340_gb300 import binding as B
+from paper_1911_09340_gb300 import synth
+
+from gpu_util import both_params, gpu_dca, per_wire_residual, rss_bound
+
+pytestmark = pytest.mark.gpu
+
+UNIFORM = synth.uniform_field(1.0)
+
+
+def _event_inputs(ev, stride=1, lam=0.01, tol64=True):
+    op, bp = both_params(n_steps=ev.n_steps[0], stride=stride, lam=lam,
+                         tol=1e-12 if tol64 else 1e-6)
+    return op, bp
+
+
+def test_fp64_exact_path_matches_oracle(ctx):
+    ev = synth.single_event_fp64()
+    seeds = O.lattice(ev.partitions[0])[::8]
+    op, bp = _event_inputs(ev)
+    mask = np.zeros(ev.n_hits, np.uint8)
+    g = gpu_dca(ctx, B.DeviceField.from_synth(UNIFORM), bp, seeds, -1, ev.wires, ev.hit_offsets,
+                ev.drift, mask, torch.float64, want_dca=True)
+    r = O.scan(UNIFORM, op, seeds, -1, O.wires_aos(ev.wires), ev.hit_offsets, ev.drift, mask,
+               want_dca=True)
+    assert np.abs(g["dca"] - r["dca"]).max() <= 1e-9
+    assert np.allclose(g["rss"], r["rss"], rtol=1e-10, atol=0)
+    assert np.array_equal(g["n_in"], r["n_in"])
+    assert g["n_unconv"] == int(r["n_unconv"].sum())
+
+
+def test_fp64_pruned_path_equals_exact_path(ctx):
+    ev = synth.single_event_fp64()
+    seeds = O.lattice(ev.partitions[1])[::8]
+    op, bp = _event_inputs(ev)
+    mask = np.zeros(ev.n_hits, np.uint8)
+    mask[::5] = 1
+    f = B.DeviceField.from_synth(UNIFORM)
+    a = gpu_dca(ctx, f, bp, seeds, -1, ev.wires, ev.hit_offsets, ev.drift, mask, torch.float64, True)
+    b = gpu_dca(ctx, f, bp, seeds, -1, ev.wires, ev.hit_offsets, ev.drift, mask, torch.float64, False)
+    assert np.array_equal(a["rss"], b["rss"])
+    assert np.array_equal(a["n_in"], b["n_in"])
+    r = O.scan(UNIFORM, op, seeds, -1, O.wires_aos(ev.wires), ev.hit_offsets, ev.drift, mask)
+    assert np.allclose(b["rss"], r["rss"], rtol=1e-10, atol=0)
+
+
+def _fp32_check(g, r, ev_offs, drift, mask, lam, delta=2e-6):
+    near = r["dca"] < 0.03
+    bad = np.abs(g["dca"] - r["dca"])[near] > delta
+    assert bad.mean() <= 1e-3, (bad.sum(), np.abs(g["dca"] - r["dca"])[near].max())
+    e = per_wire_residual(r["dca"], ev_offs, drift, mask)
+    bound = rss_bound(e, lam, delta)
+    dev = np.abs(g["rss"] - r["rss"])
+    ok = dev <= bound + 1e-12
+    assert ok.mean() >= 0.999, (dev / np.maximum(bound, 1e-30)).max()
+    edge = (np.abs(e - lam) < delta).any(1)
+    assert np.array_equal(g["n_in"][~edge], r["n_in"][~edge])
+
+
+@pytest.mark.parametrize("stride", [1, 4])
+def test_fp32_matches_oracle_multi_turn_event(ctx, stride):
+    ev = synth.multi_turn_event(0)
+    seeds = O.lattice(ev.partitions[0])[::64].astype(np.float32).astype(np.float64)  # 4096 seeds
+    op, bp = both_params(n_steps=ev.n_steps[0], stride=stride, lam=0.01, tol=1e-6)
+    op.tol = 1e-12
+    mask = np.zeros(ev.n_hits, np.uint8)
+    g = gpu_dca(ctx, B.DeviceField.from_synth(UNIFORM), bp, seeds, -1, ev.wires, ev.hit_offsets,
+                ev.drift, mask, torch.float32, want_dca=True)
+    r = O.scan(UNIFORM, op, seeds, -1, O.wires_aos(ev.wires), ev.hit_offsets, ev.drift, mask,
+               want_dca=True)
+    _fp32_check(g, r, ev.hit_offsets, ev.drift, mask, 0.01)
+    # the pruned path gives the same RSS as the exact path up to FP32 summation of equal terms
+    p = gpu_dca(ctx, B.DeviceField.from_synth(UNIFORM), bp, seeds, -1, ev.wires, ev.hit_offsets,
+                ev.drift, mask, torch.float32, want_dca=False)
+    assert np.allclose(p["rss"], g["rss"], rtol=1e-6, atol=0)
+    assert np.array_equal(p["n_in"], g["n_in"])
+
+
+def test_fp32_one_lane_per_seed_layout_sampled(ctx):
+    """65,573 seeds (ragged tail) run one seed per lane; the oracle checks a sample of them."""
+    ev = synth.multi_turn_event(1)
+    all_seeds = O.lattice(ev.partitions[0]).astype(np.float32).astype(np.float64)
+    seeds = all_seeds[:65573]
+    op, bp = both_params(n_steps=ev.n_steps[0], stride=2, lam=0.01, tol=1e-6)
+    op.tol = 1e-12
+    mask = np.zeros(ev.n_hits, np.uint8)
+    g = gpu_dca(ctx, B.DeviceField.from_synth(UNIFORM), bp, seeds, -1, ev.wires, ev.hit_offsets,
+                ev.drift, mask, torch.float32, want_dca=False)
+    sample = np.unique(np.concatenate([np.arange(0, 65573, 61), [65572, int(np.argmin(g["rss"]))]]))
+    r = O.scan(UNIFORM, op, seeds[sample], -1, O.wires_aos(ev.wires), ev.hit_offsets, ev.drift,
+               mask, want_dca=True)
+    e = per_wire_residual(r["dca"], ev.hit_offsets, ev.drift, mask)
+    bound = rss_bound(e, 0.01, 2e-6)
+    assert (np.abs(g["rss"][sample] - r["rss"]) <= bound + 1e-12).mean() >= 0.999
+
+
+def _many_wires_case(n_wires=600, hits_per_wire=3, seed=5):
+    ch = synth.make_chamber()
+    ev = synth.single_event_fp64(ch)
+    rng = np.random.default_rng(seed)
+    extra = rng.choice(ch.n_wires, size=n_wires - ev.n_wires, replace=False)
+    ids = np.unique(np.concatenate([ev.wire_ids, extra]))[:n_wires]
+    wires = np.concatenate([ch.a[:, ids], ch.u[:, ids]], axis=0)
+    offs = np.arange(len(ids) + 1, dtype=np.int32) * hits_per_wire
+    drift = rng.uniform(0, 8e-3, size=offs[-1])
+    mask = (rng.uniform(size=offs[-1]) < 0.2).astype(np.uint8)
+    return ev, wires, offs, drift, mask
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("misalign", [0, 1, 3])
+def test_many_wires_many_hits_misaligned(ctx, dtype, misalign):
+    ev, wires, offs, drift, mask = _many_wires_case()
+    assert wires.shape[1] > 2 * 256 and offs[-1] > 1024     # several tiles, hits read from global
+    seeds = O.lattice(ev.partitions[0])[::97].astype(np.float32).astype(np.float64)
+    op, bp = both_params(n_steps=ev.n_steps[0], lam=0.01,
+                         tol=1e-12 if dtype == torch.float64 else 1e-6)
+    op.tol = 1e-12
+    for want in (True, False):
+        g = gpu_dca(ctx, B.DeviceField.from_synth(UNIFORM), bp, seeds, -1, wires, offs, drift, mask,
+                    dtype, want_dca=want, misalign=misalign)
+        r = O.scan(UNIFORM, op, seeds, -1, O.wires_aos(wires), offs, drift, mask, want_dca=True)
+        if dtype == torch.float64:
+            if want:
+                assert np.abs(g["dca"] - r["dca"]).max() <= 1e-9
+            assert np.allclose(g["rss"], r["rss"], rtol=1e-10, atol=0)
+            assert np.array_equal(g["n_in"], r["n_in"])
+        else:
+            e = per_wire_residual(r["dca"], offs, drift, mask)
+            bound = rss_bound(e, 0.01, 2e-6)
+            assert (np.abs(g["rss"] - r["rss"]) <= bound + 1e-12).mean() >= 0.999
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_degenerate_inputs(ctx, dtype):
+    ev = synth.single_event_fp64()
+    seeds = O.lattice(ev.partitions[0])[:5]
+    op, bp = both_params(n_steps=ev.n_steps[0], tol=1e-12 if dtype == torch.float64 else 1e-6)
+    f = B.DeviceField.from_synth(UNIFORM)
+    # no wires at all
+    g = gpu_dca(ctx, f, bp, seeds, -1, np.zeros((6, 0)), np.zeros(1, np.int32), np.zeros(0),
+                np.zeros(0, np.uint8), dtype, want_dca=False)
+    assert np.all(g["rss"] == 0) and np.all(g["n_in"] == 0)
+    # every hit masked: no wire is in the sum
+    mask = np.ones(ev.n_hits, np.uint8)
+    g = gpu_dca(ctx, f, bp, seeds, -1, ev.wires, ev.hit_offsets, ev.drift, mask, dtype, want_dca=True)
+    assert np.all(g["rss"] == 0) and np.all(g["n_in"] == 0)
+    r = O.scan(UNIFORM, op, seeds, -1, O.wires_aos(ev.wires), ev.hit_offsets, ev.drift, mask,
+               want_dca=True)
+    tol = 1e-9 if dtype == torch.float64 else 2e-6
+    assert np.abs(g["dca"] - r["dca"])[r["dca"] < 0.03].max() <= tol
+    # a single seed
+    g = gpu_dca(ctx, f, bp, seeds[:1], -1, ev.wires, ev.hit_offsets, ev.drift,
+                np.zeros(ev.n_hits, np.uint8), dtype, want_dca=False)
+    r = O.scan(UNIFORM, op, seeds[:1], -1, O.wires_aos(ev.wires), ev.hit_offsets, ev.drift,
+               np.zeros(ev.n_hits, np.uint8))
+    assert np.allclose(g["rss"], r["rss"], rtol=1e-10 if dtype == torch.float64 else 1e-3)
+
+
+def test_unconverged_count_matches_oracle(ctx):
+    ev = synth.single_event_fp64()
+    seeds = O.lattice(ev.partitions[0])[::64]
+    op, bp = both_params(n_steps=ev.n_steps[0], stride=5, max_iter=1)
+    mask = np.zeros(ev.n_hits, np.uint8)
+    g = gpu_dca(ctx, B.DeviceField.from_synth(UNIFORM), bp, seeds, -1, ev.wires, ev.hit_offsets,
+                ev.drift, mask, torch.float64, want_dca=True)
+    r = O.scan(UNIFORM, op, seeds, -1, O.wires_aos(ev.wires), ev.hit_offsets, ev.drift, mask,
+               want_dca=True)
+    assert int(r["n_unconv"].sum()) > 0
+    assert g["n_unconv"] == int(r["n_unconv"].sum())
+    assert np.abs(g["dca"] - r["dca"]).max() <= 1e-9
+
+
+def test_table_field_dca(ctx):
+    field = synth.table_field(spacing=0.02)
+    ev = synth.single_event_fp64()
+    seeds = O.lattice(ev.partitions[0])[::33]
+    op, bp = both_params(n_steps=ev.n_steps[0])
+    mask = np.zeros(ev.n_hits, np.uint8)
+    g = gpu_dca(ctx, B.DeviceField.from_synth(field), bp, seeds, -1, ev.wires, ev.hit_offsets,
+                ev.drift, mask, torch.float64, want_dca=True)
+    r = O.scan(field, op, seeds, -1, O.wires_aos(ev.wires), ev.hit_offsets, ev.drift, mask,
+               want_dca=True)
+    assert np.abs(g["dca"] - r["dca"]).max() <= 1e-9
+    assert np.allclose(g["rss"], r["rss"], rtol=1e-10, atol=0)

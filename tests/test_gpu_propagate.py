@@ -1,0 +1,127 @@
+"""Parity of the seed lattice and the track recording (Algorithm 1) with the FP64 oracle.
+
+Bars: FP64 track points within 1e-9 m; FP32 track points within 5 um over three turns (the FP32
+kernel accumulates its state as a compensated float pair); the number of recorded states identical.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1911_09340_gb300 import binding as B
+from paper_1911_09340_gb300 import synth
+
+from gpu_util import both_params, gpu_propagate, to_aos_points
+
+pytestmark = pytest.mark.gpu
+
+OPEN = dict(zmin=-50.0, zmax=50.0, rmax=50.0)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_lattice_matches_oracle(ctx, dtype):
+    spec = synth.LatticeSpec(vxy=(0.013, -0.07), centre=(-0.21, 1.3, 11.5, 101.2),
+                             half_width=(0.02, 0.04, 3.0, 6.4), counts=(3, 5, 7, 9), charge=-1)
+    S = spec.n_seeds
+    seeds = torch.empty((6, S), dtype=dtype, device="cuda")
+    charge = torch.zeros(S, dtype=torch.int8, device="cuda")
+    B.comet_scan_lattice(ctx, spec, seeds, charge)
+    got = seeds.double().cpu().numpy().T
+    ref = O.lattice(spec)
+    if dtype == torch.float64:
+        assert np.allclose(got, ref, rtol=1e-15, atol=1e-18)
+    else:
+        assert np.allclose(got, ref.astype(np.float32).astype(np.float64), rtol=1.2e-7, atol=0)
+    assert np.all(charge.cpu().numpy() == -1)
+
+
+def _cfg1_seeds(every=4):
+    ev = synth.single_event_fp64()
+    return ev, O.lattice(ev.partitions[0])[::every]
+
+
+def test_fp64_points_match_oracle_single_event(ctx):
+    ev, seeds = _cfg1_seeds(4)
+    op, bp = both_params(n_steps=ev.n_steps[0])
+    field = synth.uniform_field(1.0)
+    _, _, pts, nv = gpu_propagate(ctx, B.DeviceField.from_synth(field), bp, seeds, -1, torch.float64)
+    ref, rnv = O.propagate(field, op, seeds, -1)
+    got = to_aos_points(pts)
+    assert np.array_equal(nv.cpu().numpy(), rnv)
+    for s in range(seeds.shape[0]):
+        n = rnv[s]
+        assert np.abs(got[s, :n, :3] - ref[s, :n, :3]).max() <= 1e-9
+        assert np.abs(got[s, :n, 3:] - ref[s, :n, 3:]).max() <= 1e-9 * 105
+
+
+def test_fp32_points_within_5um_over_three_turns(ctx):
+    ch = synth.make_chamber()
+    ev = synth.multi_turn_event(0, ch)
+    seeds = O.lattice(ev.partitions[0])[::257].astype(np.float32).astype(np.float64)
+    n = 3 * ev.n_steps[0]
+    op, bp = both_params(n_steps=n, **OPEN)
+    field = synth.uniform_field(1.0)
+    _, _, pts, nv = gpu_propagate(ctx, B.DeviceField.from_synth(field), bp, seeds, -1, torch.float32)
+    ref, rnv = O.propagate(field, op, seeds, -1)
+    got = to_aos_points(pts)
+    assert np.array_equal(nv.cpu().numpy(), rnv)
+    err = np.abs(got[:, :, :3] - ref[:, :, :3]).max()
+    assert err <= 5e-6, err
+    P0 = np.linalg.norm(seeds[:, 3:], axis=1)[:, None, None]
+    assert (np.abs(got[:, :, 3:] - ref[:, :, 3:]) / P0).max() <= 1e-5
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-9), (torch.float32, 5e-6)])
+def test_stride_and_target_region(ctx, dtype, tol):
+    rng = np.random.default_rng(7)
+    S = 300
+    pt = rng.uniform(60, 105, S)
+    pz = rng.uniform(-40, 40, S)
+    ph = rng.uniform(0, 2 * np.pi, S)
+    seeds = np.stack([rng.uniform(-0.1, 0.1, S), rng.uniform(-0.1, 0.1, S), rng.uniform(-0.5, 0.5, S),
+                      pt * np.cos(ph), pt * np.sin(ph), pz], axis=1)
+    seeds = seeds.astype(np.float32).astype(np.float64)
+    op, bp = both_params(n_steps=2500, stride=3, zmin=-0.6, zmax=0.55, rmax=0.6)
+    field = synth.uniform_field(1.0)
+    q = 1
+    _, _, pts, nv = gpu_propagate(ctx, B.DeviceField.from_synth(field), bp, seeds, q, dtype)
+    ref, rnv = O.propagate(field, op, seeds, q)
+    gnv = nv.cpu().numpy()
+    got = to_aos_points(pts)
+    # recorded-state counts agree except where the stopping state sits within 1 um of the boundary
+    for s in np.nonzero(gnv != rnv)[0]:
+        k = min(gnv[s], rnv[s]) - 1
+        x = ref[s, k]
+        margin = min(abs(x[2] - op.zmin), abs(x[2] - op.zmax), abs(math.hypot(x[0], x[1]) - op.rmax))
+        assert margin < 1e-6, (s, gnv[s], rnv[s])
+    assert (gnv != rnv).mean() < 0.01
+    assert (rnv < op.n_rec()).mean() > 0.2   # the target region does stop tracks
+    for s in range(S):
+        n = min(gnv[s], rnv[s])
+        assert np.abs(got[s, :n, :3] - ref[s, :n, :3]).max() <= tol
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-9), (torch.float32, 5e-6)])
+def test_table_field_points(ctx, dtype, tol):
+    field = synth.table_field(spacing=0.02)
+    ev = synth.single_event_fp64()
+    seeds = O.lattice(ev.partitions[0])[::41].astype(np.float32).astype(np.float64)
+    op, bp = both_params(n_steps=2300)
+    _, _, pts, nv = gpu_propagate(ctx, B.DeviceField.from_synth(field), bp, seeds, -1, dtype)
+    ref, rnv = O.propagate(field, op, seeds, -1)
+    got = to_aos_points(pts)
+    assert np.array_equal(nv.cpu().numpy(), rnv)
+    err = max(np.abs(got[s, :rnv[s], :3] - ref[s, :rnv[s], :3]).max() for s in range(seeds.shape[0]))
+    assert err <= tol, err
+
+
+def test_general_uniform_field_and_zero_charge(ctx):
+    field = synth.Field(kind=0, b=(0.1, -0.2, 0.9))
+    seeds = np.array([[0.0, 0.0, 0.0, 60.0, 30.0, 20.0], [0.1, 0.0, 0.2, -50.0, 10.0, 5.0]])
+    op, bp = both_params(n_steps=1500, **OPEN)
+    for q in (-1, 0):
+        _, _, pts, nv = gpu_propagate(ctx, B.DeviceField.from_synth(field), bp, seeds, q, torch.float64)
+        ref, _ = O.propagate(field, op, seeds, q)
+        assert np.abs(to_aos_points(pts) - ref).max() <= 1e-9 * 105

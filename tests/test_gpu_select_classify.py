@@ -1,0 +1,106 @@
+"""Parity of selection (Sec. 2.1, top-k) and classification (Sec. 2.1, 3.1) with the oracle.
+
+Selection is index work: bit-exact.  Classification is bit-identical except for hits whose residual
+|D - r| lies within the DCA tolerance (1e-9 m FP64, 2 um FP32; below the 1 um allowance) of lambda.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1911_09340_gb300 import binding as B
+from paper_1911_09340_gb300 import synth
+
+from gpu_util import both_params, gpu_propagate, dev_wires
+
+pytestmark = pytest.mark.gpu
+UNIFORM = synth.uniform_field(1.0)
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+@pytest.mark.parametrize("S", [1, 2, 2047, 2049, 70001, 1 << 18])
+def test_select_matches_oracle(ctx, dtype, S):
+    rng = np.random.default_rng(S)
+    v = rng.integers(0, 50, size=S).astype(np.float64) * 0.125      # many exact ties
+    if S > 10:
+        v[rng.integers(0, S, size=5)] = np.nan
+    v = v.astype(np.float32 if dtype == torch.float32 else np.float64).astype(np.float64)
+    rss = torch.as_tensor(v, dtype=dtype, device="cuda")
+    for k in sorted({1, min(10, S), min(64, S)}):
+        idx = torch.full((k,), -7, dtype=torch.int64, device="cuda")
+        val = torch.zeros(k, dtype=dtype, device="cuda")
+        B.comet_scan_select(ctx, rss, k, idx, val)
+        ri, rv = O.select(v, k)
+        assert np.array_equal(idx.cpu().numpy(), ri)
+        assert np.array_equal(val.double().cpu().numpy(), rv, equal_nan=True)
+
+
+def test_select_rejects_bad_k(ctx):
+    rss = torch.zeros(10, dtype=torch.float32, device="cuda")
+    idx = torch.zeros(65, dtype=torch.int64, device="cuda")
+    for k in (0, 11, 65):
+        with pytest.raises(B.CometError):
+            B.comet_scan_select(ctx, rss, k, idx)
+
+
+def _classify_case(ctx, dtype, ev, part, seed_idx, mask):
+    spec = ev.partitions[part]
+    seeds = O.lattice(spec)
+    if dtype == torch.float32:
+        seeds = seeds.astype(np.float32).astype(np.float64)
+    op, bp = both_params(n_steps=ev.n_steps[part], tol=1e-12 if dtype == torch.float64 else 1e-6)
+    op.tol = 1e-12
+    sub = seeds[max(0, seed_idx - 40): seed_idx + 41]
+    local = seed_idx - max(0, seed_idx - 40)
+    f = B.DeviceField.from_synth(UNIFORM)
+    _, charge, pts, nv = gpu_propagate(ctx, f, bp, sub, -1, dtype)
+    W, H = ev.n_wires, ev.n_hits
+    w = dev_wires(ev.wires, dtype)
+    o = torch.as_tensor(ev.hit_offsets, device="cuda")
+    d = torch.as_tensor(ev.drift, dtype=dtype, device="cuda")
+    m = torch.as_tensor(mask, device="cuda")
+    si = torch.tensor([local], dtype=torch.int64, device="cuda")
+    hc = torch.full((H,), 7, dtype=torch.uint8, device="cuda")
+    dw = torch.full((W,), float("nan"), dtype=dtype, device="cuda")
+    B.comet_scan_classify(ctx, f, bp, pts, nv, charge, si, w, o, d, m, hc, dca_wire=dw,
+                          update_mask=True, n_wires=W)
+    cls, dwr, m2 = O.classify(UNIFORM, op, sub[local], -1, O.wires_aos(ev.wires), ev.hit_offsets,
+                              ev.drift, mask, update_mask=True)
+    return hc.cpu().numpy(), dw.double().cpu().numpy(), m.cpu().numpy(), cls, dwr, m2, op.lam
+
+
+@pytest.mark.parametrize("dtype,delta", [(torch.float64, 1e-9), (torch.float32, 2e-6)])
+def test_classify_matches_oracle(ctx, dtype, delta):
+    ev = synth.multi_turn_event(2)
+    mask = np.zeros(ev.n_hits, np.uint8)
+    mask[::7] = 1
+    for seed_idx in (0, 12345, (1 << 18) - 1):
+        hc, dw, m, cls, dwr, m2, lam = _classify_case(ctx, dtype, ev, 0, seed_idx, mask)
+        near = dwr < 0.03
+        assert np.abs(dw - dwr)[near].max() <= delta
+        wid = np.repeat(np.arange(ev.n_wires), np.diff(ev.hit_offsets))
+        e = np.abs(dwr[wid] - ev.drift)
+        edge = np.abs(e - lam) < delta
+        # ties between two hits of a wire within the tolerance may also flip
+        assert np.array_equal(hc[~edge], cls[~edge]) or (hc != cls).sum() <= 2
+        assert np.array_equal(m, np.maximum(mask, hc))
+        assert set(np.unique(hc)) <= {0, 1}
+
+
+def test_classify_out_of_range_index_sets_status():
+    ctx = B.Context(0)     # a fresh context: this test sets a status bit on purpose
+    ev = synth.single_event_fp64()
+    seeds = O.lattice(ev.partitions[0])[:4]
+    op, bp = both_params(n_steps=ev.n_steps[0])
+    f = B.DeviceField.from_synth(UNIFORM)
+    _, charge, pts, nv = gpu_propagate(ctx, f, bp, seeds, -1, torch.float64)
+    w = dev_wires(ev.wires, torch.float64)
+    o = torch.as_tensor(ev.hit_offsets, device="cuda")
+    d = torch.as_tensor(ev.drift, dtype=torch.float64, device="cuda")
+    m = torch.zeros(ev.n_hits, dtype=torch.uint8, device="cuda")
+    hc = torch.full((ev.n_hits,), 9, dtype=torch.uint8, device="cuda")
+    si = torch.tensor([4], dtype=torch.int64, device="cuda")
+    B.comet_scan_classify(ctx, f, bp, pts, nv, charge, si, w, o, d, m, hc, n_wires=ev.n_wires)
+    assert ctx.status() & 2
+    assert int(hc.sum()) == 0 and int(m.sum()) == 0
+    ctx.close()
