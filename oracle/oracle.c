@@ -171,7 +171,11 @@ static double line_dist2(const double x[3], const double w[6])
     return e[0] * e[0] + e[1] * e[1] + e[2] * e[2];
 }
 
-/* Returns the DCA; *converged is 0 when the refinement hit max_iter or the plane was undefined. */
+/* Returns the DCA; *converged is 0 when the refinement hit max_iter, met a track parallel to the
+   wire, or was held at the edge of its search interval.  The refinement is local (Sec. 2.2: the
+   closest recorded state "serves as a new seed to find the DCA within a few extrapolation steps"):
+   the state moves at most one recording interval h_rec along the track from the closest recorded
+   state, which brackets the distance minimum of that state's valley. */
 static double dca_one(const or_field *f, const or_params *P, const double *pts, int n_valid,
                       int q, double P0, const double w[6], int *converged)
 {
@@ -187,6 +191,8 @@ static double dca_one(const or_field *f, const or_params *P, const double *pts, 
     }
     double y[6];
     memcpy(y, pts + 6 * (size_t)kbest, sizeof y);
+    const double h_rec = P->h * P->stride;
+    double sigma = 0.0;   /* arc length moved so far */
     *converged = 0;
     for (int it = 0;; ++it) {
         /* virtual plane: contains the wire axis, normal along the part of the track direction
@@ -203,8 +209,14 @@ static double dca_one(const or_field *f, const or_params *P, const double *pts, 
             break;
         }
         if (it == P->max_iter) break;
-        rk4_step(f, (double)q, P0, y, -dist / nn);  /* moving ds along the track moves the state
-                                                        nn*ds towards the plane */
+        /* moving ds along the track moves the state nn*ds towards the plane */
+        double target = sigma - dist / nn;
+        if (target > h_rec) target = h_rec;
+        if (target < -h_rec) target = -h_rec;
+        double ds = target - sigma;
+        if (ds == 0.0) break;                     /* held at the edge of the interval */
+        rk4_step(f, (double)q, P0, y, ds);
+        sigma = target;
     }
     return sqrt(line_dist2(y, w));
 }

@@ -290,6 +290,7 @@ comet_status comet_scan_dca(comet_ctx *ctx, comet_dtype dtype, const comet_field
     const double margin = dtype == COMET_F32 ? 4e-6 : 1e-9;
     a.R1 = (a.G / 2) * h_rec * (1.0 + 1e-4) + margin;
     a.half_rec = 0.5 * h_rec * (1.0 + 1e-4) + margin;
+    a.h_rec = h_rec;
     a.exact_all = dca_out != nullptr;
     cudaError_t e = comet::launch_dca(dtype, *field, a, (cudaStream_t)stream);
     return e == cudaSuccess ? COMET_OK : cuda_fail(e, "dca launch");
@@ -372,6 +373,7 @@ comet_status comet_scan_classify(comet_ctx *ctx, comet_dtype dtype, const comet_
     a.status = ctx->status;
     a.lambda = params->lambda;
     a.tol = params->tol;
+    a.h_rec = params->h * params->stride;
     a.max_iter = params->max_iter;
     a.update_mask = update_mask;
     cudaError_t e = comet::launch_classify(dtype, *field, a, (cudaStream_t)stream);

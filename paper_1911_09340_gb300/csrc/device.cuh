@@ -206,13 +206,17 @@ __device__ __forceinline__ void lex_min(T &bd, int &bk, T d, int k)
 // Virtual-plane refinement of Algorithm 2 from state y: the plane contains the wire axis and has
 // normal n = t - (t.u) u (t the unit direction); d is the state's signed distance to it.  While
 // |d| >= tol, step along the track by -d/|n| with one RK4 step (moving ds along the track moves the
-// state |n| ds towards the plane).  Returns 1 if |d| < tol was reached within max_iter steps, 0 if
-// not or if the track runs parallel to the wire.  D = distance of the final state to the wire line.
+// state |n| ds towards the plane).  The search is local: the state moves at most h_rec (one
+// recording interval) along the track from where it started, which brackets the distance minimum
+// of the starting state's valley; a step is shortened to stay inside.  Returns 1 if |d| < tol was
+// reached within max_iter steps, 0 if not, if the track runs parallel to the wire, or if the state
+// is held at the edge of the interval.  D = distance of the final state to the wire line.
 template <typename T, class F>
 __device__ __forceinline__ int refine_dca(const F &f, T c, T ip, T y[6], T ax, T ay, T az, T ux,
-                                          T uy, T uz, T tol, int max_iter, T &D)
+                                          T uy, T uz, T tol, int max_iter, T h_rec, T &D)
 {
     int conv = 0;
+    T sigma = T(0);
     for (int it = 0;; ++it) {
         const T rp = rsqrt_t<T>(y[3] * y[3] + y[4] * y[4] + y[5] * y[5]);
         const T tx = y[3] * rp, ty = y[4] * rp, tz = y[5] * rp;
@@ -227,7 +231,13 @@ __device__ __forceinline__ int refine_dca(const F &f, T c, T ip, T y[6], T ax, T
             break;
         }
         if (it >= max_iter) break;
-        rk4_step<T, F>(f, c, ip, y, -dist * rn);
+        T target = sigma - dist * rn;
+        target = target > h_rec ? h_rec : target;
+        target = target < -h_rec ? -h_rec : target;
+        const T ds = target - sigma;
+        if (ds == T(0)) break;
+        rk4_step<T, F>(f, c, ip, y, ds);
+        sigma = target;
     }
     D = sqrt(line_dist2<T>(y[0], y[1], y[2], ax, ay, az, ux, uy, uz));
     return conv;

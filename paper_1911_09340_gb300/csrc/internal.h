@@ -46,6 +46,7 @@ struct DcaArgs {
     double lambda, tol;
     double R1;             // level-1 segment radius (m), margins included
     double half_rec;       // half a recording interval (m), margins included
+    double h_rec;          // recording interval stride*h (m): reach of the local refinement
     int max_iter;
     int G;                 // recorded states per level-1 segment
     int exact_all;         // refine every wire (dca_out requested)
@@ -76,7 +77,7 @@ struct ClsArgs {
     uint8_t *hit_class;
     void *dca_wire;
     int32_t *status;       // bit 1: seed_index out of range
-    double lambda, tol;
+    double lambda, tol, h_rec;
     int max_iter;
     int update_mask;
 };

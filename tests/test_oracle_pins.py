@@ -162,13 +162,19 @@ def test_dca_zero_field_is_line_line_distance():
     seed = np.array([0.0, 0.0, -0.3, 60.0, 20.0, 15.0])
     t = seed[3:] / np.linalg.norm(seed[3:])
     wires = []
-    for _ in range(40):
+    while len(wires) < 40:
         a = rng.uniform(-0.3, 0.6, 3)
         a[2] = 0.0
         u = rng.normal(size=3)
         u[2] = abs(u[2]) + 2.0
         u /= np.linalg.norm(u)
-        wires.append(np.concatenate([a, u]))
+        # keep wires whose closest approach lies inside the recorded track (the method searches
+        # near the closest recorded state)
+        g = a - seed[:3]
+        tu = t @ u
+        ts = (g @ t - (g @ u) * tu) / (1.0 - tu * tu)
+        if 0.05 < ts < 1.15:
+            wires.append(np.concatenate([a, u]))
     wires = np.array(wires)
     r = _scan_dca(synth.uniform_field(0.0), seed, -1, wires, O.Params(n_steps=1200, **OPEN))
     for i, w in enumerate(wires):
@@ -404,3 +410,29 @@ def test_classify_ties_take_the_lowest_hit_index():
     cls, _, _ = O.classify(synth.uniform_field(0.0), P, seed, -1, wires, offs, drift,
                            np.zeros(3, np.uint8))
     assert np.array_equal(cls, np.array([0, 1, 0], np.uint8))
+
+
+@pytest.mark.parametrize("stride", [1, 4])
+def test_refined_dca_stays_in_its_valley(chamber, stride):
+    # the continuous distance minimum near the closest recorded state lies within half a recording
+    # interval (in arc length) of a recorded state, so the refined DCA can be at most h_rec/2 below
+    # the closest recorded distance; the refined state stays within one interval of that state, so
+    # at most h_rec above it; and near wires (where the refinement converges) end below it
+    ev = synth.multi_turn_event(0, chamber)
+    seeds = O.lattice(ev.partitions[0])[::4099]
+    P = O.Params(n_steps=ev.n_steps[0], stride=stride)
+    wires = O.wires_aos(ev.wires)
+    r = O.scan(synth.uniform_field(1.0), P, seeds, -1, wires, ev.hit_offsets, ev.drift,
+               np.zeros(ev.n_hits, np.uint8), want_dca=True)
+    pts, nv = O.propagate(synth.uniform_field(1.0), P, seeds, -1)
+    h_rec = 1e-3 * stride
+    for s in range(seeds.shape[0]):
+        x = pts[s, :nv[s], :3]
+        for i, w in enumerate(wires):
+            d = x - w[:3]
+            t = d @ w[3:]
+            dmin = np.linalg.norm(d - t[:, None] * w[3:], axis=1).min()
+            D = r["dca"][s, i]
+            assert dmin - 0.5 * h_rec - 1e-12 <= D <= dmin + h_rec + 1e-12
+            if dmin < 0.05:
+                assert D <= dmin + 1e-12
