@@ -183,6 +183,25 @@ comet_status comet_scan_dca(comet_ctx *ctx, comet_dtype dtype, const comet_field
 comet_status comet_scan_select(comet_ctx *ctx, comet_dtype dtype, const void *rss, int64_t S,
                                int32_t k, int64_t *idx_out, void *rss_out, comet_stream stream);
 
+/* ---- selection without device allocation (the paper has no counterpart) -------------------------
+ * Same result as comet_scan_select, for callers that cannot allocate device memory: for example a
+ * process whose device memory is owned by a caching allocator or held to a fixed budget, where an
+ * extra cudaMalloc can fail or fragment the pool, or a caller that cannot create a comet_ctx (whose
+ * creation allocates).  It takes no context, allocates nothing and calls no cudaMalloc or cudaFree.
+ *   Runs on the CURRENT device (cudaGetDevice); stream must belong to it.  Arguments as for
+ *   comet_scan_select.
+ *   Scratch: a 1 MiB file-scope device array, present on every device that loads the library until
+ *   the process exits.  A call needs ceil(S / 2048) * k * (sizeof(T) + 8) + 64 bytes of it and is
+ *   rejected with COMET_ERR_INVALID_ARG beyond 1 MiB (k = 1: S up to about 134 million FP64 or
+ *   178 million FP32 seeds; k = 64: about 2.09 million FP64 or 2.79 million FP32).
+ *   The first call on a device looks the array's device address up (cudaGetSymbolAddress, with that
+ *   device current); make that first call before any stream capture.
+ *   Every call shares the array and it keeps the last call's contents; nothing in it needs to start
+ *   at zero (each call writes every entry it reads).  Calls that overlap on the GPU (other streams,
+ *   other host threads) race on the array: serialise them. */
+comet_status comet_scan_select_noalloc(comet_dtype dtype, const void *rss, int64_t S, int32_t k,
+                                       int64_t *idx_out, void *rss_out, comet_stream stream);
+
 /* ---- a8/a9: classification (Sec. 2.1) and the mask of the next turn partition (Sec. 3.1) -------
  *   points, n_valid, charge, S, wires, W, ldw, hit_offsets, drift  as for comet_scan_dca.
  *   seed_index  device [1] int64: the seed to classify (for example idx_out of comet_scan_select);

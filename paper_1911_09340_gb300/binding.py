@@ -62,6 +62,7 @@ SIGNATURES = {
     "comet_scan_dca": [_vp, C.c_int, C.POINTER(_Field), C.POINTER(_Params), _vp, _vp, _vp, _i64,
                        _vp, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "comet_scan_select": [_vp, C.c_int, _vp, _i64, _i32, _vp, _vp, _vp],
+    "comet_scan_select_noalloc": [C.c_int, _vp, _i64, _i32, _vp, _vp, _vp],
     "comet_scan_classify": [_vp, C.c_int, C.POINTER(_Field), C.POINTER(_Params), _vp, _vp, _vp,
                             _i64, _vp, _vp, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _i32, _vp],
 }
@@ -235,6 +236,14 @@ def comet_scan_select(ctx: Context, rss, k: int, idx_out, rss_out=None, stream=N
     _check(lib().comet_scan_select(ctx.handle, _dtype_code(rss), _ptr(rss), rss.shape[0], int(k),
                                    _ptr(idx_out, torch.int64), _ptr(rss_out, rss.dtype),
                                    _stream(stream)))
+
+
+def comet_scan_select_noalloc(rss, k: int, idx_out, rss_out=None, stream=None):
+    """comet_scan_select without a context and without device allocation (static scratch on the
+    current device; see include/comet_scan.h for its size limit and sharing rules)."""
+    _check(lib().comet_scan_select_noalloc(_dtype_code(rss), _ptr(rss), rss.shape[0], int(k),
+                                           _ptr(idx_out, torch.int64), _ptr(rss_out, rss.dtype),
+                                           _stream(stream)))
 
 
 def comet_scan_classify(ctx: Context, field: DeviceField, params: ScanParams, points, n_valid,

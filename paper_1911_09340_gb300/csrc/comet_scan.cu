@@ -333,6 +333,32 @@ comet_status comet_scan_select(comet_ctx *ctx, comet_dtype dtype, const void *rs
     return e == cudaSuccess ? COMET_OK : cuda_fail(e, "select launch");
 }
 
+comet_status comet_scan_select_noalloc(comet_dtype dtype, const void *rss, int64_t S, int32_t k,
+                                       int64_t *idx_out, void *rss_out, comet_stream stream)
+{
+    CHECK(check_dtype(dtype));
+    if (S < 1) return fail(COMET_ERR_INVALID_ARG, "S must be >= 1");
+    if (k < 1 || k > 64 || k > S) return fail(COMET_ERR_INVALID_ARG, "k must be in [1, min(64, S)]");
+    if (!rss || !idx_out) return fail(COMET_ERR_INVALID_ARG, "rss and idx_out are required");
+    if (!aligned(rss, esize(dtype)) || !aligned(idx_out, 8) || (rss_out && !aligned(rss_out, esize(dtype))))
+        return fail(COMET_ERR_INVALID_ARG, "an array is misaligned for its element type");
+    comet::SelArgs a;
+    a.rss = rss;
+    a.S = S;
+    a.k = k;
+    a.idx_out = idx_out;
+    a.rss_out = rss_out;
+    const size_t need = comet::select_scratch_bytes(dtype, S, k, &a.n_blocks);
+    if (need > comet::kStaticSelectScratchBytes)
+        return fail(COMET_ERR_INVALID_ARG,
+                    "S = %lld with k = %d needs %zu bytes of scratch; the static scratch holds %zu",
+                    (long long)S, k, need, comet::kStaticSelectScratchBytes);
+    cudaError_t e = comet::static_select_scratch(&a.scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(select scratch)");
+    e = comet::launch_select(dtype, a, (cudaStream_t)stream);
+    return e == cudaSuccess ? COMET_OK : cuda_fail(e, "select launch");
+}
+
 comet_status comet_scan_classify(comet_ctx *ctx, comet_dtype dtype, const comet_field *field,
                                  const comet_scan_params *params, const void *points,
                                  const int32_t *n_valid, const int8_t *charge, int64_t S,

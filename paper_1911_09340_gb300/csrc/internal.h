@@ -88,6 +88,10 @@ cudaError_t launch_dca(comet_dtype dt, const comet_field &f, const DcaArgs &a, c
 int dca_n1max(comet_dtype dt);   // maximum number of level-1 segments per seed
 cudaError_t launch_select(comet_dtype dt, const SelArgs &a, cudaStream_t st);
 size_t select_scratch_bytes(comet_dtype dt, int64_t S, int k, int *n_blocks);
+// Allocation-free selection: size of the file-scope scratch array and its device address on the
+// current device (looked up on the first call per device).
+constexpr size_t kStaticSelectScratchBytes = (size_t)1 << 20;
+cudaError_t static_select_scratch(void **ptr);
 cudaError_t launch_classify(comet_dtype dt, const comet_field &f, const ClsArgs &a, cudaStream_t st);
 
 // Field kinds the kernels are specialised for.

@@ -11,6 +11,8 @@
 #include <float.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "device.cuh"
 #include "internal.h"
 
@@ -133,6 +135,32 @@ static void sel_launch(const SelArgs &a, cudaStream_t st)
     select_pass1<T><<<nb, kSelThreads, 0, st>>>((const T *)a.rss, a.S, a.k, pv, pi);
     select_pass2<T><<<1, kSelThreads, 0, st>>>(pv, pi, (int64_t)nb * a.k, a.k, a.idx_out,
                                               (T *)a.rss_out);
+}
+
+// Scratch of comet_scan_select_noalloc: one file-scope device array per device that loads the
+// library, held until the process exits.  In host code `g_select_scratch` is only a host-side
+// stand-in for the symbol, never a device address: the device address is looked up once per device
+// with cudaGetSymbolAddress, with that device current, and cached here.
+static __device__ __align__(256) unsigned char g_select_scratch[kStaticSelectScratchBytes];
+
+cudaError_t static_select_scratch(void **ptr)
+{
+    constexpr int kMaxDevices = 64;
+    static std::mutex mu;
+    static void *addr[kMaxDevices] = {};
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_select_scratch);
+        if (e != cudaSuccess) return e;
+        addr[dev] = p;
+    }
+    *ptr = addr[dev];
+    return cudaSuccess;
 }
 
 cudaError_t launch_select(comet_dtype dt, const SelArgs &a, cudaStream_t st)
