@@ -127,10 +127,10 @@ def sum_over_ranks(x: float, world: int) -> float:
     return float(t.item())
 
 
-def make_events(indices):
+def make_events(indices, counts=(16, 16, 32, 32)):
     from paper_1911_09340_gb300 import synth
     ch = synth.make_chamber()
-    return [synth.multi_turn_event(i, ch) for i in indices]
+    return [synth.multi_turn_event(i, ch, counts=tuple(counts)) for i in indices]
 
 
 def evals_of(ev, classes):
@@ -214,7 +214,7 @@ def run_ours(args, rank, world):
     dtype = torch.float32
     n_ev = args.warmup + args.steps
     idx = [rank + world * i for i in range(n_ev)]
-    events = make_events(idx)
+    events = make_events(idx, args.lattice)
     max_rec = max(n // args.stride + 1 for ev in events for n in ev.n_steps)
     max_h = max(ev.n_hits for ev in events)
     max_w = max(ev.n_wires for ev in events)
@@ -268,6 +268,12 @@ def run_ours(args, rank, world):
     clocks = clk.summary()
 
     # ---- end to end through host buffers (pinned), copies inside the timed region
+    if args.no_e2e:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": "evals/s",
+                              "kernel_ms": {k: round(v[0], 3) for k, v in kt.items()},
+                              "note": "profiling run (--no-e2e)"}), flush=True)
+        return
     runner = scan.HostEventRunner(ctx, field, ws, max_w, max_h, dtype)
     pinned = [runner.pin(ev, dtype) for ev in events]
     for i in range(args.warmup):
@@ -363,7 +369,11 @@ def main():
     ap.add_argument("--stride", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-seconds", type=float, default=8.0)
-    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling)")
+    ap.add_argument("--lattice", type=lambda s: [int(x) for x in s.split(",")],
+                    default=[16, 16, 32, 32], help="seed lattice counts (z0,phi,pz,pt); "
+                    "the workload is 16,16,32,32, smaller lattices are for profiling only")
     args = ap.parse_args()
     rank, world = dist_setup(args.gpus)
     if args.impl == "reference":

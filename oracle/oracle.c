@@ -225,30 +225,49 @@ static double dca_one(const or_field *f, const or_params *P, const double *pts, 
 /* Public entry points (ctypes)                                                                   */
 /* ---------------------------------------------------------------------------------------------- */
 
-/* Seed lattice.  Dimensions slowest to fastest: z0, phi, pz, pt; node i of n at
-   centre + half_width*(2i/(n-1) - 1).  The seed is (vx, vy, z0, pt cos phi, pt sin phi, pz). */
+/* Seed lattice (Sec. 2.1: seeds combined from grids over the prior range of each component).
+   Dimensions: z0, phi, pz, pt; node i of n sits at centre + half_width*(2i/(n-1) - 1).  The seed is
+   (vx, vy, z0, pt cos phi, pt sin phi, pz).  Enumeration: the lattice is cut into blocks of
+   b = (2, 2, 2, 4) nodes (a dimension whose count the block does not divide gets block 1; pt gets 2
+   when 4 does not divide it but 2 does); blocks are numbered row-major (z0 slowest) and the nodes
+   inside a block row-major, so seed s = block * (b0 b1 b2 b3) + node-in-block. */
+void oracle_block_shape(const int counts[4], int b[4])
+{
+    for (int d = 0; d < 3; ++d) b[d] = counts[d] % 2 == 0 ? 2 : 1;
+    b[3] = counts[3] % 4 == 0 ? 4 : (counts[3] % 2 == 0 ? 2 : 1);
+}
+
 void oracle_lattice(double vx, double vy, const double centre[4], const double half_width[4],
                     const int counts[4], double *seeds /* [S][6] */)
 {
-    int64_t s = 0;
-    double v[4];
-    for (int i0 = 0; i0 < counts[0]; ++i0)
-        for (int i1 = 0; i1 < counts[1]; ++i1)
-            for (int i2 = 0; i2 < counts[2]; ++i2)
-                for (int i3 = 0; i3 < counts[3]; ++i3, ++s) {
-                    int ii[4] = {i0, i1, i2, i3};
-                    for (int d = 0; d < 4; ++d)
-                        v[d] = counts[d] == 1 ? centre[d]
-                                              : centre[d] + half_width[d] *
-                                                    (2.0 * ii[d] / (double)(counts[d] - 1) - 1.0);
-                    double *o = seeds + 6 * s;
-                    o[0] = vx;
-                    o[1] = vy;
-                    o[2] = v[0];
-                    o[3] = v[3] * cos(v[1]);
-                    o[4] = v[3] * sin(v[1]);
-                    o[5] = v[2];
-                }
+    int b[4], nb[4];
+    oracle_block_shape(counts, b);
+    for (int d = 0; d < 4; ++d) nb[d] = counts[d] / b[d];
+    int64_t vol = (int64_t)b[0] * b[1] * b[2] * b[3];
+    int64_t S = (int64_t)counts[0] * counts[1] * counts[2] * counts[3];
+    for (int64_t s = 0; s < S; ++s) {
+        int64_t blk = s / vol, in = s % vol;
+        int ii[4], bi[4];
+        for (int d = 3; d >= 0; --d) {
+            ii[d] = (int)(in % b[d]);
+            in /= b[d];
+            bi[d] = (int)(blk % nb[d]);
+            blk /= nb[d];
+        }
+        double v[4];
+        for (int d = 0; d < 4; ++d) {
+            int node = bi[d] * b[d] + ii[d];
+            v[d] = counts[d] == 1 ? centre[d]
+                                  : centre[d] + half_width[d] * (2.0 * node / (double)(counts[d] - 1) - 1.0);
+        }
+        double *o = seeds + 6 * s;
+        o[0] = vx;
+        o[1] = vy;
+        o[2] = v[0];
+        o[3] = v[3] * cos(v[1]);
+        o[4] = v[3] * sin(v[1]);
+        o[5] = v[2];
+    }
 }
 
 typedef struct {

@@ -281,14 +281,13 @@ comet_status comet_scan_dca(comet_ctx *ctx, comet_dtype dtype, const comet_field
     a.lambda = params->lambda;
     a.tol = params->tol;
     a.max_iter = params->max_iter;
-    const int n1max = comet::dca_n1max(dtype);
-    a.G = (a.n_rec + n1max - 1) / n1max;
-    if (a.G < 1) a.G = 1;
+    comet::dca_segments(a.n_rec, &a.G0, &a.G1);
     // consecutive recorded states are at most stride*h apart along the track (|dx/ds| = |p|/P0 = 1
     // up to rounding); the margins cover the rounding of the distances in the working precision
     const double h_rec = params->h * params->stride;
     const double margin = dtype == COMET_F32 ? 4e-6 : 1e-9;
-    a.R1 = (a.G / 2) * h_rec * (1.0 + 1e-4) + margin;
+    a.R0 = (a.G0 / 2) * h_rec * (1.0 + 1e-4) + margin;
+    a.R1 = (a.G1 / 2) * h_rec * (1.0 + 1e-4) + margin;
     a.half_rec = 0.5 * h_rec * (1.0 + 1e-4) + margin;
     a.h_rec = h_rec;
     a.exact_all = dca_out != nullptr;

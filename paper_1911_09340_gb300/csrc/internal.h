@@ -44,11 +44,13 @@ struct DcaArgs {
     int32_t *n_unconv;
     int32_t *status;       // device status word of the context (bit 0: a bulk-copy wait timed out)
     double lambda, tol;
+    double R0;             // super-segment radius (m), margins included
     double R1;             // level-1 segment radius (m), margins included
     double half_rec;       // half a recording interval (m), margins included
     double h_rec;          // recording interval stride*h (m): reach of the local refinement
     int max_iter;
-    int G;                 // recorded states per level-1 segment
+    int G0;                // recorded states per super-segment
+    int G1;                // recorded states per level-1 segment
     int exact_all;         // refine every wire (dca_out requested)
 };
 
@@ -85,7 +87,7 @@ struct ClsArgs {
 cudaError_t launch_lattice(comet_dtype dt, const LatArgs &a, void *seeds, int64_t S, cudaStream_t st);
 cudaError_t launch_propagate(comet_dtype dt, const comet_field &f, const PropArgs &a, cudaStream_t st);
 cudaError_t launch_dca(comet_dtype dt, const comet_field &f, const DcaArgs &a, cudaStream_t st);
-int dca_n1max(comet_dtype dt);   // maximum number of level-1 segments per seed
+void dca_segments(int n_rec, int *G0, int *G1);   // segment sizes of the closest-state search
 cudaError_t launch_select(comet_dtype dt, const SelArgs &a, cudaStream_t st);
 size_t select_scratch_bytes(comet_dtype dt, int64_t S, int k, int *n_blocks);
 // Allocation-free selection: size of the file-scope scratch array and its device address on the

@@ -6,20 +6,22 @@
 // shared memory with the bulk-copy engine (cp.async.bulk + mbarrier), in tiles of 256 wires.
 //
 // Closest recorded state of a (seed, wire) pair, found exactly without visiting every state: the
-// recorded states of a seed are cut into segments of G consecutive states, at most N1MAX segments.
-// A state within G/2 recording intervals of a segment's centre is within R1 = (G/2) h_rec of it in
-// space (consecutive recorded states are at most h_rec apart along the track), so
-//     dist(any state of segment j) >= dist(centre j) - R1.
-// The centres live in shared memory.  Segments whose bound exceeds the best centre distance cannot
-// hold the closest state; they are skipped.  The remaining segments (the union over the warp, so the
-// loads stay coalesced: all lanes read the same state index of 32 consecutive seeds) are scanned in
-// full, keeping the lexicographic minimum (distance, index).  Scanning a superset of the segments that
-// can hold the minimum returns the same minimum.
+// recorded states of a seed are cut into at most N0MAX super-segments of G0 states, each cut into
+// level-1 segments of G1 states.  A state within g/2 recording intervals of a segment's centre is
+// within R = (g/2) h_rec of it in space (consecutive recorded states are at most h_rec apart along
+// the track), so dist(any state of the segment) >= dist(centre) - R.  The super-segment centres of
+// each seed live in shared memory; the level-1 centres and the states are read from the track array.
+// At each level a segment is visited only if its bound does not exceed the best distance found so
+// far; visiting a superset of the segments that can hold the minimum returns the same lexicographic
+// (distance, index) minimum.  Candidate sets are united over the warp so that every load is
+// warp-uniform in the state index (32 consecutive seeds: one 128-byte line); the seed lattice numbers
+// neighbouring nodes consecutively, so the 32 tracks of a warp are close and the union stays small.
 //
 // Without dca_out, a wire whose closest recorded state is farther than (largest unmasked drift +
 // lambda + h_rec/2) is not refined: the true DCA is then at least (largest drift + lambda), so every
 // residual |D - r| of that wire is at least lambda and the wire adds exactly lambda^2 to the RSS.
-// The same bound also drops segments beyond that distance from the candidate set.
+// The same bound drops segments at every level (a segment is skipped only if it cannot hold a state
+// within that distance, or if it cannot hold the minimum).
 //
 // RSS: each lane sums its wires' d_i^2 in ascending wire order (FP32 as a TwoSum pair, FP64 plainly);
 // lanes sharing a seed are combined in a fixed shuffle tree.  No atomics: the result does not depend
@@ -40,16 +42,9 @@ constexpr int kHitMax = 1024;                // hits staged in shared memory whe
 constexpr int kHitCap = kHitMax + 32;
 constexpr uint64_t kWaitNs = 2000000000ull;  // bulk-copy wait limit (2 s)
 
-template <typename T>
-struct Cfg;
-template <>
-struct Cfg<float> {
-    static constexpr int N1MAX = 32;
-};
-template <>
-struct Cfg<double> {
-    static constexpr int N1MAX = 16;
-};
+// super-segment centres per seed kept in shared memory; level-1 segments per super-segment
+constexpr int kN0Max = 16;
+constexpr int kN1Max = 32;
 
 constexpr size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
@@ -57,8 +52,8 @@ template <typename T, int LPS>
 struct Smem {
     static constexpr int SPB = kThreads / LPS;
     static constexpr size_t bar = 0;
-    static constexpr size_t c1 = 16;
-    static constexpr size_t wrow = align16(c1 + sizeof(T) * Cfg<T>::N1MAX * 3 * SPB);
+    static constexpr size_t c0 = 16;
+    static constexpr size_t wrow = align16(c0 + sizeof(T) * kN0Max * 3 * SPB);
     static constexpr size_t orow = align16(wrow + sizeof(T) * 6 * kWireCap);
     static constexpr size_t cap = align16(orow + sizeof(int32_t) * (kWireCap + 8));
     static constexpr size_t drift = align16(cap + sizeof(T) * kWireTile);
@@ -123,10 +118,9 @@ __global__ void __launch_bounds__(kThreads) dca_kernel(F f, DcaArgs a)
 {
     using L = Smem<T, LPS>;
     constexpr int SPB = L::SPB;
-    constexpr int N1MAX = Cfg<T>::N1MAX;
     extern __shared__ __align__(128) unsigned char sm[];
     uint64_t *bar = (uint64_t *)(sm + L::bar);
-    T *c1 = (T *)(sm + L::c1);
+    T *c0 = (T *)(sm + L::c0);
     T *wrow = (T *)(sm + L::wrow);
     int32_t *orow = (int32_t *)(sm + L::orow);
     T *capv = (T *)(sm + L::cap);
@@ -145,10 +139,12 @@ __global__ void __launch_bounds__(kThreads) dca_kernel(F f, DcaArgs a)
     const T *__restrict__ Dg = (const T *)a.drift;
     const T lam = (T)a.lambda;
     const T tol = (T)a.tol;
+    const T R0 = (T)a.R0;
     const T R1 = (T)a.R1;
     const T half_rec = (T)a.half_rec;
     const T h_rec = (T)a.h_rec;
-    const int G = a.G;
+    const int G0 = a.G0, G1 = a.G1;
+    const int N1 = (G0 + G1 - 1) / G1;
 
     if (tid == 0) mbar_init(bar, 1);
 
@@ -163,19 +159,19 @@ __global__ void __launch_bounds__(kThreads) dca_kernel(F f, DcaArgs a)
         c = (T)(kKappa * q / pd);
         ip = (T)(1.0 / pd);
     }
-    const int n1 = (nv + G - 1) / G;
-    for (int j = sub; j < N1MAX; j += LPS) {
+    const int n0 = (nv + G0 - 1) / G0;
+    for (int j = sub; j < kN0Max; j += LPS) {
         T x = T(0), y = T(0), z = T(0);
-        if (valid && j < n1) {
-            const int k = min(j * G + G / 2, nv - 1);
+        if (valid && j < n0) {
+            const int k = min(j * G0 + G0 / 2, nv - 1);
             const int64_t o = (int64_t)k * S + s;
             x = P[o];
             y = P[plane + o];
             z = P[2 * plane + o];
         }
-        c1[(j * 3 + 0) * SPB + ls] = x;
-        c1[(j * 3 + 1) * SPB + ls] = y;
-        c1[(j * 3 + 2) * SPB + ls] = z;
+        c0[(j * 3 + 0) * SPB + ls] = x;
+        c0[(j * 3 + 1) * SPB + ls] = y;
+        c0[(j * 3 + 2) * SPB + ls] = z;
     }
 
     const int W = a.W;
@@ -275,50 +271,102 @@ __global__ void __launch_bounds__(kThreads) dca_kernel(F f, DcaArgs a)
             }
             const bool want = valid && inw && (cap >= T(0) || a.exact_all);
 
-            // level 1: segment centres from shared memory
+            // level 0: super-segment centres from shared memory
             T bd = T(INFINITY);
             int bk = 0x7fffffff;
-            T d2a[N1MAX];
+            T d0[kN0Max];
 #pragma unroll
-            for (int j = 0; j < N1MAX; ++j) {
+            for (int j = 0; j < kN0Max; ++j) {
                 T d2 = T(INFINITY);
-                if (want && j < n1) {
-                    d2 = line_dist2<T>(c1[(j * 3 + 0) * SPB + ls], c1[(j * 3 + 1) * SPB + ls],
-                                       c1[(j * 3 + 2) * SPB + ls], ax, ay, az, ux, uy, uz);
-                    lex_min<T>(bd, bk, d2, min(j * G + G / 2, nv - 1));
+                if (want && j < n0) {
+                    d2 = line_dist2<T>(c0[(j * 3 + 0) * SPB + ls], c0[(j * 3 + 1) * SPB + ls],
+                                       c0[(j * 3 + 2) * SPB + ls], ax, ay, az, ux, uy, uz);
+                    lex_min<T>(bd, bk, d2, min(j * G0 + G0 / 2, nv - 1));
                 }
-                d2a[j] = d2;
+                d0[j] = d2;
             }
-            uint32_t cand = 0;
+            const T capth = a.exact_all ? T(INFINITY) : cap + half_rec;
+            uint32_t cand0 = 0;
             if (want) {
-                T thr = sqrt(bd);
-                if (!a.exact_all) thr = fmin(thr, cap + half_rec);
-                const T lim = thr + R1;
+                const T lim = fmin(sqrt(bd), capth) + R0;
                 const T lim2 = lim * lim;
 #pragma unroll
-                for (int j = 0; j < N1MAX; ++j)
-                    if (d2a[j] <= lim2) cand |= 1u << j;
+                for (int j = 0; j < kN0Max; ++j)
+                    if (d0[j] <= lim2) cand0 |= 1u << j;
             }
-            uint32_t ucand = __reduce_or_sync(0xffffffffu, cand);
+            uint32_t u0 = __reduce_or_sync(0xffffffffu, cand0);
 
-            // level 2: every state of the candidate segments (warp-uniform order)
-            while (ucand) {
-                const int j = __ffs(ucand) - 1;
-                ucand &= ucand - 1;
-                const int k0 = j * G;
-                for (int t = 0; t < G; ++t) {
-                    const int k = k0 + t;
-                    if (want && k < nv) {
-                        const int64_t o = (int64_t)k * S + s;
-                        const T d2 = line_dist2<T>(P[o], P[plane + o], P[2 * plane + o], ax, ay, az,
-                                                   ux, uy, uz);
-                        lex_min<T>(bd, bk, d2, k);
+            constexpr int kUnroll = 4;
+            while (u0) {
+                const int j = __ffs(u0) - 1;
+                u0 &= u0 - 1;
+                const int sb = j * G0;
+                const int se = min(sb + G0, nv);          // this lane's end of super-segment j
+                // level 1: centres of the level-1 segments of super-segment j
+                uint32_t cand1 = 0;
+                {
+                    const T lim = want ? fmin(sqrt(bd), capth) + R1 : T(0);
+                    const T lim2 = lim * lim;
+                    for (int m0 = 0; m0 < N1; m0 += kUnroll) {
+                        T xs[kUnroll], ys[kUnroll], zs[kUnroll];
+                        int ks[kUnroll];
+#pragma unroll
+                        for (int u = 0; u < kUnroll; ++u) {
+                            const int m = m0 + u;
+                            const int st = sb + m * G1;
+                            xs[u] = ys[u] = zs[u] = T(0);
+                            ks[u] = -1;
+                            if (want && m < N1 && st < se) {
+                                const int k = min(st + G1 / 2, min(st + G1, se) - 1);
+                                const int64_t o = (int64_t)k * S + s;
+                                xs[u] = P[o];
+                                ys[u] = P[plane + o];
+                                zs[u] = P[2 * plane + o];
+                                ks[u] = k;
+                            }
+                        }
+#pragma unroll
+                        for (int u = 0; u < kUnroll; ++u) {
+                            if (ks[u] >= 0) {
+                                const T d2 = line_dist2<T>(xs[u], ys[u], zs[u], ax, ay, az, ux, uy, uz);
+                                lex_min<T>(bd, bk, d2, ks[u]);
+                                if (d2 <= lim2) cand1 |= 1u << (m0 + u);
+                            }
+                        }
+                    }
+                }
+                uint32_t u1 = __reduce_or_sync(0xffffffffu, cand1);
+                // level 2: every state of the candidate level-1 segments
+                while (u1) {
+                    const int m = __ffs(u1) - 1;
+                    u1 &= u1 - 1;
+                    const int k0 = sb + m * G1;
+                    const int kend = min(k0 + G1, se);
+                    for (int t0 = k0; t0 < k0 + G1; t0 += kUnroll) {
+                        T xs[kUnroll], ys[kUnroll], zs[kUnroll];
+#pragma unroll
+                        for (int u = 0; u < kUnroll; ++u) {
+                            const int k = t0 + u;
+                            xs[u] = ys[u] = zs[u] = T(0);
+                            if (want && k < kend) {
+                                const int64_t o = (int64_t)k * S + s;
+                                xs[u] = P[o];
+                                ys[u] = P[plane + o];
+                                zs[u] = P[2 * plane + o];
+                            }
+                        }
+#pragma unroll
+                        for (int u = 0; u < kUnroll; ++u) {
+                            const int k = t0 + u;
+                            if (want && k < kend)
+                                lex_min<T>(bd, bk, line_dist2<T>(xs[u], ys[u], zs[u], ax, ay, az, ux, uy, uz), k);
+                        }
                     }
                 }
             }
 
             // refinement from the closest recorded state (skipped when the wire cannot contribute)
-            const bool refine = want && (a.exact_all || sqrt(bd) <= cap + half_rec);
+            const bool refine = want && (a.exact_all || sqrt(bd) <= capth);
             T D = T(INFINITY);
             if (refine) {
                 T yv[6];
@@ -414,7 +462,19 @@ static cudaError_t dca_dispatch(const comet_field &f, const DcaArgs &a, cudaStre
     }
 }
 
-int dca_n1max(comet_dtype dt) { return dt == COMET_F32 ? Cfg<float>::N1MAX : Cfg<double>::N1MAX; }
+void dca_segments(int n_rec, int *G0, int *G1)
+{
+    // about cbrt(n_rec) super-segments of about sqrt(G0)-state level-1 segments
+    int n0 = (int)lround(cbrt((double)n_rec));
+    n0 = n0 < 2 ? 2 : (n0 > kN0Max ? kN0Max : n0);
+    int g0 = (n_rec + n0 - 1) / n0;
+    if ((n_rec + g0 - 1) / g0 > kN0Max) g0 = (n_rec + kN0Max - 1) / kN0Max;
+    int g1 = (int)lround(sqrt((double)g0));
+    g1 = g1 < 1 ? 1 : g1;
+    if ((g0 + g1 - 1) / g1 > kN1Max) g1 = (g0 + kN1Max - 1) / kN1Max;
+    *G0 = g0;
+    *G1 = g1;
+}
 
 cudaError_t launch_dca(comet_dtype dt, const comet_field &f, const DcaArgs &a, cudaStream_t st)
 {

@@ -11,20 +11,31 @@
 
 namespace comet {
 
+// Seed s of the lattice: blocks of b = (2, 2, 2, 4) nodes (1 where the count is not divisible; 2
+// for pt when only 2 divides it) numbered row-major, nodes inside a block row-major.  Consecutive
+// seeds are therefore neighbours in all four dimensions, so the 32 lanes of a warp follow similar
+// tracks in the DCA kernel.
 template <typename T>
 __global__ void __launch_bounds__(256) lattice_kernel(LatArgs a, T *__restrict__ seeds, int64_t S)
 {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= S) return;
-    int64_t r = s;
+    int b[4];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) b[d] = a.counts[d] % 2 == 0 ? 2 : 1;
+    b[3] = a.counts[3] % 4 == 0 ? 4 : (a.counts[3] % 2 == 0 ? 2 : 1);
+    const int64_t vol = (int64_t)b[0] * b[1] * b[2] * b[3];
+    int64_t blk = s / vol, in = s % vol;
     int ii[4];
-    ii[3] = (int)(r % a.counts[3]);
-    r /= a.counts[3];
-    ii[2] = (int)(r % a.counts[2]);
-    r /= a.counts[2];
-    ii[1] = (int)(r % a.counts[1]);
-    r /= a.counts[1];
-    ii[0] = (int)r;
+#pragma unroll
+    for (int d = 3; d >= 0; --d) {
+        const int nb = a.counts[d] / b[d];
+        const int i_in = (int)(in % b[d]);
+        in /= b[d];
+        const int i_bl = (int)(blk % nb);
+        blk /= nb;
+        ii[d] = i_bl * b[d] + i_in;
+    }
     double v[4];
 #pragma unroll
     for (int d = 0; d < 4; ++d) {

@@ -21,9 +21,10 @@ OPEN = dict(zmin=-50.0, zmax=50.0, rmax=50.0)
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
-def test_lattice_matches_oracle(ctx, dtype):
+@pytest.mark.parametrize("counts", [(3, 5, 7, 9), (4, 6, 2, 8), (2, 2, 3, 6), (16, 16, 32, 32)])
+def test_lattice_matches_oracle(ctx, dtype, counts):
     spec = synth.LatticeSpec(vxy=(0.013, -0.07), centre=(-0.21, 1.3, 11.5, 101.2),
-                             half_width=(0.02, 0.04, 3.0, 6.4), counts=(3, 5, 7, 9), charge=-1)
+                             half_width=(0.02, 0.04, 3.0, 6.4), counts=counts, charge=-1)
     S = spec.n_seeds
     seeds = torch.empty((6, S), dtype=dtype, device="cuda")
     charge = torch.zeros(S, dtype=torch.int8, device="cuda")

@@ -348,20 +348,43 @@ def test_scan_is_deterministic_for_any_thread_count(chamber):
 # Lattice, selection, classification
 # ------------------------------------------------------------------------------------------------
 
-def test_lattice_matches_meshgrid():
+def _blocked_expectation(spec):
+    """Seeds in the blocked enumeration, built independently with meshgrid + reshape/transpose."""
+    n = spec.counts
+    b = [2 if n[d] % 2 == 0 else 1 for d in range(3)]
+    b.append(4 if n[3] % 4 == 0 else (2 if n[3] % 2 == 0 else 1))
+    axes = [np.linspace(c - h, c + h, k) for c, h, k in zip(spec.centre, spec.half_width, n)]
+    grids = np.meshgrid(*axes, indexing="ij")
+    shape = (n[0] // b[0], b[0], n[1] // b[1], b[1], n[2] // b[2], b[2], n[3] // b[3], b[3])
+    Z, PH, PZ, PT = [g.reshape(shape).transpose(0, 2, 4, 6, 1, 3, 5, 7).ravel() for g in grids]
+    return np.stack([np.full_like(Z, spec.vxy[0]), np.full_like(Z, spec.vxy[1]), Z, PT * np.cos(PH),
+                     PT * np.sin(PH), PZ], axis=1)
+
+
+@pytest.mark.parametrize("counts", [(3, 4, 2, 5), (4, 6, 2, 8), (2, 2, 3, 6), (16, 16, 32, 32)])
+def test_lattice_matches_meshgrid(counts):
     spec = synth.LatticeSpec(vxy=(0.01, -0.02), centre=(-0.1, 0.7, 15.0, 100.0),
-                             half_width=(0.02, 0.04, 3.0, 6.4), counts=(3, 4, 2, 5))
+                             half_width=(0.02, 0.04, 3.0, 6.4), counts=counts)
     seeds = O.lattice(spec)
-    axes = [np.linspace(c - h, c + h, n) for c, h, n in zip(spec.centre, spec.half_width, spec.counts)]
-    Z, PH, PZ, PT = np.meshgrid(*axes, indexing="ij")
-    Z, PH, PZ, PT = Z.ravel(), PH.ravel(), PZ.ravel(), PT.ravel()
-    expect = np.stack([np.full_like(Z, 0.01), np.full_like(Z, -0.02), Z, PT * np.cos(PH),
-                       PT * np.sin(PH), PZ], axis=1)
-    assert np.allclose(seeds, expect, rtol=1e-15, atol=1e-15)
+    assert np.allclose(seeds, _blocked_expectation(spec), rtol=1e-15, atol=1e-15)
     one = synth.LatticeSpec(vxy=(0, 0), centre=(0.1, 0.2, 3.0, 90.0), half_width=(1, 1, 1, 1),
                             counts=(1, 1, 1, 1))
     s1 = O.lattice(one)
     assert np.allclose(s1[0], [0, 0, 0.1, 90 * math.cos(0.2), 90 * math.sin(0.2), 3.0], rtol=1e-15)
+
+
+def test_lattice_blocks_are_neighbours():
+    spec = synth.LatticeSpec(vxy=(0, 0), centre=(0.0, 0.0, 10.0, 100.0),
+                             half_width=(0.02, 0.04, 3.0, 6.4), counts=(16, 16, 32, 32))
+    seeds = O.lattice(spec)
+    # every run of 32 consecutive seeds spans 2 nodes of z0, phi, pz and 4 of pt
+    step = np.array([0.04 / 15, 0.08 / 15, 6.0 / 31, 12.8 / 31])
+    for blk in (0, 1, 777, 8191):
+        s = seeds[blk * 32:(blk + 1) * 32]
+        pt = np.hypot(s[:, 3], s[:, 4])
+        ph = np.arctan2(s[:, 4], s[:, 3])
+        span = np.array([np.ptp(s[:, 2]), np.ptp(ph), np.ptp(s[:, 5]), np.ptp(pt)])
+        assert np.allclose(span, step * np.array([1, 1, 1, 3]), rtol=1e-9)
 
 
 def test_select_matches_brute_force():
