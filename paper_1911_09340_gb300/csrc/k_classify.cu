@@ -34,12 +34,21 @@ __global__ void __launch_bounds__(256) classify_kernel(F f, ClsArgs a)
             uz = Wg[5 * (size_t)a.ldw + i];
     const int nv = a.n_valid[s];
 
+    // same frame and distance as comet_scan_dca's search, so both find the same closest state
+    [[maybe_unused]] const WireFrame<T> fr = wire_frame<T>(ax, ay, az, ux, uy, uz);
     T bd = T(INFINITY);
     int bk = 0x7fffffff;
     for (int k = lane; k < nv; k += 32) {
         const int64_t o = (int64_t)k * S + s;
+#if COMET_SEARCH_FRAME
+        lex_min<T>(bd, bk,
+                   frame_dist2<T>(P[o], P[plane + o], P[2 * plane + o], fr.vx, fr.vy, fr.vz, fr.av,
+                                  fr.wx, fr.wy, fr.wz, fr.aw),
+                   k);
+#else
         lex_min<T>(bd, bk, line_dist2<T>(P[o], P[plane + o], P[2 * plane + o], ax, ay, az, ux, uy, uz),
                    k);
+#endif
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {

@@ -1,62 +1,69 @@
 // DCA finding and RSS (Algorithm 2, Eq. 1, Sec. 2.2.2).
 //
-// Layout of the work: a CTA of 128 threads owns 128/LPS seeds; LPS lanes share a seed and split its
-// wires (LPS = 1 for large seed counts, 4 when there are too few seeds to fill the GPU).  The wire
+// Layout of the work: one thread per seed, 128 seeds per CTA, all wires per seed.  The wire
 // geometry, the CSR hit offsets and (when they fit) the drift distances and masks are staged in
-// shared memory with the bulk-copy engine (cp.async.bulk + mbarrier), in tiles of 256 wires.
+// shared memory with the bulk-copy engine (cp.async.bulk + mbarrier), in tiles of 128 wires.
 //
-// Closest recorded state of a (seed, wire) pair, found exactly without visiting every state: the
-// recorded states of a seed are cut into at most N0MAX super-segments of G0 states, each cut into
-// level-1 segments of G1 states.  A state within g/2 recording intervals of a segment's centre is
-// within R = (g/2) h_rec of it in space (consecutive recorded states are at most h_rec apart along
-// the track), so dist(any state of the segment) >= dist(centre) - R.  The super-segment centres of
-// each seed live in shared memory; the level-1 centres and the states are read from the track array.
-// At each level a segment is visited only if its bound does not exceed the best distance found so
-// far; visiting a superset of the segments that can hold the minimum returns the same lexicographic
-// (distance, index) minimum.  Candidate sets are united over the warp so that every load is
-// warp-uniform in the state index (32 consecutive seeds: one 128-byte line); the seed lattice numbers
-// neighbouring nodes consecutively, so the 32 tracks of a warp are close and the union stays small.
+// Closest recorded state of a (seed, wire) pair, found exactly without visiting every state.  The
+// recorded states of each seed are cut into at most 8 super-segments of G0 states, each cut into at
+// most 24 level-1 segments of G1 states.  Because the seed lattice numbers neighbouring nodes
+// consecutively, the 32 tracks of a warp are close, and one bounding sphere per segment covers all
+// 32 of them: its centre is one lane's segment centre C, its radius the largest distance from C to
+// any lane's segment centre plus (g/2) h_rec (a recorded state within g/2 recording intervals of a
+// centre is at most that far from it along the track).  Every recorded state x of that segment of
+// every seed of the warp then satisfies dist(x, wire) >= dist(C, wire) - radius.  The spheres live
+// in shared memory.  For each wire, the lanes test the spheres in parallel (lane t: wire t against
+// the super-segment spheres; then lane m: level-1 sphere m of a candidate super-segment) and only
+// segments whose bound does not exceed the wire's capture radius (largest unmasked drift + lambda +
+// h_rec/2) are scanned state by state, each lane its own seed's states, keeping the lexicographic
+// (distance, index) minimum.  If a seed's closest state is within the capture radius it lies in a
+// scanned segment, so the minimum is exact; if not, every residual of the wire is at least lambda
+// and the wire adds exactly lambda^2 to the RSS, with or without a refinement.  With dca_out every
+// state is scanned (exact DCA for every wire).
 //
-// Without dca_out, a wire whose closest recorded state is farther than (largest unmasked drift +
-// lambda + h_rec/2) is not refined: the true DCA is then at least (largest drift + lambda), so every
-// residual |D - r| of that wire is at least lambda and the wire adds exactly lambda^2 to the RSS.
-// The same bound drops segments at every level (a segment is skipped only if it cannot hold a state
-// within that distance, or if it cannot hold the minimum).
-//
-// RSS: each lane sums its wires' d_i^2 in ascending wire order (FP32 as a TwoSum pair, FP64 plainly);
-// lanes sharing a seed are combined in a fixed shuffle tree.  No atomics: the result does not depend
-// on scheduling (the paper's GPU kernel used atomics and was not deterministic, Sec. 4.1).
+// RSS: each thread sums its wires' d_i^2 in ascending wire order (FP32 as a TwoSum pair, FP64
+// plainly).  No atomics: the result does not depend on scheduling (the paper's GPU kernel used
+// atomics and was not deterministic, Sec. 4.1).
 #include <float.h>
 
 #include "device.cuh"
 #include "internal.h"
+
+// Tuning constants (compile-time): minimum resident CTAs per SM requested from the register
+// allocator, and how many states are loaded together.
+#ifndef COMET_DCA_MINB
+#define COMET_DCA_MINB 6
+#endif
+#ifndef COMET_DCA_U2
+#define COMET_DCA_U2 8
+#endif
 
 namespace comet {
 
 namespace {
 
 constexpr int kThreads = 128;
+constexpr int kWarps = kThreads / 32;
 constexpr int kWireTile = 256;
 constexpr int kWireCap = kWireTile + 32;     // elements per staged row (room for the 16-B shift)
 constexpr int kHitMax = 1024;                // hits staged in shared memory when H <= kHitMax
 constexpr int kHitCap = kHitMax + 32;
 constexpr uint64_t kWaitNs = 2000000000ull;  // bulk-copy wait limit (2 s)
-
-// super-segment centres per seed kept in shared memory; level-1 segments per super-segment
-constexpr int kN0Max = 16;
-constexpr int kN1Max = 32;
+constexpr int kN0Max = 8;                    // super-segments per seed
+constexpr int kN1Max = 24;                   // level-1 segments per super-segment
 
 constexpr size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
-template <typename T, int LPS>
+template <typename T>
 struct Smem {
-    static constexpr int SPB = kThreads / LPS;
     static constexpr size_t bar = 0;
-    static constexpr size_t c0 = 16;
-    static constexpr size_t wrow = align16(c0 + sizeof(T) * kN0Max * 3 * SPB);
+    static constexpr size_t sph0 = 16;                                            // [warp][j][4]
+    static constexpr size_t sph1 = align16(sph0 + sizeof(float) * kWarps * kN0Max * 4);  // [warp][j][m][4]
+    static constexpr size_t wrow = align16(sph1 + sizeof(float) * kWarps * kN0Max * kN1Max * 4);
     static constexpr size_t orow = align16(wrow + sizeof(T) * 6 * kWireCap);
     static constexpr size_t cap = align16(orow + sizeof(int32_t) * (kWireCap + 8));
-    static constexpr size_t drift = align16(cap + sizeof(T) * kWireTile);
+    static constexpr size_t frame = align16(cap + sizeof(T) * kWireTile);
+    static constexpr size_t drift = align16(frame + sizeof(T) * 8 * kWireTile);
     static constexpr size_t mask = align16(drift + sizeof(T) * kHitCap);
     static constexpr size_t total = align16(mask + kHitCap);
 };
@@ -113,25 +120,58 @@ struct Acc<double> {
 
 } // namespace
 
-template <typename T, class F, int LPS>
-__global__ void __launch_bounds__(kThreads) dca_kernel(F f, DcaArgs a)
+// Builds the warp's bounding sphere of one segment: lane `has` holds its seed's segment centre
+// (x, y, z); the sphere is centred on the first such lane's centre.  Returns (cx, cy, cz, radius) in
+// every lane, radius < 0 when no lane of the warp has the segment.
+template <typename T>
+__device__ __forceinline__ float4 warp_sphere(bool has, T x, T y, T z, T reach)
 {
-    using L = Smem<T, LPS>;
-    constexpr int SPB = L::SPB;
+    const uint32_t hm = __ballot_sync(0xffffffffu, has);
+    if (hm == 0u) return make_float4(0.f, 0.f, 0.f, -1.f);
+    const int src = __ffs(hm) - 1;
+    const T cx = __shfl_sync(0xffffffffu, x, src), cy = __shfl_sync(0xffffffffu, y, src),
+            cz = __shfl_sync(0xffffffffu, z, src);
+    T d = has ? sqrt((x - cx) * (x - cx) + (y - cy) * (y - cy) + (z - cz) * (z - cz)) : T(0);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) d = fmax(d, __shfl_xor_sync(0xffffffffu, d, off));
+    // the float radius is rounded up by a relative 1e-6 so that it never shrinks
+    return make_float4((float)cx, (float)cy, (float)cz, (float)((d + reach) * T(1.000001)));
+}
+
+template <typename T>
+__device__ __forceinline__ bool sphere_within(const float4 &sp, T fvx, T fvy, T fvz, T fav, T fwx,
+                                              T fwy, T fwz, T faw, T ax, T ay, T az, T ux, T uy,
+                                              T uz, T lim)
+{
+    if (sp.w < 0.f) return false;
+#if COMET_SEARCH_FRAME
+    const T d2 = frame_dist2<T>((T)sp.x, (T)sp.y, (T)sp.z, fvx, fvy, fvz, fav, fwx, fwy, fwz, faw);
+#else
+    const T d2 = line_dist2<T>((T)sp.x, (T)sp.y, (T)sp.z, ax, ay, az, ux, uy, uz);
+#endif
+    const T l = lim + (T)sp.w;
+    return d2 <= l * l;
+}
+
+template <typename T, class F>
+__global__ void __launch_bounds__(kThreads, COMET_DCA_MINB) dca_kernel(F f, DcaArgs a)
+{
+    using L = Smem<T>;
     extern __shared__ __align__(128) unsigned char sm[];
     uint64_t *bar = (uint64_t *)(sm + L::bar);
-    T *c0 = (T *)(sm + L::c0);
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    float4 *sph0 = (float4 *)(sm + L::sph0) + warp * kN0Max;
+    float4 *sph1 = (float4 *)(sm + L::sph1) + warp * kN0Max * kN1Max;
     T *wrow = (T *)(sm + L::wrow);
     int32_t *orow = (int32_t *)(sm + L::orow);
     T *capv = (T *)(sm + L::cap);
+    T *frm = (T *)(sm + L::frame);   // [8][kWireTile]: v (3), w (3), a.v, a.w
     T *dsm = (T *)(sm + L::drift);
     uint8_t *msm = (uint8_t *)(sm + L::mask);
 
-    const int tid = threadIdx.x;
-    const int ls = tid / LPS;
-    const int sub = tid % LPS;
     const int64_t S = a.S;
-    const int64_t s = (int64_t)blockIdx.x * SPB + ls;
+    const int64_t s = (int64_t)blockIdx.x * kThreads + tid;
     const bool valid = s < S;
     const T *__restrict__ P = (const T *)a.points;
     const int64_t plane = (int64_t)a.n_rec * S;
@@ -139,8 +179,6 @@ __global__ void __launch_bounds__(kThreads) dca_kernel(F f, DcaArgs a)
     const T *__restrict__ Dg = (const T *)a.drift;
     const T lam = (T)a.lambda;
     const T tol = (T)a.tol;
-    const T R0 = (T)a.R0;
-    const T R1 = (T)a.R1;
     const T half_rec = (T)a.half_rec;
     const T h_rec = (T)a.h_rec;
     const int G0 = a.G0, G1 = a.G1;
@@ -148,7 +186,6 @@ __global__ void __launch_bounds__(kThreads) dca_kernel(F f, DcaArgs a)
 
     if (tid == 0) mbar_init(bar, 1);
 
-    // per-seed constants and the level-1 centres
     int nv = 1;
     T c = T(0), ip = T(0);
     if (valid) {
@@ -160,18 +197,38 @@ __global__ void __launch_bounds__(kThreads) dca_kernel(F f, DcaArgs a)
         ip = (T)(1.0 / pd);
     }
     const int n0 = (nv + G0 - 1) / G0;
-    for (int j = sub; j < kN0Max; j += LPS) {
-        T x = T(0), y = T(0), z = T(0);
-        if (valid && j < n0) {
-            const int k = min(j * G0 + G0 / 2, nv - 1);
-            const int64_t o = (int64_t)k * S + s;
-            x = P[o];
-            y = P[plane + o];
-            z = P[2 * plane + o];
+    int n0w = valid ? n0 : 0;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) n0w = max(n0w, __shfl_xor_sync(0xffffffffu, n0w, off));
+
+    // ---- the warp's bounding spheres (super-segments and their level-1 segments)
+    if (!a.exact_all) {
+        for (int j = 0; j < kN0Max; ++j) {
+            const int sb = j * G0, se = min(sb + G0, nv);
+            bool has = valid && sb < nv;
+            T x = T(0), y = T(0), z = T(0);
+            if (has) {
+                const int64_t o = (int64_t)min(sb + G0 / 2, se - 1) * S + s;
+                x = P[o];
+                y = P[plane + o];
+                z = P[2 * plane + o];
+            }
+            const float4 sp = warp_sphere<T>(has, x, y, z, (T)a.R0);
+            if (lane == 0) sph0[j] = sp;
+            for (int m = 0; m < N1; ++m) {
+                const int st = sb + m * G1;
+                const bool h1 = has && st < se;
+                T x1 = T(0), y1 = T(0), z1 = T(0);
+                if (h1) {
+                    const int64_t o = (int64_t)min(st + G1 / 2, min(st + G1, se) - 1) * S + s;
+                    x1 = P[o];
+                    y1 = P[plane + o];
+                    z1 = P[2 * plane + o];
+                }
+                const float4 sp1 = warp_sphere<T>(h1, x1, y1, z1, (T)a.R1);
+                if (lane == 0) sph1[j * kN1Max + m] = sp1;
+            }
         }
-        c0[(j * 3 + 0) * SPB + ls] = x;
-        c0[(j * 3 + 1) * SPB + ls] = y;
-        c0[(j * 3 + 2) * SPB + ls] = z;
     }
 
     const int W = a.W;
@@ -180,7 +237,7 @@ __global__ void __launch_bounds__(kThreads) dca_kernel(F f, DcaArgs a)
     uint32_t parity = 0;
     bool any_timeout = false;
     int doff = 0, moff = 0;
-    __syncthreads();   // barrier initialised, centres written
+    __syncthreads();   // barrier initialised, spheres written
 
     // hits: staged once per CTA when they fit
     if (hits_sm && H > 0) {
@@ -206,6 +263,7 @@ __global__ void __launch_bounds__(kThreads) dca_kernel(F f, DcaArgs a)
 
     Acc<T> acc;
     int nin = 0, nunc = 0;
+    constexpr int kU = COMET_DCA_U2;
 
     for (int w0 = 0; w0 < W; w0 += kWireTile) {
         const int wn = min(kWireTile, W - w0);
@@ -235,7 +293,14 @@ __global__ void __launch_bounds__(kThreads) dca_kernel(F f, DcaArgs a)
             stage_fallback<int32_t>(orow, a.offs + w0, wn + 1);
         }
         __syncthreads();
-        // ---- per-wire capture radius: largest unmasked drift + lambda (-1: no unmasked hit)
+        const T *wax = wrow + 0 * kWireCap + woff[0];
+        const T *way = wrow + 1 * kWireCap + woff[1];
+        const T *waz = wrow + 2 * kWireCap + woff[2];
+        const T *wux = wrow + 3 * kWireCap + woff[3];
+        const T *wuy = wrow + 4 * kWireCap + woff[4];
+        const T *wuz = wrow + 5 * kWireCap + woff[5];
+        // ---- per wire: capture radius (largest unmasked drift + lambda; -1: no unmasked hit) and
+        // the wire frame
         for (int i = tid; i < wn; i += kThreads) {
             const int hb = orow[ooff + i], he = orow[ooff + i + 1];
             T mr = T(-1);
@@ -245,110 +310,73 @@ __global__ void __launch_bounds__(kThreads) dca_kernel(F f, DcaArgs a)
                 if (!m && r > mr) mr = r;
             }
             capv[i] = mr >= T(0) ? mr + lam : T(-1);
+            const WireFrame<T> fr = wire_frame<T>(wax[i], way[i], waz[i], wux[i], wuy[i], wuz[i]);
+            frm[0 * kWireTile + i] = fr.vx;
+            frm[1 * kWireTile + i] = fr.vy;
+            frm[2 * kWireTile + i] = fr.vz;
+            frm[3 * kWireTile + i] = fr.wx;
+            frm[4 * kWireTile + i] = fr.wy;
+            frm[5 * kWireTile + i] = fr.wz;
+            frm[6 * kWireTile + i] = fr.av;
+            frm[7 * kWireTile + i] = fr.aw;
         }
         __syncthreads();
 
-        const T *wax = wrow + 0 * kWireCap + woff[0];
-        const T *way = wrow + 1 * kWireCap + woff[1];
-        const T *waz = wrow + 2 * kWireCap + woff[2];
-        const T *wux = wrow + 3 * kWireCap + woff[3];
-        const T *wuy = wrow + 4 * kWireCap + woff[4];
-        const T *wuz = wrow + 5 * kWireCap + woff[5];
-
-        // ---- the wires of this tile (trip count uniform across the warp)
-        for (int base = 0; base < wn; base += LPS) {
-            const int ii = base + sub;
-            const bool inw = ii < wn;
-            T cap = T(-1), ax = T(0), ay = T(0), az = T(0), ux = T(0), uy = T(0), uz = T(1);
-            if (inw) {
-                cap = capv[ii];
-                ax = wax[ii];
-                ay = way[ii];
-                az = waz[ii];
-                ux = wux[ii];
-                uy = wuy[ii];
-                uz = wuz[ii];
-            }
-            const bool want = valid && inw && (cap >= T(0) || a.exact_all);
-
-            // level 0: super-segment centres from shared memory
-            T bd = T(INFINITY);
-            int bk = 0x7fffffff;
-            T d0[kN0Max];
-#pragma unroll
-            for (int j = 0; j < kN0Max; ++j) {
-                T d2 = T(INFINITY);
-                if (want && j < n0) {
-                    d2 = line_dist2<T>(c0[(j * 3 + 0) * SPB + ls], c0[(j * 3 + 1) * SPB + ls],
-                                       c0[(j * 3 + 2) * SPB + ls], ax, ay, az, ux, uy, uz);
-                    lex_min<T>(bd, bk, d2, min(j * G0 + G0 / 2, nv - 1));
+        for (int base = 0; base < wn; base += 32) {
+            const int clen = min(32, wn - base);
+            // lane t: which super-segments can bring wire base + t within its capture radius
+            uint32_t mask0 = 0;
+            if (lane < clen) {
+                const int iw = base + lane;
+                const T capw = capv[iw];
+                if (a.exact_all) {
+                    mask0 = 1u;
+                } else if (capw >= T(0)) {
+                    const T lim = capw + half_rec;
+                    for (int j = 0; j < n0w; ++j)
+                        if (sphere_within<T>(sph0[j], frm[0 * kWireTile + iw], frm[1 * kWireTile + iw],
+                                             frm[2 * kWireTile + iw], frm[6 * kWireTile + iw],
+                                             frm[3 * kWireTile + iw], frm[4 * kWireTile + iw],
+                                             frm[5 * kWireTile + iw], frm[7 * kWireTile + iw], wax[iw],
+                                             way[iw], waz[iw], wux[iw], wuy[iw], wuz[iw], lim))
+                            mask0 |= 1u << j;
                 }
-                d0[j] = d2;
             }
-            const T capth = a.exact_all ? T(INFINITY) : cap + half_rec;
-            uint32_t cand0 = 0;
-            if (want) {
-                const T lim = fmin(sqrt(bd), capth) + R0;
-                const T lim2 = lim * lim;
-#pragma unroll
-                for (int j = 0; j < kN0Max; ++j)
-                    if (d0[j] <= lim2) cand0 |= 1u << j;
-            }
-            uint32_t u0 = __reduce_or_sync(0xffffffffu, cand0);
-
-            constexpr int kUnroll = 4;
-            while (u0) {
-                const int j = __ffs(u0) - 1;
-                u0 &= u0 - 1;
-                const int sb = j * G0;
-                const int se = min(sb + G0, nv);          // this lane's end of super-segment j
-                // level 1: centres of the level-1 segments of super-segment j
-                uint32_t cand1 = 0;
-                {
-                    const T lim = want ? fmin(sqrt(bd), capth) + R1 : T(0);
-                    const T lim2 = lim * lim;
-                    for (int m0 = 0; m0 < N1; m0 += kUnroll) {
-                        T xs[kUnroll], ys[kUnroll], zs[kUnroll];
-                        int ks[kUnroll];
-#pragma unroll
-                        for (int u = 0; u < kUnroll; ++u) {
-                            const int m = m0 + u;
-                            const int st = sb + m * G1;
-                            xs[u] = ys[u] = zs[u] = T(0);
-                            ks[u] = -1;
-                            if (want && m < N1 && st < se) {
-                                const int k = min(st + G1 / 2, min(st + G1, se) - 1);
-                                const int64_t o = (int64_t)k * S + s;
-                                xs[u] = P[o];
-                                ys[u] = P[plane + o];
-                                zs[u] = P[2 * plane + o];
-                                ks[u] = k;
-                            }
-                        }
-#pragma unroll
-                        for (int u = 0; u < kUnroll; ++u) {
-                            if (ks[u] >= 0) {
-                                const T d2 = line_dist2<T>(xs[u], ys[u], zs[u], ax, ay, az, ux, uy, uz);
-                                lex_min<T>(bd, bk, d2, ks[u]);
-                                if (d2 <= lim2) cand1 |= 1u << (m0 + u);
-                            }
-                        }
-                    }
+            for (int t = 0; t < clen; ++t) {
+                const int ii = base + t;
+                const uint32_t m0 = __shfl_sync(0xffffffffu, mask0, t);
+                const T cap = capv[ii];
+                if (m0 == 0u) {
+                    // beyond every seed's capture radius (or no unmasked hit): lambda^2 if in the sum
+                    if (valid && cap >= T(0)) acc.add(lam * lam);
+                    continue;
                 }
-                uint32_t u1 = __reduce_or_sync(0xffffffffu, cand1);
-                // level 2: every state of the candidate level-1 segments
-                while (u1) {
-                    const int m = __ffs(u1) - 1;
-                    u1 &= u1 - 1;
-                    const int k0 = sb + m * G1;
-                    const int kend = min(k0 + G1, se);
-                    for (int t0 = k0; t0 < k0 + G1; t0 += kUnroll) {
-                        T xs[kUnroll], ys[kUnroll], zs[kUnroll];
+                const T ax = wax[ii], ay = way[ii], az = waz[ii];
+                const T ux = wux[ii], uy = wuy[ii], uz = wuz[ii];
+                const T fvx = frm[0 * kWireTile + ii], fvy = frm[1 * kWireTile + ii],
+                        fvz = frm[2 * kWireTile + ii], fwx = frm[3 * kWireTile + ii],
+                        fwy = frm[4 * kWireTile + ii], fwz = frm[5 * kWireTile + ii],
+                        fav = frm[6 * kWireTile + ii], faw = frm[7 * kWireTile + ii];
+#if COMET_SEARCH_FRAME
+                auto sd2 = [&](T x, T y, T z) {
+                    return frame_dist2<T>(x, y, z, fvx, fvy, fvz, fav, fwx, fwy, fwz, faw);
+                };
+#else
+                auto sd2 = [&](T x, T y, T z) { return line_dist2<T>(x, y, z, ax, ay, az, ux, uy, uz); };
+#endif
+                const bool want = valid && (cap >= T(0) || a.exact_all);
+                const T capth = a.exact_all ? T(INFINITY) : cap + half_rec;
+                T bd = T(INFINITY);
+                int bk = 0x7fffffff;
+                // scans states [k0, k1) of this lane's seed
+                auto scan = [&](int k0, int k1, int span) {
+                    for (int t0 = 0; t0 < span; t0 += kU) {
+                        T xs[kU], ys[kU], zs[kU];
 #pragma unroll
-                        for (int u = 0; u < kUnroll; ++u) {
-                            const int k = t0 + u;
+                        for (int u = 0; u < kU; ++u) {
+                            const int k = k0 + t0 + u;
                             xs[u] = ys[u] = zs[u] = T(0);
-                            if (want && k < kend) {
+                            if (want && k < k1) {
                                 const int64_t o = (int64_t)k * S + s;
                                 xs[u] = P[o];
                                 ys[u] = P[plane + o];
@@ -356,60 +384,74 @@ __global__ void __launch_bounds__(kThreads) dca_kernel(F f, DcaArgs a)
                             }
                         }
 #pragma unroll
-                        for (int u = 0; u < kUnroll; ++u) {
-                            const int k = t0 + u;
-                            if (want && k < kend)
-                                lex_min<T>(bd, bk, line_dist2<T>(xs[u], ys[u], zs[u], ax, ay, az, ux, uy, uz), k);
+                        for (int u = 0; u < kU; ++u) {
+                            const int k = k0 + t0 + u;
+                            if (want && k < k1) lex_min<T>(bd, bk, sd2(xs[u], ys[u], zs[u]), k);
+                        }
+                    }
+                };
+                if (a.exact_all) {
+                    int nvw = nv;
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) nvw = max(nvw, __shfl_xor_sync(0xffffffffu, nvw, off));
+                    scan(0, nv, nvw);
+                } else {
+                    uint32_t u0 = m0;
+                    while (u0) {
+                        const int j = __ffs(u0) - 1;
+                        u0 &= u0 - 1;
+                        // lane m tests level-1 segment m of super-segment j
+                        const bool hit1 = lane < N1 &&
+                                          sphere_within<T>(sph1[j * kN1Max + lane], fvx, fvy, fvz, fav,
+                                                           fwx, fwy, fwz, faw, ax, ay, az, ux, uy, uz,
+                                                           capth);
+                        const uint32_t u1 = __ballot_sync(0xffffffffu, hit1);
+                        if (u1) {
+                            // one contiguous range from the first to the last candidate level-1
+                            // segment (a superset of the candidates; their loads go out together)
+                            const int m_lo = __ffs(u1) - 1, m_hi = 31 - __clz(u1);
+                            const int sb = j * G0, se = min(sb + G0, nv);
+                            const int k0 = sb + m_lo * G1;
+                            scan(k0, min(sb + (m_hi + 1) * G1, se), (m_hi - m_lo + 1) * G1);
                         }
                     }
                 }
-            }
 
-            // refinement from the closest recorded state (skipped when the wire cannot contribute)
-            const bool refine = want && (a.exact_all || sqrt(bd) <= capth);
-            T D = T(INFINITY);
-            if (refine) {
-                T yv[6];
-                const int64_t o = (int64_t)bk * S + s;
-#pragma unroll
-                for (int cc = 0; cc < 6; ++cc) yv[cc] = P[cc * plane + o];
-                const int conv = refine_dca<T, F>(f, c, ip, yv, ax, ay, az, ux, uy, uz, tol,
-                                                  a.max_iter, h_rec, D);
-                if (cap >= T(0)) nunc += 1 - conv;
-                if (a.dca_out) ((T *)a.dca_out)[(int64_t)(w0 + ii) * S + s] = D;
-            }
-            if (valid && inw && cap >= T(0)) {
-                T emin = T(INFINITY);
+                // refinement from the closest recorded state (only when it can matter)
+                const bool refine = want && bk != 0x7fffffff && (a.exact_all || sqrt(bd) <= capth);
+                T D = T(INFINITY);
                 if (refine) {
-                    const int hb = orow[ooff + ii], he = orow[ooff + ii + 1];
-                    for (int j = hb; j < he; ++j) {
-                        const bool m = hits_sm ? msm[moff + j] != 0 : a.mask[j] != 0;
-                        if (m) continue;
-                        const T r = hits_sm ? dsm[doff + j] : Dg[j];
-                        const T e = fabs(D - r);
-                        emin = e < emin ? e : emin;
-                    }
+                    T yv[6];
+                    const int64_t o = (int64_t)bk * S + s;
+#pragma unroll
+                    for (int cc = 0; cc < 6; ++cc) yv[cc] = P[cc * plane + o];
+                    const int conv = refine_dca<T, F>(f, c, ip, yv, ax, ay, az, ux, uy, uz, tol,
+                                                      a.max_iter, h_rec, D);
+                    if (cap >= T(0)) nunc += 1 - conv;
+                    if (a.dca_out) ((T *)a.dca_out)[(int64_t)(w0 + ii) * S + s] = D;
                 }
-                const T d = emin < lam ? emin : lam;
-                nin += emin < lam ? 1 : 0;
-                acc.add(d * d);
+                if (valid && cap >= T(0)) {
+                    T emin = T(INFINITY);
+                    if (refine) {
+                        const int hb = orow[ooff + ii], he = orow[ooff + ii + 1];
+                        for (int j = hb; j < he; ++j) {
+                            const bool m = hits_sm ? msm[moff + j] != 0 : a.mask[j] != 0;
+                            if (m) continue;
+                            const T r = hits_sm ? dsm[doff + j] : Dg[j];
+                            const T e = fabs(D - r);
+                            emin = e < emin ? e : emin;
+                        }
+                    }
+                    const T d = emin < lam ? emin : lam;
+                    nin += emin < lam ? 1 : 0;
+                    acc.add(d * d);
+                }
             }
         }
-        __syncthreads();   // tile consumed before the next staging overwrites it
+        if (w0 + kWireTile < W) __syncthreads();   // tile consumed before the next staging
     }
 
-    // combine the lanes of a seed in a fixed order
-#pragma unroll
-    for (int off = LPS / 2; off > 0; off >>= 1) {
-        const T oh = __shfl_xor_sync(0xffffffffu, acc.hi, off);
-        const T ol = __shfl_xor_sync(0xffffffffu, acc.lo, off);
-        const int on = __shfl_xor_sync(0xffffffffu, nin, off);
-        if ((sub & off) == 0) {
-            acc.add_pair(oh, ol);
-            nin += on;
-        }
-    }
-    if (valid && sub == 0) {
+    if (valid) {
         ((T *)a.rss)[s] = acc.value();
         a.n_in[s] = nin;
     }
@@ -417,7 +459,7 @@ __global__ void __launch_bounds__(kThreads) dca_kernel(F f, DcaArgs a)
         int t = nunc;
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
-        if ((tid & 31) == 0 && t) atomicAdd(a.n_unconv, t);
+        if (lane == 0 && t) atomicAdd(a.n_unconv, t);
     }
     if (any_timeout) {
         if (tid == 0 && a.status) atomicOr(a.status, 1);
@@ -426,24 +468,16 @@ __global__ void __launch_bounds__(kThreads) dca_kernel(F f, DcaArgs a)
     }
 }
 
-template <typename T, class F, int LPS>
-static cudaError_t dca_launch_one(const F &fld, const DcaArgs &a, cudaStream_t st)
-{
-    using L = Smem<T, LPS>;
-    static const cudaError_t attr = cudaFuncSetAttribute(
-        dca_kernel<T, F, LPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::total);
-    if (attr != cudaSuccess) return attr;
-    const int64_t nb = (a.S + L::SPB - 1) / L::SPB;
-    dca_kernel<T, F, LPS><<<(unsigned)nb, kThreads, L::total, st>>>(fld, a);
-    return cudaGetLastError();
-}
-
 template <typename T, class F>
-static cudaError_t dca_lps(const F &fld, const DcaArgs &a, cudaStream_t st)
+static cudaError_t dca_launch(const F &fld, const DcaArgs &a, cudaStream_t st)
 {
-    // fewer seeds than ~8 resident threads per FP32 lane of the GPU: share seeds among 4 lanes
-    if (a.S < 65536) return dca_launch_one<T, F, 4>(fld, a, st);
-    return dca_launch_one<T, F, 1>(fld, a, st);
+    using L = Smem<T>;
+    static const cudaError_t attr = cudaFuncSetAttribute(
+        dca_kernel<T, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::total);
+    if (attr != cudaSuccess) return attr;
+    const int64_t nb = (a.S + kThreads - 1) / kThreads;
+    dca_kernel<T, F><<<(unsigned)nb, kThreads, L::total, st>>>(fld, a);
+    return cudaGetLastError();
 }
 
 template <typename T>
@@ -451,29 +485,28 @@ static cudaError_t dca_dispatch(const comet_field &f, const DcaArgs &a, cudaStre
 {
     switch (field_kind(f)) {
     case FieldKind::Axial:
-        return dca_lps<T>(FieldAxial<T>{(T)f.b[2]}, a, st);
+        return dca_launch<T>(FieldAxial<T>{(T)f.b[2]}, a, st);
     case FieldKind::Uniform:
-        return dca_lps<T>(FieldUniform<T>{(T)f.b[0], (T)f.b[1], (T)f.b[2]}, a, st);
+        return dca_launch<T>(FieldUniform<T>{(T)f.b[0], (T)f.b[1], (T)f.b[2]}, a, st);
     case FieldKind::Table:
     default:
-        return dca_lps<T>(FieldTable<T>{(const float *)f.table, f.nx, f.ny, f.nz, (T)f.origin[0],
-                                        (T)f.origin[1], (T)f.origin[2], (T)(1.0 / f.spacing)},
-                          a, st);
+        return dca_launch<T>(FieldTable<T>{(const float *)f.table, f.nx, f.ny, f.nz, (T)f.origin[0],
+                                           (T)f.origin[1], (T)f.origin[2], (T)(1.0 / f.spacing)},
+                             a, st);
     }
 }
 
 void dca_segments(int n_rec, int *G0, int *G1)
 {
-    // about cbrt(n_rec) super-segments of about sqrt(G0)-state level-1 segments
+    // up to 8 super-segments, each cut into level-1 segments of 3 states (more when a super-segment
+    // would have more than kN1Max of them)
     int n0 = (int)lround(cbrt((double)n_rec));
-    n0 = n0 < 2 ? 2 : (n0 > kN0Max ? kN0Max : n0);
-    int g0 = (n_rec + n0 - 1) / n0;
-    if ((n_rec + g0 - 1) / g0 > kN0Max) g0 = (n_rec + kN0Max - 1) / kN0Max;
-    int g1 = (int)lround(sqrt((double)g0));
-    g1 = g1 < 1 ? 1 : g1;
+    n0 = n0 < 1 ? 1 : (n0 > kN0Max ? kN0Max : n0);
+    const int g0 = (n_rec + n0 - 1) / n0;
+    int g1 = 3;
     if ((g0 + g1 - 1) / g1 > kN1Max) g1 = (g0 + kN1Max - 1) / kN1Max;
     *G0 = g0;
-    *G1 = g1;
+    *G1 = g1 > g0 ? g0 : g1;
 }
 
 cudaError_t launch_dca(comet_dtype dt, const comet_field &f, const DcaArgs &a, cudaStream_t st)

@@ -43,14 +43,15 @@ def test_single_event_fp64_all_partitions(ctx):
         omask = r["mask"]
 
 
-def test_multi_turn_event_fp32_full_size_sampled(ctx):
+@pytest.mark.parametrize("stride", [1, 4])
+def test_multi_turn_event_fp32_full_size_sampled(ctx, stride):
     ev = synth.multi_turn_event(4)
     spec = ev.partitions[0]
     S = spec.n_seeds
     assert S == 1 << 18
     f = B.DeviceField.from_synth(UNIFORM)
     dev = scan.DeviceEvent.from_event(ev, torch.float32)
-    bp = scan.event_params(ev, torch.float32)[0]
+    bp = scan.event_params(ev, torch.float32, stride=stride)[0]
     ws = scan.Workspace(S, bp.n_rec, ev.n_hits, torch.float32)
     scan.scan_partition(ctx, f, bp, spec, dev, ws)
     torch.cuda.synchronize()
