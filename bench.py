@@ -213,7 +213,8 @@ def run_ours(args, rank, world):
     field = B.DeviceField.from_synth(synth.uniform_field(1.0))
     dtype = torch.float32
     n_ev = args.warmup + args.steps
-    idx = [rank + world * i for i in range(n_ev)]
+    from paper_1911_09340_gb300 import multi
+    idx = multi.event_indices(n_ev, rank, world)
     events = make_events(idx, args.lattice)
     max_rec = max(n // args.stride + 1 for ev in events for n in ev.n_steps)
     max_h = max(ev.n_hits for ev in events)
