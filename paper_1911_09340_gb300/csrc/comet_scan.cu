@@ -278,6 +278,7 @@ comet_status comet_scan_dca(comet_ctx *ctx, comet_dtype dtype, const comet_field
     a.dca_out = W > 0 ? dca_out : nullptr;
     a.n_unconv = n_unconverged;
     a.status = ctx->status;
+    a.counter = ctx->status + 16;
     a.lambda = params->lambda;
     a.tol = params->tol;
     a.max_iter = params->max_iter;

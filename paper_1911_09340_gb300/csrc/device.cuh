@@ -193,6 +193,16 @@ __device__ __forceinline__ void two_sum_add(float &hi, float &lo, float d)
     lo = err;
 }
 
+// c = KAPPA q / P0 and 1 / P0 of a seed from its recorded momentum (state 0), in the working
+// precision; the DCA and classification kernels use the same helper, hence the same values.
+template <typename T>
+__device__ __forceinline__ void seed_kinematics(T px, T py, T pz, int q, T &c, T &ip)
+{
+    const T P0 = sqrt(px * px + py * py + pz * pz);
+    ip = T(1) / P0;
+    c = T(kKappa) * T(q) * ip;
+}
+
 // ------------------------------------------------------------------------------------------------
 // Geometry
 // ------------------------------------------------------------------------------------------------

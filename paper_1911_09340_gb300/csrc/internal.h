@@ -43,6 +43,7 @@ struct DcaArgs {
     void *dca_out;
     int32_t *n_unconv;
     int32_t *status;       // device status word of the context (bit 0: a bulk-copy wait timed out)
+    int32_t *counter;      // device work counter (context-owned; zeroed before each launch)
     double lambda, tol;
     double R0;             // super-segment radius (m), margins included
     double R1;             // level-1 segment radius (m), margins included

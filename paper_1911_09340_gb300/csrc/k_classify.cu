@@ -58,16 +58,14 @@ __global__ void __launch_bounds__(256) classify_kernel(F f, ClsArgs a)
     }
     if (lane != 0) return;
 
-    const double px = P[3 * plane + s], py = P[4 * plane + s], pz = P[5 * plane + s];
-    const double pd = sqrt(px * px + py * py + pz * pz);
-    const int q = a.charge[s];
+    T c, ip;
+    seed_kinematics<T>(P[3 * plane + s], P[4 * plane + s], P[5 * plane + s], a.charge[s], c, ip);
     T y[6];
     const int64_t o = (int64_t)bk * S + s;
 #pragma unroll
     for (int c = 0; c < 6; ++c) y[c] = P[c * plane + o];
     T D;
-    refine_dca<T, F>(f, (T)(kKappa * q / pd), (T)(1.0 / pd), y, ax, ay, az, ux,
-                     uy, uz, (T)a.tol, a.max_iter, (T)a.h_rec, D);
+    refine_dca<T, F>(f, c, ip, y, ax, ay, az, ux, uy, uz, (T)a.tol, a.max_iter, (T)a.h_rec, D);
     if (a.dca_wire) ((T *)a.dca_wire)[i] = D;
 
     const T *__restrict__ Dg = (const T *)a.drift;

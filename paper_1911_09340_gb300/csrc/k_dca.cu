@@ -52,7 +52,7 @@ constexpr uint64_t kWaitNs = 2000000000ull;  // bulk-copy wait limit (2 s)
 constexpr int kN0Max = 8;                    // super-segments per seed
 constexpr int kN1Max = 24;                   // level-1 segments per super-segment
 
-constexpr size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+__host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
 template <typename T>
 struct Smem {
@@ -153,8 +153,419 @@ __device__ __forceinline__ bool sphere_within(const float4 &sp, T fvx, T fvy, T 
     return d2 <= l * l;
 }
 
+// ------------------------------------------------------------------------------------------------
+// One 32-seed group (one warp): per-lane seed state, bounding spheres, and the wire loop
+// ------------------------------------------------------------------------------------------------
+
+template <typename T>
+struct Group {
+    int64_t s;       // this lane's seed
+    bool valid;
+    int nv;          // recorded states of the seed
+    int n0w;         // super-segments of the longest track of the warp
+    T c, ip;         // KAPPA q / P0, 1 / P0
+};
+
+template <typename T>
+__device__ __forceinline__ Group<T> load_group(const DcaArgs &a, int64_t g, int lane)
+{
+    const T *__restrict__ P = (const T *)a.points;
+    const int64_t S = a.S;
+    const int64_t plane = (int64_t)a.n_rec * S;
+    Group<T> gr;
+    gr.s = g * 32 + lane;
+    gr.valid = gr.s < S;
+    gr.nv = 1;
+    gr.c = T(0);
+    gr.ip = T(0);
+    if (gr.valid) {
+        gr.nv = a.n_valid[gr.s];
+        seed_kinematics<T>(P[3 * plane + gr.s], P[4 * plane + gr.s], P[5 * plane + gr.s],
+                           a.charge[gr.s], gr.c, gr.ip);
+    }
+    int n0w = gr.valid ? (gr.nv + a.G0 - 1) / a.G0 : 0;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) n0w = max(n0w, __shfl_xor_sync(0xffffffffu, n0w, off));
+    gr.n0w = n0w;
+    return gr;
+}
+
+// The warp's bounding spheres of its super-segments (sph0[j]) and level-1 segments
+// (sph1[j * kN1Max + m]), written by lane 0.
+template <typename T>
+__device__ __forceinline__ void build_spheres(const DcaArgs &a, const Group<T> &gr, int lane,
+                                              float4 *sph0, float4 *sph1)
+{
+    const T *__restrict__ P = (const T *)a.points;
+    const int64_t S = a.S;
+    const int64_t plane = (int64_t)a.n_rec * S;
+    const int G0 = a.G0, G1 = a.G1;
+    const int N1 = (G0 + G1 - 1) / G1;
+    for (int j = 0; j < kN0Max; ++j) {
+        const int sb = j * G0, se = min(sb + G0, gr.nv);
+        const bool has = gr.valid && sb < gr.nv;
+        T x = T(0), y = T(0), z = T(0);
+        if (has) {
+            const int64_t o = (int64_t)min(sb + G0 / 2, se - 1) * S + gr.s;
+            x = P[o];
+            y = P[plane + o];
+            z = P[2 * plane + o];
+        }
+        const float4 sp = warp_sphere<T>(has, x, y, z, (T)a.R0);
+        if (lane == 0) sph0[j] = sp;
+        for (int m = 0; m < N1; ++m) {
+            const int st = sb + m * G1;
+            const bool h1 = has && st < se;
+            T x1 = T(0), y1 = T(0), z1 = T(0);
+            if (h1) {
+                const int64_t o = (int64_t)min(st + G1 / 2, min(st + G1, se) - 1) * S + gr.s;
+                x1 = P[o];
+                y1 = P[plane + o];
+                z1 = P[2 * plane + o];
+            }
+            const float4 sp1 = warp_sphere<T>(h1, x1, y1, z1, (T)a.R1);
+            if (lane == 0) sph1[j * kN1Max + m] = sp1;
+        }
+    }
+    __syncwarp();
+}
+
+// A staged range of wires [w0, w0 + wn) in shared memory.
+template <typename T>
+struct Tile {
+    const T *ax, *ay, *az, *ux, *uy, *uz;   // wire point and direction, element i = wire w0 + i
+    const T *frm;                            // frames [8][fs]: v, w, a.v, a.w
+    int fs;
+    const T *cap;                            // capture radius (< 0: no unmasked hit)
+    const int32_t *offs;                     // CSR offsets, element i = wire w0 + i
+    const T *dsm;                            // drifts / masks: staged (global hit index) or global
+    const uint8_t *msm;
+    int w0, wn;
+};
+
+// Capture radius and frame of wire i of a staged tile (one thread per wire).
+template <typename T>
+__device__ __forceinline__ void tile_wire_setup(const Tile<T> &tl, int i, T lam, T *capv, T *frm)
+{
+    const int hb = tl.offs[i], he = tl.offs[i + 1];
+    T mr = T(-1);
+    for (int j = hb; j < he; ++j)
+        if (!tl.msm[j] && tl.dsm[j] > mr) mr = tl.dsm[j];
+    capv[i] = mr >= T(0) ? mr + lam : T(-1);
+    const WireFrame<T> fr = wire_frame<T>(tl.ax[i], tl.ay[i], tl.az[i], tl.ux[i], tl.uy[i], tl.uz[i]);
+    frm[0 * tl.fs + i] = fr.vx;
+    frm[1 * tl.fs + i] = fr.vy;
+    frm[2 * tl.fs + i] = fr.vz;
+    frm[3 * tl.fs + i] = fr.wx;
+    frm[4 * tl.fs + i] = fr.wy;
+    frm[5 * tl.fs + i] = fr.wz;
+    frm[6 * tl.fs + i] = fr.av;
+    frm[7 * tl.fs + i] = fr.aw;
+}
+
+// The wires of one tile for one 32-seed group: accumulates d_i^2, n_in and unconverged counts.
 template <typename T, class F>
-__global__ void __launch_bounds__(kThreads, COMET_DCA_MINB) dca_kernel(F f, DcaArgs a)
+__device__ __forceinline__ void group_wires(const F &f, const DcaArgs &a, const Group<T> &gr,
+                                            const Tile<T> &tl, const float4 *sph0,
+                                            const float4 *sph1, int lane, Acc<T> &acc, int &nin,
+                                            int &nunc)
+{
+    const T *__restrict__ P = (const T *)a.points;
+    const int64_t S = a.S;
+    const int64_t plane = (int64_t)a.n_rec * S;
+    const int64_t s = gr.s;
+    const bool valid = gr.valid;
+    const int nv = gr.nv;
+    const T lam = (T)a.lambda, tol = (T)a.tol, half_rec = (T)a.half_rec, h_rec = (T)a.h_rec;
+    const int G0 = a.G0, G1 = a.G1;
+    const int N1 = (G0 + G1 - 1) / G1;
+    const int fs = tl.fs;
+    const T *frm = tl.frm;
+    constexpr int kU = COMET_DCA_U2;
+
+    for (int base = 0; base < tl.wn; base += 32) {
+        const int clen = min(32, tl.wn - base);
+        // lane t: which super-segments can bring wire base + t within its capture radius
+        uint32_t mask0 = 0;
+        if (lane < clen) {
+            const int iw = base + lane;
+            const T capw = tl.cap[iw];
+            if (a.exact_all) {
+                mask0 = 1u;
+            } else if (capw >= T(0)) {
+                const T lim = capw + half_rec;
+                for (int j = 0; j < gr.n0w; ++j)
+                    if (sphere_within<T>(sph0[j], frm[0 * fs + iw], frm[1 * fs + iw], frm[2 * fs + iw],
+                                         frm[6 * fs + iw], frm[3 * fs + iw], frm[4 * fs + iw],
+                                         frm[5 * fs + iw], frm[7 * fs + iw], tl.ax[iw], tl.ay[iw],
+                                         tl.az[iw], tl.ux[iw], tl.uy[iw], tl.uz[iw], lim))
+                        mask0 |= 1u << j;
+            }
+        }
+        for (int t = 0; t < clen; ++t) {
+            const int ii = base + t;
+            const uint32_t m0 = __shfl_sync(0xffffffffu, mask0, t);
+            const T cap = tl.cap[ii];
+            if (m0 == 0u) {
+                // beyond every seed's capture radius (or no unmasked hit): lambda^2 if in the sum
+                if (valid && cap >= T(0)) acc.add(lam * lam);
+                continue;
+            }
+            const T ax = tl.ax[ii], ay = tl.ay[ii], az = tl.az[ii];
+            const T ux = tl.ux[ii], uy = tl.uy[ii], uz = tl.uz[ii];
+            const T fvx = frm[0 * fs + ii], fvy = frm[1 * fs + ii], fvz = frm[2 * fs + ii],
+                    fwx = frm[3 * fs + ii], fwy = frm[4 * fs + ii], fwz = frm[5 * fs + ii],
+                    fav = frm[6 * fs + ii], faw = frm[7 * fs + ii];
+#if COMET_SEARCH_FRAME
+            auto sd2 = [&](T x, T y, T z) {
+                return frame_dist2<T>(x, y, z, fvx, fvy, fvz, fav, fwx, fwy, fwz, faw);
+            };
+#else
+            auto sd2 = [&](T x, T y, T z) { return line_dist2<T>(x, y, z, ax, ay, az, ux, uy, uz); };
+#endif
+            const bool want = valid && (cap >= T(0) || a.exact_all);
+            const T capth = a.exact_all ? T(INFINITY) : cap + half_rec;
+            T bd = T(INFINITY);
+            int bk = 0x7fffffff;
+            // scans states [k0, k1) of this lane's seed, kU at a time (span is warp-uniform)
+            auto scan = [&](int k0, int k1, int span) {
+                for (int t0 = 0; t0 < span; t0 += kU) {
+                    T xs[kU], ys[kU], zs[kU];
+#pragma unroll
+                    for (int u = 0; u < kU; ++u) {
+                        const int k = k0 + t0 + u;
+                        xs[u] = ys[u] = zs[u] = T(0);
+                        if (want && k < k1) {
+                            const int64_t o = (int64_t)k * S + s;
+                            xs[u] = P[o];
+                            ys[u] = P[plane + o];
+                            zs[u] = P[2 * plane + o];
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < kU; ++u) {
+                        const int k = k0 + t0 + u;
+                        if (want && k < k1) lex_min<T>(bd, bk, sd2(xs[u], ys[u], zs[u]), k);
+                    }
+                }
+            };
+            if (a.exact_all) {
+                int nvw = nv;
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) nvw = max(nvw, __shfl_xor_sync(0xffffffffu, nvw, off));
+                scan(0, nv, nvw);
+            } else {
+                uint32_t u0 = m0;
+                while (u0) {
+                    const int j = __ffs(u0) - 1;
+                    u0 &= u0 - 1;
+                    // lane m tests level-1 segment m of super-segment j
+                    const bool hit1 = lane < N1 &&
+                                      sphere_within<T>(sph1[j * kN1Max + lane], fvx, fvy, fvz, fav,
+                                                       fwx, fwy, fwz, faw, ax, ay, az, ux, uy, uz,
+                                                       capth);
+                    const uint32_t u1 = __ballot_sync(0xffffffffu, hit1);
+                    if (u1) {
+                        // one contiguous range from the first to the last candidate level-1
+                        // segment (a superset of the candidates; their loads go out together)
+                        const int m_lo = __ffs(u1) - 1, m_hi = 31 - __clz(u1);
+                        const int sb = j * G0, se = min(sb + G0, nv);
+                        const int k0 = sb + m_lo * G1;
+                        scan(k0, min(sb + (m_hi + 1) * G1, se), (m_hi - m_lo + 1) * G1);
+                    }
+                }
+            }
+
+            // refinement from the closest recorded state (only when it can matter)
+            const bool refine = want && bk != 0x7fffffff && (a.exact_all || sqrt(bd) <= capth);
+            T D = T(INFINITY);
+            if (refine) {
+                T yv[6];
+                const int64_t o = (int64_t)bk * S + s;
+#pragma unroll
+                for (int cc = 0; cc < 6; ++cc) yv[cc] = P[cc * plane + o];
+                const int conv = refine_dca<T, F>(f, gr.c, gr.ip, yv, ax, ay, az, ux, uy, uz, tol,
+                                                  a.max_iter, h_rec, D);
+                if (cap >= T(0)) nunc += 1 - conv;
+                if (a.dca_out) ((T *)a.dca_out)[(int64_t)(tl.w0 + ii) * S + s] = D;
+            }
+            if (valid && cap >= T(0)) {
+                T emin = T(INFINITY);
+                if (refine) {
+                    const int hb = tl.offs[ii], he = tl.offs[ii + 1];
+                    for (int j = hb; j < he; ++j) {
+                        if (tl.msm[j]) continue;
+                        const T e = fabs(D - tl.dsm[j]);
+                        emin = e < emin ? e : emin;
+                    }
+                }
+                const T d = emin < lam ? emin : lam;
+                nin += emin < lam ? 1 : 0;
+                acc.add(d * d);
+            }
+        }
+    }
+}
+
+// Stages n_arrays arrays with one bulk-copy transaction (thread 0 issues, everyone waits).  Returns
+// true if the wait timed out anywhere in the CTA (the caller then re-reads with plain loads).
+__device__ __forceinline__ bool finish_stage(uint64_t *bar, uint32_t &parity, uint32_t bytes)
+{
+    bool to = false;
+    if (bytes > 0) {
+        to = !mbar_wait(bar, parity, kWaitNs);
+        parity ^= 1u;
+    }
+    return __syncthreads_or(to);
+}
+
+// ------------------------------------------------------------------------------------------------
+// Persistent kernel: all wires fit one shared-memory tile (the common case).  Each CTA stages the
+// wires and hits once; each warp then takes 32-seed groups from a device counter until none is left,
+// with no CTA-wide barrier between groups.
+// ------------------------------------------------------------------------------------------------
+
+struct PLayout {
+    size_t sph0, sph1, wrow, orow, cap, frame, drift, mask, total;
+    int wcap;
+};
+
+__host__ __device__ inline PLayout p_layout(int W, int es)
+{
+    PLayout L;
+    int wc = ((W + 31) / 32) * 32;
+    wc = wc < 32 ? 32 : wc;
+    L.wcap = wc;
+    L.sph0 = 16;
+    L.sph1 = align16(L.sph0 + 16 * kWarps * kN0Max);
+    L.wrow = align16(L.sph1 + (size_t)16 * kWarps * kN0Max * kN1Max);
+    L.orow = align16(L.wrow + (size_t)es * 6 * (wc + 32));
+    L.cap = align16(L.orow + (size_t)4 * (wc + 40));
+    L.frame = align16(L.cap + (size_t)es * wc);
+    L.drift = align16(L.frame + (size_t)es * 8 * wc);
+    L.mask = align16(L.drift + (size_t)es * kHitCap);
+    L.total = align16(L.mask + kHitCap);
+    return L;
+}
+
+constexpr int kPersistMaxW = 1024;
+
+template <typename T, class F>
+__global__ void __launch_bounds__(kThreads, COMET_DCA_MINB) dca_persistent_kernel(F f, DcaArgs a)
+{
+    const PLayout L = p_layout(a.W, (int)sizeof(T));
+    extern __shared__ __align__(128) unsigned char sm[];
+    uint64_t *bar = (uint64_t *)sm;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    float4 *sph0 = (float4 *)(sm + L.sph0) + warp * kN0Max;
+    float4 *sph1 = (float4 *)(sm + L.sph1) + warp * kN0Max * kN1Max;
+    T *wrow = (T *)(sm + L.wrow);
+    int32_t *orow = (int32_t *)(sm + L.orow);
+    T *capv = (T *)(sm + L.cap);
+    T *frm = (T *)(sm + L.frame);
+    T *dsm = (T *)(sm + L.drift);
+    uint8_t *msm = (uint8_t *)(sm + L.mask);
+    const int rcap = L.wcap + 32;
+    const T *__restrict__ Wg = (const T *)a.wires;
+    const T *__restrict__ Dg = (const T *)a.drift;
+    const int W = a.W;
+    const int H = W > 0 ? a.offs[W] : 0;
+    const bool hits_sm = H <= kHitMax;
+
+    if (tid == 0) mbar_init(bar, 1);
+    __syncthreads();
+
+    // ---- stage wires, offsets and (when they fit) hits: one bulk-copy transaction (W > 0 only:
+    // with no wires the pointers may be NULL and every RSS is 0)
+    uint32_t parity = 0;
+    uint32_t bytes = 0;
+    int woff[6] = {0, 0, 0, 0, 0, 0};
+    int ooff = 0, doff = 0, moff = 0;
+    if (W > 0) {
+        bytes = stage_bytes<int32_t>(a.offs, W + 1);
+#pragma unroll
+        for (int r = 0; r < 6; ++r) bytes += stage_bytes<T>(Wg + (size_t)r * a.ldw, W);
+        if (hits_sm && H > 0) bytes += stage_bytes<T>(Dg, H) + stage_bytes<uint8_t>(a.mask, H);
+        if (tid == 0 && bytes > 0) {
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(bar, bytes);
+        }
+#pragma unroll
+        for (int r = 0; r < 6; ++r)
+            woff[r] = stage_issue<T>(wrow + r * rcap, Wg + (size_t)r * a.ldw, W, bar, tid == 0);
+        ooff = stage_issue<int32_t>(orow, a.offs, W + 1, bar, tid == 0);
+        if (hits_sm && H > 0) {
+            doff = stage_issue<T>(dsm, Dg, H, bar, tid == 0);
+            moff = stage_issue<uint8_t>(msm, a.mask, H, bar, tid == 0);
+        }
+    }
+    const bool any_timeout = finish_stage(bar, parity, bytes);
+    if (any_timeout && W > 0) {
+#pragma unroll
+        for (int r = 0; r < 6; ++r) stage_fallback<T>(wrow + r * rcap, Wg + (size_t)r * a.ldw, W);
+        stage_fallback<int32_t>(orow, a.offs, W + 1);
+        if (hits_sm && H > 0) {
+            stage_fallback<T>(dsm, Dg, H);
+            stage_fallback<uint8_t>(msm, a.mask, H);
+        }
+    }
+    __syncthreads();
+    Tile<T> tl;
+    tl.ax = wrow + 0 * rcap + woff[0];
+    tl.ay = wrow + 1 * rcap + woff[1];
+    tl.az = wrow + 2 * rcap + woff[2];
+    tl.ux = wrow + 3 * rcap + woff[3];
+    tl.uy = wrow + 4 * rcap + woff[4];
+    tl.uz = wrow + 5 * rcap + woff[5];
+    tl.frm = frm;
+    tl.fs = L.wcap;
+    tl.cap = capv;
+    tl.offs = orow + ooff;
+    tl.dsm = hits_sm ? dsm + doff : Dg;
+    tl.msm = hits_sm ? msm + moff : a.mask;
+    tl.w0 = 0;
+    tl.wn = W;
+    for (int i = tid; i < W; i += kThreads) tile_wire_setup<T>(tl, i, (T)a.lambda, capv, frm);
+    __syncthreads();
+
+    // ---- 32-seed groups, taken dynamically by each warp
+    const int64_t n_groups = (a.S + 31) / 32;
+    int nunc = 0;
+    for (;;) {
+        unsigned int g = 0;
+        if (lane == 0) g = atomicAdd((unsigned int *)a.counter, 1u);
+        g = __shfl_sync(0xffffffffu, g, 0);
+        if ((int64_t)g >= n_groups) break;
+        const Group<T> gr = load_group<T>(a, (int64_t)g, lane);
+        if (!a.exact_all) build_spheres<T>(a, gr, lane, sph0, sph1);
+        Acc<T> acc;
+        int nin = 0;
+        group_wires<T, F>(f, a, gr, tl, sph0, sph1, lane, acc, nin, nunc);
+        if (gr.valid) {
+            ((T *)a.rss)[gr.s] = acc.value();
+            a.n_in[gr.s] = nin;
+        }
+        __syncwarp();   // the next group's spheres overwrite this warp's slot
+    }
+    if (a.n_unconv) {
+        int t = nunc;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+        if (lane == 0 && t) atomicAdd(a.n_unconv, t);
+    }
+    if (any_timeout) {
+        if (tid == 0 && a.status) atomicOr(a.status, 1);
+        mbar_wait(bar, parity ^ 1u, kWaitNs);
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Tiled kernel: more wires than one tile holds.  One 128-seed block per CTA; wires staged in tiles.
+// ------------------------------------------------------------------------------------------------
+
+template <typename T, class F>
+__global__ void __launch_bounds__(kThreads, COMET_DCA_MINB) dca_tiled_kernel(F f, DcaArgs a)
 {
     using L = Smem<T>;
     extern __shared__ __align__(128) unsigned char sm[];
@@ -166,70 +577,15 @@ __global__ void __launch_bounds__(kThreads, COMET_DCA_MINB) dca_kernel(F f, DcaA
     T *wrow = (T *)(sm + L::wrow);
     int32_t *orow = (int32_t *)(sm + L::orow);
     T *capv = (T *)(sm + L::cap);
-    T *frm = (T *)(sm + L::frame);   // [8][kWireTile]: v (3), w (3), a.v, a.w
+    T *frm = (T *)(sm + L::frame);
     T *dsm = (T *)(sm + L::drift);
     uint8_t *msm = (uint8_t *)(sm + L::mask);
-
-    const int64_t S = a.S;
-    const int64_t s = (int64_t)blockIdx.x * kThreads + tid;
-    const bool valid = s < S;
-    const T *__restrict__ P = (const T *)a.points;
-    const int64_t plane = (int64_t)a.n_rec * S;
     const T *__restrict__ Wg = (const T *)a.wires;
     const T *__restrict__ Dg = (const T *)a.drift;
-    const T lam = (T)a.lambda;
-    const T tol = (T)a.tol;
-    const T half_rec = (T)a.half_rec;
-    const T h_rec = (T)a.h_rec;
-    const int G0 = a.G0, G1 = a.G1;
-    const int N1 = (G0 + G1 - 1) / G1;
 
     if (tid == 0) mbar_init(bar, 1);
-
-    int nv = 1;
-    T c = T(0), ip = T(0);
-    if (valid) {
-        nv = a.n_valid[s];
-        const int q = a.charge[s];
-        const double px = P[3 * plane + s], py = P[4 * plane + s], pz = P[5 * plane + s];
-        const double pd = sqrt(px * px + py * py + pz * pz);
-        c = (T)(kKappa * q / pd);
-        ip = (T)(1.0 / pd);
-    }
-    const int n0 = (nv + G0 - 1) / G0;
-    int n0w = valid ? n0 : 0;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) n0w = max(n0w, __shfl_xor_sync(0xffffffffu, n0w, off));
-
-    // ---- the warp's bounding spheres (super-segments and their level-1 segments)
-    if (!a.exact_all) {
-        for (int j = 0; j < kN0Max; ++j) {
-            const int sb = j * G0, se = min(sb + G0, nv);
-            bool has = valid && sb < nv;
-            T x = T(0), y = T(0), z = T(0);
-            if (has) {
-                const int64_t o = (int64_t)min(sb + G0 / 2, se - 1) * S + s;
-                x = P[o];
-                y = P[plane + o];
-                z = P[2 * plane + o];
-            }
-            const float4 sp = warp_sphere<T>(has, x, y, z, (T)a.R0);
-            if (lane == 0) sph0[j] = sp;
-            for (int m = 0; m < N1; ++m) {
-                const int st = sb + m * G1;
-                const bool h1 = has && st < se;
-                T x1 = T(0), y1 = T(0), z1 = T(0);
-                if (h1) {
-                    const int64_t o = (int64_t)min(st + G1 / 2, min(st + G1, se) - 1) * S + s;
-                    x1 = P[o];
-                    y1 = P[plane + o];
-                    z1 = P[2 * plane + o];
-                }
-                const float4 sp1 = warp_sphere<T>(h1, x1, y1, z1, (T)a.R1);
-                if (lane == 0) sph1[j * kN1Max + m] = sp1;
-            }
-        }
-    }
+    const Group<T> gr = load_group<T>(a, (int64_t)blockIdx.x * kWarps + warp, lane);
+    if (!a.exact_all) build_spheres<T>(a, gr, lane, sph0, sph1);
 
     const int W = a.W;
     const int H = W > 0 ? a.offs[W] : 0;
@@ -237,9 +593,8 @@ __global__ void __launch_bounds__(kThreads, COMET_DCA_MINB) dca_kernel(F f, DcaA
     uint32_t parity = 0;
     bool any_timeout = false;
     int doff = 0, moff = 0;
-    __syncthreads();   // barrier initialised, spheres written
+    __syncthreads();   // barrier initialised
 
-    // hits: staged once per CTA when they fit
     if (hits_sm && H > 0) {
         const uint32_t bytes = stage_bytes<T>(Dg, H) + stage_bytes<uint8_t>(a.mask, H);
         if (tid == 0 && bytes > 0) {
@@ -248,12 +603,7 @@ __global__ void __launch_bounds__(kThreads, COMET_DCA_MINB) dca_kernel(F f, DcaA
         }
         doff = stage_issue<T>(dsm, Dg, H, bar, tid == 0);
         moff = stage_issue<uint8_t>(msm, a.mask, H, bar, tid == 0);
-        bool to = false;
-        if (bytes > 0) {
-            to = !mbar_wait(bar, parity, kWaitNs);
-            parity ^= 1u;
-        }
-        if (__syncthreads_or(to)) {
+        if (finish_stage(bar, parity, bytes)) {
             any_timeout = true;
             stage_fallback<T>(dsm, Dg, H);
             stage_fallback<uint8_t>(msm, a.mask, H);
@@ -263,11 +613,8 @@ __global__ void __launch_bounds__(kThreads, COMET_DCA_MINB) dca_kernel(F f, DcaA
 
     Acc<T> acc;
     int nin = 0, nunc = 0;
-    constexpr int kU = COMET_DCA_U2;
-
     for (int w0 = 0; w0 < W; w0 += kWireTile) {
         const int wn = min(kWireTile, W - w0);
-        // ---- stage the wire tile
         uint32_t bytes = stage_bytes<int32_t>(a.offs + w0, wn + 1);
 #pragma unroll
         for (int r = 0; r < 6; ++r) bytes += stage_bytes<T>(Wg + (size_t)r * a.ldw + w0, wn);
@@ -280,12 +627,7 @@ __global__ void __launch_bounds__(kThreads, COMET_DCA_MINB) dca_kernel(F f, DcaA
         for (int r = 0; r < 6; ++r)
             woff[r] = stage_issue<T>(wrow + r * kWireCap, Wg + (size_t)r * a.ldw + w0, wn, bar, tid == 0);
         const int ooff = stage_issue<int32_t>(orow, a.offs + w0, wn + 1, bar, tid == 0);
-        bool to = false;
-        if (bytes > 0) {
-            to = !mbar_wait(bar, parity, kWaitNs);
-            parity ^= 1u;
-        }
-        if (__syncthreads_or(to)) {
+        if (finish_stage(bar, parity, bytes)) {
             any_timeout = true;
 #pragma unroll
             for (int r = 0; r < 6; ++r)
@@ -293,167 +635,30 @@ __global__ void __launch_bounds__(kThreads, COMET_DCA_MINB) dca_kernel(F f, DcaA
             stage_fallback<int32_t>(orow, a.offs + w0, wn + 1);
         }
         __syncthreads();
-        const T *wax = wrow + 0 * kWireCap + woff[0];
-        const T *way = wrow + 1 * kWireCap + woff[1];
-        const T *waz = wrow + 2 * kWireCap + woff[2];
-        const T *wux = wrow + 3 * kWireCap + woff[3];
-        const T *wuy = wrow + 4 * kWireCap + woff[4];
-        const T *wuz = wrow + 5 * kWireCap + woff[5];
-        // ---- per wire: capture radius (largest unmasked drift + lambda; -1: no unmasked hit) and
-        // the wire frame
-        for (int i = tid; i < wn; i += kThreads) {
-            const int hb = orow[ooff + i], he = orow[ooff + i + 1];
-            T mr = T(-1);
-            for (int j = hb; j < he; ++j) {
-                const bool m = hits_sm ? msm[moff + j] != 0 : a.mask[j] != 0;
-                const T r = hits_sm ? dsm[doff + j] : Dg[j];
-                if (!m && r > mr) mr = r;
-            }
-            capv[i] = mr >= T(0) ? mr + lam : T(-1);
-            const WireFrame<T> fr = wire_frame<T>(wax[i], way[i], waz[i], wux[i], wuy[i], wuz[i]);
-            frm[0 * kWireTile + i] = fr.vx;
-            frm[1 * kWireTile + i] = fr.vy;
-            frm[2 * kWireTile + i] = fr.vz;
-            frm[3 * kWireTile + i] = fr.wx;
-            frm[4 * kWireTile + i] = fr.wy;
-            frm[5 * kWireTile + i] = fr.wz;
-            frm[6 * kWireTile + i] = fr.av;
-            frm[7 * kWireTile + i] = fr.aw;
-        }
+        Tile<T> tl;
+        tl.ax = wrow + 0 * kWireCap + woff[0];
+        tl.ay = wrow + 1 * kWireCap + woff[1];
+        tl.az = wrow + 2 * kWireCap + woff[2];
+        tl.ux = wrow + 3 * kWireCap + woff[3];
+        tl.uy = wrow + 4 * kWireCap + woff[4];
+        tl.uz = wrow + 5 * kWireCap + woff[5];
+        tl.frm = frm;
+        tl.fs = kWireTile;
+        tl.cap = capv;
+        tl.offs = orow + ooff;
+        tl.dsm = hits_sm ? dsm + doff : Dg;
+        tl.msm = hits_sm ? msm + moff : a.mask;
+        tl.w0 = w0;
+        tl.wn = wn;
+        for (int i = tid; i < wn; i += kThreads) tile_wire_setup<T>(tl, i, (T)a.lambda, capv, frm);
         __syncthreads();
-
-        for (int base = 0; base < wn; base += 32) {
-            const int clen = min(32, wn - base);
-            // lane t: which super-segments can bring wire base + t within its capture radius
-            uint32_t mask0 = 0;
-            if (lane < clen) {
-                const int iw = base + lane;
-                const T capw = capv[iw];
-                if (a.exact_all) {
-                    mask0 = 1u;
-                } else if (capw >= T(0)) {
-                    const T lim = capw + half_rec;
-                    for (int j = 0; j < n0w; ++j)
-                        if (sphere_within<T>(sph0[j], frm[0 * kWireTile + iw], frm[1 * kWireTile + iw],
-                                             frm[2 * kWireTile + iw], frm[6 * kWireTile + iw],
-                                             frm[3 * kWireTile + iw], frm[4 * kWireTile + iw],
-                                             frm[5 * kWireTile + iw], frm[7 * kWireTile + iw], wax[iw],
-                                             way[iw], waz[iw], wux[iw], wuy[iw], wuz[iw], lim))
-                            mask0 |= 1u << j;
-                }
-            }
-            for (int t = 0; t < clen; ++t) {
-                const int ii = base + t;
-                const uint32_t m0 = __shfl_sync(0xffffffffu, mask0, t);
-                const T cap = capv[ii];
-                if (m0 == 0u) {
-                    // beyond every seed's capture radius (or no unmasked hit): lambda^2 if in the sum
-                    if (valid && cap >= T(0)) acc.add(lam * lam);
-                    continue;
-                }
-                const T ax = wax[ii], ay = way[ii], az = waz[ii];
-                const T ux = wux[ii], uy = wuy[ii], uz = wuz[ii];
-                const T fvx = frm[0 * kWireTile + ii], fvy = frm[1 * kWireTile + ii],
-                        fvz = frm[2 * kWireTile + ii], fwx = frm[3 * kWireTile + ii],
-                        fwy = frm[4 * kWireTile + ii], fwz = frm[5 * kWireTile + ii],
-                        fav = frm[6 * kWireTile + ii], faw = frm[7 * kWireTile + ii];
-#if COMET_SEARCH_FRAME
-                auto sd2 = [&](T x, T y, T z) {
-                    return frame_dist2<T>(x, y, z, fvx, fvy, fvz, fav, fwx, fwy, fwz, faw);
-                };
-#else
-                auto sd2 = [&](T x, T y, T z) { return line_dist2<T>(x, y, z, ax, ay, az, ux, uy, uz); };
-#endif
-                const bool want = valid && (cap >= T(0) || a.exact_all);
-                const T capth = a.exact_all ? T(INFINITY) : cap + half_rec;
-                T bd = T(INFINITY);
-                int bk = 0x7fffffff;
-                // scans states [k0, k1) of this lane's seed
-                auto scan = [&](int k0, int k1, int span) {
-                    for (int t0 = 0; t0 < span; t0 += kU) {
-                        T xs[kU], ys[kU], zs[kU];
-#pragma unroll
-                        for (int u = 0; u < kU; ++u) {
-                            const int k = k0 + t0 + u;
-                            xs[u] = ys[u] = zs[u] = T(0);
-                            if (want && k < k1) {
-                                const int64_t o = (int64_t)k * S + s;
-                                xs[u] = P[o];
-                                ys[u] = P[plane + o];
-                                zs[u] = P[2 * plane + o];
-                            }
-                        }
-#pragma unroll
-                        for (int u = 0; u < kU; ++u) {
-                            const int k = k0 + t0 + u;
-                            if (want && k < k1) lex_min<T>(bd, bk, sd2(xs[u], ys[u], zs[u]), k);
-                        }
-                    }
-                };
-                if (a.exact_all) {
-                    int nvw = nv;
-#pragma unroll
-                    for (int off = 16; off > 0; off >>= 1) nvw = max(nvw, __shfl_xor_sync(0xffffffffu, nvw, off));
-                    scan(0, nv, nvw);
-                } else {
-                    uint32_t u0 = m0;
-                    while (u0) {
-                        const int j = __ffs(u0) - 1;
-                        u0 &= u0 - 1;
-                        // lane m tests level-1 segment m of super-segment j
-                        const bool hit1 = lane < N1 &&
-                                          sphere_within<T>(sph1[j * kN1Max + lane], fvx, fvy, fvz, fav,
-                                                           fwx, fwy, fwz, faw, ax, ay, az, ux, uy, uz,
-                                                           capth);
-                        const uint32_t u1 = __ballot_sync(0xffffffffu, hit1);
-                        if (u1) {
-                            // one contiguous range from the first to the last candidate level-1
-                            // segment (a superset of the candidates; their loads go out together)
-                            const int m_lo = __ffs(u1) - 1, m_hi = 31 - __clz(u1);
-                            const int sb = j * G0, se = min(sb + G0, nv);
-                            const int k0 = sb + m_lo * G1;
-                            scan(k0, min(sb + (m_hi + 1) * G1, se), (m_hi - m_lo + 1) * G1);
-                        }
-                    }
-                }
-
-                // refinement from the closest recorded state (only when it can matter)
-                const bool refine = want && bk != 0x7fffffff && (a.exact_all || sqrt(bd) <= capth);
-                T D = T(INFINITY);
-                if (refine) {
-                    T yv[6];
-                    const int64_t o = (int64_t)bk * S + s;
-#pragma unroll
-                    for (int cc = 0; cc < 6; ++cc) yv[cc] = P[cc * plane + o];
-                    const int conv = refine_dca<T, F>(f, c, ip, yv, ax, ay, az, ux, uy, uz, tol,
-                                                      a.max_iter, h_rec, D);
-                    if (cap >= T(0)) nunc += 1 - conv;
-                    if (a.dca_out) ((T *)a.dca_out)[(int64_t)(w0 + ii) * S + s] = D;
-                }
-                if (valid && cap >= T(0)) {
-                    T emin = T(INFINITY);
-                    if (refine) {
-                        const int hb = orow[ooff + ii], he = orow[ooff + ii + 1];
-                        for (int j = hb; j < he; ++j) {
-                            const bool m = hits_sm ? msm[moff + j] != 0 : a.mask[j] != 0;
-                            if (m) continue;
-                            const T r = hits_sm ? dsm[doff + j] : Dg[j];
-                            const T e = fabs(D - r);
-                            emin = e < emin ? e : emin;
-                        }
-                    }
-                    const T d = emin < lam ? emin : lam;
-                    nin += emin < lam ? 1 : 0;
-                    acc.add(d * d);
-                }
-            }
-        }
+        group_wires<T, F>(f, a, gr, tl, sph0, sph1, lane, acc, nin, nunc);
         if (w0 + kWireTile < W) __syncthreads();   // tile consumed before the next staging
     }
 
-    if (valid) {
-        ((T *)a.rss)[s] = acc.value();
-        a.n_in[s] = nin;
+    if (gr.valid) {
+        ((T *)a.rss)[gr.s] = acc.value();
+        a.n_in[gr.s] = nin;
     }
     if (a.n_unconv) {
         int t = nunc;
@@ -463,20 +668,49 @@ __global__ void __launch_bounds__(kThreads, COMET_DCA_MINB) dca_kernel(F f, DcaA
     }
     if (any_timeout) {
         if (tid == 0 && a.status) atomicOr(a.status, 1);
-        // no bulk copy may still be writing into shared memory when the CTA exits
         mbar_wait(bar, parity ^ 1u, kWaitNs);
     }
+}
+
+static int sm_count()
+{
+    static int n = [] {
+        int dev = 0, v = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        return v > 0 ? v : 1;
+    }();
+    return n;
 }
 
 template <typename T, class F>
 static cudaError_t dca_launch(const F &fld, const DcaArgs &a, cudaStream_t st)
 {
+    if (a.W <= kPersistMaxW && a.counter) {
+        const PLayout L = p_layout(a.W, (int)sizeof(T));
+        cudaError_t e = cudaFuncSetAttribute(dca_persistent_kernel<T, F>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dca_persistent_kernel<T, F>,
+                                                          kThreads, L.total);
+        if (e != cudaSuccess) return e;
+        per_sm = per_sm < 1 ? 1 : per_sm;
+        const int64_t groups = (a.S + 31) / 32;
+        int64_t nb = (groups + kWarps - 1) / kWarps;
+        const int64_t cap = (int64_t)per_sm * sm_count();
+        nb = nb < cap ? nb : cap;
+        e = cudaMemsetAsync(a.counter, 0, sizeof(int32_t), st);
+        if (e != cudaSuccess) return e;
+        dca_persistent_kernel<T, F><<<(unsigned)nb, kThreads, L.total, st>>>(fld, a);
+        return cudaGetLastError();
+    }
     using L = Smem<T>;
     static const cudaError_t attr = cudaFuncSetAttribute(
-        dca_kernel<T, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::total);
+        dca_tiled_kernel<T, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::total);
     if (attr != cudaSuccess) return attr;
     const int64_t nb = (a.S + kThreads - 1) / kThreads;
-    dca_kernel<T, F><<<(unsigned)nb, kThreads, L::total, st>>>(fld, a);
+    dca_tiled_kernel<T, F><<<(unsigned)nb, kThreads, L::total, st>>>(fld, a);
     return cudaGetLastError();
 }
 

@@ -18,9 +18,37 @@ namespace comet {
 // for pt when only 2 divides it) numbered row-major, nodes inside a block row-major.  Consecutive
 // seeds are therefore neighbours in all four dimensions, so the 32 lanes of a warp follow similar
 // tracks in the DCA kernel.
+// Node value i of a dimension with n nodes (computed in double with rounded operations only, so
+// that it equals the oracle's value).
+__device__ __forceinline__ double lattice_node(double centre, double half_width, int n, int i)
+{
+    return n == 1 ? centre
+                  : __dadd_rn(centre, __dmul_rn(half_width, __dadd_rn(__ddiv_rn(2.0 * i, (double)(n - 1)), -1.0)));
+}
+
+constexpr int kLatTab = 512;   // node values tabulated per block when the four counts sum to <= this
+
 template <typename T>
 __global__ void __launch_bounds__(256) lattice_kernel(LatArgs a, T *__restrict__ seeds, int64_t S)
 {
+    // every node value (and cos / sin of every phi node) once per block, in shared memory
+    __shared__ double nodes[kLatTab];
+    __shared__ double cphi[kLatTab], sphi[kLatTab];
+    int off[4];
+    off[0] = 0;
+    for (int d = 1; d < 4; ++d) off[d] = off[d - 1] + a.counts[d - 1];
+    const int tot = off[3] + a.counts[3];
+    const bool tab = tot <= kLatTab;
+    if (tab) {
+        for (int i = threadIdx.x; i < tot; i += blockDim.x) {
+            const int d = i < off[1] ? 0 : (i < off[2] ? 1 : (i < off[3] ? 2 : 3));
+            const int k = i - off[d];
+            const double v = lattice_node(a.centre[d], a.half_width[d], a.counts[d], k);
+            nodes[i] = v;
+            if (d == 1) sincos(v, &sphi[k], &cphi[k]);
+        }
+        __syncthreads();
+    }
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= S) return;
     int b[4];
@@ -39,17 +67,17 @@ __global__ void __launch_bounds__(256) lattice_kernel(LatArgs a, T *__restrict__
         blk /= nb;
         ii[d] = i_bl * b[d] + i_in;
     }
-    double v[4];
+    double v[4], sp, cp;
+    if (tab) {
 #pragma unroll
-    for (int d = 0; d < 4; ++d) {
-        const int n = a.counts[d];
-        v[d] = n == 1 ? a.centre[d]
-                      : __dadd_rn(a.centre[d],
-                                  __dmul_rn(a.half_width[d],
-                                            __dadd_rn(__ddiv_rn(2.0 * ii[d], (double)(n - 1)), -1.0)));
+        for (int d = 0; d < 4; ++d) v[d] = nodes[off[d] + ii[d]];
+        sp = sphi[ii[1]];
+        cp = cphi[ii[1]];
+    } else {
+#pragma unroll
+        for (int d = 0; d < 4; ++d) v[d] = lattice_node(a.centre[d], a.half_width[d], a.counts[d], ii[d]);
+        sincos(v[1], &sp, &cp);
     }
-    double sp, cp;
-    sincos(v[1], &sp, &cp);
     seeds[0 * S + s] = (T)a.vx;
     seeds[1 * S + s] = (T)a.vy;
     seeds[2 * S + s] = (T)v[0];
