@@ -135,16 +135,23 @@ comet_status comet_scan_lattice(comet_ctx *ctx, comet_dtype dtype, const comet_l
  *   points   out, SoA [6][n_rec][S] T: recorded state k of seed s is points[c][k][s].  Entries past
  *            n_valid[s] are left unwritten.
  *   n_valid  out, [S] int32: number of recorded states of each seed (1 .. n_rec).
+ *   bounds   optional out (NULL to skip), [ceil(S/32)][200][4] float32, 16-byte aligned: search
+ *            bounds for comet_scan_dca with the same params -- for each group of 32 consecutive
+ *            seeds, the bounding spheres (x, y, z, radius) of its track segments (8 super-segments,
+ *            24 level-1 segments each).  Writing them costs a few percent of this call and saves
+ *            comet_scan_dca from rebuilding them.
  * One thread extrapolates one seed with fixed-step RK4.  The FP32 path carries each state component
  * as an unevaluated float pair (a compensated sum), so that 6,500 steps stay within a few um of FP64;
  * the recorded value is the leading float. */
 comet_status comet_scan_propagate(comet_ctx *ctx, comet_dtype dtype, const comet_field *field,
                                   const comet_scan_params *params, const void *seeds,
                                   const int8_t *charge, int64_t S, void *points, int32_t *n_valid,
-                                  comet_stream stream);
+                                  void *bounds, comet_stream stream);
 
 /* ---- a4-a6: DCA finding and RSS (Algorithm 2, Eq. 1, Sec. 2.2.2) --------------------------------
  *   points, n_valid, charge, S   as written by comet_scan_propagate with the same params.
+ *   bounds       optional (NULL: built here), the bounds comet_scan_propagate wrote for these
+ *                points with the same params.
  *   wires        SoA [6][ldw] T: (a_x, a_y, a_z, u_x, u_y, u_z) of wire i in column i: a point on
  *                the wire and its unit direction.  ldw >= W is the row stride in elements.
  *   W            number of wires (>= 0).  W = 0 gives rss = 0 and n_in = 0.
@@ -170,11 +177,12 @@ comet_status comet_scan_propagate(comet_ctx *ctx, comet_dtype dtype, const comet
  * the wire and d the distance to the plane that contains the wire axis with normal n, until
  * |d| < tol (Algorithm 2's loop; the Newton step length is the reading of "the distance").
  * The closest recorded state is found exactly by a bounded search over the recorded states (recorded
- * states one recording interval apart are at most that arc length apart). */
+ * states one recording interval apart are at most that arc length apart).  The kernel takes a
+ * device work counter from the context: dca calls of one context must not overlap on the GPU. */
 comet_status comet_scan_dca(comet_ctx *ctx, comet_dtype dtype, const comet_field *field,
                             const comet_scan_params *params, const void *points,
                             const int32_t *n_valid, const int8_t *charge, int64_t S,
-                            const void *wires, int32_t W, int32_t ldw, const int32_t *hit_offsets,
+                            const void *bounds, const void *wires, int32_t W, int32_t ldw, const int32_t *hit_offsets,
                             const void *drift, const uint8_t *hit_mask, void *rss, int32_t *n_in,
                             void *dca_out, int32_t *n_unconverged, comet_stream stream);
 

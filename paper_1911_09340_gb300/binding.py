@@ -58,9 +58,9 @@ SIGNATURES = {
     "comet_last_error": [],
     "comet_scan_lattice": [_vp, C.c_int, C.POINTER(_Lattice), _vp, _vp, _i64, _vp],
     "comet_scan_propagate": [_vp, C.c_int, C.POINTER(_Field), C.POINTER(_Params), _vp, _vp, _i64,
-                             _vp, _vp, _vp],
+                             _vp, _vp, _vp, _vp],
     "comet_scan_dca": [_vp, C.c_int, C.POINTER(_Field), C.POINTER(_Params), _vp, _vp, _vp, _i64,
-                       _vp, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
+                       _vp, _vp, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "comet_scan_select": [_vp, C.c_int, _vp, _i64, _i32, _vp, _vp, _vp],
     "comet_scan_select_noalloc": [C.c_int, _vp, _i64, _i32, _vp, _vp, _vp],
     "comet_scan_classify": [_vp, C.c_int, C.POINTER(_Field), C.POINTER(_Params), _vp, _vp, _vp,
@@ -204,19 +204,28 @@ def comet_scan_lattice(ctx: Context, spec, seeds: torch.Tensor, charge: Optional
                                     _ptr(charge, torch.int8), seeds.shape[-1], _stream(stream)))
 
 
+BOUNDS_PER_GROUP = 200     # float4 bounding spheres per 32-seed group (8 + 8 * 24)
+
+
+def bounds_shape(S: int):
+    """Shape of the optional search-bounds tensor (float32) for S seeds."""
+    return ((S + 31) // 32, BOUNDS_PER_GROUP, 4)
+
+
 def comet_scan_propagate(ctx: Context, field: DeviceField, params: ScanParams, seeds, charge,
-                         points, n_valid, stream=None):
+                         points, n_valid, bounds=None, stream=None):
     dt = _dtype_code(seeds)
     S = seeds.shape[-1]
     f, p = field.c(), params.c()
     _check(lib().comet_scan_propagate(ctx.handle, dt, C.byref(f), C.byref(p), _ptr(seeds),
                                       _ptr(charge, torch.int8), S, _ptr(points, seeds.dtype),
-                                      _ptr(n_valid, torch.int32), _stream(stream)))
+                                      _ptr(n_valid, torch.int32), _ptr(bounds, torch.float32),
+                                      _stream(stream)))
 
 
 def comet_scan_dca(ctx: Context, field: DeviceField, params: ScanParams, points, n_valid, charge,
                    wires, hit_offsets, drift, hit_mask, rss, n_in, dca_out=None, n_unconverged=None,
-                   n_wires: Optional[int] = None, stream=None):
+                   n_wires: Optional[int] = None, bounds=None, stream=None):
     """``wires`` is [6][ldw]; the first ``n_wires`` columns (default: all) are the wires."""
     dt = _dtype_code(points)
     S = n_valid.shape[0]
@@ -225,7 +234,7 @@ def comet_scan_dca(ctx: Context, field: DeviceField, params: ScanParams, points,
     f, p = field.c(), params.c()
     _check(lib().comet_scan_dca(ctx.handle, dt, C.byref(f), C.byref(p), _ptr(points),
                                 _ptr(n_valid, torch.int32), _ptr(charge, torch.int8), S,
-                                _ptr(wires, points.dtype), W, ldw, _ptr(hit_offsets, torch.int32),
+                                _ptr(bounds, torch.float32), _ptr(wires, points.dtype), W, ldw, _ptr(hit_offsets, torch.int32),
                                 _ptr(drift, points.dtype), _ptr(hit_mask, torch.uint8),
                                 _ptr(rss, points.dtype), _ptr(n_in, torch.int32),
                                 _ptr(dca_out, points.dtype), _ptr(n_unconverged, torch.int32),

@@ -116,6 +116,29 @@ comet_status check_hits(comet_dtype dt, const void *wires, int32_t W, int32_t ld
 
 int n_rec_of(const comet_scan_params *p) { return p->n_steps / p->stride + 1; }
 
+// Segmentation and reaches of the closest-state search: identical for propagate (which writes the
+// segment bounding spheres) and dca (which reads them).  Consecutive recorded states are at most
+// stride*h apart along the track (|dx/ds| = |p|/P0 = 1 up to rounding); the margins cover the
+// rounding of the distances in the working precision.
+struct SearchGeometry {
+    int G0, G1;
+    double R0, R1, half_rec, h_rec;
+};
+
+SearchGeometry search_geometry(comet_dtype dtype, const comet_scan_params *p)
+{
+    SearchGeometry g;
+    comet::dca_segments(n_rec_of(p), &g.G0, &g.G1);
+    g.h_rec = p->h * p->stride;
+    const double margin = dtype == COMET_F32 ? 4e-6 : 1e-9;
+    g.R0 = (g.G0 / 2) * g.h_rec * (1.0 + 1e-4) + margin;
+    g.R1 = (g.G1 / 2) * g.h_rec * (1.0 + 1e-4) + margin;
+    g.half_rec = 0.5 * g.h_rec * (1.0 + 1e-4) + margin;
+    return g;
+}
+
+bool bounds_aligned(const void *b) { return b == nullptr || ((uintptr_t)b % 16) == 0; }
+
 } // namespace
 
 extern "C" {
@@ -210,7 +233,7 @@ comet_status comet_scan_lattice(comet_ctx *ctx, comet_dtype dtype, const comet_l
 comet_status comet_scan_propagate(comet_ctx *ctx, comet_dtype dtype, const comet_field *field,
                                   const comet_scan_params *params, const void *seeds,
                                   const int8_t *charge, int64_t S, void *points, int32_t *n_valid,
-                                  comet_stream stream)
+                                  void *bounds, comet_stream stream)
 {
     if (!ctx) return fail(COMET_ERR_INVALID_ARG, "ctx is NULL");
     CHECK(check_dtype(dtype));
@@ -219,11 +242,18 @@ comet_status comet_scan_propagate(comet_ctx *ctx, comet_dtype dtype, const comet
     if (S < 0) return fail(COMET_ERR_INVALID_ARG, "S must be >= 0");
     if (S == 0) return COMET_OK;
     if (!seeds || !charge || !points || !n_valid) return fail(COMET_ERR_INVALID_ARG, "seeds, charge, points and n_valid are required");
-    if (!aligned(seeds, esize(dtype)) || !aligned(points, esize(dtype)) || !aligned(n_valid, 4))
-        return fail(COMET_ERR_INVALID_ARG, "seeds/points/n_valid misaligned for their element type");
+    if (!aligned(seeds, esize(dtype)) || !aligned(points, esize(dtype)) || !aligned(n_valid, 4) ||
+        !bounds_aligned(bounds))
+        return fail(COMET_ERR_INVALID_ARG, "seeds/points/n_valid/bounds misaligned for their element type");
     DeviceGuard g(ctx->device);
     if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+    const SearchGeometry sg = search_geometry(dtype, params);
     comet::PropArgs a;
+    a.bounds = bounds;
+    a.G0 = sg.G0;
+    a.G1 = sg.G1;
+    a.R0 = sg.R0;
+    a.R1 = sg.R1;
     a.seeds = seeds;
     a.charge = charge;
     a.S = S;
@@ -243,7 +273,7 @@ comet_status comet_scan_propagate(comet_ctx *ctx, comet_dtype dtype, const comet
 comet_status comet_scan_dca(comet_ctx *ctx, comet_dtype dtype, const comet_field *field,
                             const comet_scan_params *params, const void *points,
                             const int32_t *n_valid, const int8_t *charge, int64_t S,
-                            const void *wires, int32_t W, int32_t ldw, const int32_t *hit_offsets,
+                            const void *bounds, const void *wires, int32_t W, int32_t ldw, const int32_t *hit_offsets,
                             const void *drift, const uint8_t *hit_mask, void *rss, int32_t *n_in,
                             void *dca_out, int32_t *n_unconverged, comet_stream stream)
 {
@@ -257,7 +287,7 @@ comet_status comet_scan_dca(comet_ctx *ctx, comet_dtype dtype, const comet_field
     if (!points || !n_valid || !charge || !rss || !n_in) return fail(COMET_ERR_INVALID_ARG, "points, n_valid, charge, rss and n_in are required");
     if (!aligned(points, esize(dtype)) || !aligned(rss, esize(dtype)) || !aligned(n_valid, 4) ||
         !aligned(n_in, 4) || (dca_out && !aligned(dca_out, esize(dtype))) ||
-        (n_unconverged && !aligned(n_unconverged, 4)))
+        (n_unconverged && !aligned(n_unconverged, 4)) || !bounds_aligned(bounds))
         return fail(COMET_ERR_INVALID_ARG, "an array is misaligned for its element type");
     DeviceGuard g(ctx->device);
     if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
@@ -282,15 +312,14 @@ comet_status comet_scan_dca(comet_ctx *ctx, comet_dtype dtype, const comet_field
     a.lambda = params->lambda;
     a.tol = params->tol;
     a.max_iter = params->max_iter;
-    comet::dca_segments(a.n_rec, &a.G0, &a.G1);
-    // consecutive recorded states are at most stride*h apart along the track (|dx/ds| = |p|/P0 = 1
-    // up to rounding); the margins cover the rounding of the distances in the working precision
-    const double h_rec = params->h * params->stride;
-    const double margin = dtype == COMET_F32 ? 4e-6 : 1e-9;
-    a.R0 = (a.G0 / 2) * h_rec * (1.0 + 1e-4) + margin;
-    a.R1 = (a.G1 / 2) * h_rec * (1.0 + 1e-4) + margin;
-    a.half_rec = 0.5 * h_rec * (1.0 + 1e-4) + margin;
-    a.h_rec = h_rec;
+    const SearchGeometry sg = search_geometry(dtype, params);
+    a.G0 = sg.G0;
+    a.G1 = sg.G1;
+    a.R0 = sg.R0;
+    a.R1 = sg.R1;
+    a.half_rec = sg.half_rec;
+    a.h_rec = sg.h_rec;
+    a.bounds = bounds;
     a.exact_all = dca_out != nullptr;
     cudaError_t e = comet::launch_dca(dtype, *field, a, (cudaStream_t)stream);
     return e == cudaSuccess ? COMET_OK : cuda_fail(e, "dca launch");

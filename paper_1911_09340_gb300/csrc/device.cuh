@@ -331,6 +331,42 @@ __device__ __forceinline__ int refine_dca(const F &f, T c, T ip, T y[6], T ax, T
 }
 
 // ------------------------------------------------------------------------------------------------
+// Bounding spheres of track segments (closest-state search)
+// ------------------------------------------------------------------------------------------------
+
+// The recorded states of a seed are cut into at most kN0Max super-segments of G0 states, each cut
+// into at most kN1Max level-1 segments of G1 states.  For every group of 32 consecutive seeds (one
+// warp) the search keeps one bounding sphere per segment: kBoundsPerGroup float4 (x, y, z, radius),
+// super-segment j at [j], level-1 segment (j, m) at [kN0Max + j * kN1Max + m]; radius < 0 marks a
+// segment no seed of the group has.
+constexpr int kN0Max = 8;
+constexpr int kN1Max = 24;
+constexpr int kBoundsPerGroup = kN0Max + kN0Max * kN1Max;
+
+// Centre index of a lane's segment [st, st + g) inside [.., end) (end = its last state + 1).
+__device__ __forceinline__ int segment_centre(int st, int g, int end) { return min(st + g / 2, min(st + g, end) - 1); }
+
+// The warp's bounding sphere of one segment: lanes with `has` hold their seed's segment centre
+// (x, y, z); the sphere is centred on the first such lane's centre, its radius is the largest
+// distance to any lane's centre plus `reach` (a state within g/2 recording intervals of a centre is
+// at most (g/2) h_rec from it along the track).  Rounded up so that it never shrinks; in double the
+// rounding of the centre to float is added.  Returns radius < 0 when no lane has the segment.
+template <typename T>
+__device__ __forceinline__ float4 warp_sphere(bool has, T x, T y, T z, T reach)
+{
+    const uint32_t hm = __ballot_sync(0xffffffffu, has);
+    if (hm == 0u) return make_float4(0.f, 0.f, 0.f, -1.f);
+    const int src = __ffs(hm) - 1;
+    const T cx = __shfl_sync(0xffffffffu, x, src), cy = __shfl_sync(0xffffffffu, y, src),
+            cz = __shfl_sync(0xffffffffu, z, src);
+    T d = has ? sqrt((x - cx) * (x - cx) + (y - cy) * (y - cy) + (z - cz) * (z - cz)) : T(0);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) d = fmax(d, __shfl_xor_sync(0xffffffffu, d, off));
+    const T extra = sizeof(T) == 8 ? T(2e-7) : T(0);
+    return make_float4((float)cx, (float)cy, (float)cz, (float)((d + reach + extra) * T(1.000001)));
+}
+
+// ------------------------------------------------------------------------------------------------
 // Shared-memory staging with the bulk-copy engine (cp.async.bulk + mbarrier)
 // ------------------------------------------------------------------------------------------------
 

@@ -23,12 +23,16 @@ struct PropArgs {
     int64_t S;
     void *points;
     int32_t *n_valid;
+    void *bounds;          // optional: segment bounding spheres per 32-seed group (float4)
     double h, zmin, zmax, rmax;
     int n_steps, stride, n_rec;
+    int G0, G1;            // segment sizes of the closest-state search
+    double R0, R1;         // segment reaches (m), margins included
 };
 
 struct DcaArgs {
     const void *points;
+    const void *bounds;    // optional: written by propagate with the same params
     const int32_t *n_valid;
     const int8_t *charge;
     int64_t S;

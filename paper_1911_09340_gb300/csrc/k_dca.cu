@@ -32,10 +32,10 @@
 // Tuning constants (compile-time): minimum resident CTAs per SM requested from the register
 // allocator, and how many states are loaded together.
 #ifndef COMET_DCA_MINB
-#define COMET_DCA_MINB 6
+#define COMET_DCA_MINB 8
 #endif
 #ifndef COMET_DCA_U2
-#define COMET_DCA_U2 8
+#define COMET_DCA_U2 4
 #endif
 
 namespace comet {
@@ -49,8 +49,6 @@ constexpr int kWireCap = kWireTile + 32;     // elements per staged row (room fo
 constexpr int kHitMax = 1024;                // hits staged in shared memory when H <= kHitMax
 constexpr int kHitCap = kHitMax + 32;
 constexpr uint64_t kWaitNs = 2000000000ull;  // bulk-copy wait limit (2 s)
-constexpr int kN0Max = 8;                    // super-segments per seed
-constexpr int kN1Max = 24;                   // level-1 segments per super-segment
 
 __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
@@ -120,24 +118,6 @@ struct Acc<double> {
 
 } // namespace
 
-// Builds the warp's bounding sphere of one segment: lane `has` holds its seed's segment centre
-// (x, y, z); the sphere is centred on the first such lane's centre.  Returns (cx, cy, cz, radius) in
-// every lane, radius < 0 when no lane of the warp has the segment.
-template <typename T>
-__device__ __forceinline__ float4 warp_sphere(bool has, T x, T y, T z, T reach)
-{
-    const uint32_t hm = __ballot_sync(0xffffffffu, has);
-    if (hm == 0u) return make_float4(0.f, 0.f, 0.f, -1.f);
-    const int src = __ffs(hm) - 1;
-    const T cx = __shfl_sync(0xffffffffu, x, src), cy = __shfl_sync(0xffffffffu, y, src),
-            cz = __shfl_sync(0xffffffffu, z, src);
-    T d = has ? sqrt((x - cx) * (x - cx) + (y - cy) * (y - cy) + (z - cz) * (z - cz)) : T(0);
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) d = fmax(d, __shfl_xor_sync(0xffffffffu, d, off));
-    // the float radius is rounded up by a relative 1e-6 so that it never shrinks
-    return make_float4((float)cx, (float)cy, (float)cz, (float)((d + reach) * T(1.000001)));
-}
-
 template <typename T>
 __device__ __forceinline__ bool sphere_within(const float4 &sp, T fvx, T fvy, T fvz, T fav, T fwx,
                                               T fwy, T fwz, T faw, T ax, T ay, T az, T ux, T uy,
@@ -194,8 +174,22 @@ __device__ __forceinline__ Group<T> load_group(const DcaArgs &a, int64_t g, int 
 // (sph1[j * kN1Max + m]), written by lane 0.
 template <typename T>
 __device__ __forceinline__ void build_spheres(const DcaArgs &a, const Group<T> &gr, int lane,
-                                              float4 *sph0, float4 *sph1)
+                                              float4 *sph0, float4 *sph1, int64_t g)
 {
+    if (g * 32 >= a.S) return;   // no seed in this group: nothing will be searched
+    if (a.bounds) {
+        // written by comet_scan_propagate: copy this group's table into the warp's slot
+        const float4 *src = (const float4 *)a.bounds + g * kBoundsPerGroup;
+        for (int i = lane; i < kBoundsPerGroup; i += 32) {
+            const float4 v = __ldg(src + i);
+            if (i < kN0Max)
+                sph0[i] = v;
+            else
+                sph1[i - kN0Max] = v;
+        }
+        __syncwarp();
+        return;
+    }
     const T *__restrict__ P = (const T *)a.points;
     const int64_t S = a.S;
     const int64_t plane = (int64_t)a.n_rec * S;
@@ -538,7 +532,7 @@ __global__ void __launch_bounds__(kThreads, COMET_DCA_MINB) dca_persistent_kerne
         g = __shfl_sync(0xffffffffu, g, 0);
         if ((int64_t)g >= n_groups) break;
         const Group<T> gr = load_group<T>(a, (int64_t)g, lane);
-        if (!a.exact_all) build_spheres<T>(a, gr, lane, sph0, sph1);
+        if (!a.exact_all) build_spheres<T>(a, gr, lane, sph0, sph1, (int64_t)g);
         Acc<T> acc;
         int nin = 0;
         group_wires<T, F>(f, a, gr, tl, sph0, sph1, lane, acc, nin, nunc);
@@ -584,8 +578,9 @@ __global__ void __launch_bounds__(kThreads, COMET_DCA_MINB) dca_tiled_kernel(F f
     const T *__restrict__ Dg = (const T *)a.drift;
 
     if (tid == 0) mbar_init(bar, 1);
-    const Group<T> gr = load_group<T>(a, (int64_t)blockIdx.x * kWarps + warp, lane);
-    if (!a.exact_all) build_spheres<T>(a, gr, lane, sph0, sph1);
+    const int64_t g = (int64_t)blockIdx.x * kWarps + warp;
+    const Group<T> gr = load_group<T>(a, g, lane);
+    if (!a.exact_all) build_spheres<T>(a, gr, lane, sph0, sph1, g);
 
     const int W = a.W;
     const int H = W > 0 ? a.offs[W] : 0;

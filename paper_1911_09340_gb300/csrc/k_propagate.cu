@@ -5,7 +5,10 @@
 // warp store 32 consecutive values of one component: full 128-byte lines).  In a uniform axial field
 // the RK4 step is applied as its exact linear map (device.cuh), with the coefficients of the seed
 // computed once in double.  Steps after the last recorded state (n_steps not a multiple of stride)
-// cannot change any output and are not taken.  The FP32 path keeps
+// cannot change any output and are not taken.  Optionally the kernel also writes the bounding
+// spheres of the track segments of each group of 32 consecutive seeds (one warp), which the DCA
+// kernel's closest-state search uses: the 32 lanes record state r together, so a segment's sphere
+// is one warp reduction at the moment its centre state is recorded.  The FP32 path keeps
 // every state component as an unevaluated float pair (hi, lo) updated with TwoSum, so that the
 // rounding of 6,500 steps does not accumulate (plain FP32 drifts ~0.1 mm over three turns; the pair
 // stays within ~1 um of FP64).  The RK4 stages read the leading float only.
@@ -93,108 +96,161 @@ __device__ __forceinline__ bool outside_region(T x, T y, T z, T zmin, T zmax, T 
     return z < zmin || z > zmax || x * x + y * y > rmax2;
 }
 
-template <typename T, class F>
+// One recording interval (stride RK4 steps) of one seed.  FP32 in an axial field: the increments
+// of the interval are summed in small accumulators (|acc| <= stride mm, stride * 0.3 MeV/c: their
+// rounding is negligible); each step's map reads p = p_hi + acc_p; once per interval the
+// accumulators go into the compensated (hi, lo) state.  pz is constant in an axial field.
+// STRIDE > 0 fixes the number of steps at compile time (fully unrolled); 0 takes a.stride.
+template <typename T, class F, int STRIDE>
+__device__ __forceinline__ void advance_interval(const F &f, const PropArgs &a, const AxialStep<T> &ks,
+                                                 T c, T ip, T h, T y[6], float lo[6])
+{
+    const int stride = STRIDE > 0 ? STRIDE : a.stride;
+    if constexpr (sizeof(T) == 4 && F::kAxial) {
+        float ax0 = 0.f, ax1 = 0.f, ax2 = 0.f, ap0 = 0.f, ap1 = 0.f;
+#pragma unroll
+        for (int st = 0; st < (STRIDE > 0 ? STRIDE : 1); ++st) {
+            const float px = y[3] + ap0, py = y[4] + ap1;
+            ax0 += ks.c * px + ks.d * py;
+            ax1 += ks.c * py - ks.d * px;
+            ax2 += ks.dz;
+            ap0 += ks.am1 * px + ks.b * py;
+            ap1 += ks.am1 * py - ks.b * px;
+        }
+        if constexpr (STRIDE == 0) {
+            for (int st = 1; st < stride; ++st) {
+                const float px = y[3] + ap0, py = y[4] + ap1;
+                ax0 += ks.c * px + ks.d * py;
+                ax1 += ks.c * py - ks.d * px;
+                ax2 += ks.dz;
+                ap0 += ks.am1 * px + ks.b * py;
+                ap1 += ks.am1 * py - ks.b * px;
+            }
+        }
+        two_sum_add(y[0], lo[0], ax0);
+        two_sum_add(y[1], lo[1], ax1);
+        two_sum_add(y[2], lo[2], ax2);
+        two_sum_add(y[3], lo[3], ap0);
+        two_sum_add(y[4], lo[4], ap1);
+    } else if constexpr (sizeof(T) == 4) {
+        for (int st = 0; st < stride; ++st) {
+            float inc[6];
+            rk4_increment<float, F>(f, c, ip, y, h, inc);
+#pragma unroll
+            for (int i = 0; i < 6; ++i) two_sum_add(y[i], lo[i], inc[i]);
+        }
+    } else {
+        for (int st = 0; st < stride; ++st) {
+            T inc[6];
+            if constexpr (F::kAxial)
+                axial_increment<T>(ks, y, inc);
+            else
+                rk4_increment<T, F>(f, c, ip, y, h, inc);
+#pragma unroll
+            for (int i = 0; i < 6; ++i) y[i] += inc[i];
+        }
+    }
+}
+
+template <typename T, class F, int STRIDE>
 __global__ void __launch_bounds__(128) propagate_kernel(F f, PropArgs a)
 {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= a.S) return;
+    const int lane = threadIdx.x & 31;
+    const bool valid = s < a.S;
+    const bool wb = a.bounds != nullptr;   // whole warps then stay in the loop (warp reductions)
+    if (!valid && !wb) return;
+    // a warp with no seed at all (past the end) has no bounds entry: it leaves as a whole
+    if ((s & ~(int64_t)31) >= a.S) return;
     const int64_t S = a.S;
     const T *__restrict__ seeds = (const T *)a.seeds;
     T *__restrict__ pts = (T *)a.points;
     const int64_t plane = (int64_t)a.n_rec * S;
+    const int n_rec = a.n_rec;
 
-    T y[6];
+    T y[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+    int q = 0;
+    if (valid) {
 #pragma unroll
-    for (int c = 0; c < 6; ++c) y[c] = seeds[c * S + s];
-    const int q = a.charge[s];
-    const double pd = sqrt((double)y[3] * y[3] + (double)y[4] * y[4] + (double)y[5] * y[5]);
+        for (int c = 0; c < 6; ++c) y[c] = seeds[c * S + s];
+        q = a.charge[s];
+    }
+    const double pd = valid ? sqrt((double)y[3] * y[3] + (double)y[4] * y[4] + (double)y[5] * y[5]) : 1.0;
     const T c = (T)(kKappa * q / pd);
     const T ip = (T)(1.0 / pd);
     const T h = (T)a.h;
     const T zmin = (T)a.zmin, zmax = (T)a.zmax, rmax2 = (T)(a.rmax * a.rmax);
+    const T R0 = (T)a.R0, R1 = (T)a.R1;
+    // uniform axial field: the step's coefficients are fixed per seed (computed in double)
+    AxialStep<T> ks{};
+    if constexpr (F::kAxial) {
+        const double w = kKappa * q * (double)f.bz / pd;
+        const double t = a.h * w, t2 = t * t, hp = a.h / pd;
+        ks.am1 = (T)(t2 * (-0.5 + t2 / 24.0));
+        ks.b = (T)(t * (1.0 - t2 / 6.0));
+        ks.c = (T)(hp * (1.0 - t2 / 6.0));
+        ks.d = (T)(hp * t * (0.5 - t2 / 24.0));
+        ks.dz = (T)(hp * (double)y[5]);
+    }
+    float lo[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // FP32: low words of the compensated state
 
+    // Bounding spheres of the segments whose centre is the state just recorded (see device.cuh);
+    // lanes that stopped earlier contribute their last recorded state if the segment holds it.
+    // The next centres are tracked incrementally.
+    float4 *tab = wb ? (float4 *)a.bounds + (s >> 5) * kBoundsPerGroup : nullptr;
+    int last_k = 0;
+    const int G0 = a.G0, G1 = a.G1;
+    int j1 = 0, m1 = 0, st1 = 0, se1 = min(G0, n_rec);   // current level-1 segment
+    int c1 = segment_centre(0, G1, se1);
+    int j0 = 0, sb0 = 0;                                 // current super-segment
+    int c0 = segment_centre(0, G0, se1);
+
+    if (wb) {
+        for (int i = lane; i < kBoundsPerGroup; i += 32) tab[i] = make_float4(0.f, 0.f, 0.f, -1.f);
+        __syncwarp();
+    }
+    if (valid) {
 #pragma unroll
-    for (int cc = 0; cc < 6; ++cc) pts[cc * plane + s] = y[cc];
+        for (int cc = 0; cc < 6; ++cc) pts[cc * plane + s] = y[cc];
+    }
     int n = 1;
-    if (!outside_region<T>(y[0], y[1], y[2], zmin, zmax, rmax2)) {
-        int since = 0;
-        // uniform axial field: the step's coefficients are fixed per seed (computed in double)
-        AxialStep<T> ks{};
-        if constexpr (F::kAxial) {
-            const double w = kKappa * q * (double)f.bz / pd;
-            const double t = a.h * w, t2 = t * t, hp = a.h / pd;
-            ks.am1 = (T)(t2 * (-0.5 + t2 / 24.0));
-            ks.b = (T)(t * (1.0 - t2 / 6.0));
-            ks.c = (T)(hp * (1.0 - t2 / 6.0));
-            ks.d = (T)(hp * t * (0.5 - t2 / 24.0));
-            ks.dz = (T)(hp * (double)y[5]);
+    bool active = valid && !outside_region<T>(y[0], y[1], y[2], zmin, zmax, rmax2);
+    for (int r = 0; r < n_rec; ++r) {
+        if (r > 0 && active) {
+            advance_interval<T, F, STRIDE>(f, a, ks, c, ip, h, y, lo);
+            const int64_t o = (int64_t)r * S + s;
+#pragma unroll
+            for (int cc = 0; cc < 6; ++cc) pts[cc * plane + o] = y[cc];
+            n = r + 1;
+            last_k = r;
+            if (outside_region<T>(y[0], y[1], y[2], zmin, zmax, rmax2)) active = false;
         }
-        if constexpr (sizeof(T) == 4 && F::kAxial) {
-            // FP32, axial field: the increments of one recording interval are summed in small
-            // accumulators (|acc| <= stride mm / stride*0.3 MeV/c, so their rounding is negligible);
-            // each step's map reads p = p_hi + acc_p; once per interval the accumulators are added
-            // to the compensated (hi, lo) state with TwoSum.  pz is constant and is not updated.
-            float lo[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-            const int n_rec = a.n_rec;
-            for (int r = 1; r < n_rec; ++r) {
-                float ax0 = 0.f, ax1 = 0.f, ax2 = 0.f, ap0 = 0.f, ap1 = 0.f;
-#pragma unroll 4
-                for (int st = 0; st < a.stride; ++st) {
-                    const float px = y[3] + ap0, py = y[4] + ap1;
-                    ax0 += ks.c * px + ks.d * py;
-                    ax1 += ks.c * py - ks.d * px;
-                    ax2 += ks.dz;
-                    ap0 += ks.am1 * px + ks.b * py;
-                    ap1 += ks.am1 * py - ks.b * px;
+        if (wb) {
+            if (r == c1) {
+                const float4 sp = warp_sphere<T>(valid && last_k >= st1, y[0], y[1], y[2], R1);
+                if (lane == 0) tab[kN0Max + j1 * kN1Max + m1] = sp;
+                ++m1;
+                st1 += G1;
+                if (st1 >= se1) {
+                    ++j1;
+                    m1 = 0;
+                    st1 = j1 * G0;
+                    se1 = min(st1 + G0, n_rec);
                 }
-                two_sum_add(y[0], lo[0], ax0);
-                two_sum_add(y[1], lo[1], ax1);
-                two_sum_add(y[2], lo[2], ax2);
-                two_sum_add(y[3], lo[3], ap0);
-                two_sum_add(y[4], lo[4], ap1);
-                const int64_t o = (int64_t)n * S + s;
-#pragma unroll
-                for (int cc = 0; cc < 6; ++cc) pts[cc * plane + o] = y[cc];
-                ++n;
-                if (outside_region<T>(y[0], y[1], y[2], zmin, zmax, rmax2)) break;
+                c1 = st1 < n_rec ? segment_centre(st1, G1, se1) : 0x7fffffff;
             }
-        } else if constexpr (sizeof(T) == 4) {
-            float lo[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            for (int step = 1; step <= a.n_steps; ++step) {
-                float inc[6];
-                rk4_increment<float, F>(f, c, ip, y, h, inc);
-#pragma unroll
-                for (int i = 0; i < 6; ++i) two_sum_add(y[i], lo[i], inc[i]);
-                if (++since == a.stride) {
-                    since = 0;
-                    const int64_t o = (int64_t)n * S + s;
-#pragma unroll
-                    for (int cc = 0; cc < 6; ++cc) pts[cc * plane + o] = y[cc];
-                    ++n;
-                    if (outside_region<T>(y[0], y[1], y[2], zmin, zmax, rmax2)) break;
-                }
+            if (r == c0) {
+                const float4 sp = warp_sphere<T>(valid && last_k >= sb0, y[0], y[1], y[2], R0);
+                if (lane == 0) tab[j0] = sp;
+                ++j0;
+                sb0 += G0;
+                c0 = sb0 < n_rec ? segment_centre(sb0, G0, min(sb0 + G0, n_rec)) : 0x7fffffff;
             }
-        } else {
-            for (int step = 1; step <= a.n_steps; ++step) {
-                T inc[6];
-                if constexpr (F::kAxial)
-                    axial_increment<T>(ks, y, inc);
-                else
-                    rk4_increment<T, F>(f, c, ip, y, h, inc);
-#pragma unroll
-                for (int i = 0; i < 6; ++i) y[i] += inc[i];
-                if (++since == a.stride) {
-                    since = 0;
-                    const int64_t o = (int64_t)n * S + s;
-#pragma unroll
-                    for (int cc = 0; cc < 6; ++cc) pts[cc * plane + o] = y[cc];
-                    ++n;
-                    if (outside_region<T>(y[0], y[1], y[2], zmin, zmax, rmax2)) break;
-                }
-            }
+        } else if (!active) {
+            break;
         }
     }
-    a.n_valid[s] = n;
+    if (valid) a.n_valid[s] = n;
 }
 
 cudaError_t launch_lattice(comet_dtype dt, const LatArgs &a, void *seeds, int64_t S, cudaStream_t st)
@@ -208,28 +264,35 @@ cudaError_t launch_lattice(comet_dtype dt, const LatArgs &a, void *seeds, int64_
     return cudaGetLastError();
 }
 
-template <typename T>
-static void prop_dispatch(const comet_field &f, const PropArgs &a, cudaStream_t st)
+template <typename T, class F>
+static void prop_launch(const F &fld, const PropArgs &a, cudaStream_t st)
 {
     const int nt = 128;
     const unsigned nb = (unsigned)((a.S + nt - 1) / nt);
+    switch (a.stride) {
+    case 1: propagate_kernel<T, F, 1><<<nb, nt, 0, st>>>(fld, a); break;
+    case 2: propagate_kernel<T, F, 2><<<nb, nt, 0, st>>>(fld, a); break;
+    case 4: propagate_kernel<T, F, 4><<<nb, nt, 0, st>>>(fld, a); break;
+    case 8: propagate_kernel<T, F, 8><<<nb, nt, 0, st>>>(fld, a); break;
+    default: propagate_kernel<T, F, 0><<<nb, nt, 0, st>>>(fld, a); break;
+    }
+}
+
+template <typename T>
+static void prop_dispatch(const comet_field &f, const PropArgs &a, cudaStream_t st)
+{
     switch (field_kind(f)) {
-    case FieldKind::Axial: {
-        FieldAxial<T> F{(T)f.b[2]};
-        propagate_kernel<T, FieldAxial<T>><<<nb, nt, 0, st>>>(F, a);
+    case FieldKind::Axial:
+        prop_launch<T>(FieldAxial<T>{(T)f.b[2]}, a, st);
         break;
-    }
-    case FieldKind::Uniform: {
-        FieldUniform<T> F{(T)f.b[0], (T)f.b[1], (T)f.b[2]};
-        propagate_kernel<T, FieldUniform<T>><<<nb, nt, 0, st>>>(F, a);
+    case FieldKind::Uniform:
+        prop_launch<T>(FieldUniform<T>{(T)f.b[0], (T)f.b[1], (T)f.b[2]}, a, st);
         break;
-    }
-    case FieldKind::Table: {
-        FieldTable<T> F{(const float *)f.table, f.nx, f.ny, f.nz, (T)f.origin[0], (T)f.origin[1],
-                        (T)f.origin[2], (T)(1.0 / f.spacing)};
-        propagate_kernel<T, FieldTable<T>><<<nb, nt, 0, st>>>(F, a);
+    case FieldKind::Table:
+        prop_launch<T>(FieldTable<T>{(const float *)f.table, f.nx, f.ny, f.nz, (T)f.origin[0],
+                                     (T)f.origin[1], (T)f.origin[2], (T)(1.0 / f.spacing)},
+                       a, st);
         break;
-    }
     }
 }
 

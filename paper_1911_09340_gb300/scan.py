@@ -63,6 +63,7 @@ class Workspace:
         self.charge = torch.empty(S, dtype=torch.int8, device=device)
         self.points = torch.empty((6, n_rec, S), dtype=dtype, device=device)
         self.n_valid = torch.empty(S, dtype=torch.int32, device=device)
+        self.bounds = torch.empty(B.bounds_shape(S), dtype=torch.float32, device=device)
         self.rss = torch.empty(S, dtype=dtype, device=device)
         self.n_in = torch.empty(S, dtype=torch.int32, device=device)
         self.idx = torch.empty(k, dtype=torch.int64, device=device)
@@ -98,10 +99,12 @@ def scan_partition(ctx: B.Context, field: B.DeviceField, params: B.ScanParams, s
     mark("lattice")
     B.comet_scan_lattice(ctx, spec, seeds, charge)
     mark("propagate")
-    B.comet_scan_propagate(ctx, field, params, seeds, charge, pts, nv)
+    bounds = ws.bounds[: (S + 31) // 32]
+    B.comet_scan_propagate(ctx, field, params, seeds, charge, pts, nv, bounds=bounds)
     mark("dca")
     B.comet_scan_dca(ctx, field, params, pts, nv, charge, ev.wires, ev.hit_offsets, ev.drift,
-                     ev.mask, rss, n_in, dca_out=want_dca, n_unconverged=ws.n_unconv, n_wires=ev.W)
+                     ev.mask, rss, n_in, dca_out=want_dca, n_unconverged=ws.n_unconv, n_wires=ev.W,
+                     bounds=bounds)
     mark("select")
     B.comet_scan_select(ctx, rss, k, ws.idx[:k], ws.best[:k])
     mark("classify")

@@ -25,13 +25,13 @@ def dev_wires(wires_soa, dtype, misalign=0, pad_to=4):
     return w
 
 
-def gpu_propagate(ctx, field, bp, seeds_aos, q, dtype):
+def gpu_propagate(ctx, field, bp, seeds_aos, q, dtype, bounds=None):
     S = seeds_aos.shape[0]
     seeds = dev_seeds(seeds_aos, dtype)
     charge = torch.full((S,), int(q), dtype=torch.int8, device="cuda")
     pts = torch.full((6, bp.n_rec, S), float("nan"), dtype=dtype, device="cuda")
     nv = torch.zeros(S, dtype=torch.int32, device="cuda")
-    B.comet_scan_propagate(ctx, field, bp, seeds, charge, pts, nv)
+    B.comet_scan_propagate(ctx, field, bp, seeds, charge, pts, nv, bounds=bounds)
     return seeds, charge, pts, nv
 
 
@@ -40,8 +40,10 @@ def to_aos_points(pts):
 
 
 def gpu_dca(ctx, field, bp, seeds_aos, q, wires_soa, offs, drift, mask, dtype, want_dca=True,
-            misalign=0):
-    seeds, charge, pts, nv = gpu_propagate(ctx, field, bp, seeds_aos, q, dtype)
+            misalign=0, use_bounds=True):
+    bounds = (torch.full(B.bounds_shape(seeds_aos.shape[0]), float("nan"), dtype=torch.float32,
+                         device="cuda") if use_bounds else None)
+    seeds, charge, pts, nv = gpu_propagate(ctx, field, bp, seeds_aos, q, dtype, bounds=bounds)
     S = seeds_aos.shape[0]
     W = wires_soa.shape[1]
     w = dev_wires(wires_soa, dtype, misalign)
@@ -53,10 +55,10 @@ def gpu_dca(ctx, field, bp, seeds_aos, q, wires_soa, offs, drift, mask, dtype, w
     dca = torch.full((max(W, 1), S), float("nan"), dtype=dtype, device="cuda") if want_dca else None
     nunc = torch.zeros(1, dtype=torch.int32, device="cuda")
     B.comet_scan_dca(ctx, field, bp, pts, nv, charge, w, o, d, m, rss, n_in, dca_out=dca,
-                     n_unconverged=nunc, n_wires=W)
+                     n_unconverged=nunc, n_wires=W, bounds=bounds)
     torch.cuda.synchronize()
     out = dict(rss=rss.double().cpu().numpy(), n_in=n_in.cpu().numpy(), n_unconv=int(nunc.item()),
-               pts=pts, nv=nv, charge=charge, w=w, o=o, d=d, m=m)
+               pts=pts, nv=nv, charge=charge, w=w, o=o, d=d, m=m, bounds=bounds)
     if want_dca:
         out["dca"] = dca[:W].double().cpu().numpy().T   # [S][W]
     return out

@@ -94,6 +94,10 @@ def test_fp32_matches_oracle_multi_turn_event(ctx, stride):
                 ev.drift, mask, torch.float32, want_dca=False)
     assert np.allclose(p["rss"], g["rss"], rtol=1e-6, atol=0)
     assert np.array_equal(p["n_in"], g["n_in"])
+    # search bounds written by propagate or built by dca itself: the same results
+    q = gpu_dca(ctx, B.DeviceField.from_synth(UNIFORM), bp, seeds, -1, ev.wires, ev.hit_offsets,
+                ev.drift, mask, torch.float32, want_dca=False, use_bounds=False)
+    assert np.array_equal(q["rss"], p["rss"]) and np.array_equal(q["n_in"], p["n_in"])
 
 
 def test_fp32_large_seed_count_sampled(ctx):

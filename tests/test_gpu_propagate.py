@@ -18,6 +18,7 @@ from gpu_util import both_params, gpu_propagate, to_aos_points
 pytestmark = pytest.mark.gpu
 
 OPEN = dict(zmin=-50.0, zmax=50.0, rmax=50.0)
+UNIFORM = synth.uniform_field(1.0)
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
@@ -126,3 +127,44 @@ def test_general_uniform_field_and_zero_charge(ctx):
         _, _, pts, nv = gpu_propagate(ctx, B.DeviceField.from_synth(field), bp, seeds, q, torch.float64)
         ref, _ = O.propagate(field, op, seeds, q)
         assert np.abs(to_aos_points(pts) - ref).max() <= 1e-9 * 105
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+@pytest.mark.parametrize("stride", [1, 4])
+def test_search_bounds_contain_every_recorded_state(ctx, dtype, stride):
+    """The segment spheres propagate writes for each 32-seed group contain every recorded state of
+    the segment, for every seed of the group, including tracks stopped by the target region."""
+    from paper_1911_09340_gb300 import binding
+    ev = synth.multi_turn_event(5)
+    seeds = O.lattice(ev.partitions[0])[:96 + 17].astype(np.float32).astype(np.float64)
+    seeds[40:52, 5] *= 6.0       # steep tracks: some leave through |z| = zmax mid-partition
+    op, bp = both_params(n_steps=ev.n_steps[0], stride=stride, zmax=0.45)
+    bounds = torch.full(binding.bounds_shape(seeds.shape[0]), float("nan"), dtype=torch.float32,
+                        device="cuda")
+    _, _, pts, nv = gpu_propagate(ctx, B.DeviceField.from_synth(UNIFORM), bp, seeds, -1, dtype, bounds)
+    x = to_aos_points(pts)[:, :, :3]
+    nv = nv.cpu().numpy()
+    tab = bounds.cpu().numpy().astype(np.float64)
+    assert np.isfinite(tab).all() and (nv < bp.n_rec).any()
+    # the segmentation the library uses for this n_rec
+    n_rec = bp.n_rec
+    n0 = min(8, max(1, round(n_rec ** (1 / 3))))
+    G0 = -(-n_rec // n0)
+    G1 = 3 if -(-G0 // 3) <= 24 else -(-G0 // 24)
+    for gi in range(tab.shape[0]):
+        lanes = range(gi * 32, min(gi * 32 + 32, seeds.shape[0]))
+        for j in range(8):
+            sb = j * G0
+            for m in range(-1, 24):
+                sp = tab[gi, j] if m < 0 else tab[gi, 8 + j * 24 + m]
+                lo = sb if m < 0 else sb + m * G1
+                hi = sb + G0 if m < 0 else min(sb + (m + 1) * G1, sb + G0)
+                for l in lanes:
+                    ks = np.arange(lo, min(hi, nv[l]))
+                    if m >= 0 and lo >= sb + G0:
+                        continue
+                    if ks.size == 0:
+                        continue
+                    assert sp[3] >= 0, (gi, j, m)
+                    d = np.linalg.norm(x[l, ks] - sp[:3], axis=1)
+                    assert d.max() <= sp[3] + 1e-7, (gi, j, m, l, d.max(), sp[3])
