@@ -323,17 +323,19 @@ __device__ __forceinline__ void group_wires(const F &f, const DcaArgs &a, const 
             int bk = 0x7fffffff;
             // scans states [k0, k1) of this lane's seed, kU at a time (span is warp-uniform)
             auto scan = [&](int k0, int k1, int span) {
-                for (int t0 = 0; t0 < span; t0 += kU) {
+                // one 64-bit multiply per range; states are S elements apart
+                const T *q0 = P + ((int64_t)k0 * S + s);
+                for (int t0 = 0; t0 < span; t0 += kU, q0 += kU * S) {
                     T xs[kU], ys[kU], zs[kU];
 #pragma unroll
                     for (int u = 0; u < kU; ++u) {
                         const int k = k0 + t0 + u;
                         xs[u] = ys[u] = zs[u] = T(0);
                         if (want && k < k1) {
-                            const int64_t o = (int64_t)k * S + s;
-                            xs[u] = P[o];
-                            ys[u] = P[plane + o];
-                            zs[u] = P[2 * plane + o];
+                            const T *q = q0 + u * S;
+                            xs[u] = q[0];
+                            ys[u] = q[plane];
+                            zs[u] = q[2 * plane];
                         }
                     }
 #pragma unroll
