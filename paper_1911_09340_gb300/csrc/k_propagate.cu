@@ -3,15 +3,16 @@
 // propagate_kernel: one thread extrapolates one seed with fixed-step RK4 and writes every
 // stride-th state to the SoA track array points[c][k][s] (seed index fastest, so the 32 lanes of a
 // warp store 32 consecutive values of one component: full 128-byte lines).  In a uniform axial field
-// the RK4 step is applied as its exact linear map (device.cuh), with the coefficients of the seed
-// computed once in double.  Steps after the last recorded state (n_steps not a multiple of stride)
-// cannot change any output and are not taken.  Optionally the kernel also writes the bounding
-// spheres of the track segments of each group of 32 consecutive seeds (one warp), which the DCA
-// kernel's closest-state search uses: the 32 lanes record state r together, so a segment's sphere
-// is one warp reduction at the moment its centre state is recorded.  The FP32 path keeps
-// every state component as an unevaluated float pair (hi, lo) updated with TwoSum, so that the
-// rounding of 6,500 steps does not accumulate (plain FP32 drifts ~0.1 mm over three turns; the pair
-// stays within ~1 um of FP64).  The RK4 stages read the leading float only.
+// one RK4 step is a linear map (device.cuh), so a recording interval of `stride` steps is the
+// product of `stride` such maps, formed once per seed in double and applied once per record.
+// Steps after the last recorded state (n_steps not a multiple of stride) cannot change any output
+// and are not taken.  Optionally the kernel also writes the bounding spheres of the track segments
+// of each group of 32 consecutive seeds (one warp), which the DCA kernel's closest-state search
+// uses: the 32 lanes record state r together, so a segment's sphere is one warp reduction at the
+// moment its centre state is recorded.  The FP32 path keeps every state component as an
+// unevaluated float pair (hi, lo) updated with TwoSum, so that the rounding of 6,500 steps does not
+// accumulate (plain FP32 drifts ~0.1 mm over three turns; the pair stays within ~1 um of FP64).
+// The step maps read the leading float only.
 #include "device.cuh"
 #include "internal.h"
 
@@ -96,42 +97,53 @@ __device__ __forceinline__ bool outside_region(T x, T y, T z, T zmin, T zmax, T 
     return z < zmin || z > zmax || x * x + y * y > rmax2;
 }
 
-// One recording interval (stride RK4 steps) of one seed.  FP32 in an axial field: the increments
-// of the interval are summed in small accumulators (|acc| <= stride mm, stride * 0.3 MeV/c: their
-// rounding is negligible); each step's map reads p = p_hi + acc_p; once per interval the
-// accumulators go into the compensated (hi, lo) state.  pz is constant in an axial field.
-// STRIDE > 0 fixes the number of steps at compile time (fully unrolled); 0 takes a.stride.
+// Map of one recording interval (stride RK4 steps) in a uniform axial field.  With P = px + i py
+// and X = x + i y, one RK4 step is P' = m P, X' = X + n P, z' = z + dz (device.cuh), so `stride`
+// steps are P' = m^k P, X' = X + n (1 + m + ... + m^(k-1)) P, z' = z + k dz: the same map in exact
+// arithmetic, formed once per seed in double and then applied once per recorded state.
+__device__ __forceinline__ void axial_interval(double am1, double b, double c, double d, double dz,
+                                               int k, double out[5])
+{
+    const double mr = 1.0 + am1, mi = -b;      // m
+    double Ar = 0.0, Ai = 0.0;                 // A = m^j - 1 (kept apart from 1: no cancellation)
+    double Sr = 0.0, Si = 0.0;                 // sum of m^i, i < j
+    for (int j = 0; j < k; ++j) {
+        Sr += 1.0 + Ar;
+        Si += Ai;
+        const double r = Ar * mr - Ai * mi + am1;   // A m + (m - 1)
+        const double i = Ar * mi + Ai * mr + mi;
+        Ar = r;
+        Ai = i;
+    }
+    const double nr = c, ni = -d;              // n
+    out[0] = Ar;                               // am1 of the interval
+    out[1] = -Ai;                              // b
+    out[2] = nr * Sr - ni * Si;                // c
+    out[3] = -(nr * Si + ni * Sr);             // d
+    out[4] = dz * k;                           // dz
+}
+
+// One recording interval (stride RK4 steps) of one seed.  In an axial field the interval's map is
+// applied once (axial_interval); FP32 adds its increments to the compensated (hi, lo) state.  pz
+// is constant in an axial field.  Other fields take the steps one by one.  STRIDE > 0 fixes the
+// number of steps at compile time; 0 takes a.stride.
 template <typename T, class F, int STRIDE>
 __device__ __forceinline__ void advance_interval(const F &f, const PropArgs &a, const AxialStep<T> &ks,
                                                  T c, T ip, T h, T y[6], float lo[6])
 {
     const int stride = STRIDE > 0 ? STRIDE : a.stride;
     if constexpr (sizeof(T) == 4 && F::kAxial) {
-        float ax0 = 0.f, ax1 = 0.f, ax2 = 0.f, ap0 = 0.f, ap1 = 0.f;
+        const float px = y[3], py = y[4];
+        two_sum_add(y[0], lo[0], ks.c * px + ks.d * py);
+        two_sum_add(y[1], lo[1], ks.c * py - ks.d * px);
+        two_sum_add(y[2], lo[2], ks.dz);
+        two_sum_add(y[3], lo[3], ks.am1 * px + ks.b * py);
+        two_sum_add(y[4], lo[4], ks.am1 * py - ks.b * px);
+    } else if constexpr (F::kAxial) {
+        T inc[6];
+        axial_increment<T>(ks, y, inc);
 #pragma unroll
-        for (int st = 0; st < (STRIDE > 0 ? STRIDE : 1); ++st) {
-            const float px = y[3] + ap0, py = y[4] + ap1;
-            ax0 += ks.c * px + ks.d * py;
-            ax1 += ks.c * py - ks.d * px;
-            ax2 += ks.dz;
-            ap0 += ks.am1 * px + ks.b * py;
-            ap1 += ks.am1 * py - ks.b * px;
-        }
-        if constexpr (STRIDE == 0) {
-            for (int st = 1; st < stride; ++st) {
-                const float px = y[3] + ap0, py = y[4] + ap1;
-                ax0 += ks.c * px + ks.d * py;
-                ax1 += ks.c * py - ks.d * px;
-                ax2 += ks.dz;
-                ap0 += ks.am1 * px + ks.b * py;
-                ap1 += ks.am1 * py - ks.b * px;
-            }
-        }
-        two_sum_add(y[0], lo[0], ax0);
-        two_sum_add(y[1], lo[1], ax1);
-        two_sum_add(y[2], lo[2], ax2);
-        two_sum_add(y[3], lo[3], ap0);
-        two_sum_add(y[4], lo[4], ap1);
+        for (int i = 0; i < 6; ++i) y[i] += inc[i];
     } else if constexpr (sizeof(T) == 4) {
         for (int st = 0; st < stride; ++st) {
             float inc[6];
@@ -142,10 +154,7 @@ __device__ __forceinline__ void advance_interval(const F &f, const PropArgs &a, 
     } else {
         for (int st = 0; st < stride; ++st) {
             T inc[6];
-            if constexpr (F::kAxial)
-                axial_increment<T>(ks, y, inc);
-            else
-                rk4_increment<T, F>(f, c, ip, y, h, inc);
+            rk4_increment<T, F>(f, c, ip, y, h, inc);
 #pragma unroll
             for (int i = 0; i < 6; ++i) y[i] += inc[i];
         }
@@ -181,16 +190,19 @@ __global__ void __launch_bounds__(128) propagate_kernel(F f, PropArgs a)
     const T h = (T)a.h;
     const T zmin = (T)a.zmin, zmax = (T)a.zmax, rmax2 = (T)(a.rmax * a.rmax);
     const T R0 = (T)a.R0, R1 = (T)a.R1;
-    // uniform axial field: the step's coefficients are fixed per seed (computed in double)
+    // uniform axial field: the interval's map is fixed per seed (computed in double)
     AxialStep<T> ks{};
     if constexpr (F::kAxial) {
         const double w = kKappa * q * (double)f.bz / pd;
         const double t = a.h * w, t2 = t * t, hp = a.h / pd;
-        ks.am1 = (T)(t2 * (-0.5 + t2 / 24.0));
-        ks.b = (T)(t * (1.0 - t2 / 6.0));
-        ks.c = (T)(hp * (1.0 - t2 / 6.0));
-        ks.d = (T)(hp * t * (0.5 - t2 / 24.0));
-        ks.dz = (T)(hp * (double)y[5]);
+        double m[5];
+        axial_interval(t2 * (-0.5 + t2 / 24.0), t * (1.0 - t2 / 6.0), hp * (1.0 - t2 / 6.0),
+                       hp * t * (0.5 - t2 / 24.0), hp * (double)y[5], STRIDE > 0 ? STRIDE : a.stride, m);
+        ks.am1 = (T)m[0];
+        ks.b = (T)m[1];
+        ks.c = (T)m[2];
+        ks.d = (T)m[3];
+        ks.dz = (T)m[4];
     }
     float lo[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // FP32: low words of the compensated state
 
