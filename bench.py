@@ -379,7 +379,7 @@ def main():
     ap.add_argument("--steps", type=int, default=8)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--stride", type=int, default=4,
+    ap.add_argument("--stride", type=int, default=16,
                     help="record every stride-th RK4 state (h = 1 mm is unchanged)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-seconds", type=float, default=8.0)

@@ -319,6 +319,10 @@ comet_status comet_scan_dca(comet_ctx *ctx, comet_dtype dtype, const comet_field
     a.R1 = sg.R1;
     a.half_rec = sg.half_rec;
     a.h_rec = sg.h_rec;
+    a.lambda_f = (float)a.lambda;
+    a.tol_f = (float)a.tol;
+    a.half_rec_f = (float)a.half_rec;
+    a.h_rec_f = (float)a.h_rec;
     a.bounds = bounds;
     a.exact_all = dca_out != nullptr;
     cudaError_t e = comet::launch_dca(dtype, *field, a, (cudaStream_t)stream);

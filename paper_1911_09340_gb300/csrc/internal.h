@@ -53,6 +53,9 @@ struct DcaArgs {
     double R1;             // level-1 segment radius (m), margins included
     double half_rec;       // half a recording interval (m), margins included
     double h_rec;          // recording interval stride*h (m): reach of the local refinement
+    // the four scalars above rounded to float on the host: the FP32 kernel reads these, so that
+    // no double-to-float conversion is re-done inside its loops
+    float lambda_f, tol_f, half_rec_f, h_rec_f;
     int max_iter;
     int G0;                // recorded states per super-segment
     int G1;                // recorded states per level-1 segment

@@ -94,6 +94,16 @@ __device__ __forceinline__ void stage_fallback(E *dst, const E *src, int n)
     for (int i = p.head + threadIdx.x; i < p.head + p.body; i += blockDim.x) dst[p.off + i] = src[i];
 }
 
+// A launch scalar in the working precision: the host-rounded float copy for FP32.
+template <typename T>
+__device__ __forceinline__ T in_prec(double d, float f)
+{
+    if constexpr (sizeof(T) == 4)
+        return f;
+    else
+        return d;
+}
+
 // Twosum accumulator for FP32, plain for FP64.
 template <typename T>
 struct Acc;
@@ -270,7 +280,8 @@ __device__ __forceinline__ void group_wires(const F &f, const DcaArgs &a, const 
     const int64_t s = gr.s;
     const bool valid = gr.valid;
     const int nv = gr.nv;
-    const T lam = (T)a.lambda, tol = (T)a.tol, half_rec = (T)a.half_rec, h_rec = (T)a.h_rec;
+    const T lam = in_prec<T>(a.lambda, a.lambda_f), tol = in_prec<T>(a.tol, a.tol_f),
+            half_rec = in_prec<T>(a.half_rec, a.half_rec_f), h_rec = in_prec<T>(a.h_rec, a.h_rec_f);
     const int G0 = a.G0, G1 = a.G1;
     const int N1 = (G0 + G1 - 1) / G1;
     const int fs = tl.fs;
@@ -522,7 +533,7 @@ __global__ void __launch_bounds__(kThreads, COMET_DCA_MINB) dca_persistent_kerne
     tl.msm = hits_sm ? msm + moff : a.mask;
     tl.w0 = 0;
     tl.wn = W;
-    for (int i = tid; i < W; i += kThreads) tile_wire_setup<T>(tl, i, (T)a.lambda, capv, frm);
+    for (int i = tid; i < W; i += kThreads) tile_wire_setup<T>(tl, i, in_prec<T>(a.lambda, a.lambda_f), capv, frm);
     __syncthreads();
 
     // ---- 32-seed groups, taken dynamically by each warp
@@ -647,7 +658,7 @@ __global__ void __launch_bounds__(kThreads, COMET_DCA_MINB) dca_tiled_kernel(F f
         tl.msm = hits_sm ? msm + moff : a.mask;
         tl.w0 = w0;
         tl.wn = wn;
-        for (int i = tid; i < wn; i += kThreads) tile_wire_setup<T>(tl, i, (T)a.lambda, capv, frm);
+        for (int i = tid; i < wn; i += kThreads) tile_wire_setup<T>(tl, i, in_prec<T>(a.lambda, a.lambda_f), capv, frm);
         __syncthreads();
         group_wires<T, F>(f, a, gr, tl, sph0, sph1, lane, acc, nin, nunc);
         if (w0 + kWireTile < W) __syncthreads();   // tile consumed before the next staging

@@ -99,25 +99,39 @@ __device__ __forceinline__ bool outside_region(T x, T y, T z, T zmin, T zmax, T 
 
 // Map of one recording interval (stride RK4 steps) in a uniform axial field.  With P = px + i py
 // and X = x + i y, one RK4 step is P' = m P, X' = X + n P, z' = z + dz (device.cuh), so `stride`
-// steps are P' = m^k P, X' = X + n (1 + m + ... + m^(k-1)) P, z' = z + k dz: the same map in exact
-// arithmetic, formed once per seed in double and then applied once per recorded state.
+// steps are P' = m^k P, X' = X + n (m^k - 1) / (m - 1) P, z' = z + k dz: the same map in exact
+// arithmetic, formed once per seed in double and then applied once per recorded state.  m^k - 1 is
+// built by binary powering on A = m - 1 ((1 + A)(1 + B) - 1 = A + B + A B), never forming 1 + A,
+// so nothing cancels.
 __device__ __forceinline__ void axial_interval(double am1, double b, double c, double d, double dz,
                                                int k, double out[5])
 {
-    const double mr = 1.0 + am1, mi = -b;      // m
-    double Ar = 0.0, Ai = 0.0;                 // A = m^j - 1 (kept apart from 1: no cancellation)
-    double Sr = 0.0, Si = 0.0;                 // sum of m^i, i < j
-    for (int j = 0; j < k; ++j) {
-        Sr += 1.0 + Ar;
-        Si += Ai;
-        const double r = Ar * mr - Ai * mi + am1;   // A m + (m - 1)
-        const double i = Ar * mi + Ai * mr + mi;
-        Ar = r;
-        Ai = i;
+    const double a0r = am1, a0i = -b;          // m - 1
+    double Rr = 0.0, Ri = 0.0;                 // m^(bits taken so far) - 1
+    double Br = a0r, Bi = a0i;                 // m^(2^j) - 1
+    for (int e = k; e > 0; e >>= 1) {
+        if (e & 1) {
+            const double r = Rr + Br + (Rr * Br - Ri * Bi);
+            const double i = Ri + Bi + (Rr * Bi + Ri * Br);
+            Rr = r;
+            Ri = i;
+        }
+        const double r = 2.0 * Br + (Br * Br - Bi * Bi);
+        const double i = 2.0 * Bi + 2.0 * Br * Bi;
+        Br = r;
+        Bi = i;
+    }
+    // sum of m^j for j < k: (m^k - 1) / (m - 1), or k when the step does not turn
+    double Sr = (double)k, Si = 0.0;
+    const double den = a0r * a0r + a0i * a0i;
+    if (den > 0.0) {
+        const double inv = 1.0 / den;
+        Sr = (Rr * a0r + Ri * a0i) * inv;
+        Si = (Ri * a0r - Rr * a0i) * inv;
     }
     const double nr = c, ni = -d;              // n
-    out[0] = Ar;                               // am1 of the interval
-    out[1] = -Ai;                              // b
+    out[0] = Rr;                               // am1 of the interval
+    out[1] = -Ri;                              // b
     out[2] = nr * Sr - ni * Si;                // c
     out[3] = -(nr * Si + ni * Sr);             // d
     out[4] = dz * k;                           // dz
@@ -185,16 +199,17 @@ __global__ void __launch_bounds__(128) propagate_kernel(F f, PropArgs a)
         q = a.charge[s];
     }
     const double pd = valid ? sqrt((double)y[3] * y[3] + (double)y[4] * y[4] + (double)y[5] * y[5]) : 1.0;
-    const T c = (T)(kKappa * q / pd);
-    const T ip = (T)(1.0 / pd);
+    const double ipd = 1.0 / pd;
+    const T c = (T)(kKappa * q * ipd);
+    const T ip = (T)ipd;
     const T h = (T)a.h;
     const T zmin = (T)a.zmin, zmax = (T)a.zmax, rmax2 = (T)(a.rmax * a.rmax);
     const T R0 = (T)a.R0, R1 = (T)a.R1;
     // uniform axial field: the interval's map is fixed per seed (computed in double)
     AxialStep<T> ks{};
     if constexpr (F::kAxial) {
-        const double w = kKappa * q * (double)f.bz / pd;
-        const double t = a.h * w, t2 = t * t, hp = a.h / pd;
+        const double w = kKappa * q * (double)f.bz * ipd;
+        const double t = a.h * w, t2 = t * t, hp = a.h * ipd;
         double m[5];
         axial_interval(t2 * (-0.5 + t2 / 24.0), t * (1.0 - t2 / 6.0), hp * (1.0 - t2 / 6.0),
                        hp * t * (0.5 - t2 / 24.0), hp * (double)y[5], STRIDE > 0 ? STRIDE : a.stride, m);

@@ -130,7 +130,7 @@ def test_general_uniform_field_and_zero_charge(ctx):
 
 
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
-@pytest.mark.parametrize("stride", [1, 4])
+@pytest.mark.parametrize("stride", [1, 4, 16])
 def test_search_bounds_contain_every_recorded_state(ctx, dtype, stride):
     """The segment spheres propagate writes for each 32-seed group contain every recorded state of
     the segment, for every seed of the group, including tracks stopped by the target region."""

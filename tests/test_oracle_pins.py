@@ -251,7 +251,7 @@ def test_dca_same_for_every_recording_stride(chamber):
     wires = O.wires_aos(ev.wires)
     mask = np.zeros(ev.n_hits, np.uint8)
     out = []
-    for stride in (1, 3, 8):
+    for stride in (1, 3, 8, 16, 24):
         P = O.Params(n_steps=ev.n_steps[0], stride=stride)
         out.append(O.scan(synth.uniform_field(1.0), P, seeds, -1, wires, ev.hit_offsets, ev.drift,
                           mask, want_dca=True))
@@ -435,7 +435,7 @@ def test_classify_ties_take_the_lowest_hit_index():
     assert np.array_equal(cls, np.array([0, 1, 0], np.uint8))
 
 
-@pytest.mark.parametrize("stride", [1, 4])
+@pytest.mark.parametrize("stride", [1, 4, 16])
 def test_refined_dca_stays_in_its_valley(chamber, stride):
     # the continuous distance minimum near the closest recorded state lies within half a recording
     # interval (in arc length) of a recorded state, so the refined DCA can be at most h_rec/2 below
