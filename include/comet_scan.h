@@ -93,11 +93,11 @@ typedef struct {
  * dimension with n nodes sits at centre + half_width * (2i/(n-1) - 1) (the centre alone when
  * n = 1).  Seed = (vx, vy, z0, pT cos phi, pT sin phi, pz), of charge `charge` (units of e; -1 for
  * the electron, +1 for the positron of the paper's Sec. 5.1 outlook).
- * Seed numbering: the lattice is cut into blocks of b = (2, 2, 2, 4) nodes along (z0, phi, pz, pT)
- * (b = 1 along a dimension whose count is odd; b = 2 along pT when its count is even but not a
- * multiple of 4).  Blocks are numbered row-major with z0 slowest, nodes inside a block row-major,
- * and seed s = block * (b0 b1 b2 b3) + node-in-block: consecutive seeds are lattice neighbours in
- * every dimension. */
+ * Seed numbering: the lattice is cut into blocks of b = (2, 4, 4, 1) nodes along (z0, phi, pz, pT)
+ * (b = 1 along a dimension whose count is odd; b = 2 along phi or pz when its count is even but not
+ * a multiple of 4).  Blocks are numbered row-major with z0 slowest, nodes inside a block row-major,
+ * and seed s = block * (b0 b1 b2 b3) + node-in-block: consecutive seeds are lattice neighbours, and
+ * pT (the parameter that separates tracks fastest along a turn) is not mixed inside a block. */
 typedef struct {
     double vx, vy;
     double centre[4];

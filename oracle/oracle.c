@@ -228,13 +228,22 @@ static double dca_one(const or_field *f, const or_params *P, const double *pts, 
 /* Seed lattice (Sec. 2.1: seeds combined from grids over the prior range of each component).
    Dimensions: z0, phi, pz, pt; node i of n sits at centre + half_width*(2i/(n-1) - 1).  The seed is
    (vx, vy, z0, pt cos phi, pt sin phi, pz).  Enumeration: the lattice is cut into blocks of
-   b = (2, 2, 2, 4) nodes (a dimension whose count the block does not divide gets block 1; pt gets 2
-   when 4 does not divide it but 2 does); blocks are numbered row-major (z0 slowest) and the nodes
-   inside a block row-major, so seed s = block * (b0 b1 b2 b3) + node-in-block. */
+   b = (2, 4, 4, 1) nodes along (z0, phi, pz, pt) (z0: 1 when its count is odd; phi and pz: 2 when
+   4 does not divide the count but 2 does, 1 when it is odd); blocks are numbered row-major (z0
+   slowest) and the nodes inside a block row-major, so seed s = block * (b0 b1 b2 b3) +
+   node-in-block. */
+static int block_of(int n, int pref)
+{
+    if (pref >= 4 && n % 4 == 0) return 4;
+    return n % 2 == 0 ? 2 : 1;
+}
+
 void oracle_block_shape(const int counts[4], int b[4])
 {
-    for (int d = 0; d < 3; ++d) b[d] = counts[d] % 2 == 0 ? 2 : 1;
-    b[3] = counts[3] % 4 == 0 ? 4 : (counts[3] % 2 == 0 ? 2 : 1);
+    b[0] = block_of(counts[0], 2);
+    b[1] = block_of(counts[1], 4);
+    b[2] = block_of(counts[2], 4);
+    b[3] = 1;
 }
 
 void oracle_lattice(double vx, double vy, const double centre[4], const double half_width[4],

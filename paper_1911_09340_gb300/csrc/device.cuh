@@ -347,18 +347,22 @@ constexpr int kBoundsPerGroup = kN0Max + kN0Max * kN1Max;
 __device__ __forceinline__ int segment_centre(int st, int g, int end) { return min(st + g / 2, min(st + g, end) - 1); }
 
 // The warp's bounding sphere of one segment: lanes with `has` hold their seed's segment centre
-// (x, y, z); the sphere is centred on the first such lane's centre, its radius is the largest
-// distance to any lane's centre plus `reach` (a state within g/2 recording intervals of a centre is
-// at most (g/2) h_rec from it along the track).  Rounded up so that it never shrinks; in double the
-// rounding of the centre to float is added.  Returns radius < 0 when no lane has the segment.
+// (x, y, z); the sphere is centred on the midpoint of the first and the last such lane's centres
+// (opposite corners of the lattice block, so about the middle of the group's tracks), its radius
+// is the largest distance to any lane's centre plus `reach` (a state within g/2 recording intervals
+// of a centre is at most (g/2) h_rec from it along the track).  Any centre gives a valid sphere;
+// the radius is measured from the centre as rounded, and rounded up so that it never shrinks; in
+// double the rounding of the centre to float is added.  Returns radius < 0 when no lane has the
+// segment.
 template <typename T>
 __device__ __forceinline__ float4 warp_sphere(bool has, T x, T y, T z, T reach)
 {
     const uint32_t hm = __ballot_sync(0xffffffffu, has);
     if (hm == 0u) return make_float4(0.f, 0.f, 0.f, -1.f);
-    const int src = __ffs(hm) - 1;
-    const T cx = __shfl_sync(0xffffffffu, x, src), cy = __shfl_sync(0xffffffffu, y, src),
-            cz = __shfl_sync(0xffffffffu, z, src);
+    const int l0 = __ffs(hm) - 1, l1 = 31 - __clz(hm);
+    const T cx = T(0.5) * (__shfl_sync(0xffffffffu, x, l0) + __shfl_sync(0xffffffffu, x, l1));
+    const T cy = T(0.5) * (__shfl_sync(0xffffffffu, y, l0) + __shfl_sync(0xffffffffu, y, l1));
+    const T cz = T(0.5) * (__shfl_sync(0xffffffffu, z, l0) + __shfl_sync(0xffffffffu, z, l1));
     T d = has ? sqrt((x - cx) * (x - cx) + (y - cy) * (y - cy) + (z - cz) * (z - cz)) : T(0);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) d = fmax(d, __shfl_xor_sync(0xffffffffu, d, off));

@@ -18,10 +18,11 @@
 
 namespace comet {
 
-// Seed s of the lattice: blocks of b = (2, 2, 2, 4) nodes (1 where the count is not divisible; 2
-// for pt when only 2 divides it) numbered row-major, nodes inside a block row-major.  Consecutive
-// seeds are therefore neighbours in all four dimensions, so the 32 lanes of a warp follow similar
-// tracks in the DCA kernel.
+// Seed s of the lattice: blocks of b = (2, 4, 4, 1) nodes along (z0, phi, pz, pt) (2 for phi or pz
+// when only 2 divides the count, 1 when it is odd) numbered row-major, nodes inside a block
+// row-major.  Consecutive seeds are therefore lattice neighbours of one pT, so the 32 lanes of a
+// warp follow similar tracks in the DCA kernel (a pT step moves a track ~8 mm by the end of a turn,
+// a phi or pz step ~3-4 mm).
 // Node value i of a dimension with n nodes (computed in double with rounded operations only, so
 // that it equals the oracle's value).
 __device__ __forceinline__ double lattice_node(double centre, double half_width, int n, int i)
@@ -56,9 +57,10 @@ __global__ void __launch_bounds__(256) lattice_kernel(LatArgs a, T *__restrict__
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= S) return;
     int b[4];
+    b[0] = a.counts[0] % 2 == 0 ? 2 : 1;
 #pragma unroll
-    for (int d = 0; d < 3; ++d) b[d] = a.counts[d] % 2 == 0 ? 2 : 1;
-    b[3] = a.counts[3] % 4 == 0 ? 4 : (a.counts[3] % 2 == 0 ? 2 : 1);
+    for (int d = 1; d < 3; ++d) b[d] = a.counts[d] % 4 == 0 ? 4 : (a.counts[d] % 2 == 0 ? 2 : 1);
+    b[3] = 1;
     const int64_t vol = (int64_t)b[0] * b[1] * b[2] * b[3];
     int64_t blk = s / vol, in = s % vol;
     int ii[4];

@@ -351,8 +351,9 @@ def test_scan_is_deterministic_for_any_thread_count(chamber):
 def _blocked_expectation(spec):
     """Seeds in the blocked enumeration, built independently with meshgrid + reshape/transpose."""
     n = spec.counts
-    b = [2 if n[d] % 2 == 0 else 1 for d in range(3)]
-    b.append(4 if n[3] % 4 == 0 else (2 if n[3] % 2 == 0 else 1))
+    b = [2 if n[0] % 2 == 0 else 1]
+    b += [4 if n[d] % 4 == 0 else (2 if n[d] % 2 == 0 else 1) for d in (1, 2)]
+    b.append(1)
     axes = [np.linspace(c - h, c + h, k) for c, h, k in zip(spec.centre, spec.half_width, n)]
     grids = np.meshgrid(*axes, indexing="ij")
     shape = (n[0] // b[0], b[0], n[1] // b[1], b[1], n[2] // b[2], b[2], n[3] // b[3], b[3])
@@ -361,7 +362,8 @@ def _blocked_expectation(spec):
                      PT * np.sin(PH), PZ], axis=1)
 
 
-@pytest.mark.parametrize("counts", [(3, 4, 2, 5), (4, 6, 2, 8), (2, 2, 3, 6), (16, 16, 32, 32)])
+@pytest.mark.parametrize("counts", [(3, 4, 2, 5), (4, 6, 2, 8), (2, 2, 3, 6), (5, 8, 12, 3),
+                                    (16, 16, 32, 32)])
 def test_lattice_matches_meshgrid(counts):
     spec = synth.LatticeSpec(vxy=(0.01, -0.02), centre=(-0.1, 0.7, 15.0, 100.0),
                              half_width=(0.02, 0.04, 3.0, 6.4), counts=counts)
@@ -377,14 +379,14 @@ def test_lattice_blocks_are_neighbours():
     spec = synth.LatticeSpec(vxy=(0, 0), centre=(0.0, 0.0, 10.0, 100.0),
                              half_width=(0.02, 0.04, 3.0, 6.4), counts=(16, 16, 32, 32))
     seeds = O.lattice(spec)
-    # every run of 32 consecutive seeds spans 2 nodes of z0, phi, pz and 4 of pt
+    # every run of 32 consecutive seeds spans 2 nodes of z0, 4 of phi and pz, one pt
     step = np.array([0.04 / 15, 0.08 / 15, 6.0 / 31, 12.8 / 31])
     for blk in (0, 1, 777, 8191):
         s = seeds[blk * 32:(blk + 1) * 32]
         pt = np.hypot(s[:, 3], s[:, 4])
         ph = np.arctan2(s[:, 4], s[:, 3])
         span = np.array([np.ptp(s[:, 2]), np.ptp(ph), np.ptp(s[:, 5]), np.ptp(pt)])
-        assert np.allclose(span, step * np.array([1, 1, 1, 3]), rtol=1e-9)
+        assert np.allclose(span, step * np.array([1, 3, 3, 0]), rtol=1e-9, atol=1e-12)
 
 
 def test_select_matches_brute_force():
