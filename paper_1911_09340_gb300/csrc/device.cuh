@@ -364,8 +364,13 @@ __device__ __forceinline__ float4 warp_sphere(bool has, T x, T y, T z, T reach)
     const T cy = T(0.5) * (__shfl_sync(0xffffffffu, y, l0) + __shfl_sync(0xffffffffu, y, l1));
     const T cz = T(0.5) * (__shfl_sync(0xffffffffu, z, l0) + __shfl_sync(0xffffffffu, z, l1));
     T d = has ? sqrt((x - cx) * (x - cx) + (y - cy) * (y - cy) + (z - cz) * (z - cz)) : T(0);
+    if constexpr (sizeof(T) == 4) {
+        // d >= 0: its bit pattern orders like its value, so one integer warp reduction finds the max
+        d = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(d)));
+    } else {
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) d = fmax(d, __shfl_xor_sync(0xffffffffu, d, off));
+        for (int off = 16; off > 0; off >>= 1) d = fmax(d, __shfl_xor_sync(0xffffffffu, d, off));
+    }
     const T extra = sizeof(T) == 8 ? T(2e-7) : T(0);
     return make_float4((float)cx, (float)cy, (float)cz, (float)((d + reach + extra) * T(1.000001)));
 }

@@ -740,6 +740,13 @@ static cudaError_t dca_dispatch(const comet_field &f, const DcaArgs &a, cudaStre
 
 void dca_segments(int n_rec, int *G0, int *G1)
 {
+    if (n_rec <= kN0Max * kN1Max) {
+        // one state per level-1 segment: its sphere is then just the spread of the group's tracks
+        const int n0 = (n_rec + kN1Max - 1) / kN1Max;
+        *G0 = (n_rec + n0 - 1) / n0;
+        *G1 = 1;
+        return;
+    }
     // up to 8 super-segments, each cut into level-1 segments of 3 states (more when a super-segment
     // would have more than kN1Max of them)
     int n0 = (int)lround(cbrt((double)n_rec));

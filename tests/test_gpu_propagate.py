@@ -146,11 +146,16 @@ def test_search_bounds_contain_every_recorded_state(ctx, dtype, stride):
     nv = nv.cpu().numpy()
     tab = bounds.cpu().numpy().astype(np.float64)
     assert np.isfinite(tab).all() and (nv < bp.n_rec).any()
-    # the segmentation the library uses for this n_rec
+    # the segmentation the library uses for this n_rec: one state per level-1 segment when at most
+    # 8 x 24 states, else ~cbrt(n_rec) super-segments of level-1 segments of 3 (or more) states
     n_rec = bp.n_rec
-    n0 = min(8, max(1, round(n_rec ** (1 / 3))))
-    G0 = -(-n_rec // n0)
-    G1 = 3 if -(-G0 // 3) <= 24 else -(-G0 // 24)
+    if n_rec <= 8 * 24:
+        n0 = -(-n_rec // 24)
+        G0, G1 = -(-n_rec // n0), 1
+    else:
+        n0 = min(8, max(1, round(n_rec ** (1 / 3))))
+        G0 = -(-n_rec // n0)
+        G1 = 3 if -(-G0 // 3) <= 24 else -(-G0 // 24)
     for gi in range(tab.shape[0]):
         lanes = range(gi * 32, min(gi * 32 + 32, seeds.shape[0]))
         for j in range(8):
