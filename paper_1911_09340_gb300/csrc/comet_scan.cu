@@ -265,6 +265,13 @@ comet_status comet_scan_propagate(comet_ctx *ctx, comet_dtype dtype, const comet
     a.rmax = params->rmax;
     a.n_steps = params->n_steps;
     a.stride = params->stride;
+    a.h_ff.hi = (float)params->h;
+    a.h_ff.lo = (float)(params->h - (double)a.h_ff.hi);
+    a.lim_f[0] = (float)params->zmin;
+    a.lim_f[1] = (float)params->zmax;
+    a.lim_f[2] = (float)(params->rmax * params->rmax);
+    a.lim_f[3] = (float)sg.R0;
+    a.lim_f[4] = (float)sg.R1;
     a.n_rec = n_rec_of(params);
     cudaError_t e = comet::launch_propagate(dtype, *field, a, (cudaStream_t)stream);
     return e == cudaSuccess ? COMET_OK : cuda_fail(e, "propagate launch");

@@ -11,6 +11,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "internal.h"   // struct ff
+
 namespace comet {
 
 constexpr double kKappa = 299.792458;
@@ -191,6 +193,71 @@ __device__ __forceinline__ void two_sum_add(float &hi, float &lo, float d)
     const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(t, bb));
     hi = s;
     lo = err;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Float-float arithmetic: a value is the unevaluated sum hi + lo of two floats (about 48 bits).
+// Products use the exact FMA residual (TwoProd), sums Knuth's TwoSum; results are renormalised so
+// that hi is the float nearest to the pair.  Used for per-seed constants of the FP32 path, which
+// are then rounded to float once: on this part FP32 instructions are far cheaper than FP64 ones.
+// ------------------------------------------------------------------------------------------------
+
+__device__ __forceinline__ ff ff_renorm(float s, float e)   // |e| small against |s| (or s = 0)
+{
+    const float h = __fadd_rn(s, e);
+    return ff{h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+
+__device__ __forceinline__ ff ff_add(ff x, ff y)
+{
+    const float s = __fadd_rn(x.hi, y.hi);
+    const float v = __fsub_rn(s, x.hi);
+    float e = __fadd_rn(__fsub_rn(x.hi, __fsub_rn(s, v)), __fsub_rn(y.hi, v));
+    e = __fadd_rn(e, __fadd_rn(x.lo, y.lo));
+    return ff_renorm(s, e);
+}
+
+__device__ __forceinline__ ff ff_neg(ff x) { return ff{-x.hi, -x.lo}; }
+__device__ __forceinline__ ff ff_sub(ff x, ff y) { return ff_add(x, ff_neg(y)); }
+
+__device__ __forceinline__ ff ff_mul(ff x, ff y)
+{
+    const float p = __fmul_rn(x.hi, y.hi);
+    float e = __fmaf_rn(x.hi, y.hi, -p);
+    e = __fmaf_rn(x.hi, y.lo, e);
+    e = __fmaf_rn(x.lo, y.hi, e);
+    return ff_renorm(p, e);
+}
+
+__device__ __forceinline__ ff ff_mulf(ff x, float b)
+{
+    const float p = __fmul_rn(x.hi, b);
+    float e = __fmaf_rn(x.hi, b, -p);
+    e = __fmaf_rn(x.lo, b, e);
+    return ff_renorm(p, e);
+}
+
+// 1 / x: one Newton step r + r (1 - x r) from the float reciprocal, the residual in float-float.
+__device__ __forceinline__ ff ff_recip(ff x)
+{
+    const float r = __frcp_rn(x.hi);
+    const ff e = ff_sub(ff{1.f, 0.f}, ff_mulf(x, r));
+    return ff_add(ff{r, 0.f}, ff_mulf(e, r));
+}
+
+// sqrt(x), x > 0: one Newton step s + (x - s^2) / (2 s) from the float square root.
+__device__ __forceinline__ ff ff_sqrt(ff x)
+{
+    const float s = __fsqrt_rn(x.hi);
+    const float p = __fmul_rn(s, s);
+    const ff d = ff_sub(x, ff{p, __fmaf_rn(s, s, -p)});
+    return ff_renorm(s, __fdiv_rn(d.hi, __fmul_rn(2.f, s)));
+}
+
+// Exact float-float value of a double (host-side or constant operands).
+__host__ __device__ constexpr ff ff_of(double v)
+{
+    return ff{(float)v, (float)(v - (double)(float)v)};
 }
 
 // c = KAPPA q / P0 and 1 / P0 of a seed from its recorded momentum (state 0), in the working

@@ -9,6 +9,11 @@
 
 namespace comet {
 
+// A float-float value hi + lo (device.cuh holds its arithmetic).
+struct ff {
+    float hi, lo;
+};
+
 struct LatArgs {
     double vx, vy;
     double centre[4], half_width[4];
@@ -28,6 +33,9 @@ struct PropArgs {
     int n_steps, stride, n_rec;
     int G0, G1;            // segment sizes of the closest-state search
     double R0, R1;         // segment reaches (m), margins included
+    // FP32 copies rounded on the host: h as a float-float pair; zmin, zmax, rmax^2, R0, R1
+    ff h_ff;
+    float lim_f[5];
 };
 
 struct DcaArgs {

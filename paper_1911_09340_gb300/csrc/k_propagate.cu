@@ -139,6 +139,68 @@ __device__ __forceinline__ void axial_interval(double am1, double b, double c, d
     out[4] = dz * k;                           // dz
 }
 
+// The same interval map for the FP32 kernel, in float-float arithmetic (device.cuh) from the
+// seed's float momentum: P0 = |p| and the single-step coefficients, then the binary powering and
+// the geometric sum, each carried to ~48 bits and rounded to float once at the end.
+__device__ __forceinline__ AxialStep<float> axial_interval_ff(float px, float py, float pz, int q,
+                                                              float bz, ff h, int k)
+{
+    auto sq = [](float v) {
+        const float p = __fmul_rn(v, v);
+        return ff{p, __fmaf_rn(v, v, -p)};
+    };
+    const ff P0 = ff_sqrt(ff_add(ff_add(sq(px), sq(py)), sq(pz)));
+    const ff ip = ff_recip(P0);
+    const ff w = ff_mulf(ff_mul(ff_of(kKappa), ip), (float)q * bz);
+    const ff t = ff_mul(h, w);
+    const ff t2 = ff_mul(t, t);
+    const ff hp = ff_mul(h, ip);
+    const float t2f = t2.hi;
+    const ff g = ff_renorm(1.f, -t2f * (1.f / 6.f));                        // 1 - t^2/6
+    const ff a0r = ff_mul(t2, ff_renorm(-0.5f, t2f * (1.f / 24.f)));       // am1
+    const ff a0i = ff_neg(ff_mul(t, g));                                   // -b
+    const ff c = ff_mul(hp, g);
+    const ff d = ff_mul(ff_mul(hp, t), ff_renorm(0.5f, -t2f * (1.f / 24.f)));
+    // m^k - 1 by binary powering on A = m - 1, as in axial_interval
+    ff Rr{0.f, 0.f}, Ri{0.f, 0.f}, Br = a0r, Bi = a0i;
+    bool first = true;
+    for (int e = k; e > 0; e >>= 1) {
+        if (e & 1) {
+            if (first) {
+                Rr = Br;
+                Ri = Bi;
+                first = false;
+            } else {
+                const ff r = ff_add(ff_add(Rr, Br), ff_sub(ff_mul(Rr, Br), ff_mul(Ri, Bi)));
+                const ff i = ff_add(ff_add(Ri, Bi), ff_add(ff_mul(Rr, Bi), ff_mul(Ri, Br)));
+                Rr = r;
+                Ri = i;
+            }
+        }
+        if (e > 1) {
+            const ff r = ff_add(ff_mulf(Br, 2.f), ff_sub(ff_mul(Br, Br), ff_mul(Bi, Bi)));
+            const ff i = ff_mulf(ff_add(Bi, ff_mul(Br, Bi)), 2.f);
+            Br = r;
+            Bi = i;
+        }
+    }
+    // sum of m^j, j < k: (m^k - 1) / (m - 1), or k when the step does not turn
+    ff Sr{(float)k, 0.f}, Si{0.f, 0.f};
+    const ff den = ff_add(ff_mul(a0r, a0r), ff_mul(a0i, a0i));
+    if (den.hi > 0.f) {
+        const ff inv = ff_recip(den);
+        Sr = ff_mul(ff_add(ff_mul(Rr, a0r), ff_mul(Ri, a0i)), inv);
+        Si = ff_mul(ff_sub(ff_mul(Ri, a0r), ff_mul(Rr, a0i)), inv);
+    }
+    AxialStep<float> ks;
+    ks.am1 = Rr.hi;
+    ks.b = -Ri.hi;
+    ks.c = ff_add(ff_mul(c, Sr), ff_mul(d, Si)).hi;
+    ks.d = ff_sub(ff_mul(d, Sr), ff_mul(c, Si)).hi;
+    ks.dz = ff_mulf(ff_mulf(hp, pz), (float)k).hi;
+    return ks;
+}
+
 // One recording interval (stride RK4 steps) of one seed.  In an axial field the interval's map is
 // applied once (axial_interval); FP32 adds its increments to the compensated (hi, lo) state.  pz
 // is constant in an axial field.  Other fields take the steps one by one.  STRIDE > 0 fixes the
@@ -200,16 +262,25 @@ __global__ void __launch_bounds__(128) propagate_kernel(F f, PropArgs a)
         for (int c = 0; c < 6; ++c) y[c] = seeds[c * S + s];
         q = a.charge[s];
     }
-    const double pd = valid ? sqrt((double)y[3] * y[3] + (double)y[4] * y[4] + (double)y[5] * y[5]) : 1.0;
-    const double ipd = 1.0 / pd;
-    const T c = (T)(kKappa * q * ipd);
-    const T ip = (T)ipd;
-    const T h = (T)a.h;
-    const T zmin = (T)a.zmin, zmax = (T)a.zmax, rmax2 = (T)(a.rmax * a.rmax);
-    const T R0 = (T)a.R0, R1 = (T)a.R1;
-    // uniform axial field: the interval's map is fixed per seed (computed in double)
+    constexpr bool kFF = sizeof(T) == 4 && F::kAxial;   // FP32 axial: no double arithmetic at all
+    T c = T(0), ip = T(0);
+    double ipd = 1.0;
+    if constexpr (!kFF) {
+        const double pd = valid ? sqrt((double)y[3] * y[3] + (double)y[4] * y[4] + (double)y[5] * y[5]) : 1.0;
+        ipd = 1.0 / pd;
+        c = (T)(kKappa * q * ipd);
+        ip = (T)ipd;
+    }
+    const T h = kFF ? (T)a.h_ff.hi : (T)a.h;
+    const T zmin = kFF ? (T)a.lim_f[0] : (T)a.zmin, zmax = kFF ? (T)a.lim_f[1] : (T)a.zmax;
+    const T rmax2 = kFF ? (T)a.lim_f[2] : (T)(a.rmax * a.rmax);
+    const T R0 = kFF ? (T)a.lim_f[3] : (T)a.R0, R1 = kFF ? (T)a.lim_f[4] : (T)a.R1;
+    // uniform axial field: the interval's map is fixed per seed
     AxialStep<T> ks{};
-    if constexpr (F::kAxial) {
+    if constexpr (kFF) {
+        ks = axial_interval_ff(y[3], y[4], y[5], valid ? q : 0, f.bz, a.h_ff,
+                               STRIDE > 0 ? STRIDE : a.stride);
+    } else if constexpr (F::kAxial) {
         const double w = kKappa * q * (double)f.bz * ipd;
         const double t = a.h * w, t2 = t * t, hp = a.h * ipd;
         double m[5];

@@ -58,21 +58,25 @@ def test_fp64_points_match_oracle_single_event(ctx):
         assert np.abs(got[s, :n, 3:] - ref[s, :n, 3:]).max() <= 1e-9 * 105
 
 
-def test_fp32_points_within_5um_over_three_turns(ctx):
+@pytest.mark.parametrize("stride", [1, 16])
+def test_fp32_points_within_1um_over_three_turns(ctx, stride):
+    """The compensated FP32 state (and, in an axial field, the per-seed interval map formed in
+    float-float) stays within 1 um and 2e-6 relative momentum of the FP64 oracle over ~6,700 steps
+    (about 0.3 um is typical)."""
     ch = synth.make_chamber()
     ev = synth.multi_turn_event(0, ch)
     seeds = O.lattice(ev.partitions[0])[::257].astype(np.float32).astype(np.float64)
-    n = 3 * ev.n_steps[0]
-    op, bp = both_params(n_steps=n, **OPEN)
+    n = 3 * ev.n_steps[0] // stride * stride
+    op, bp = both_params(n_steps=n, stride=stride, **OPEN)
     field = synth.uniform_field(1.0)
     _, _, pts, nv = gpu_propagate(ctx, B.DeviceField.from_synth(field), bp, seeds, -1, torch.float32)
     ref, rnv = O.propagate(field, op, seeds, -1)
     got = to_aos_points(pts)
     assert np.array_equal(nv.cpu().numpy(), rnv)
     err = np.abs(got[:, :, :3] - ref[:, :, :3]).max()
-    assert err <= 5e-6, err
+    assert err <= 1e-6, err
     P0 = np.linalg.norm(seeds[:, 3:], axis=1)[:, None, None]
-    assert (np.abs(got[:, :, 3:] - ref[:, :, 3:]) / P0).max() <= 1e-5
+    assert (np.abs(got[:, :, 3:] - ref[:, :, 3:]) / P0).max() <= 2e-6
 
 
 @pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-9), (torch.float32, 5e-6)])
