@@ -260,6 +260,17 @@ __host__ __device__ constexpr ff ff_of(double v)
     return ff{(float)v, (float)(v - (double)(float)v)};
 }
 
+// hi + lo + d as a new pair by Fast2Sum (3 additions fewer than TwoSum): exact whenever |hi| is at
+// least |d + lo| in exponent; when a component passes through zero it is off by at most about
+// ulp(d), i.e. ~2e-9 m for a 16 mm step or ~5e-7 MeV/c for a 5 MeV/c one, a few times per turn.
+__device__ __forceinline__ void fast_two_sum_add(float &hi, float &lo, float d)
+{
+    const float t = __fadd_rn(d, lo);
+    const float s = __fadd_rn(hi, t);
+    lo = __fsub_rn(t, __fsub_rn(s, hi));
+    hi = s;
+}
+
 // c = KAPPA q / P0 and 1 / P0 of a seed from its recorded momentum (state 0), in the working
 // precision; the DCA and classification kernels use the same helper, hence the same values.
 template <typename T>
@@ -430,11 +441,16 @@ __device__ __forceinline__ float4 warp_sphere(bool has, T x, T y, T z, T reach)
     const T cx = T(0.5) * (__shfl_sync(0xffffffffu, x, l0) + __shfl_sync(0xffffffffu, x, l1));
     const T cy = T(0.5) * (__shfl_sync(0xffffffffu, y, l0) + __shfl_sync(0xffffffffu, y, l1));
     const T cz = T(0.5) * (__shfl_sync(0xffffffffu, z, l0) + __shfl_sync(0xffffffffu, z, l1));
-    T d = has ? sqrt((x - cx) * (x - cx) + (y - cy) * (y - cy) + (z - cz) * (z - cz)) : T(0);
+    T d;
     if constexpr (sizeof(T) == 4) {
-        // d >= 0: its bit pattern orders like its value, so one integer warp reduction finds the max
-        d = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(d)));
+        // d^2 >= 0: its bit pattern orders like its value, so one integer warp reduction finds the
+        // max; then one root by the hardware reciprocal square root (a few ulp, inside the 1e-6
+        // relative margin below)
+        const float d2 = has ? (x - cx) * (x - cx) + (y - cy) * (y - cy) + (z - cz) * (z - cz) : 0.f;
+        const float m2 = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(d2)));
+        d = m2 * rsqrtf(fmaxf(m2, 1e-30f));
     } else {
+        d = has ? sqrt((x - cx) * (x - cx) + (y - cy) * (y - cy) + (z - cz) * (z - cz)) : T(0);
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) d = fmax(d, __shfl_xor_sync(0xffffffffu, d, off));
     }

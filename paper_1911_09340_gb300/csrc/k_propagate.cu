@@ -10,9 +10,10 @@
 // of each group of 32 consecutive seeds (one warp), which the DCA kernel's closest-state search
 // uses: the 32 lanes record state r together, so a segment's sphere is one warp reduction at the
 // moment its centre state is recorded.  The FP32 path keeps every state component as an
-// unevaluated float pair (hi, lo) updated with TwoSum, so that the rounding of 6,500 steps does not
-// accumulate (plain FP32 drifts ~0.1 mm over three turns; the pair stays within ~1 um of FP64).
-// The step maps read the leading float only.
+// unevaluated float pair (hi, lo) updated with TwoSum (Fast2Sum for the axial interval map, see
+// device.cuh), so that the rounding of 6,500 steps does not accumulate (plain FP32 drifts ~0.1 mm
+// over three turns; the pair stays within ~0.3 um of FP64).  The step maps read the leading float
+// only.
 #include "device.cuh"
 #include "internal.h"
 
@@ -212,11 +213,11 @@ __device__ __forceinline__ void advance_interval(const F &f, const PropArgs &a, 
     const int stride = STRIDE > 0 ? STRIDE : a.stride;
     if constexpr (sizeof(T) == 4 && F::kAxial) {
         const float px = y[3], py = y[4];
-        two_sum_add(y[0], lo[0], ks.c * px + ks.d * py);
-        two_sum_add(y[1], lo[1], ks.c * py - ks.d * px);
-        two_sum_add(y[2], lo[2], ks.dz);
-        two_sum_add(y[3], lo[3], ks.am1 * px + ks.b * py);
-        two_sum_add(y[4], lo[4], ks.am1 * py - ks.b * px);
+        fast_two_sum_add(y[0], lo[0], ks.c * px + ks.d * py);
+        fast_two_sum_add(y[1], lo[1], ks.c * py - ks.d * px);
+        fast_two_sum_add(y[2], lo[2], ks.dz);
+        fast_two_sum_add(y[3], lo[3], ks.am1 * px + ks.b * py);
+        fast_two_sum_add(y[4], lo[4], ks.am1 * py - ks.b * px);
     } else if constexpr (F::kAxial) {
         T inc[6];
         axial_increment<T>(ks, y, inc);
@@ -326,7 +327,15 @@ __global__ void __launch_bounds__(128) propagate_kernel(F f, PropArgs a)
             if (outside_region<T>(y[0], y[1], y[2], zmin, zmax, rmax2)) active = false;
         }
         if (wb) {
-            if (r == c1) {
+            if (G1 == 1) {
+                // every recorded state is a level-1 segment of its own: (j1, m1) = (r / G0, r % G0)
+                const float4 sp = warp_sphere<T>(valid && last_k >= r, y[0], y[1], y[2], R1);
+                if (lane == 0) tab[kN0Max + j1 * kN1Max + m1] = sp;
+                if (++m1 == G0) {
+                    m1 = 0;
+                    ++j1;
+                }
+            } else if (r == c1) {
                 const float4 sp = warp_sphere<T>(valid && last_k >= st1, y[0], y[1], y[2], R1);
                 if (lane == 0) tab[kN0Max + j1 * kN1Max + m1] = sp;
                 ++m1;
