@@ -135,13 +135,23 @@ def make_events(indices, counts=(16, 16, 32, 32)):
 
 def evals_of(ev, classes):
     """Seed x unmasked-hit pairs of each partition, from the per-partition hit classes."""
+    return pairs_of(ev, classes)[0]
+
+
+def pairs_of(ev, classes):
+    """(seed x unmasked hit, seed x wire with an unmasked hit) pairs summed over the partitions."""
     H = ev.n_hits
     masked = np.zeros(H, bool)
-    total = 0
+    hits = wires = 0
+    offs = np.asarray(ev.hit_offsets)
     for spec, cls in zip(ev.partitions, classes):
-        total += spec.n_seeds * int((~masked).sum())
+        live = ~masked
+        hits += spec.n_seeds * int(live.sum())
+        per_wire = np.add.reduceat(live.astype(np.int64), offs[:-1]) if H else np.zeros(0)
+        per_wire[offs[:-1] == offs[1:]] = 0
+        wires += spec.n_seeds * int((per_wire > 0).sum())
         masked |= cls[:H].astype(bool)
-    return total
+    return hits, wires
 
 
 # ------------------------------------------------------------------------------------------------
@@ -254,12 +264,15 @@ def run_ours(args, rank, world):
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     dev_s = sum(step_ms) / 1e3
     evals = 0
+    wire_pairs = 0
     n_parts = 0
     for j in range(args.steps):
         i = args.warmup + j
         ev = events[i]
         cl = classes[i].cpu().numpy()
-        evals += evals_of(ev, cl)
+        e_h, e_w = pairs_of(ev, cl)
+        evals += e_h
+        wire_pairs += e_w
         n_parts += len(ev.partitions)
     kt = timer.totals()
     t_max = max_over_ranks(dev_s, world)
@@ -305,11 +318,12 @@ def run_ours(args, rank, world):
     peaks = _peaks()
     dom = max(kt, key=lambda k: kt[k][0])
     dom_ms, dom_launches = kt[dom]
+    dca_flops = (DCA_FLOPS_PER_WIRE * wire_pairs + DCA_FLOPS_PER_HIT * evals) / max(n_parts, 1)
     roof = roofline_entry(dom, dom_ms / dom_launches, events[args.warmup:], params[args.warmup:], S,
-                          clocks, peaks, evals / max(n_parts, 1))
+                          clocks, peaks, dca_flops)
     second = "propagate" if dom != "propagate" else "dca"
     roof_prop = roofline_entry(second, kt[second][0] / kt[second][1], events[args.warmup:],
-                               params[args.warmup:], S, clocks, peaks, evals / max(n_parts, 1))
+                               params[args.warmup:], S, clocks, peaks, dca_flops)
     cpu = oracle_rate(make_events([0])[0], target_s=args.cpu_seconds) if not args.no_cpu else None
     out = {
         "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
@@ -338,13 +352,14 @@ def run_ours(args, rank, world):
     ctx.close()
 
 
-# Algorithmic work of the kernels (counted from the formulas; the derivation is in the design doc):
-#  - one (seed, hit) DCA evaluation of Algorithm 2 from the closest recorded state: 3 virtual-plane
-#    evaluations (35 flops each), 2 RK4 refinement steps in the axial-field map (38 each), the DCA
-#    (20) and residual/cap/square/accumulate (8): 209 FP32 flops per refined wire, taken as 200 per
-#    hit (1.05 hits per wire); FMA = 2 flops;
+# Algorithmic work of the kernels (counted from the formulas; FMA = 2 flops):
+#  - per (seed, wire with an unmasked hit), Algorithm 2 from the closest recorded state: 3
+#    virtual-plane evaluations (35 flops each), 2 RK4 refinement steps in the axial-field map (38
+#    each) and the DCA (20) = 201 FP32 flops; per (seed, unmasked hit) the residual, min, cap,
+#    square and accumulate of Eq. 1 = 8 flops.  The closest-state search is not counted;
 #  - the recording of one state: 6 FP32 stores = 24 bytes (the propagate kernel is store-bound).
-DCA_FLOPS_PER_EVAL = 200
+DCA_FLOPS_PER_WIRE = 201
+DCA_FLOPS_PER_HIT = 8
 PROP_BYTES_PER_REC = 24
 
 
@@ -353,7 +368,7 @@ def fp32_peak_tflops(peaks):
     return 2 * 152 * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
 
 
-def roofline_entry(kernel, avg_ms, events, params, S, clocks, peaks, evals_per_launch):
+def roofline_entry(kernel, avg_ms, events, params, S, clocks, peaks, dca_flops_per_launch):
     n_launch = sum(len(ev.partitions) for ev in events)
     if kernel == "propagate":
         recs = sum(bp.n_rec for ps in params for bp in ps) / n_launch
@@ -363,12 +378,14 @@ def roofline_entry(kernel, avg_ms, events, params, S, clocks, peaks, evals_per_l
         return {"kernel": kernel, "bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
                 "frac": gbs / hbm, "traffic": None, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
     if kernel == "dca":
-        tf = evals_per_launch * DCA_FLOPS_PER_EVAL / (avg_ms * 1e-3) / 1e12
+        tf = dca_flops_per_launch / (avg_ms * 1e-3) / 1e12
         peak = fp32_peak_tflops(peaks)
         return {"kernel": kernel, "bound": "alu", "achieved": tf, "peak": peak, "unit": "TFLOP/s",
                 "frac": tf / peak, "traffic": None,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
-                "flops_per_eval": DCA_FLOPS_PER_EVAL, "avg_launch_ms": avg_ms}
+                "flops_per_launch": dca_flops_per_launch,
+                "flops_per_unit": {"seed_wire": DCA_FLOPS_PER_WIRE, "seed_hit": DCA_FLOPS_PER_HIT},
+                "avg_launch_ms": avg_ms}
     return {"kernel": kernel, "bound": None, "achieved": None, "peak": None, "unit": None,
             "frac": None, "traffic": None, "avg_launch_ms": avg_ms}
 

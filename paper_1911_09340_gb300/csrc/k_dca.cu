@@ -384,7 +384,8 @@ __device__ __forceinline__ void group_wires(const F &f, const DcaArgs &a, const 
             }
 
             // refinement from the closest recorded state (only when it can matter)
-            const bool refine = want && bk != 0x7fffffff && (a.exact_all || sqrt(bd) <= capth);
+            // (compared squared: capth carries margins far above the rounding of the square)
+            const bool refine = want && bk != 0x7fffffff && (a.exact_all || bd <= capth * capth);
             T D = T(INFINITY);
             if (refine) {
                 T yv[6];
