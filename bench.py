@@ -158,15 +158,16 @@ def pairs_of(ev, classes):
 # CPU oracle timing (cpu_baseline of our arm, and the whole reference arm)
 # ------------------------------------------------------------------------------------------------
 
-def oracle_rate(ev, target_s: float = 10.0, nthreads=None):
+def oracle_rate(ev, target_s: float = 10.0, nthreads=None, stride: int = 16):
     """Times the oracle's RSS scan of partition 0 on a strided sample of its seeds, sized for
-    ~target_s of CPU time; returns (evals/s, threads, sample description)."""
+    ~target_s of CPU time, recording every stride-th state like the GPU arm; returns (evals/s,
+    threads, sample description)."""
     import oracle as O
     from paper_1911_09340_gb300 import synth
     nthreads = nthreads or O.default_threads()
     spec = ev.partitions[0]
     seeds = O.lattice(spec).astype(np.float32).astype(np.float64)
-    op = O.Params(n_steps=ev.n_steps[0], stride=1, lam=0.01, tol=1e-12)
+    op = O.Params(n_steps=ev.n_steps[0], stride=stride, lam=0.01, tol=1e-12)
     field = synth.uniform_field(1.0)
     wires = O.wires_aos(ev.wires)
     mask = np.zeros(ev.n_hits, np.uint8)
@@ -182,7 +183,14 @@ def oracle_rate(ev, target_s: float = 10.0, nthreads=None):
     dt, n = run(n2)
     evals = n * ev.n_hits
     return evals / dt, nthreads, f"{n} of {spec.n_seeds} seeds (strided) of turn partition 0 of event 0, " \
-                                f"{ev.n_hits} hits, FP64 oracle, {dt:.1f} s"
+                                f"{ev.n_hits} hits, stride {stride}, FP64 oracle, {dt:.1f} s"
+
+
+def workload_config(args):
+    """The workload keys both arms report."""
+    counts = args.lattice or (16, 16, 32, 32)
+    return {"workload": WORKLOAD, "seeds_per_partition": int(np.prod(counts)), "stride": args.stride,
+            "lambda_m": 0.01, "rk4_step_m": 1e-3}
 
 
 def run_reference(args, rank, world):
@@ -192,7 +200,7 @@ def run_reference(args, rank, world):
     ev = make_events([0])[0]
     steps = []
     for i in range(args.warmup + args.steps):
-        rate, cores, sample = oracle_rate(ev, target_s=args.ref_seconds)
+        rate, cores, sample = oracle_rate(ev, target_s=args.ref_seconds, stride=args.stride)
         if i >= args.warmup:
             steps.append(rate)
     value = statistics.median(steps)
@@ -200,7 +208,7 @@ def run_reference(args, rank, world):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "parallelism": "host threads"},
+        "config": dict(workload_config(args), parallelism=f"host threads ({cores})"),
         "cpu_baseline": {"value": value, "unit": "evals/s", "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -319,22 +327,37 @@ def run_ours(args, rank, world):
     dom = max(kt, key=lambda k: kt[k][0])
     dom_ms, dom_launches = kt[dom]
     dca_flops = (DCA_FLOPS_PER_WIRE * wire_pairs + DCA_FLOPS_PER_HIT * evals) / max(n_parts, 1)
-    roof = roofline_entry(dom, dom_ms / dom_launches, events[args.warmup:], params[args.warmup:], S,
-                          clocks, peaks, dca_flops)
+    # states the timed propagate launches recorded (tracks leaving the target region stop early):
+    # lattice + propagate of each timed partition once more, untimed, summing n_valid
+    recorded = 0
+    for j in range(args.steps):
+        i = args.warmup + j
+        for spec, bp in zip(events[i].partitions, params[i]):
+            seeds, charge, pts, nv, _, _ = ws.views(spec.n_seeds, bp.n_rec)
+            B.comet_scan_lattice(ctx, spec, seeds, charge)
+            B.comet_scan_propagate(ctx, field, bp, seeds, charge, pts, nv)
+            recorded += int(nv.sum().item())
+    prop_bytes = (PROP_BYTES_PER_REC * recorded + 24 * S * n_parts) / max(n_parts, 1)
+    roof = roofline_entry(dom, dom_ms / dom_launches, prop_bytes, clocks, peaks, dca_flops,
+                          args.stride)
     second = "propagate" if dom != "propagate" else "dca"
-    roof_prop = roofline_entry(second, kt[second][0] / kt[second][1], events[args.warmup:],
-                               params[args.warmup:], S, clocks, peaks, dca_flops)
-    cpu = oracle_rate(make_events([0])[0], target_s=args.cpu_seconds) if not args.no_cpu else None
+    roof_prop = roofline_entry(second, kt[second][0] / kt[second][1], prop_bytes, clocks, peaks,
+                               dca_flops, args.stride)
+    cpu = (oracle_rate(make_events([0])[0], target_s=args.cpu_seconds, stride=args.stride)
+           if not args.no_cpu else None)
+    cpu1 = (oracle_rate(make_events([0])[0], target_s=max(1.0, args.cpu_seconds / 4), nthreads=1,
+                        stride=args.stride) if not args.no_cpu else None)
     out = {
         "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "events_per_s": events_all / t_max,
-        "config": {"workload": WORKLOAD, "events": events_all, "seeds_per_partition": S,
-                   "partitions": n_parts * world, "stride": args.stride, "lambda_m": 0.01,
-                   "rk4_step_m": 1e-3, "l2": "256 MiB buffer written between timed steps; "
-                   "track points (>1 GB per partition) also exceed L2",
-                   "parallelism": f"replicas: {world} GPU(s), disjoint events"},
+        "event_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
+                     "max": max(step_ms)},
+        "config": dict(workload_config(args), events=events_all, partitions=n_parts * world,
+                       l2="256 MiB buffer written between timed steps; track points (~0.9 GB per "
+                          "partition) also exceed L2",
+                       parallelism=f"replicas: {world} GPU(s), disjoint events"),
         "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": h2d // args.steps,
                 "d2h_bytes_per_step": d2h // args.steps},
         "gpu_launches": scan.LAUNCHES_PER_PARTITION * n_parts,
@@ -347,7 +370,8 @@ def run_ours(args, rank, world):
     }
     if cpu is not None:
         out["cpu_baseline"] = {"value": cpu[0], "unit": "evals/s", "cores": cpu[1], "kind": "oracle",
-                               "sample": cpu[2]}
+                               "sample": cpu[2], "value_1_thread": cpu1[0],
+                               "sample_1_thread": cpu1[2]}
     print(json.dumps(out), flush=True)
     ctx.close()
 
@@ -357,10 +381,38 @@ def run_ours(args, rank, world):
 #    virtual-plane evaluations (35 flops each), 2 RK4 refinement steps in the axial-field map (38
 #    each) and the DCA (20) = 201 FP32 flops; per (seed, unmasked hit) the residual, min, cap,
 #    square and accumulate of Eq. 1 = 8 flops.  The closest-state search is not counted;
-#  - the recording of one state: 6 FP32 stores = 24 bytes (the propagate kernel is store-bound).
+#  - the recording of one state: 6 FP32 stores = 24 bytes (the propagate kernel is store-bound),
+#    counted over the states actually recorded (sum of n_valid), plus 24 bytes per seed read.
 DCA_FLOPS_PER_WIRE = 201
 DCA_FLOPS_PER_HIT = 8
 PROP_BYTES_PER_REC = 24
+
+# DRAM bytes (read + write) per launch of the two main kernels on this workload at stride 16, from
+# the ncu launch list in profiles/launches_multi_turn_2e18_stride16.md (mean over its 80 launches).
+# Valid only for the kernel sources they were measured on (SHA-1 of the package's csrc/ files);
+# reported as null once those change.
+NCU_TRAFFIC = {"csrc_sha1": "97d6be73e52b2631f9ff257f1bbac17ac5a09afb", "stride": 16,
+               "dca": 301857859.2, "propagate": 851682790.4}
+
+
+def csrc_sha1() -> str:
+    import hashlib
+    d = os.path.join(ROOT, "paper_1911_09340_gb300", "csrc")
+    h = hashlib.sha1()
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(f.encode())
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(kernel: str, stride: int):
+    try:
+        ok = csrc_sha1() == NCU_TRAFFIC["csrc_sha1"] and stride == NCU_TRAFFIC["stride"]
+    except OSError:
+        ok = False
+    return NCU_TRAFFIC.get(kernel) if ok else None
 
 
 def fp32_peak_tflops(peaks):
@@ -368,20 +420,21 @@ def fp32_peak_tflops(peaks):
     return 2 * 152 * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
 
 
-def roofline_entry(kernel, avg_ms, events, params, S, clocks, peaks, dca_flops_per_launch):
-    n_launch = sum(len(ev.partitions) for ev in events)
+def roofline_entry(kernel, avg_ms, prop_bytes_per_launch, clocks, peaks, dca_flops_per_launch,
+                   stride=None):
+    traffic = measured_traffic(kernel, stride)
     if kernel == "propagate":
-        recs = sum(bp.n_rec for ps in params for bp in ps) / n_launch
-        bytes_ = S * recs * PROP_BYTES_PER_REC + S * 24
+        bytes_ = prop_bytes_per_launch
         gbs = bytes_ / (avg_ms * 1e-3) / 1e9
         hbm = peaks.get("hbm_gbs", 6782.8)
         return {"kernel": kernel, "bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
-                "frac": gbs / hbm, "traffic": None, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
+                "frac": gbs / hbm, "traffic": traffic, "algorithmic_bytes": bytes_,
+                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
     if kernel == "dca":
         tf = dca_flops_per_launch / (avg_ms * 1e-3) / 1e12
         peak = fp32_peak_tflops(peaks)
         return {"kernel": kernel, "bound": "alu", "achieved": tf, "peak": peak, "unit": "TFLOP/s",
-                "frac": tf / peak, "traffic": None,
+                "frac": tf / peak, "traffic": traffic,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
                 "flops_per_launch": dca_flops_per_launch,
                 "flops_per_unit": {"seed_wire": DCA_FLOPS_PER_WIRE, "seed_hit": DCA_FLOPS_PER_HIT},
