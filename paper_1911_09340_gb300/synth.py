@@ -373,6 +373,22 @@ def partition_lattices(track, s_turn, q, n_turns, counts, rng,
     return out
 
 
+def backward_partition(ev: "Event", k: int, half_width=None) -> LatticeSpec:
+    """Lattice spec scanning turn partition k backwards from its end (the paper's exit-side half
+    track, Sec. 3.1: extrapolation backwards by flipping the charge and the momentum).  Reversing
+    q and p turns dp/ds = (KAPPA q/P0) p x B into itself along the reversed path, so the seed at the
+    end of turn k with (-q, -p) retraces the turn.  Uniform field: the end state has the vertex's
+    x, y, z advanced by one turn, the same momentum; the lattice keeps the forward partition's
+    offsets of its centre from the truth, with phi + pi and -p_z, and its half-widths and counts."""
+    fwd = ev.partitions[k]
+    dz = ev.pz / math.hypot(ev.pt, ev.pz) * ev.s_turn
+    z0, phi, pz, pt = fwd.centre
+    phib = math.atan2(math.sin(phi + math.pi), math.cos(phi + math.pi))
+    return LatticeSpec(vxy=fwd.vxy, centre=(z0 + dz, phib, -pz, pt),
+                       half_width=tuple(half_width or fwd.half_width), counts=fwd.counts,
+                       charge=-fwd.charge)
+
+
 def steps_for(spec: LatticeSpec, bz: float = 1.0, h: float = 1e-3, margin: float = 1.02) -> int:
     """RK4 steps of one turn partition: one helix turn's arc length at the lattice centre
     (2*pi*P0/(KAPPA*|q|*B)), plus a 2% margin."""

@@ -80,3 +80,54 @@ def test_multi_turn_event_fp32_full_size_sampled(ctx, stride):
     wid = np.repeat(np.arange(ev.n_wires), np.diff(ev.hit_offsets))
     edge = np.abs(np.abs(dwr[wid] - ev.drift) - bp.lam) < 2e-6
     assert np.array_equal(g_cls[~edge], cls[~edge]) or (g_cls != cls).sum() <= 2
+
+
+def test_backward_partition_fp64_matches_oracle(ctx):
+    """The exit-side (backward) scan of turn partition 0 — flipped charge and momentum — through the
+    library against the oracle's pipeline, same bars as the forward scan."""
+    ev = synth.single_event_fp64()
+    f = B.DeviceField.from_synth(UNIFORM)
+    dev = scan.DeviceEvent.from_event(ev, torch.float64)
+    spec = synth.backward_partition(ev, 0)
+    bp = scan.params_for(spec, ev.n_steps[0], torch.float64)
+    ws = scan.Workspace(spec.n_seeds, bp.n_rec, ev.n_hits, torch.float64)
+    scan.scan_partition(ctx, f, bp, spec, dev, ws)
+    torch.cuda.synchronize()
+    op = O.Params(n_steps=bp.n_steps, stride=bp.stride, lam=bp.lam, tol=1e-12)
+    r = O.scan_partition(UNIFORM, op, spec, O.wires_aos(ev.wires), ev.hit_offsets, ev.drift,
+                         np.zeros(ev.n_hits, np.uint8))
+    g_rss = ws.rss[:spec.n_seeds].cpu().numpy()
+    g_idx = int(ws.idx[0])
+    assert np.allclose(g_rss, r["rss"], rtol=1e-10, atol=0)
+    assert g_idx == int(r["idx"][0]) or r["rss"][g_idx] <= r["best_rss"][0] * (1 + 1e-5)
+    assert np.array_equal(ws.hit_class[:ev.n_hits].cpu().numpy(), r["hit_class"])
+    # the backward scan represents turn 0 and finds most of its hits, as the forward scan does
+    from paper_1911_09340_gb300 import metrics as M
+    m = M.stage_metrics(r["hit_class"].astype(bool), ev.hit_turn)
+    rf = O.scan_partition(UNIFORM, op, ev.partitions[0], O.wires_aos(ev.wires), ev.hit_offsets,
+                          ev.drift, np.zeros(ev.n_hits, np.uint8))
+    mf = M.stage_metrics(rf["hit_class"].astype(bool), ev.hit_turn)
+    assert m.turn == mf.turn == 0 and m.efficiency > 0.8
+    assert abs(m.efficiency - mf.efficiency) <= 0.05
+
+
+def test_stage_metrics_from_gpu_equal_oracle_at_0_8_mm(ctx):
+    """Stage metrics (lambda = 0.8 mm, the paper's optimum) from the library's stages equal those
+    from the oracle's stages, FP64, every partition of the single event."""
+    from paper_1911_09340_gb300 import experiments as X
+    from paper_1911_09340_gb300 import metrics as M
+    ev = synth.single_event_fp64()
+    f = B.DeviceField.from_synth(UNIFORM)
+    dev = scan.DeviceEvent.from_event(ev, torch.float64)
+    ws = scan.Workspace(ev.partitions[0].n_seeds, max(ev.n_steps) + 1, ev.n_hits, torch.float64)
+    g = X.scan_stages(ctx, f, ev, dev, ws, ev.partitions, ev.n_steps, torch.float64, 1, 8e-4)
+    omask = np.zeros(ev.n_hits, np.uint8)
+    o = []
+    for spec, n in zip(ev.partitions, ev.n_steps):
+        r = O.scan_partition(UNIFORM, O.Params(n_steps=n, stride=1, lam=8e-4, tol=1e-12), spec,
+                             O.wires_aos(ev.wires), ev.hit_offsets, ev.drift, omask)
+        o.append(r["hit_class"].astype(bool))
+        omask = r["mask"]
+    for a, b in zip(g, o):
+        assert np.array_equal(a, b)
+    assert M.event_metrics(g, ev.hit_turn) == M.event_metrics(o, ev.hit_turn)

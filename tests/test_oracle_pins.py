@@ -461,3 +461,26 @@ def test_refined_dca_stays_in_its_valley(chamber, stride):
             assert dmin - 0.5 * h_rec - 1e-12 <= D <= dmin + h_rec + 1e-12
             if dmin < 0.05:
                 assert D <= dmin + 1e-12
+
+
+def test_backward_seed_retraces_the_turn():
+    """Flipping q and p at the end of a turn (the exit-side half track, Sec. 3.1) retraces the turn:
+    the backward recording, read in reverse, is the forward one; the backward lattice of
+    synth.backward_partition is centred on that reversed state with the forward lattice's offsets."""
+    ev = synth.single_event_fp64()
+    field = synth.uniform_field(1.0)
+    n = int(ev.s_turn / 1e-3)
+    tr0 = np.array([*ev.vertex, ev.pt * math.cos(ev.phi0), ev.pt * math.sin(ev.phi0), ev.pz])
+    P = O.Params(n_steps=n, stride=1, **OPEN)
+    fwd, _ = O.propagate(field, P, tr0[None], ev.q)
+    pos, mom = synth.helix_points(ev.vertex, ev.pt, ev.phi0, ev.pz, ev.q, 1.0, np.array([n * 1e-3]))
+    end = np.array([*pos[:, 0], *(-mom[:, 0])])
+    bwd, _ = O.propagate(field, P, end[None], -ev.q)
+    assert np.abs(bwd[0, :, :3] - fwd[0, ::-1, :3]).max() <= 1e-9
+    assert np.abs(bwd[0, :, 3:] + fwd[0, ::-1, 3:]).max() <= 1e-9 * ev.p
+    spec, back = ev.partitions[0], synth.backward_partition(ev, 0)
+    dz_turn = ev.pz / ev.p * ev.s_turn
+    assert back.charge == -spec.charge and back.counts == spec.counts
+    assert back.centre[0] - spec.centre[0] == pytest.approx(dz_turn, abs=1e-12)
+    assert math.cos(back.centre[1] - spec.centre[1]) == pytest.approx(-1.0, abs=1e-12)
+    assert back.centre[2] == -spec.centre[2] and back.centre[3] == spec.centre[3]
