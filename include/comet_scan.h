@@ -9,6 +9,8 @@
  *   comet_scan_propagate  track recording: extrapolate every seed, record its states (Algorithm 1)
  *   comet_scan_dca        DCA of every (seed, wire) and the capped per-seed RSS      (Algorithm 2, Eq. 1)
  *   comet_scan_select     the seeds of lowest RSS                                     (Sec. 2.1)
+ *   comet_scan_refine_refs, comet_scan_lattice_refined
+ *                         sparse references and finer lattices around them            (Sec. 2.1)
  *   comet_scan_classify   classify the selected seed's hits; mask them for the next   (Sec. 2.1, 3.1)
  *                         turn partition
  *
@@ -195,6 +197,43 @@ comet_status comet_scan_dca(comet_ctx *ctx, comet_dtype dtype, const comet_field
  * Uses the context's device scratch (allocated on first use). */
 comet_status comet_scan_select(comet_ctx *ctx, comet_dtype dtype, const void *rss, int64_t S,
                                int32_t k, int64_t *idx_out, void *rss_out, comet_stream stream);
+
+/* ---- iterative refinement: references for a finer scan (Sec. 2.1) --------------------------------
+ * Sec. 2.1: the seeds of lowest RSS become reference points for the next scan, whose seeds are taken
+ * in their vicinity with a finer granularity; the references are kept sparse enough that the new
+ * seed sets do not overlap.
+ *   seeds       SoA [6][S] T: the scanned seeds (as written by comet_scan_lattice or
+ *               comet_scan_lattice_refined).
+ *   idx         [M] int64 device: candidate seed indices in the order to consider them (ascending
+ *               RSS, as comet_scan_select returns them); indices outside [0, S) are skipped.
+ *   M           1 .. 1048576.
+ *   half_width  HOST [4] double >= 0: half-widths (z0, phi, pz, pT) of the lattices that will be
+ *               built around the references.
+ *   K           1 .. 32: the most references to take.
+ *   refs_out    out, [K][4] double device: lattice coordinates (z0, phi = atan2(py, px), pz,
+ *               pT = hypot(px, py)) of each accepted reference, best first.
+ *   n_refs_out  out, [1] int32 device: number accepted (1 .. K when any index is valid).
+ * A candidate is accepted unless some accepted reference lies within 2 * half_width[d] of it in
+ * every coordinate d (phi modulo 2 pi): the two new lattices would overlap.  One warp; the greedy
+ * walk is sequential in the candidate order. */
+comet_status comet_scan_refine_refs(comet_ctx *ctx, comet_dtype dtype, const void *seeds, int64_t S,
+                                    const int64_t *idx, int32_t M, const double half_width[4],
+                                    int32_t K, double *refs_out, int32_t *n_refs_out,
+                                    comet_stream stream);
+
+/* ---- iterative refinement: the finer lattices (Sec. 2.1) ------------------------------------------
+ *   shape     lattice of comet_scan_lattice whose centre is ignored: vertex (vx, vy), half-widths,
+ *             counts and charge of every new lattice.
+ *   refs      [K][4] double device, n_refs [1] int32 device: as written by comet_scan_refine_refs.
+ *   K         1 .. 32 lattices; seeds k*S1 .. (k+1)*S1 - 1 (S1 = product of shape.counts) form
+ *             lattice k, centred at refs[k] while k < *n_refs and at refs[0] beyond (a repeat, so
+ *             that the seed count stays K*S1 whatever the number of references).
+ *   seeds     out, SoA [6][S] T with S = K * S1; charge_out out, [S] int8 (may be NULL).
+ * Inside each lattice the seeds follow the blocked numbering of comet_scan_lattice. */
+comet_status comet_scan_lattice_refined(comet_ctx *ctx, comet_dtype dtype, const comet_lattice *shape,
+                                        const double *refs, const int32_t *n_refs, int32_t K,
+                                        void *seeds, int8_t *charge_out, int64_t S,
+                                        comet_stream stream);
 
 /* ---- selection without device allocation (the paper has no counterpart) -------------------------
  * Same result as comet_scan_select, for callers that cannot allocate device memory: for example a

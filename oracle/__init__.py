@@ -229,3 +229,45 @@ def scan_partition(field, params: Params, spec, wires, hit_offsets, drift, mask,
                            mask, update_mask)
     res.update(seeds=seeds, idx=idx, best_rss=val, hit_class=cls, dca_wire=dw, mask=m2)
     return res
+
+
+def refine_refs(seeds, idx, half_width, K):
+    """Sec. 2.1, iterative refinement: "several seeds with the lowest RSS are selected as reference
+    points for the next seed scanning", kept "sparse enough to avoid overlaps between new seed sets".
+    Walks the candidate indices in the given order (ascending RSS) and keeps a candidate unless an
+    already kept reference lies closer than 2 * half_width[d] in every lattice coordinate d of
+    (z0, phi, pz, pT) (phi modulo 2 pi), i.e. unless the two new lattices would overlap; stops at K.
+    ``seeds`` is AoS [S][6].  Returns the kept references as an [n, 4] float64 array."""
+    seeds = np.asarray(seeds, dtype=np.float64)
+    hw = np.asarray(half_width, dtype=np.float64)
+    kept = []
+    for s in np.asarray(idx).tolist():
+        if len(kept) == K:
+            break
+        if s < 0 or s >= seeds.shape[0]:
+            continue
+        x = seeds[s]
+        c = np.array([x[2], np.arctan2(x[4], x[3]), x[5], np.hypot(x[3], x[4])])
+        clash = False
+        for r in kept:
+            d = c - r
+            d[1] = np.remainder(d[1] + np.pi, 2.0 * np.pi) - np.pi
+            if np.all(np.abs(d) < 2.0 * hw):
+                clash = True
+                break
+        if not clash:
+            kept.append(c)
+    return np.array(kept, dtype=np.float64).reshape(-1, 4)
+
+
+def lattice_refined(shape, refs, K):
+    """The finer scan's seeds: K lattices of ``shape``'s vertex, half-widths and counts, lattice k
+    centred at refs[k] (refs[0] again for k beyond the references found), one after the other, each
+    in the oracle's lattice order.  Returns AoS [K * S1][6]."""
+    import dataclasses as _dc
+    refs = np.asarray(refs, dtype=np.float64).reshape(-1, 4)
+    out = []
+    for k in range(K):
+        c = refs[k] if k < refs.shape[0] else refs[0]
+        out.append(lattice(_dc.replace(shape, centre=tuple(float(v) for v in c))))
+    return np.concatenate(out, axis=0)

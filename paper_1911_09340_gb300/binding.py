@@ -63,6 +63,10 @@ SIGNATURES = {
                        _vp, _vp, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "comet_scan_select": [_vp, C.c_int, _vp, _i64, _i32, _vp, _vp, _vp],
     "comet_scan_select_noalloc": [C.c_int, _vp, _i64, _i32, _vp, _vp, _vp],
+    "comet_scan_refine_refs": [_vp, C.c_int, _vp, _i64, _vp, _i32, C.POINTER(C.c_double), _i32, _vp,
+                               _vp, _vp],
+    "comet_scan_lattice_refined": [_vp, C.c_int, C.POINTER(_Lattice), _vp, _vp, _i32, _vp, _vp, _i64,
+                                   _vp],
     "comet_scan_classify": [_vp, C.c_int, C.POINTER(_Field), C.POINTER(_Params), _vp, _vp, _vp,
                             _i64, _vp, _vp, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _i32, _vp],
 }
@@ -253,6 +257,27 @@ def comet_scan_select_noalloc(rss, k: int, idx_out, rss_out=None, stream=None):
     _check(lib().comet_scan_select_noalloc(_dtype_code(rss), _ptr(rss), rss.shape[0], int(k),
                                            _ptr(idx_out, torch.int64), _ptr(rss_out, rss.dtype),
                                            _stream(stream)))
+
+
+def comet_scan_refine_refs(ctx: Context, seeds, idx, half_width, K: int, refs_out, n_refs_out,
+                           stream=None):
+    """Sparse reference points for a finer scan: ``refs_out`` [K, 4] float64 (z0, phi, pz, pT),
+    ``n_refs_out`` [1] int32, both on the device."""
+    hw = (C.c_double * 4)(*[float(v) for v in half_width])
+    _check(lib().comet_scan_refine_refs(ctx.handle, _dtype_code(seeds), _ptr(seeds), seeds.shape[-1],
+                                        _ptr(idx, torch.int64), idx.shape[0], hw, int(K),
+                                        _ptr(refs_out, torch.float64), _ptr(n_refs_out, torch.int32),
+                                        _stream(stream)))
+
+
+def comet_scan_lattice_refined(ctx: Context, shape_spec, refs, n_refs, K: int, seeds,
+                               charge: Optional[torch.Tensor] = None, stream=None):
+    """K lattices of ``shape_spec``'s half-widths and counts around the references (centre ignored)."""
+    lat = lattice_struct(shape_spec)
+    _check(lib().comet_scan_lattice_refined(ctx.handle, _dtype_code(seeds), C.byref(lat),
+                                            _ptr(refs, torch.float64), _ptr(n_refs, torch.int32),
+                                            int(K), _ptr(seeds), _ptr(charge, torch.int8),
+                                            seeds.shape[-1], _stream(stream)))
 
 
 def comet_scan_classify(ctx: Context, field: DeviceField, params: ScanParams, points, n_valid,

@@ -230,6 +230,77 @@ comet_status comet_scan_lattice(comet_ctx *ctx, comet_dtype dtype, const comet_l
     return e == cudaSuccess ? COMET_OK : cuda_fail(e, "lattice launch");
 }
 
+comet_status comet_scan_refine_refs(comet_ctx *ctx, comet_dtype dtype, const void *seeds, int64_t S,
+                                    const int64_t *idx, int32_t M, const double half_width[4],
+                                    int32_t K, double *refs_out, int32_t *n_refs_out,
+                                    comet_stream stream)
+{
+    if (!ctx) return fail(COMET_ERR_INVALID_ARG, "ctx is NULL");
+    CHECK(check_dtype(dtype));
+    if (S <= 0) return fail(COMET_ERR_INVALID_ARG, "S must be > 0");
+    if (!seeds || !aligned(seeds, esize(dtype))) return fail(COMET_ERR_INVALID_ARG, "seeds is NULL or misaligned");
+    if (!idx || !aligned(idx, 8)) return fail(COMET_ERR_INVALID_ARG, "idx is NULL or misaligned");
+    if (M < 1 || M > (1 << 20)) return fail(COMET_ERR_INVALID_ARG, "M must be in 1 .. 1048576");
+    if (K < 1 || K > 32) return fail(COMET_ERR_INVALID_ARG, "K must be in 1 .. 32");
+    if (!half_width) return fail(COMET_ERR_INVALID_ARG, "half_width is NULL");
+    for (int d = 0; d < 4; ++d)
+        if (!std::isfinite(half_width[d]) || half_width[d] < 0.0)
+            return fail(COMET_ERR_INVALID_ARG, "half_width must be finite and >= 0");
+    if (!refs_out || !aligned(refs_out, 8)) return fail(COMET_ERR_INVALID_ARG, "refs_out is NULL or misaligned");
+    if (!n_refs_out || !aligned(n_refs_out, 4)) return fail(COMET_ERR_INVALID_ARG, "n_refs_out is NULL or misaligned");
+    DeviceGuard g(ctx->device);
+    if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+    comet::RefArgs a;
+    a.seeds = seeds;
+    a.S = S;
+    a.idx = idx;
+    a.M = M;
+    a.K = K;
+    for (int d = 0; d < 4; ++d) a.half_width[d] = half_width[d];
+    a.refs_out = refs_out;
+    a.n_refs_out = n_refs_out;
+    cudaError_t e = comet::launch_refine_refs(dtype, a, (cudaStream_t)stream);
+    return e == cudaSuccess ? COMET_OK : cuda_fail(e, "refine_refs launch");
+}
+
+comet_status comet_scan_lattice_refined(comet_ctx *ctx, comet_dtype dtype, const comet_lattice *shape,
+                                        const double *refs, const int32_t *n_refs, int32_t K,
+                                        void *seeds, int8_t *charge_out, int64_t S,
+                                        comet_stream stream)
+{
+    if (!ctx) return fail(COMET_ERR_INVALID_ARG, "ctx is NULL");
+    CHECK(check_dtype(dtype));
+    if (!shape) return fail(COMET_ERR_INVALID_ARG, "shape is NULL");
+    if (K < 1 || K > 32) return fail(COMET_ERR_INVALID_ARG, "K must be in 1 .. 32");
+    int64_t prod = 1;
+    for (int d = 0; d < 4; ++d) {
+        if (shape->counts[d] < 1) return fail(COMET_ERR_INVALID_ARG, "shape.counts must be >= 1");
+        prod *= shape->counts[d];
+        if (prod > (int64_t)1 << 36) return fail(COMET_ERR_INVALID_ARG, "lattice too large");
+        if (!std::isfinite(shape->half_width[d]))
+            return fail(COMET_ERR_INVALID_ARG, "shape.half_width must be finite");
+    }
+    if (S != prod * K) return fail(COMET_ERR_INVALID_ARG, "S (%lld) != K x product of shape counts (%lld)", (long long)S, (long long)(prod * K));
+    if (!refs || !aligned(refs, 8)) return fail(COMET_ERR_INVALID_ARG, "refs is NULL or misaligned");
+    if (!n_refs || !aligned(n_refs, 4)) return fail(COMET_ERR_INVALID_ARG, "n_refs is NULL or misaligned");
+    if (!seeds || !aligned(seeds, esize(dtype))) return fail(COMET_ERR_INVALID_ARG, "seeds is NULL or misaligned");
+    if (shape->charge < -128 || shape->charge > 127) return fail(COMET_ERR_INVALID_ARG, "shape.charge must fit int8");
+    DeviceGuard g(ctx->device);
+    if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+    comet::LatArgs a;
+    a.vx = shape->vx;
+    a.vy = shape->vy;
+    for (int d = 0; d < 4; ++d) {
+        a.centre[d] = 0.0;
+        a.half_width[d] = shape->half_width[d];
+        a.counts[d] = shape->counts[d];
+    }
+    a.charge = shape->charge;
+    a.charge_out = charge_out;
+    cudaError_t e = comet::launch_lattice_refined(dtype, a, refs, n_refs, K, seeds, S, (cudaStream_t)stream);
+    return e == cudaSuccess ? COMET_OK : cuda_fail(e, "lattice_refined launch");
+}
+
 comet_status comet_scan_propagate(comet_ctx *ctx, comet_dtype dtype, const comet_field *field,
                                   const comet_scan_params *params, const void *seeds,
                                   const int8_t *charge, int64_t S, void *points, int32_t *n_valid,

@@ -101,6 +101,20 @@ struct ClsArgs {
 };
 
 cudaError_t launch_lattice(comet_dtype dt, const LatArgs &a, void *seeds, int64_t S, cudaStream_t st);
+cudaError_t launch_lattice_refined(comet_dtype dt, const LatArgs &a, const double *refs,
+                                   const int32_t *n_refs, int K, void *seeds, int64_t S,
+                                   cudaStream_t st);
+
+struct RefArgs {
+    const void *seeds;
+    int64_t S;
+    const int64_t *idx;
+    int M, K;
+    double half_width[4];
+    double *refs_out;
+    int32_t *n_refs_out;
+};
+cudaError_t launch_refine_refs(comet_dtype dt, const RefArgs &a, cudaStream_t st);
 cudaError_t launch_propagate(comet_dtype dt, const comet_field &f, const PropArgs &a, cudaStream_t st);
 cudaError_t launch_dca(comet_dtype dt, const comet_field &f, const DcaArgs &a, cudaStream_t st);
 void dca_segments(int n_rec, int *G0, int *G1);   // segment sizes of the closest-state search

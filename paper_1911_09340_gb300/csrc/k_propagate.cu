@@ -34,12 +34,24 @@ __device__ __forceinline__ double lattice_node(double centre, double half_width,
 
 constexpr int kLatTab = 512;   // node values tabulated per block when the four counts sum to <= this
 
+// Grid (blocks, K): row k of the grid writes lattice k, seeds [k*S1, (k+1)*S1).  With refs == NULL
+// there is one lattice centred at a.centre; otherwise lattice k is centred at refs[k'] (4 doubles:
+// z0, phi, pz, pt), k' = k while k < *n_refs, else 0 (a repeat of the first, so that the seed count
+// stays fixed whatever the number of references found).
 template <typename T>
-__global__ void __launch_bounds__(256) lattice_kernel(LatArgs a, T *__restrict__ seeds, int64_t S)
+__global__ void __launch_bounds__(256) lattice_kernel(LatArgs a, const double *__restrict__ refs,
+                                                      const int32_t *__restrict__ n_refs,
+                                                      T *__restrict__ seeds, int64_t S1, int64_t S)
 {
     // every node value (and cos / sin of every phi node) once per block, in shared memory
     __shared__ double nodes[kLatTab];
     __shared__ double cphi[kLatTab], sphi[kLatTab];
+    const int64_t kb = blockIdx.y;
+    if (refs) {
+        const int64_t kr = kb < (int64_t)*n_refs ? kb : 0;
+#pragma unroll
+        for (int d = 0; d < 4; ++d) a.centre[d] = refs[kr * 4 + d];
+    }
     int off[4];
     off[0] = 0;
     for (int d = 1; d < 4; ++d) off[d] = off[d - 1] + a.counts[d - 1];
@@ -56,7 +68,7 @@ __global__ void __launch_bounds__(256) lattice_kernel(LatArgs a, T *__restrict__
         __syncthreads();
     }
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= S) return;
+    if (s >= S1) return;
     int b[4];
     b[0] = a.counts[0] % 2 == 0 ? 2 : 1;
 #pragma unroll
@@ -85,13 +97,14 @@ __global__ void __launch_bounds__(256) lattice_kernel(LatArgs a, T *__restrict__
         for (int d = 0; d < 4; ++d) v[d] = lattice_node(a.centre[d], a.half_width[d], a.counts[d], ii[d]);
         sincos(v[1], &sp, &cp);
     }
-    seeds[0 * S + s] = (T)a.vx;
-    seeds[1 * S + s] = (T)a.vy;
-    seeds[2 * S + s] = (T)v[0];
-    seeds[3 * S + s] = (T)__dmul_rn(v[3], cp);
-    seeds[4 * S + s] = (T)__dmul_rn(v[3], sp);
-    seeds[5 * S + s] = (T)v[2];
-    if (a.charge_out) a.charge_out[s] = (int8_t)a.charge;
+    const int64_t o = kb * S1 + s;
+    seeds[0 * S + o] = (T)a.vx;
+    seeds[1 * S + o] = (T)a.vy;
+    seeds[2 * S + o] = (T)v[0];
+    seeds[3 * S + o] = (T)__dmul_rn(v[3], cp);
+    seeds[4 * S + o] = (T)__dmul_rn(v[3], sp);
+    seeds[5 * S + o] = (T)v[2];
+    if (a.charge_out) a.charge_out[o] = (int8_t)a.charge;
 }
 
 template <typename T>
@@ -364,12 +377,20 @@ __global__ void __launch_bounds__(128) propagate_kernel(F f, PropArgs a)
 
 cudaError_t launch_lattice(comet_dtype dt, const LatArgs &a, void *seeds, int64_t S, cudaStream_t st)
 {
+    return launch_lattice_refined(dt, a, nullptr, nullptr, 1, seeds, S, st);
+}
+
+cudaError_t launch_lattice_refined(comet_dtype dt, const LatArgs &a, const double *refs,
+                                   const int32_t *n_refs, int K, void *seeds, int64_t S,
+                                   cudaStream_t st)
+{
     const int nt = 256;
-    const unsigned nb = (unsigned)((S + nt - 1) / nt);
+    const int64_t S1 = S / K;
+    const dim3 grid((unsigned)((S1 + nt - 1) / nt), (unsigned)K);
     if (dt == COMET_F32)
-        lattice_kernel<float><<<nb, nt, 0, st>>>(a, (float *)seeds, S);
+        lattice_kernel<float><<<grid, nt, 0, st>>>(a, refs, n_refs, (float *)seeds, S1, S);
     else
-        lattice_kernel<double><<<nb, nt, 0, st>>>(a, (double *)seeds, S);
+        lattice_kernel<double><<<grid, nt, 0, st>>>(a, refs, n_refs, (double *)seeds, S1, S);
     return cudaGetLastError();
 }
 

@@ -2,6 +2,7 @@
 
     python -m paper_1911_09340_gb300.experiments lambda-sweep [--events N] [--stride s]
     python -m paper_1911_09340_gb300.experiments backward [--events N] [--stride s]
+    python -m paper_1911_09340_gb300.experiments iterative [--events N] [--stride s]
 
 * ``lambda-sweep``: hit-classification efficiency and purity (metrics.py) of the first stage and of
   all stages as the cutoff lambda runs over 0.5-1.2 mm in 0.1 mm steps (the range of the paper's
@@ -10,6 +11,8 @@
 * ``backward``: the first stage scanned forwards from the start of the turn and backwards from its
   end with the charge and momentum flipped (the paper's two half tracks, Sec. 3.1), each over the
   whole turn.
+* ``iterative``: the dense 2^18-seed grid against an iterative scan (Sec. 2.1: sparse low-RSS
+  references, finer lattices around them) of a 2^14 coarse grid refined twice.
 
 Every scan runs through the library's kernels (scan.scan_partition); only the metrics are computed
 on the host from the copied-back hit classes.  One JSON line per result.
@@ -100,15 +103,119 @@ def backward_study(n_events: int = 32, stride: int = 16, lam: float = 1e-2, dtyp
              "same_turn": float(np.mean([a.turn == b.turn for a, b in zip(fwd, bwd)]))}]
 
 
+def _scan_seeds(ctx, field, bp, dev, ws, S, M):
+    """propagate -> dca -> select(top M) on the S seeds already in ws.seeds / ws.charge."""
+    seeds, charge, pts, nv, rss, n_in = ws.views(S, bp.n_rec)
+    bounds = ws.bounds[: (S + 31) // 32]
+    B.comet_scan_propagate(ctx, field, bp, seeds, charge, pts, nv, bounds=bounds)
+    B.comet_scan_dca(ctx, field, bp, pts, nv, charge, dev.wires, dev.hit_offsets, dev.drift, dev.mask,
+                     rss, n_in, n_unconverged=ws.n_unconv, n_wires=dev.W, bounds=bounds)
+    B.comet_scan_select(ctx, rss, M, ws.idx[:M], ws.best[:M])
+
+
+def refine_partition(ctx, ev, part: int, dtype=torch.float32, stride: int = 16, lam: float = 1e-2,
+                     coarse=(8, 8, 16, 16), fine=(5, 5, 5, 5), levels: int = 2, M: int = 64,
+                     K: int = 16, shrink: float = 0.75):
+    """Iterative scan of one turn partition (Sec. 2.1): a coarse lattice over the prior ranges, then
+    ``levels`` rounds of: the top-M seeds -> up to K sparse references (comet_scan_refine_refs) ->
+    K lattices of ``fine`` counts around them with half-widths ``shrink`` x the previous spacing
+    (comet_scan_lattice_refined) -> scan.  Odd ``fine`` counts keep each reference on its own finer
+    lattice and shrink the spacing by 2 x shrink / (count - 1) per level.  Everything stays on the
+    device; the per-level best seed and RSS are copied back at the end.  Returns
+    {"levels": [...], "ms": total GPU time}."""
+    import dataclasses as dc
+    spec0 = ev.partitions[part]
+    n = ev.n_steps[part]
+    field = B.DeviceField.from_synth(synth.uniform_field(1.0))
+    dev = scan.DeviceEvent.from_event(ev, dtype)
+    bp = scan.params_for(spec0, n, dtype, stride, lam)
+    S0 = int(np.prod(coarse))
+    S1 = K * int(np.prod(fine))
+    ws = scan.Workspace(max(S0, S1), bp.n_rec, ev.n_hits, dtype, k=M)
+    refs = torch.zeros((K, 4), dtype=torch.float64, device="cuda")
+    nref = torch.zeros(1, dtype=torch.int32, device="cuda")
+    coarse_spec = dc.replace(spec0, counts=tuple(coarse))
+    best_idx, best_rss, best_seed, sizes, marks = [], [], [], [], []
+    t0 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    B.comet_scan_lattice(ctx, coarse_spec, ws.seeds.view(-1)[: 6 * S0].view(6, S0), ws.charge[:S0])
+    _scan_seeds(ctx, field, bp, dev, ws, S0, M)
+    hw = list(coarse_spec.half_width)
+    counts = list(coarse)
+    S = S0
+    for lv in range(levels + 1):
+        seeds = ws.seeds.view(-1)[: 6 * S].view(6, S)
+        best_idx.append(ws.idx[:1].clone())
+        best_rss.append(ws.best[:1].clone())
+        best_seed.append(torch.index_select(seeds, 1, ws.idx[:1]).clone())
+        sizes.append(S)
+        e = torch.cuda.Event(enable_timing=True)
+        e.record()
+        marks.append(e)
+        if lv == levels:
+            break
+        hw = [shrink * 2.0 * h / (c - 1) if c > 1 else h for h, c in zip(hw, counts)]
+        counts = list(fine)
+        B.comet_scan_refine_refs(ctx, seeds, ws.idx[:M], hw, K, refs, nref)
+        shape = dc.replace(spec0, half_width=tuple(hw), counts=tuple(fine))
+        S = S1
+        B.comet_scan_lattice_refined(ctx, shape, refs, nref, K, ws.seeds.view(-1)[: 6 * S].view(6, S),
+                                     ws.charge[:S])
+        _scan_seeds(ctx, field, bp, dev, ws, S, M)
+    torch.cuda.synchronize()
+    out = []
+    prev = t0
+    for lv in range(levels + 1):
+        out.append({"level": lv, "seeds": sizes[lv], "best_rss": float(best_rss[lv].item()),
+                    "best_seed": best_seed[lv][:, 0].double().cpu().numpy(),
+                    "ms": prev.elapsed_time(marks[lv])})
+        prev = marks[lv]
+    return {"levels": out, "ms": t0.elapsed_time(marks[-1])}
+
+
+def iterative_study(n_events: int = 16, stride: int = 16, lam: float = 1e-2, dtype=torch.float32):
+    """Best RSS, momentum error of the best seed against the truth and GPU time: the dense 2^18 grid
+    of the benchmark against a coarse 2^14 grid refined twice (16 references, 5^4 seeds each)."""
+    ctx = B.Context(torch.cuda.current_device())
+    dense, itr = [], []
+    for i in range(n_events):
+        ev = synth.multi_turn_event(i)
+        p_true = float(np.hypot(ev.pt, ev.pz))
+        runs = []
+        for kw in (dict(coarse=(16, 16, 32, 32), levels=0, M=1, K=1),
+                   dict(coarse=(8, 8, 16, 16), fine=(5, 5, 5, 5), levels=2, M=64, K=16)):
+            refine_partition(ctx, ev, 0, dtype, stride, lam, **kw)          # warm: allocations
+            runs.append(refine_partition(ctx, ev, 0, dtype, stride, lam, **kw))
+        d, r = runs
+        for res, acc in ((d, dense), (r, itr)):
+            lv = res["levels"][-1]
+            sd = lv["best_seed"]
+            acc.append((lv["best_rss"], abs(float(np.linalg.norm(sd[3:])) - p_true), res["ms"],
+                        sum(x["seeds"] for x in res["levels"])))
+    ctx.close()
+
+    def summ(a):
+        a = np.array(a)
+        return {"mean_best_rss": float(a[:, 0].mean()), "mean_abs_dp_MeV": float(a[:, 1].mean()),
+                "rms_dp_MeV": float(np.sqrt((a[:, 1] ** 2).mean())), "mean_ms": float(a[:, 2].mean()),
+                "seeds": int(a[0, 3])}
+    wins = float(np.mean([b[0] <= a[0] for a, b in zip(dense, itr)]))
+    return [{"study": "iterative", "events": n_events, "stride": stride, "lambda_mm": lam * 1e3,
+             "dense_16x16x32x32": summ(dense), "iterative_2^14+2x16x5^4": summ(itr),
+             "iterative_rss_le_dense": wins}]
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("study", choices=["lambda-sweep", "backward"])
+    ap.add_argument("study", choices=["lambda-sweep", "backward", "iterative"])
     ap.add_argument("--events", type=int, default=32)
     ap.add_argument("--stride", type=int, default=16)
     ap.add_argument("--lambda-mm", type=float, default=10.0, help="cutoff of the backward study")
     args = ap.parse_args(argv)
     if args.study == "lambda-sweep":
         rows = lambda_sweep(args.events, stride=args.stride)
+    elif args.study == "iterative":
+        rows = iterative_study(args.events, args.stride, args.lambda_mm * 1e-3)
     else:
         rows = backward_study(args.events, args.stride, args.lambda_mm * 1e-3)
     for r in rows:
