@@ -11,6 +11,8 @@
  *   comet_scan_select     the seeds of lowest RSS                                     (Sec. 2.1)
  *   comet_scan_refine_refs, comet_scan_lattice_refined
  *                         sparse references and finer lattices around them            (Sec. 2.1)
+ *   comet_scan_jacobian, comet_scan_gn_step
+ *                         smoothed RSS, dD/dseed, Gauss-Newton steps for the best seeds
  *   comet_scan_classify   classify the selected seed's hits; mask them for the next   (Sec. 2.1, 3.1)
  *                         turn partition
  *
@@ -234,6 +236,43 @@ comet_status comet_scan_lattice_refined(comet_ctx *ctx, comet_dtype dtype, const
                                         const double *refs, const int32_t *n_refs, int32_t K,
                                         void *seeds, int8_t *charge_out, int64_t S,
                                         comet_stream stream);
+
+/* ---- residual Jacobians and Gauss-Newton steps for the best seeds ---------------------------------
+ * Refines a few seeds continuously instead of by a finer grid.  The paper scans grids because its
+ * RSS (Eq. 1) is not smooth in the seed (Sec. 2.1); this call smooths the cap of Eq. 1 and gives the
+ * derivatives needed for Gauss-Newton.
+ *   Seeds are theta [S][4] double device = (z0, phi, pz, pT) with vertex (vx, vy) and `charge`, as
+ *   in comet_scan_lattice.  dtype must be COMET_F64; the field must be uniform along z
+ *   (kind 0 with b[0] = b[1] = 0), else COMET_ERR_UNSUPPORTED.  params as for the scan (h, n_steps,
+ *   stride, target region, tol, max_iter, lambda).
+ *   For each (seed, wire): D = the DCA exactly as comet_scan_dca finds it (closest recorded state,
+ *   then the local virtual-plane refinement of Algorithm 2) and dD/dtheta by forward-mode
+ *   derivatives of the recorded states (closed form in an axial field) and of the refinement steps
+ *   at fixed lengths (at the point of closest approach the distance is stationary along the track).
+ *   For each wire with an unmasked hit: e = min_j |D - r_j|, w = 1 / (1 + exp(-(lambda - e)/tau)),
+ *   term = w e^2 + (1 - w) lambda^2 (Eq. 1 with a smooth cap; tau > 0, in metres).
+ *   work       [S][W][9] double device scratch.
+ *   srss_out   out, [S] double: sum of the terms in ascending wire order (the smoothed RSS).
+ *   grad_out   out, [S][4] double: its gradient in theta.
+ *   jtj_out    out, [S][4][4] double: sum over wires of w J J^T (J = dD/dtheta);
+ *   jtr_out    out, [S][4] double: sum of w J (D - r_j*), the Gauss-Newton normal equations with
+ *              the weights held fixed.
+ *   dca_out    optional out, [S][W] double: D.   jac_out optional out, [S][W][4] double: dD/dtheta.
+ *   n_unconverged optional [1] int32 device, incremented for refinements that did not converge. */
+comet_status comet_scan_jacobian(comet_ctx *ctx, comet_dtype dtype, const comet_field *field,
+                                 const comet_scan_params *params, const double *theta, int64_t S,
+                                 double vx, double vy, int32_t charge, const void *wires, int32_t W,
+                                 int32_t ldw, const int32_t *hit_offsets, const void *drift,
+                                 const uint8_t *hit_mask, double tau, double *work,
+                                 double *srss_out, double *grad_out, double *jtj_out,
+                                 double *jtr_out, double *dca_out, double *jac_out,
+                                 int32_t *n_unconverged, comet_stream stream);
+
+/* theta[s] += delta with (JTJ + mu diag(JTJ)) delta = -JTR (Cholesky; a seed whose matrix is not
+ * positive definite keeps its theta).  theta [S][4], jtj [S][4][4], jtr [S][4]: double device, as
+ * written by comet_scan_jacobian.  mu >= 0 (Levenberg-Marquardt damping). */
+comet_status comet_scan_gn_step(comet_ctx *ctx, double *theta, int64_t S, const double *jtj,
+                                const double *jtr, double mu, comet_stream stream);
 
 /* ---- selection without device allocation (the paper has no counterpart) -------------------------
  * Same result as comet_scan_select, for callers that cannot allocate device memory: for example a

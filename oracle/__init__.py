@@ -271,3 +271,38 @@ def lattice_refined(shape, refs, K):
         c = refs[k] if k < refs.shape[0] else refs[0]
         out.append(lattice(_dc.replace(shape, centre=tuple(float(v) for v in c))))
     return np.concatenate(out, axis=0)
+
+
+def seeds_from_theta(theta, vx, vy):
+    """Seeds (AoS [S][6]) of lattice coordinates theta [S][4] = (z0, phi, pz, pT) at vertex (vx, vy),
+    as the lattice builds them (Sec. 2.1)."""
+    th = np.asarray(theta, dtype=np.float64).reshape(-1, 4)
+    n = th.shape[0]
+    return np.stack([np.full(n, vx), np.full(n, vy), th[:, 0], th[:, 3] * np.cos(th[:, 1]),
+                     th[:, 3] * np.sin(th[:, 1]), th[:, 2]], axis=1)
+
+
+def smoothed_rss(field, params: Params, theta, vx, vy, q, wires, hit_offsets, drift, mask, tau):
+    """Eq. 1 with a smooth cap, for Gauss-Newton refinement of the best seeds: for every wire with an
+    unmasked hit, e = min_j |D - r_j| (D from this oracle's scan), w = 1 / (1 + exp(-(lam - e)/tau)),
+    term = w e^2 + (1 - w) lam^2; summed in ascending wire order.  Returns (srss [S], dca [S][W])."""
+    seeds = seeds_from_theta(theta, vx, vy)
+    r = scan(field, params, seeds, q, wires, hit_offsets, drift, mask, want_dca=True)
+    D = r["dca"]
+    offs = np.asarray(hit_offsets)
+    dr = np.asarray(drift, dtype=np.float64)
+    mk = np.asarray(mask)
+    lam = params.lam
+    out = np.zeros(seeds.shape[0])
+    for s in range(seeds.shape[0]):
+        tot = 0.0
+        for i in range(offs.shape[0] - 1):
+            live = [j for j in range(offs[i], offs[i + 1]) if not mk[j]]
+            if not live:
+                continue
+            e = min(abs(D[s, i] - dr[j]) for j in live)
+            x = (lam - e) / tau
+            w = 1.0 / (1.0 + np.exp(-x)) if x >= 0 else np.exp(x) / (1.0 + np.exp(x))
+            tot += w * e * e + (1.0 - w) * lam * lam
+        out[s] = tot
+    return out, D

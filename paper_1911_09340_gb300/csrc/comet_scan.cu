@@ -301,6 +301,87 @@ comet_status comet_scan_lattice_refined(comet_ctx *ctx, comet_dtype dtype, const
     return e == cudaSuccess ? COMET_OK : cuda_fail(e, "lattice_refined launch");
 }
 
+comet_status comet_scan_jacobian(comet_ctx *ctx, comet_dtype dtype, const comet_field *field,
+                                 const comet_scan_params *params, const double *theta, int64_t S,
+                                 double vx, double vy, int32_t charge, const void *wires, int32_t W,
+                                 int32_t ldw, const int32_t *hit_offsets, const void *drift,
+                                 const uint8_t *hit_mask, double tau, double *work,
+                                 double *srss_out, double *grad_out, double *jtj_out,
+                                 double *jtr_out, double *dca_out, double *jac_out,
+                                 int32_t *n_unconverged, comet_stream stream)
+{
+    if (!ctx) return fail(COMET_ERR_INVALID_ARG, "ctx is NULL");
+    CHECK(check_dtype(dtype));
+    if (dtype != COMET_F64) return fail(COMET_ERR_UNSUPPORTED, "comet_scan_jacobian needs COMET_F64");
+    CHECK(check_field(field));
+    if (field->kind != 0 || field->b[0] != 0.0 || field->b[1] != 0.0)
+        return fail(COMET_ERR_UNSUPPORTED, "comet_scan_jacobian needs a uniform field along z");
+    CHECK(check_params(params, true));
+    if (S <= 0 || S > ((int64_t)1 << 24)) return fail(COMET_ERR_INVALID_ARG, "S must be in 1 .. 2^24");
+    if (W < 0 || ldw < W) return fail(COMET_ERR_INVALID_ARG, "need 0 <= W <= ldw");
+    if (!(tau > 0.0) || !std::isfinite(tau)) return fail(COMET_ERR_INVALID_ARG, "tau must be > 0");
+    if (!std::isfinite(vx) || !std::isfinite(vy)) return fail(COMET_ERR_INVALID_ARG, "vertex must be finite");
+    const void *req[] = {theta, work, srss_out, grad_out, jtj_out, jtr_out};
+    for (const void *q : req)
+        if (!q || !aligned(q, 8)) return fail(COMET_ERR_INVALID_ARG, "a required array is NULL or misaligned");
+    if (W > 0 && (!wires || !hit_offsets || !drift || !hit_mask || !aligned(wires, 8) || !aligned(drift, 8) ||
+                  !aligned(hit_offsets, 4)))
+        return fail(COMET_ERR_INVALID_ARG, "wires / hits NULL or misaligned");
+    if ((dca_out && !aligned(dca_out, 8)) || (jac_out && !aligned(jac_out, 8)))
+        return fail(COMET_ERR_INVALID_ARG, "dca_out / jac_out misaligned");
+    if (charge < -128 || charge > 127) return fail(COMET_ERR_INVALID_ARG, "charge must fit int8");
+    DeviceGuard g(ctx->device);
+    if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+    comet::JacArgs a;
+    a.theta = theta;
+    a.S = S;
+    a.vx = vx;
+    a.vy = vy;
+    a.bz = field->b[2];
+    a.charge = charge;
+    a.h = params->h;
+    a.stride = params->stride;
+    a.n_rec = n_rec_of(params);
+    a.h_rec = params->h * params->stride;
+    a.zmin = params->zmin;
+    a.zmax = params->zmax;
+    a.rmax2 = params->rmax * params->rmax;
+    a.tol = params->tol;
+    a.max_iter = params->max_iter;
+    a.lambda = params->lambda;
+    a.tau = tau;
+    a.wires = wires;
+    a.W = W;
+    a.ldw = ldw;
+    a.offs = hit_offsets;
+    a.drift = (const double *)drift;
+    a.mask = hit_mask;
+    a.work = work;
+    a.srss_out = srss_out;
+    a.grad_out = grad_out;
+    a.jtj_out = jtj_out;
+    a.jtr_out = jtr_out;
+    a.dca_out = dca_out;
+    a.jac_out = jac_out;
+    a.n_unconv = n_unconverged;
+    cudaError_t e = comet::launch_jacobian(a, (cudaStream_t)stream);
+    return e == cudaSuccess ? COMET_OK : cuda_fail(e, "jacobian launch");
+}
+
+comet_status comet_scan_gn_step(comet_ctx *ctx, double *theta, int64_t S, const double *jtj,
+                                const double *jtr, double mu, comet_stream stream)
+{
+    if (!ctx) return fail(COMET_ERR_INVALID_ARG, "ctx is NULL");
+    if (S <= 0 || S > ((int64_t)1 << 24)) return fail(COMET_ERR_INVALID_ARG, "S must be in 1 .. 2^24");
+    if (!theta || !jtj || !jtr || !aligned(theta, 8) || !aligned(jtj, 8) || !aligned(jtr, 8))
+        return fail(COMET_ERR_INVALID_ARG, "theta / jtj / jtr NULL or misaligned");
+    if (!(mu >= 0.0) || !std::isfinite(mu)) return fail(COMET_ERR_INVALID_ARG, "mu must be >= 0");
+    DeviceGuard g(ctx->device);
+    if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+    cudaError_t e = comet::launch_gn_step(theta, S, jtj, jtr, mu, (cudaStream_t)stream);
+    return e == cudaSuccess ? COMET_OK : cuda_fail(e, "gn_step launch");
+}
+
 comet_status comet_scan_propagate(comet_ctx *ctx, comet_dtype dtype, const comet_field *field,
                                   const comet_scan_params *params, const void *seeds,
                                   const int8_t *charge, int64_t S, void *points, int32_t *n_valid,

@@ -115,6 +115,27 @@ struct RefArgs {
     int32_t *n_refs_out;
 };
 cudaError_t launch_refine_refs(comet_dtype dt, const RefArgs &a, cudaStream_t st);
+
+struct JacArgs {
+    const double *theta;   // [S][4] (z0, phi, pz, pT)
+    int64_t S;
+    double vx, vy, bz;
+    int charge;
+    double h, h_rec, zmin, zmax, rmax2, tol, lambda, tau;
+    int stride, n_rec, max_iter;
+    const void *wires;
+    int W, ldw;
+    const int32_t *offs;
+    const double *drift;
+    const uint8_t *mask;
+    double *work;          // [S][W][9]
+    double *srss_out, *grad_out, *jtj_out, *jtr_out;
+    double *dca_out, *jac_out;
+    int32_t *n_unconv;
+};
+cudaError_t launch_jacobian(const JacArgs &a, cudaStream_t st);
+cudaError_t launch_gn_step(double *theta, int64_t S, const double *jtj, const double *jtr, double mu,
+                           cudaStream_t st);
 cudaError_t launch_propagate(comet_dtype dt, const comet_field &f, const PropArgs &a, cudaStream_t st);
 cudaError_t launch_dca(comet_dtype dt, const comet_field &f, const DcaArgs &a, cudaStream_t st);
 void dca_segments(int n_rec, int *G0, int *G1);   // segment sizes of the closest-state search

@@ -3,6 +3,7 @@
     python -m paper_1911_09340_gb300.experiments lambda-sweep [--events N] [--stride s]
     python -m paper_1911_09340_gb300.experiments backward [--events N] [--stride s]
     python -m paper_1911_09340_gb300.experiments iterative [--events N] [--stride s]
+    python -m paper_1911_09340_gb300.experiments gauss-newton [--events N] [--lambda-mm 0.8]
 
 * ``lambda-sweep``: hit-classification efficiency and purity (metrics.py) of the first stage and of
   all stages as the cutoff lambda runs over 0.5-1.2 mm in 0.1 mm steps (the range of the paper's
@@ -13,6 +14,8 @@
   whole turn.
 * ``iterative``: the dense 2^18-seed grid against an iterative scan (Sec. 2.1: sparse low-RSS
   references, finer lattices around them) of a 2^14 coarse grid refined twice.
+* ``gauss-newton``: the dense grid against Gauss-Newton on the smoothed RSS (comet_scan_jacobian,
+  comet_scan_gn_step) started from the top 16 seeds of a 2^14 grid.
 
 Every scan runs through the library's kernels (scan.scan_partition); only the metrics are computed
 on the host from the copied-back hit classes.  One JSON line per result.
@@ -115,7 +118,7 @@ def _scan_seeds(ctx, field, bp, dev, ws, S, M):
 
 def refine_partition(ctx, ev, part: int, dtype=torch.float32, stride: int = 16, lam: float = 1e-2,
                      coarse=(8, 8, 16, 16), fine=(5, 5, 5, 5), levels: int = 2, M: int = 64,
-                     K: int = 16, shrink: float = 0.75):
+                     K: int = 16, shrink: float = 0.75, keep_top: int = 0):
     """Iterative scan of one turn partition (Sec. 2.1): a coarse lattice over the prior ranges, then
     ``levels`` rounds of: the top-M seeds -> up to K sparse references (comet_scan_refine_refs) ->
     K lattices of ``fine`` counts around them with half-widths ``shrink`` x the previous spacing
@@ -162,6 +165,10 @@ def refine_partition(ctx, ev, part: int, dtype=torch.float32, stride: int = 16, 
         B.comet_scan_lattice_refined(ctx, shape, refs, nref, K, ws.seeds.view(-1)[: 6 * S].view(6, S),
                                      ws.charge[:S])
         _scan_seeds(ctx, field, bp, dev, ws, S, M)
+    if keep_top:
+        # hand the last level's seeds and top-M indices to the caller (e.g. Gauss-Newton)
+        return {"seeds": ws.seeds.view(-1)[: 6 * S].view(6, S), "idx": ws.idx[:M], "nref": nref,
+                "ws": ws}
     torch.cuda.synchronize()
     out = []
     prev = t0
@@ -205,9 +212,84 @@ def iterative_study(n_events: int = 16, stride: int = 16, lam: float = 1e-2, dty
              "iterative_rss_le_dense": wins}]
 
 
+class GaussNewton:
+    """Gauss-Newton refinement of a few seeds of one turn partition (FP64, uniform axial field):
+    each iteration is comet_scan_jacobian (smoothed RSS, normal equations) then comet_scan_gn_step,
+    all on the device."""
+
+    def __init__(self, ctx, ev, part: int, stride: int = 16, lam: float = 8e-4, tau: float = 1e-3,
+                 K: int = 16):
+        self.ctx, self.ev, self.tau, self.K = ctx, ev, tau, K
+        spec = ev.partitions[part]
+        self.spec = spec
+        self.field = B.DeviceField.from_synth(synth.uniform_field(1.0))
+        self.params = scan.params_for(spec, ev.n_steps[part], torch.float64, stride, lam)
+        self.dev = scan.DeviceEvent.from_event(ev, torch.float64)
+        W = max(self.dev.W, 1)
+        f64 = dict(dtype=torch.float64, device="cuda")
+        self.theta = torch.zeros((K, 4), **f64)
+        self.work = torch.empty(K * W * B.JAC_WORK_PER_PAIR, **f64)
+        self.srss = torch.empty(K, **f64)
+        self.grad = torch.empty((K, 4), **f64)
+        self.jtj = torch.empty((K, 16), **f64)
+        self.jtr = torch.empty((K, 4), **f64)
+
+    def evaluate(self):
+        B.comet_scan_jacobian(self.ctx, self.field, self.params, self.theta, self.spec.vxy[0],
+                              self.spec.vxy[1], self.spec.charge, self.dev.wires, self.dev.hit_offsets,
+                              self.dev.drift, self.dev.mask, self.tau, self.work, self.srss, self.grad,
+                              self.jtj, self.jtr, n_wires=self.dev.W)
+
+    def run(self, iters: int = 10, mu: float = 1e-3):
+        for _ in range(iters):
+            self.evaluate()
+            B.comet_scan_gn_step(self.ctx, self.theta, self.jtj, self.jtr, mu)
+        self.evaluate()
+
+
+def gn_study(n_events: int = 32, stride: int = 16, lam: float = 8e-4, iters: int = 10, K: int = 16):
+    """The dense 2^18 grid (FP32) against Gauss-Newton on the top K of a 2^14 grid (FP32 scan, then
+    FP64 Gauss-Newton with the smoothed RSS, tau = 1 mm): momentum error of the selected seed
+    against the truth and warm GPU time."""
+    ctx = B.Context(torch.cuda.current_device())
+    dense, gn = [], []
+    for i in range(n_events):
+        ev = synth.multi_turn_event(i)
+        p_true = float(np.hypot(ev.pt, ev.pz))
+        kw = dict(coarse=(16, 16, 32, 32), levels=0, M=1, K=1)
+        refine_partition(ctx, ev, 0, torch.float32, stride, lam, **kw)
+        d = refine_partition(ctx, ev, 0, torch.float32, stride, lam, **kw)
+        sd = d["levels"][-1]["best_seed"]
+        dense.append((abs(float(np.linalg.norm(sd[3:])) - p_true), d["ms"]))
+        G = GaussNewton(ctx, ev, 0, stride, lam, K=K)
+        res = None
+        for rep in range(2):                                     # second run timed (warm)
+            t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t0.record()
+            c = refine_partition(ctx, ev, 0, torch.float32, stride, lam, coarse=(8, 8, 16, 16),
+                                 levels=0, M=64, K=1, keep_top=K)
+            B.comet_scan_refine_refs(ctx, c["seeds"], c["idx"], [0.0] * 4, K, G.theta, c["nref"])
+            G.run(iters)
+            t1.record()
+            t1.synchronize()
+            res = (G.srss.cpu().numpy(), G.theta.cpu().numpy(), t0.elapsed_time(t1))
+        srss, theta, ms = res
+        b = int(np.argmin(np.where(np.isfinite(srss), srss, np.inf)))
+        gn.append((abs(float(np.hypot(theta[b, 2], theta[b, 3])) - p_true), ms))
+    ctx.close()
+
+    def summ(a):
+        a = np.array(a)
+        return {"mean_abs_dp_MeV": float(a[:, 0].mean()), "rms_dp_MeV": float(np.sqrt((a[:, 0] ** 2).mean())),
+                "mean_ms": float(a[:, 1].mean())}
+    return [{"study": "gauss-newton", "events": n_events, "stride": stride, "lambda_mm": lam * 1e3,
+             "iterations": iters, "K": K, "dense_16x16x32x32": summ(dense),
+             "gn_top16_of_2^14": summ(gn)}]
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("study", choices=["lambda-sweep", "backward", "iterative"])
+    ap.add_argument("study", choices=["lambda-sweep", "backward", "iterative", "gauss-newton"])
     ap.add_argument("--events", type=int, default=32)
     ap.add_argument("--stride", type=int, default=16)
     ap.add_argument("--lambda-mm", type=float, default=10.0, help="cutoff of the backward study")
@@ -216,6 +298,8 @@ def main(argv=None):
         rows = lambda_sweep(args.events, stride=args.stride)
     elif args.study == "iterative":
         rows = iterative_study(args.events, args.stride, args.lambda_mm * 1e-3)
+    elif args.study == "gauss-newton":
+        rows = gn_study(args.events, args.stride, args.lambda_mm * 1e-3)
     else:
         rows = backward_study(args.events, args.stride, args.lambda_mm * 1e-3)
     for r in rows:
