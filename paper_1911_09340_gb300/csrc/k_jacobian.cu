@@ -8,9 +8,10 @@
 // four partial derivatives in theta (forward mode) gives the derivatives of the recorded states in
 // closed form.
 //
-// The DCA of a wire is the distance at the point of closest approach (PCA) found exactly as in the
-// scan: the closest recorded state (value only), then the local virtual-plane Newton refinement of
-// Algorithm 2, each refinement step being one RK4 step of the axial map.  At the PCA the distance
+// The DCA of a wire is the distance at the point of closest approach (PCA) found as in the scan: the
+// closest recorded state (searched in FP32, settled in FP64 among its neighbours), then the local
+// virtual-plane Newton refinement of Algorithm 2, each refinement step being one RK4 step of the
+// axial map.  At the PCA the distance
 // is stationary along the track, so dD/dtheta = nhat . dx/dtheta at the fixed arc length of the PCA
 // (envelope theorem): the refinement steps are replayed in forward mode with their lengths held
 // fixed.  nhat is the unit vector from the wire to the PCA.
@@ -176,7 +177,7 @@ __device__ __forceinline__ void apply1(const Step1 &s, double y[5])
 
 constexpr int kMaxSteps = 64;   // refinement steps replayed in forward mode (max_iter is capped)
 
-__global__ void __launch_bounds__(128) jacobian_kernel(JacArgs a)
+__global__ void __launch_bounds__(32) jacobian_kernel(JacArgs a)
 {
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (tid >= a.S * a.W) return;
@@ -207,33 +208,57 @@ __global__ void __launch_bounds__(128) jacobian_kernel(JacArgs a)
     const double ax = w[0 * a.ldw + i], ay = w[1 * a.ldw + i], az = w[2 * a.ldw + i];
     const double ux = w[3 * a.ldw + i], uy = w[4 * a.ldw + i], uz = w[5 * a.ldw + i];
 
-    // closest recorded state (values only), recording as the scan does: state 0, then each
-    // interval, stopping after the first state outside the target region
-    double v[5] = {y0.X.re.v, y0.X.im.v, y0.z.v, y0.P.re.v, y0.P.im.v};
+    // closest recorded state, recording as the scan does: state 0, then each interval, stopping
+    // after the first state outside the target region.  The walk runs in FP32 (FP64 instructions
+    // are scarce on this part); the argmin is then settled in FP64 among the FP32 choice and its
+    // two neighbours.
     const double pzv = pz.v;
-    const double am1 = itv.A.re.v, bb = -itv.A.im.v, cc = itv.n.re.v, dd = -itv.n.im.v, dzv = itv.dz.v;
-    double best = INFINITY;
-    int kbest = 0;
+    const float am1f = (float)itv.A.re.v, bbf = (float)-itv.A.im.v, ccf = (float)itv.n.re.v,
+                ddf = (float)-itv.n.im.v, dzf = (float)itv.dz.v;
+    float f[5] = {(float)y0.X.re.v, (float)y0.X.im.v, (float)y0.z.v, (float)y0.P.re.v, (float)y0.P.im.v};
+    const float axf = (float)ax, ayf = (float)ay, azf = (float)az, uxf = (float)ux, uyf = (float)uy,
+                uzf = (float)uz;
+    const float zminf = (float)a.zmin, zmaxf = (float)a.zmax, rmax2f = (float)a.rmax2;
+    float bestf = INFINITY;
+    int kbest = 0, nvalid = a.n_rec;
     for (int k = 0; k < a.n_rec; ++k) {
         if (k > 0) {
-            const double px = v[3], py = v[4];
-            v[0] += cc * px + dd * py;
-            v[1] += cc * py - dd * px;
-            v[2] += dzv;
-            v[3] += am1 * px + bb * py;
-            v[4] += am1 * py - bb * px;
+            const float px = f[3], py = f[4];
+            f[0] += ccf * px + ddf * py;
+            f[1] += ccf * py - ddf * px;
+            f[2] += dzf;
+            f[3] += am1f * px + bbf * py;
+            f[4] += am1f * py - bbf * px;
         }
-        const double d2 = line_dist2<double>(v[0], v[1], v[2], ax, ay, az, ux, uy, uz);
-        if (d2 < best) {
-            best = d2;
+        const float d2 = line_dist2<float>(f[0], f[1], f[2], axf, ayf, azf, uxf, uyf, uzf);
+        if (d2 < bestf) {
+            bestf = d2;
             kbest = k;
         }
-        if (v[2] < a.zmin || v[2] > a.zmax || v[0] * v[0] + v[1] * v[1] > a.rmax2) break;
+        if (f[2] < zminf || f[2] > zmaxf || f[0] * f[0] + f[1] * f[1] > rmax2f) {
+            nvalid = k + 1;
+            break;
+        }
     }
-
-    // the recorded state kbest in forward mode
-    State4 yk = y0;
-    if (kbest > 0) yk = apply(power_map(itv, kbest), y0);
+    // FP64 (forward mode): states kbest - 1 .. kbest + 1, the lowest distance, ties to the lower index
+    const int k0 = kbest > 0 ? kbest - 1 : 0;
+    const State4 base = k0 > 0 ? apply(power_map(itv, k0), y0) : y0;
+    {
+        double best = INFINITY;
+        int kb = kbest;
+        State4 cur = base;
+        for (int k = k0; k <= kbest + 1 && k < nvalid; ++k) {
+            if (k > k0) cur = apply(itv, cur);
+            const double d2 = line_dist2<double>(cur.X.re.v, cur.X.im.v, cur.z.v, ax, ay, az, ux, uy, uz);
+            if (d2 < best) {
+                best = d2;
+                kb = k;
+            }
+        }
+        kbest = kb;
+    }
+    State4 yk = base;
+    for (int k = k0; k < kbest; ++k) yk = apply(itv, yk);
 
     // local virtual-plane refinement (values), remembering the step lengths
     double y[6] = {yk.X.re.v, yk.X.im.v, yk.z.v, yk.P.re.v, yk.P.im.v, pzv};
@@ -386,7 +411,8 @@ cudaError_t launch_jacobian(const JacArgs &a, cudaStream_t st)
 {
     const int64_t n = a.S * a.W;
     if (n > 0) {
-        jacobian_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(a);
+        // small blocks: a few thousand threads of long FP64 chains, spread over as many SMs as possible
+        jacobian_kernel<<<(unsigned)((n + 31) / 32), 32, 0, st>>>(a);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

@@ -25,7 +25,7 @@ from __future__ import annotations
 import argparse
 import json
 import sys
-from typing import List, Sequence
+from typing import List, Optional, Sequence
 
 import numpy as np
 import torch
@@ -234,11 +234,11 @@ class GaussNewton:
         self.jtj = torch.empty((K, 16), **f64)
         self.jtr = torch.empty((K, 4), **f64)
 
-    def evaluate(self):
+    def evaluate(self, tau: Optional[float] = None):
         B.comet_scan_jacobian(self.ctx, self.field, self.params, self.theta, self.spec.vxy[0],
                               self.spec.vxy[1], self.spec.charge, self.dev.wires, self.dev.hit_offsets,
-                              self.dev.drift, self.dev.mask, self.tau, self.work, self.srss, self.grad,
-                              self.jtj, self.jtr, n_wires=self.dev.W)
+                              self.dev.drift, self.dev.mask, self.tau if tau is None else tau, self.work,
+                              self.srss, self.grad, self.jtj, self.jtr, n_wires=self.dev.W)
 
     def run(self, iters: int = 10, mu: float = 1e-3):
         for _ in range(iters):
@@ -246,13 +246,18 @@ class GaussNewton:
             B.comet_scan_gn_step(self.ctx, self.theta, self.jtj, self.jtr, mu)
         self.evaluate()
 
+    def hard_rss(self):
+        """srss <- Eq. 1's capped RSS of the current seeds (the smooth cap at tau -> 0)."""
+        self.evaluate(tau=1e-12)
 
-def gn_study(n_events: int = 32, stride: int = 16, lam: float = 8e-4, iters: int = 10, K: int = 16):
+
+def gn_study(n_events: int = 32, stride: int = 16, lam: float = 8e-4, iters: int = 10, K: int = 16,
+             tau: float = 1e-3):
     """The dense 2^18 grid (FP32) against Gauss-Newton on the top K of a 2^14 grid (FP32 scan, then
-    FP64 Gauss-Newton with the smoothed RSS, tau = 1 mm): momentum error of the selected seed
-    against the truth and warm GPU time."""
+    FP64 Gauss-Newton on the smoothed RSS; the seed of lowest capped RSS is kept): momentum error of
+    the selected seed against the truth and warm GPU time.  Also the coarse grid's own best seed."""
     ctx = B.Context(torch.cuda.current_device())
-    dense, gn = [], []
+    dense, gn, coarse_only = [], [], []
     for i in range(n_events):
         ev = synth.multi_turn_event(i)
         p_true = float(np.hypot(ev.pt, ev.pz))
@@ -261,7 +266,7 @@ def gn_study(n_events: int = 32, stride: int = 16, lam: float = 8e-4, iters: int
         d = refine_partition(ctx, ev, 0, torch.float32, stride, lam, **kw)
         sd = d["levels"][-1]["best_seed"]
         dense.append((abs(float(np.linalg.norm(sd[3:])) - p_true), d["ms"]))
-        G = GaussNewton(ctx, ev, 0, stride, lam, K=K)
+        G = GaussNewton(ctx, ev, 0, stride, lam, tau=tau, K=K)
         res = None
         for rep in range(2):                                     # second run timed (warm)
             t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -269,13 +274,16 @@ def gn_study(n_events: int = 32, stride: int = 16, lam: float = 8e-4, iters: int
             c = refine_partition(ctx, ev, 0, torch.float32, stride, lam, coarse=(8, 8, 16, 16),
                                  levels=0, M=64, K=1, keep_top=K)
             B.comet_scan_refine_refs(ctx, c["seeds"], c["idx"], [0.0] * 4, K, G.theta, c["nref"])
+            th0 = G.theta[0].clone()
             G.run(iters)
+            G.hard_rss()
             t1.record()
             t1.synchronize()
-            res = (G.srss.cpu().numpy(), G.theta.cpu().numpy(), t0.elapsed_time(t1))
-        srss, theta, ms = res
+            res = (G.srss.cpu().numpy(), G.theta.cpu().numpy(), t0.elapsed_time(t1), th0.cpu().numpy())
+        srss, theta, ms, th0 = res
         b = int(np.argmin(np.where(np.isfinite(srss), srss, np.inf)))
         gn.append((abs(float(np.hypot(theta[b, 2], theta[b, 3])) - p_true), ms))
+        coarse_only.append((abs(float(np.hypot(th0[2], th0[3])) - p_true), 0.0))
     ctx.close()
 
     def summ(a):
@@ -283,8 +291,8 @@ def gn_study(n_events: int = 32, stride: int = 16, lam: float = 8e-4, iters: int
         return {"mean_abs_dp_MeV": float(a[:, 0].mean()), "rms_dp_MeV": float(np.sqrt((a[:, 0] ** 2).mean())),
                 "mean_ms": float(a[:, 1].mean())}
     return [{"study": "gauss-newton", "events": n_events, "stride": stride, "lambda_mm": lam * 1e3,
-             "iterations": iters, "K": K, "dense_16x16x32x32": summ(dense),
-             "gn_top16_of_2^14": summ(gn)}]
+             "tau_mm": tau * 1e3, "iterations": iters, "K": K, "dense_16x16x32x32": summ(dense),
+             "gn_top16_of_2^14": summ(gn), "coarse_2^14_best": summ(coarse_only)}]
 
 
 def main(argv=None):
@@ -292,14 +300,15 @@ def main(argv=None):
     ap.add_argument("study", choices=["lambda-sweep", "backward", "iterative", "gauss-newton"])
     ap.add_argument("--events", type=int, default=32)
     ap.add_argument("--stride", type=int, default=16)
-    ap.add_argument("--lambda-mm", type=float, default=10.0, help="cutoff of the backward study")
+    ap.add_argument("--lambda-mm", type=float, default=10.0, help="cutoff (backward, iterative, gn)")
+    ap.add_argument("--tau-mm", type=float, default=1.0, help="smoothing width of the gn study")
     args = ap.parse_args(argv)
     if args.study == "lambda-sweep":
         rows = lambda_sweep(args.events, stride=args.stride)
     elif args.study == "iterative":
         rows = iterative_study(args.events, args.stride, args.lambda_mm * 1e-3)
     elif args.study == "gauss-newton":
-        rows = gn_study(args.events, args.stride, args.lambda_mm * 1e-3)
+        rows = gn_study(args.events, args.stride, args.lambda_mm * 1e-3, tau=args.tau_mm * 1e-3)
     else:
         rows = backward_study(args.events, args.stride, args.lambda_mm * 1e-3)
     for r in rows:
