@@ -13,6 +13,8 @@
  *                         sparse references and finer lattices around them            (Sec. 2.1)
  *   comet_scan_jacobian, comet_scan_gn_step
  *                         smoothed RSS, dD/dseed, Gauss-Newton steps for the best seeds
+ *   comet_scan_batch, comet_scan_batch_update
+ *                         one turn partition of many events in single launches
  *   comet_scan_classify   classify the selected seed's hits; mask them for the next   (Sec. 2.1, 3.1)
  *                         turn partition
  *
@@ -273,6 +275,61 @@ comet_status comet_scan_jacobian(comet_ctx *ctx, comet_dtype dtype, const comet_
  * written by comet_scan_jacobian.  mu >= 0 (Levenberg-Marquardt damping). */
 comet_status comet_scan_gn_step(comet_ctx *ctx, double *theta, int64_t S, const double *jtj,
                                 const double *jtr, double mu, comet_stream stream);
+
+/* ---- batches of events in single launches (many events at once) ---------------------------------
+ * One turn partition of up to caps.max_events events: for each active event its lattice, track
+ * recording, DCA and RSS, selection (k = 1) and classification with the mask update, exactly as the
+ * single-event calls with the same arguments compute them, but each step one launch for the whole
+ * batch.  A launch's blocks are apportioned to the events by their sizes (the persistent DCA launch
+ * binds each of its CTAs to one event, at least one per event, the rest in proportion to the
+ * event's 32-seed groups).  Shared by the batch: dtype, field and params except n_steps; W <= 1024.
+ *
+ * comet_scan_batch_update (host work only) validates the events and packs their descriptors into
+ * the context's pinned staging buffer; comet_scan_batch enqueues one copy of that buffer to the
+ * device and the batched launches.  Grid sizes and device offsets follow the caps alone, so the
+ * work comet_scan_batch enqueues can be captured once in a CUDA graph (stream capture) and replayed
+ * for any batch with the same caps, dtype and stride after comet_scan_batch_update has packed it.
+ * An update waits for the previous batch's descriptor copy to leave the staging buffer before it
+ * rewrites it.  Calling comet_scan_batch with events packs them first (an update); with events =
+ * NULL and B = 0 it enqueues the last packed batch.  The first update with new caps allocates the
+ * staging buffers (and synchronises the device): make it before capturing. */
+typedef struct {
+    int32_t max_events;        /* event slots per batch, 1 .. the resident DCA CTAs (~1000) */
+    int64_t max_seeds;         /* seeds of one event */
+    int64_t max_total_seeds;   /* seeds of all events of a batch */
+    int32_t max_wires;         /* wires of one event, <= 1024 */
+    int32_t max_total_wires;   /* wires of all events of a batch */
+    int32_t dca_ctas_per_sm;   /* resident CTAs per SM of the batched DCA launch; 0: as many as fit */
+} comet_batch_caps;
+
+typedef struct {
+    int32_t active;               /* 0: slot skipped, nothing read or written */
+    comet_lattice lattice;        /* the event's turn partition; S = product of the counts */
+    int32_t n_steps;              /* RK4 steps of this partition (params->n_steps is not used) */
+    void *seeds;                  /* scratch, SoA [6][S] T */
+    int8_t *charge;               /* scratch, [S] */
+    void *points;                 /* scratch, SoA [6][n_rec][S] T, n_rec = n_steps/stride + 1 */
+    int32_t *n_valid;             /* scratch, [S] */
+    void *bounds;                 /* scratch, [ceil(S/32)][200][4] float32, 16-byte aligned */
+    const void *wires;            /* SoA [6][ldw] T, as comet_scan_dca */
+    int32_t W, ldw;
+    const int32_t *hit_offsets;   /* [W+1] */
+    const void *drift;            /* [H] T */
+    uint8_t *hit_mask;            /* in/out [H]: the hits classified here are set to 1 */
+    void *rss;                    /* out [S] T */
+    int32_t *n_in;                /* out [S] */
+    int64_t *best_idx;            /* out [1]: the seed of lowest RSS */
+    void *best_rss;               /* out [1] T (may be NULL) */
+    uint8_t *hit_class;           /* out [H] (required when W > 0) */
+    int32_t *n_unconverged;       /* optional [1], incremented */
+} comet_batch_event;
+
+comet_status comet_scan_batch_update(comet_ctx *ctx, comet_dtype dtype, const comet_field *field,
+                                     const comet_scan_params *params, const comet_batch_caps *caps,
+                                     const comet_batch_event *events, int32_t B);
+comet_status comet_scan_batch(comet_ctx *ctx, comet_dtype dtype, const comet_field *field,
+                              const comet_scan_params *params, const comet_batch_caps *caps,
+                              const comet_batch_event *events, int32_t B, comet_stream stream);
 
 /* ---- selection without device allocation (the paper has no counterpart) -------------------------
  * Same result as comet_scan_select, for callers that cannot allocate device memory: for example a

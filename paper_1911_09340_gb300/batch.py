@@ -1,0 +1,219 @@
+"""Many events at once: continuous batching of the scan over event slots (comet_scan_batch).
+
+Each of ``slots`` slots holds one event for its lifetime: its wires, hits and hit mask stay on the
+device while its turn partitions are scanned one per round, in order (hits classified at one
+partition are masked for the next, Sec. 3.1).  A round is ONE comet_scan_batch: the current
+partition of every active slot in single batched launches.  When an event's last partition is
+done its slot takes the next event of the queue.  The per-round scratch (seeds, track points,
+search bounds, RSS) is bump-allocated from arenas sized by the caps; a round that would exceed the
+seed or wire budget leaves the remaining slots waiting for the next round.
+
+With ``graph=True`` the work comet_scan_batch enqueues is captured once in a CUDA graph and every
+round replays it after comet_scan_batch_update has packed the round's descriptors (grid sizes
+depend on the caps only).
+
+The host work per round is descriptor packing; every step of the scan runs in the library's
+kernels.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import math
+from collections import deque
+from typing import Dict, List, Optional
+
+import numpy as np
+import torch
+
+from . import binding as B
+from . import scan, synth
+
+
+def _pad4(n: int) -> int:
+    return max(4, (n + 3) // 4 * 4)
+
+
+@dataclasses.dataclass
+class EventResult:
+    best_idx: List[int]
+    best_rss: List[float]
+    hit_class: List[np.ndarray]
+    start_round: int = -1
+    end_round: int = -1
+
+
+class BatchScanner:
+    def __init__(self, ctx: B.Context, dtype=torch.float32, stride: int = 16, lam: float = 1e-2,
+                 slots: int = 128, max_seeds: int = 1 << 18, max_total_seeds: int = 1 << 24,
+                 max_wires: int = 512, max_hits: int = 2048, max_n_steps: int = 2400,
+                 graph: bool = True, field: Optional[synth.Field] = None, dca_ctas_per_sm: int = 0):
+        self.ctx, self.dtype, self.stride, self.lam = ctx, dtype, stride, lam
+        self.slots = slots
+        self.max_hits = max_hits
+        self.field = B.DeviceField.from_synth(field or synth.uniform_field(1.0))
+        self.params = B.ScanParams(n_steps=max_n_steps, stride=stride, lam=lam,
+                                   tol=1e-12 if dtype == torch.float64 else 1e-6, max_iter=16)
+        self.caps = B.BatchCaps(slots, max_seeds, max_total_seeds, max_wires, slots * max_wires,
+                                dca_ctas_per_sm)
+        self.n_rec_max = max_n_steps // stride + 1
+        dev = dict(device="cuda")
+        es = torch.tensor([], dtype=dtype).element_size()
+        self.es = es
+        # per-round arenas
+        T = max_total_seeds
+        self.a_seeds = torch.empty(6 * T, dtype=dtype, **dev)
+        self.a_charge = torch.empty(T, dtype=torch.int8, **dev)
+        self.a_points = torch.empty(6 * self.n_rec_max * T, dtype=dtype, **dev)
+        self.a_nvalid = torch.empty(T, dtype=torch.int32, **dev)
+        self.a_bounds = torch.empty(((T + 31) // 32 + slots) * B.BOUNDS_PER_GROUP * 4, dtype=torch.float32, **dev)
+        self.a_rss = torch.empty(T, dtype=dtype, **dev)
+        self.a_nin = torch.empty(T, dtype=torch.int32, **dev)
+        # per-slot resident buffers
+        self.ldw = _pad4(max_wires)
+        self.s_wires = torch.zeros((slots, 6, self.ldw), dtype=dtype, **dev)
+        self.s_offs = torch.zeros((slots, max_wires + 1), dtype=torch.int32, **dev)
+        self.s_drift = torch.zeros((slots, max_hits), dtype=dtype, **dev)
+        self.s_mask = torch.zeros((slots, max_hits), dtype=torch.uint8, **dev)
+        self.s_class = torch.zeros((slots, max_hits), dtype=torch.uint8, **dev)
+        self.s_best = torch.zeros(slots, dtype=torch.int64, **dev)
+        self.s_best_rss = torch.zeros(slots, dtype=dtype, **dev)
+        self.s_unconv = torch.zeros(slots, dtype=torch.int32, **dev)
+        self.desc = (B.BatchEvent * slots)()
+        self.graph = None
+        self.use_graph = graph
+        self.stream = torch.cuda.Stream()
+
+    # ---- slots -----------------------------------------------------------------------------------
+    def _load(self, slot: int, ev):
+        W, H = ev.n_wires, ev.n_hits
+        if W > self.caps.max_wires or H > self.max_hits:
+            raise ValueError(f"event with W={W}, H={H} exceeds the scanner's caps")
+        w = torch.zeros((6, self.ldw), dtype=self.dtype)
+        w[:, :W] = torch.as_tensor(ev.wires, dtype=self.dtype)
+        self.s_wires[slot].copy_(w, non_blocking=False)
+        self.s_offs[slot, : W + 1].copy_(torch.as_tensor(np.asarray(ev.hit_offsets, np.int32)))
+        if H:
+            self.s_drift[slot, :H].copy_(torch.as_tensor(ev.drift, dtype=self.dtype))
+        self.s_mask[slot].zero_()
+
+    def _fill(self, slot: int, ev, part: int, o_s: int, o_b: int):
+        d = self.desc[slot]
+        spec = ev.partitions[part]
+        S = spec.n_seeds
+        n = ev.n_steps[part]
+        d.active = 1
+        d.lattice = B.lattice_struct(spec)
+        d.n_steps = n
+        es = self.es
+        d.seeds = self.a_seeds.data_ptr() + 6 * o_s * es
+        d.charge = self.a_charge.data_ptr() + o_s
+        d.points = self.a_points.data_ptr() + 6 * self.n_rec_max * o_s * es
+        d.n_valid = self.a_nvalid.data_ptr() + 4 * o_s
+        d.bounds = self.a_bounds.data_ptr() + o_b * B.BOUNDS_PER_GROUP * 16
+        d.wires = self.s_wires[slot].data_ptr()
+        d.W = ev.n_wires
+        d.ldw = self.ldw
+        d.hit_offsets = self.s_offs[slot].data_ptr()
+        d.drift = self.s_drift[slot].data_ptr()
+        d.hit_mask = self.s_mask[slot].data_ptr()
+        d.rss = self.a_rss.data_ptr() + o_s * es
+        d.n_in = self.a_nin.data_ptr() + 4 * o_s
+        d.best_idx = self.s_best[slot:].data_ptr()
+        d.best_rss = self.s_best_rss[slot:].data_ptr()
+        d.hit_class = self.s_class[slot].data_ptr()
+        d.n_unconverged = self.s_unconv[slot:].data_ptr()
+        return S
+
+    # ---- the run -----------------------------------------------------------------------------------
+    def run(self, events, collect: bool = False) -> Dict:
+        """Scans every partition of every event.  Returns per-event results (when ``collect``: best
+        seed, its RSS and the hit classes of each partition), per-event latency in ms (from the end
+        of the round before its first partition to the end of its last) and the total GPU time."""
+        queue = deque(range(len(events)))
+        state = [None] * self.slots          # (event index, next partition)
+        results = [EventResult([], [], []) for _ in events]
+        marks: List[torch.cuda.Event] = []
+        rnd = 0
+        start = 0
+        torch.cuda.synchronize()
+        with torch.cuda.stream(self.stream):
+            t0 = torch.cuda.Event(enable_timing=True)
+            t0.record()
+            while queue or any(s is not None for s in state):
+                for slot in range(self.slots):
+                    if state[slot] is None and queue:
+                        i = queue.popleft()
+                        self._load(slot, events[i])
+                        state[slot] = (i, 0)
+                        results[i].start_round = rnd
+                o_s = o_b = w_tot = 0
+                members = []
+                for k in range(self.slots):
+                    slot = (start + k) % self.slots
+                    st = state[slot]
+                    self.desc[slot].active = 0
+                    if st is None:
+                        continue
+                    ev = events[st[0]]
+                    S = ev.partitions[st[1]].n_seeds
+                    if o_s + S > self.caps.max_total_seeds or w_tot + ev.n_wires > self.caps.max_total_wires:
+                        continue                       # waits for the next round
+                    self._fill(slot, ev, st[1], o_s, o_b)
+                    o_s += S
+                    o_b += (S + 31) // 32
+                    w_tot += ev.n_wires
+                    members.append(slot)
+                start = (start + 1) % self.slots
+                self._launch()
+                e = torch.cuda.Event(enable_timing=True)
+                e.record()
+                marks.append(e)
+                if collect:
+                    self.stream.synchronize()
+                    best = self.s_best.cpu().numpy()
+                    best_rss = self.s_best_rss.double().cpu().numpy()
+                    cls = self.s_class.cpu().numpy()
+                for slot in members:
+                    i, p = state[slot]
+                    if collect:
+                        ev = events[i]
+                        results[i].best_idx.append(int(best[slot]))
+                        results[i].best_rss.append(float(best_rss[slot]))
+                        results[i].hit_class.append(cls[slot, : ev.n_hits].copy())
+                    if p + 1 == len(events[i].partitions):
+                        results[i].end_round = rnd
+                        state[slot] = None
+                    else:
+                        state[slot] = (i, p + 1)
+                rnd += 1
+            self.stream.synchronize()
+        ms_round = [t0.elapsed_time(m) for m in marks]
+        lat = []
+        for r in results:
+            begin = 0.0 if r.start_round == 0 else ms_round[r.start_round - 1]
+            lat.append(ms_round[r.end_round] - begin)
+        return {"results": results, "latency_ms": np.array(lat), "gpu_ms": ms_round[-1] if ms_round else 0.0,
+                "rounds": rnd}
+
+    def _launch(self):
+        B.comet_scan_batch_update(self.ctx, self.dtype, self.field, self.params, self.caps, self.desc,
+                                  self.slots)
+        if not self.use_graph:
+            B.comet_scan_batch(self.ctx, self.dtype, self.field, self.params, self.caps,
+                               stream=self.stream)
+            return
+        if self.graph is None:
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=self.stream):
+                B.comet_scan_batch(self.ctx, self.dtype, self.field, self.params, self.caps,
+                                   stream=torch.cuda.current_stream())
+            self.graph = g
+        self.graph.replay()
+
+
+def batch_counts(n_turns: int):
+    """Seed lattice of a turn partition for an event of n_turns turns: 2^12, 2^13, 2^14, 2^16, 2^17,
+    2^18 seeds for 1..6 turns."""
+    return {1: (4, 4, 16, 16), 2: (4, 8, 16, 16), 3: (8, 8, 16, 16), 4: (8, 8, 32, 32),
+            5: (16, 8, 32, 32), 6: (16, 16, 32, 32)}[int(n_turns)]

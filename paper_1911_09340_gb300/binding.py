@@ -46,6 +46,23 @@ class _Lattice(C.Structure):
                 ("half_width", C.c_double * 4), ("counts", C.c_int32 * 4), ("charge", C.c_int32)]
 
 
+class BatchCaps(C.Structure):
+    """Mirror of comet_batch_caps."""
+    _fields_ = [("max_events", C.c_int32), ("max_seeds", C.c_int64), ("max_total_seeds", C.c_int64),
+                ("max_wires", C.c_int32), ("max_total_wires", C.c_int32), ("dca_ctas_per_sm", C.c_int32)]
+
+
+class BatchEvent(C.Structure):
+    """Mirror of comet_batch_event (pointers are device addresses)."""
+    _fields_ = [("active", C.c_int32), ("lattice", _Lattice), ("n_steps", C.c_int32),
+                ("seeds", C.c_void_p), ("charge", C.c_void_p), ("points", C.c_void_p),
+                ("n_valid", C.c_void_p), ("bounds", C.c_void_p), ("wires", C.c_void_p),
+                ("W", C.c_int32), ("ldw", C.c_int32), ("hit_offsets", C.c_void_p),
+                ("drift", C.c_void_p), ("hit_mask", C.c_void_p), ("rss", C.c_void_p),
+                ("n_in", C.c_void_p), ("best_idx", C.c_void_p), ("best_rss", C.c_void_p),
+                ("hit_class", C.c_void_p), ("n_unconverged", C.c_void_p)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -71,6 +88,10 @@ SIGNATURES = {
                             C.c_double, _i32, _vp, _i32, _i32, _vp, _vp, _vp, C.c_double, _vp, _vp,
                             _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "comet_scan_gn_step": [_vp, _vp, _i64, _vp, _vp, C.c_double, _vp],
+    "comet_scan_batch_update": [_vp, C.c_int, C.POINTER(_Field), C.POINTER(_Params),
+                                C.POINTER(BatchCaps), C.POINTER(BatchEvent), _i32],
+    "comet_scan_batch": [_vp, C.c_int, C.POINTER(_Field), C.POINTER(_Params), C.POINTER(BatchCaps),
+                         C.POINTER(BatchEvent), _i32, _vp],
     "comet_scan_classify": [_vp, C.c_int, C.POINTER(_Field), C.POINTER(_Params), _vp, _vp, _vp,
                             _i64, _vp, _vp, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _i32, _vp],
 }
@@ -97,6 +118,9 @@ def lib():
 def _check(status: int):
     if status != COMET_OK:
         raise CometError(status, lib().comet_last_error().decode())
+
+
+_DTYPE = {torch.float32: 0, torch.float64: 1}
 
 
 def _dtype_code(t: torch.Tensor) -> int:
@@ -310,6 +334,22 @@ def comet_scan_gn_step(ctx: Context, theta, jtj, jtr, mu: float = 0.0, stream=No
     f64 = torch.float64
     _check(lib().comet_scan_gn_step(ctx.handle, _ptr(theta, f64), theta.shape[0], _ptr(jtj, f64),
                                     _ptr(jtr, f64), float(mu), _stream(stream)))
+
+
+def comet_scan_batch_update(ctx: Context, dtype, field: DeviceField, params: ScanParams, caps: BatchCaps,
+                            events, B: int):
+    """Packs B comet_batch_event descriptors (a ctypes array) into the context's staging buffer."""
+    f, p = field.c(), params.c()
+    _check(lib().comet_scan_batch_update(ctx.handle, _DTYPE[dtype], C.byref(f), C.byref(p),
+                                         C.byref(caps), events, int(B)))
+
+
+def comet_scan_batch(ctx: Context, dtype, field: DeviceField, params: ScanParams, caps: BatchCaps,
+                     events=None, B: int = 0, stream=None):
+    """Enqueues the last packed batch (after packing ``events`` when given)."""
+    f, p = field.c(), params.c()
+    _check(lib().comet_scan_batch(ctx.handle, _DTYPE[dtype], C.byref(f), C.byref(p), C.byref(caps),
+                                  events, int(B), _stream(stream)))
 
 
 def comet_scan_classify(ctx: Context, field: DeviceField, params: ScanParams, points, n_valid,

@@ -9,15 +9,10 @@
 
 #include "comet_scan.h"
 #include "internal.h"
+#include "scan_ctx.h"
 
-struct comet_ctx {
-    int device;
-    void *scratch = nullptr;     // comet_scan_select's per-block partial results
-    size_t scratch_bytes = 0;
-    int32_t *status = nullptr;   // device status word (bit 0: bulk-copy timeout, bit 1: bad seed index)
-};
-
-namespace {
+namespace comet {
+namespace detail {
 
 thread_local char g_err[512] = "";
 
@@ -35,21 +30,28 @@ comet_status cuda_fail(cudaError_t e, const char *where)
     return fail(COMET_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
 }
 
-// Makes ctx->device current for the scope of a call and restores the caller's device afterwards.
-struct DeviceGuard {
-    int prev = -1;
-    cudaError_t err = cudaSuccess;
-    explicit DeviceGuard(int dev)
-    {
-        err = cudaGetDevice(&prev);
-        if (err == cudaSuccess && prev != dev) err = cudaSetDevice(dev);
-    }
-    ~DeviceGuard()
-    {
-        int cur = -1;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
+DeviceGuard::DeviceGuard(int dev)
+{
+    err = cudaGetDevice(&prev);
+    if (err == cudaSuccess && prev != dev) err = cudaSetDevice(dev);
+}
+
+DeviceGuard::~DeviceGuard()
+{
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+}
+
+void BatchState::release()
+{
+    if (host) cudaFreeHost(host);
+    if (dev) cudaFree(dev);
+    if (copied) cudaEventDestroy(copied);
+    host = dev = nullptr;
+    copied = nullptr;
+    recorded = ready = false;
+    dtype = -1;
+}
 
 size_t esize(comet_dtype dt) { return dt == COMET_F32 ? sizeof(float) : sizeof(double); }
 
@@ -108,23 +110,12 @@ comet_status check_hits(comet_dtype dt, const void *wires, int32_t W, int32_t ld
     return COMET_OK;
 }
 
-#define CHECK(expr)                                                                                \
-    do {                                                                                           \
-        comet_status _s = (expr);                                                                  \
-        if (_s != COMET_OK) return _s;                                                             \
-    } while (0)
-
 int n_rec_of(const comet_scan_params *p) { return p->n_steps / p->stride + 1; }
 
 // Segmentation and reaches of the closest-state search: identical for propagate (which writes the
 // segment bounding spheres) and dca (which reads them).  Consecutive recorded states are at most
 // stride*h apart along the track (|dx/ds| = |p|/P0 = 1 up to rounding); the margins cover the
 // rounding of the distances in the working precision.
-struct SearchGeometry {
-    int G0, G1;
-    double R0, R1, half_rec, h_rec;
-};
-
 SearchGeometry search_geometry(comet_dtype dtype, const comet_scan_params *p)
 {
     SearchGeometry g;
@@ -139,7 +130,120 @@ SearchGeometry search_geometry(comet_dtype dtype, const comet_scan_params *p)
 
 bool bounds_aligned(const void *b) { return b == nullptr || ((uintptr_t)b % 16) == 0; }
 
-} // namespace
+void fill_lat(const comet_lattice &lat, int8_t *charge_out, LatArgs *a)
+{
+    a->vx = lat.vx;
+    a->vy = lat.vy;
+    for (int d = 0; d < 4; ++d) {
+        a->centre[d] = lat.centre[d];
+        a->half_width[d] = lat.half_width[d];
+        a->counts[d] = lat.counts[d];
+    }
+    a->charge = lat.charge;
+    a->charge_out = charge_out;
+}
+
+void fill_prop(comet_dtype, const comet_scan_params *p, const SearchGeometry &sg, const void *seeds,
+               const int8_t *charge, int64_t S, void *points, int32_t *n_valid, void *bounds, PropArgs *a)
+{
+    a->bounds = bounds;
+    a->G0 = sg.G0;
+    a->G1 = sg.G1;
+    a->R0 = sg.R0;
+    a->R1 = sg.R1;
+    a->seeds = seeds;
+    a->charge = charge;
+    a->S = S;
+    a->points = points;
+    a->n_valid = n_valid;
+    a->h = p->h;
+    a->zmin = p->zmin;
+    a->zmax = p->zmax;
+    a->rmax = p->rmax;
+    a->n_steps = p->n_steps;
+    a->stride = p->stride;
+    a->h_ff.hi = (float)p->h;
+    a->h_ff.lo = (float)(p->h - (double)a->h_ff.hi);
+    a->lim_f[0] = (float)p->zmin;
+    a->lim_f[1] = (float)p->zmax;
+    a->lim_f[2] = (float)(p->rmax * p->rmax);
+    a->lim_f[3] = (float)sg.R0;
+    a->lim_f[4] = (float)sg.R1;
+    a->n_rec = n_rec_of(p);
+}
+
+void fill_dca(comet_ctx *ctx, comet_dtype, const comet_scan_params *p, const SearchGeometry &sg,
+              const void *points, const int32_t *n_valid, const int8_t *charge, int64_t S,
+              const void *bounds, const void *wires, int32_t W, int32_t ldw, const int32_t *offs,
+              const void *drift, const uint8_t *mask, void *rss, int32_t *n_in, void *dca_out,
+              int32_t *n_unconverged, DcaArgs *a)
+{
+    a->points = points;
+    a->n_valid = n_valid;
+    a->charge = charge;
+    a->S = S;
+    a->n_rec = n_rec_of(p);
+    a->wires = wires;
+    a->W = W;
+    a->ldw = W > 0 ? ldw : 0;
+    a->offs = offs;
+    a->drift = drift;
+    a->mask = mask;
+    a->rss = rss;
+    a->n_in = n_in;
+    a->dca_out = W > 0 ? dca_out : nullptr;
+    a->n_unconv = n_unconverged;
+    a->status = ctx->status;
+    a->counter = ctx->status + 16;
+    a->lambda = p->lambda;
+    a->tol = p->tol;
+    a->max_iter = p->max_iter;
+    a->G0 = sg.G0;
+    a->G1 = sg.G1;
+    a->R0 = sg.R0;
+    a->R1 = sg.R1;
+    a->half_rec = sg.half_rec;
+    a->h_rec = sg.h_rec;
+    a->lambda_f = (float)a->lambda;
+    a->tol_f = (float)a->tol;
+    a->half_rec_f = (float)a->half_rec;
+    a->h_rec_f = (float)a->h_rec;
+    a->bounds = bounds;
+    a->exact_all = dca_out != nullptr;
+}
+
+void fill_cls(comet_ctx *ctx, comet_dtype, const comet_scan_params *p, const void *points,
+              const int32_t *n_valid, const int8_t *charge, int64_t S, const int64_t *seed_index,
+              const void *wires, int32_t W, int32_t ldw, const int32_t *offs, const void *drift,
+              uint8_t *mask, uint8_t *hit_class, void *dca_wire, int32_t update_mask, ClsArgs *a)
+{
+    a->points = points;
+    a->n_valid = n_valid;
+    a->charge = charge;
+    a->S = S;
+    a->n_rec = n_rec_of(p);
+    a->seed_index = seed_index;
+    a->wires = wires;
+    a->W = W;
+    a->ldw = ldw;
+    a->offs = offs;
+    a->drift = drift;
+    a->mask = mask;
+    a->hit_class = hit_class;
+    a->dca_wire = dca_wire;
+    a->status = ctx->status;
+    a->lambda = p->lambda;
+    a->tol = p->tol;
+    a->h_rec = p->h * p->stride;
+    a->max_iter = p->max_iter;
+    a->update_mask = update_mask;
+}
+
+} // namespace detail
+} // namespace comet
+
+using namespace comet::detail;
+#define CHECK(expr) COMET_CHECK(expr)
 
 extern "C" {
 
@@ -181,6 +285,7 @@ void comet_ctx_destroy(comet_ctx *ctx)
         cudaDeviceSynchronize();
         if (ctx->scratch) cudaFree(ctx->scratch);
         if (ctx->status) cudaFree(ctx->status);
+        ctx->batch.release();
     }
     delete ctx;
 }
@@ -217,15 +322,7 @@ comet_status comet_scan_lattice(comet_ctx *ctx, comet_dtype dtype, const comet_l
     DeviceGuard g(ctx->device);
     if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
     comet::LatArgs a;
-    a.vx = lat->vx;
-    a.vy = lat->vy;
-    for (int d = 0; d < 4; ++d) {
-        a.centre[d] = lat->centre[d];
-        a.half_width[d] = lat->half_width[d];
-        a.counts[d] = lat->counts[d];
-    }
-    a.charge = lat->charge;
-    a.charge_out = charge_out;
+    fill_lat(*lat, charge_out, &a);
     cudaError_t e = comet::launch_lattice(dtype, a, seeds, S, (cudaStream_t)stream);
     return e == cudaSuccess ? COMET_OK : cuda_fail(e, "lattice launch");
 }
@@ -401,30 +498,7 @@ comet_status comet_scan_propagate(comet_ctx *ctx, comet_dtype dtype, const comet
     if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
     const SearchGeometry sg = search_geometry(dtype, params);
     comet::PropArgs a;
-    a.bounds = bounds;
-    a.G0 = sg.G0;
-    a.G1 = sg.G1;
-    a.R0 = sg.R0;
-    a.R1 = sg.R1;
-    a.seeds = seeds;
-    a.charge = charge;
-    a.S = S;
-    a.points = points;
-    a.n_valid = n_valid;
-    a.h = params->h;
-    a.zmin = params->zmin;
-    a.zmax = params->zmax;
-    a.rmax = params->rmax;
-    a.n_steps = params->n_steps;
-    a.stride = params->stride;
-    a.h_ff.hi = (float)params->h;
-    a.h_ff.lo = (float)(params->h - (double)a.h_ff.hi);
-    a.lim_f[0] = (float)params->zmin;
-    a.lim_f[1] = (float)params->zmax;
-    a.lim_f[2] = (float)(params->rmax * params->rmax);
-    a.lim_f[3] = (float)sg.R0;
-    a.lim_f[4] = (float)sg.R1;
-    a.n_rec = n_rec_of(params);
+    fill_prop(dtype, params, sg, seeds, charge, S, points, n_valid, bounds, &a);
     cudaError_t e = comet::launch_propagate(dtype, *field, a, (cudaStream_t)stream);
     return e == cudaSuccess ? COMET_OK : cuda_fail(e, "propagate launch");
 }
@@ -451,39 +525,8 @@ comet_status comet_scan_dca(comet_ctx *ctx, comet_dtype dtype, const comet_field
     DeviceGuard g(ctx->device);
     if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
     comet::DcaArgs a;
-    a.points = points;
-    a.n_valid = n_valid;
-    a.charge = charge;
-    a.S = S;
-    a.n_rec = n_rec_of(params);
-    a.wires = wires;
-    a.W = W;
-    a.ldw = W > 0 ? ldw : 0;
-    a.offs = hit_offsets;
-    a.drift = drift;
-    a.mask = hit_mask;
-    a.rss = rss;
-    a.n_in = n_in;
-    a.dca_out = W > 0 ? dca_out : nullptr;
-    a.n_unconv = n_unconverged;
-    a.status = ctx->status;
-    a.counter = ctx->status + 16;
-    a.lambda = params->lambda;
-    a.tol = params->tol;
-    a.max_iter = params->max_iter;
-    const SearchGeometry sg = search_geometry(dtype, params);
-    a.G0 = sg.G0;
-    a.G1 = sg.G1;
-    a.R0 = sg.R0;
-    a.R1 = sg.R1;
-    a.half_rec = sg.half_rec;
-    a.h_rec = sg.h_rec;
-    a.lambda_f = (float)a.lambda;
-    a.tol_f = (float)a.tol;
-    a.half_rec_f = (float)a.half_rec;
-    a.h_rec_f = (float)a.h_rec;
-    a.bounds = bounds;
-    a.exact_all = dca_out != nullptr;
+    fill_dca(ctx, dtype, params, search_geometry(dtype, params), points, n_valid, charge, S, bounds, wires,
+             W, ldw, hit_offsets, drift, hit_mask, rss, n_in, dca_out, n_unconverged, &a);
     cudaError_t e = comet::launch_dca(dtype, *field, a, (cudaStream_t)stream);
     return e == cudaSuccess ? COMET_OK : cuda_fail(e, "dca launch");
 }
@@ -574,26 +617,8 @@ comet_status comet_scan_classify(comet_ctx *ctx, comet_dtype dtype, const comet_
     DeviceGuard g(ctx->device);
     if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
     comet::ClsArgs a;
-    a.points = points;
-    a.n_valid = n_valid;
-    a.charge = charge;
-    a.S = S;
-    a.n_rec = n_rec_of(params);
-    a.seed_index = seed_index;
-    a.wires = wires;
-    a.W = W;
-    a.ldw = ldw;
-    a.offs = hit_offsets;
-    a.drift = drift;
-    a.mask = hit_mask;
-    a.hit_class = hit_class;
-    a.dca_wire = dca_wire;
-    a.status = ctx->status;
-    a.lambda = params->lambda;
-    a.tol = params->tol;
-    a.h_rec = params->h * params->stride;
-    a.max_iter = params->max_iter;
-    a.update_mask = update_mask;
+    fill_cls(ctx, dtype, params, points, n_valid, charge, S, seed_index, wires, W, ldw, hit_offsets, drift,
+             hit_mask, hit_class, dca_wire, update_mask, &a);
     cudaError_t e = comet::launch_classify(dtype, *field, a, (cudaStream_t)stream);
     return e == cudaSuccess ? COMET_OK : cuda_fail(e, "classify launch");
 }

@@ -134,6 +134,65 @@ struct JacArgs {
     int32_t *n_unconv;
 };
 cudaError_t launch_jacobian(const JacArgs &a, cudaStream_t st);
+
+constexpr int kDcaWarpsPerCta = 4;   // warps of a persistent DCA CTA (128 threads)
+
+// ---- batches of events (one turn partition each) in single launches ---------------------------
+// Every batched launch has a fixed grid; block b finds its event e and its block index inside the
+// event from a prefix array start[0..B] (start[e] <= b < start[e+1]); blocks past start[B] exit.
+struct BatchEvent {
+    LatArgs lat;
+    void *seeds;
+    int64_t S;
+    PropArgs prop;
+    DcaArgs dca;
+    SelArgs sel;
+    ClsArgs cls;
+};
+
+struct BatchLaunch {
+    const BatchEvent *ev;            // device [B]
+    const int64_t *lat_start;        // device [B + 1] prefix of lattice blocks (256 seeds)
+    const int64_t *prop_start;       // device [B + 1] prefix of propagate blocks (128 seeds)
+    const int64_t *sel_start;        // device [B + 1] prefix of select pass-1 blocks
+    const int64_t *cls_start;        // device [B + 1] prefix of classify blocks (8 wires)
+    const int32_t *dca_map;          // device [dca_ctas]: event of each persistent DCA CTA (-1: none)
+    int32_t *counters;               // device [B]: 32-seed group counters of the DCA launch
+    int B;
+    unsigned lat_blocks, prop_blocks, sel_blocks, cls_blocks, dca_ctas;
+    int W_max;                       // largest W of the caps (shared-memory layout of the DCA CTAs)
+};
+
+// event of block b and its block index inside the event; false when b is past the batch
+__device__ __forceinline__ bool batch_find(const int64_t *start, int B, int64_t b, int &e, int64_t &lb)
+{
+    if (b >= start[B]) return false;
+    int lo = 0, hi = B - 1;   // largest e with start[e] <= b
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (start[mid] <= b)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    e = lo;
+    lb = b - start[lo];
+    return true;
+}
+
+cudaError_t launch_lattice_batch(comet_dtype dt, const BatchLaunch &L, cudaStream_t st);
+cudaError_t launch_propagate_batch(comet_dtype dt, const comet_field &f, int stride, const BatchLaunch &L,
+                                   cudaStream_t st);
+cudaError_t launch_dca_batch(comet_dtype dt, const comet_field &f, const BatchLaunch &L, cudaStream_t st);
+cudaError_t launch_select_batch(comet_dtype dt, const BatchLaunch &L, cudaStream_t st);
+cudaError_t launch_classify_batch(comet_dtype dt, const comet_field &f, const BatchLaunch &L,
+                                  cudaStream_t st);
+// CTAs per SM of the persistent DCA kernel for a shared-memory layout of W wires
+int dca_persistent_ctas_per_sm(comet_dtype dt, const comet_field &f, int W);
+int device_sm_count();
+int select_chunk();   // RSS entries per select pass-1 block
+
+
 cudaError_t launch_gn_step(double *theta, int64_t S, const double *jtj, const double *jtr, double mu,
                            cudaStream_t st);
 cudaError_t launch_propagate(comet_dtype dt, const comet_field &f, const PropArgs &a, cudaStream_t st);

@@ -12,11 +12,21 @@
 
 namespace comet {
 
-template <typename T, class F>
-__global__ void __launch_bounds__(256) classify_kernel(F f, ClsArgs a)
+// BATCH: one launch for a batch of events; block b belongs to the event that batch_find gives
+// (8 wires per block).
+template <typename T, class F, bool BATCH>
+__global__ void __launch_bounds__(256) classify_kernel(F f, ClsArgs a, BatchLaunch L)
 {
+    int64_t bx = blockIdx.x;
+    if constexpr (BATCH) {
+        int e;
+        int64_t lb;
+        if (!batch_find(L.cls_start, L.B, blockIdx.x, e, lb)) return;
+        a = L.ev[e].cls;
+        bx = lb;
+    }
     const int lane = threadIdx.x & 31;
-    const int i = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int i = (int)((bx * blockDim.x + threadIdx.x) >> 5);
     if (i >= a.W) return;   // whole warps
     const int hb = a.offs[i], he = a.offs[i + 1];
     const int64_t s = *a.seed_index;
@@ -87,25 +97,24 @@ __global__ void __launch_bounds__(256) classify_kernel(F f, ClsArgs a)
     }
 }
 
-template <typename T>
-static void cls_dispatch(const comet_field &f, const ClsArgs &a, cudaStream_t st)
+template <typename T, bool BATCH>
+static void cls_dispatch(const comet_field &f, const ClsArgs &a, unsigned nb, const BatchLaunch &L,
+                         cudaStream_t st)
 {
     const int nt = 256;
-    const int64_t threads = (int64_t)a.W * 32;
-    const unsigned nb = (unsigned)((threads + nt - 1) / nt);
     switch (field_kind(f)) {
     case FieldKind::Axial:
-        classify_kernel<T, FieldAxial<T>><<<nb, nt, 0, st>>>(FieldAxial<T>{(T)f.b[2]}, a);
+        classify_kernel<T, FieldAxial<T>, BATCH><<<nb, nt, 0, st>>>(FieldAxial<T>{(T)f.b[2]}, a, L);
         break;
     case FieldKind::Uniform:
-        classify_kernel<T, FieldUniform<T>><<<nb, nt, 0, st>>>(
-            FieldUniform<T>{(T)f.b[0], (T)f.b[1], (T)f.b[2]}, a);
+        classify_kernel<T, FieldUniform<T>, BATCH><<<nb, nt, 0, st>>>(
+            FieldUniform<T>{(T)f.b[0], (T)f.b[1], (T)f.b[2]}, a, L);
         break;
     case FieldKind::Table:
-        classify_kernel<T, FieldTable<T>><<<nb, nt, 0, st>>>(
+        classify_kernel<T, FieldTable<T>, BATCH><<<nb, nt, 0, st>>>(
             FieldTable<T>{(const float *)f.table, f.nx, f.ny, f.nz, (T)f.origin[0], (T)f.origin[1],
                           (T)f.origin[2], (T)(1.0 / f.spacing)},
-            a);
+            a, L);
         break;
     }
 }
@@ -113,10 +122,22 @@ static void cls_dispatch(const comet_field &f, const ClsArgs &a, cudaStream_t st
 cudaError_t launch_classify(comet_dtype dt, const comet_field &f, const ClsArgs &a, cudaStream_t st)
 {
     if (a.W == 0) return cudaSuccess;
+    const unsigned nb = (unsigned)(((int64_t)a.W * 32 + 255) / 256);
     if (dt == COMET_F32)
-        cls_dispatch<float>(f, a, st);
+        cls_dispatch<float, false>(f, a, nb, BatchLaunch{}, st);
     else
-        cls_dispatch<double>(f, a, st);
+        cls_dispatch<double, false>(f, a, nb, BatchLaunch{}, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_classify_batch(comet_dtype dt, const comet_field &f, const BatchLaunch &L,
+                                  cudaStream_t st)
+{
+    if (L.cls_blocks == 0) return cudaSuccess;
+    if (dt == COMET_F32)
+        cls_dispatch<float, true>(f, ClsArgs{}, L.cls_blocks, L, st);
+    else
+        cls_dispatch<double, true>(f, ClsArgs{}, L.cls_blocks, L, st);
     return cudaGetLastError();
 }
 

@@ -44,6 +44,7 @@ namespace {
 
 constexpr int kThreads = 128;
 constexpr int kWarps = kThreads / 32;
+static_assert(kWarps == kDcaWarpsPerCta, "persistent DCA CTA size");
 constexpr int kWireTile = 256;
 constexpr int kWireCap = kWireTile + 32;     // elements per staged row (room for the 16-B shift)
 constexpr int kHitMax = 1024;                // hits staged in shared memory when H <= kHitMax
@@ -458,9 +459,18 @@ __host__ __device__ inline PLayout p_layout(int W, int es)
 
 constexpr int kPersistMaxW = 1024;
 
-template <typename T, class F>
-__global__ void __launch_bounds__(kThreads, COMET_DCA_MINB) dca_persistent_kernel(F f, DcaArgs a)
+template <typename T, class F, bool BATCH>
+__global__ void __launch_bounds__(kThreads, COMET_DCA_MINB) dca_persistent_kernel(F f, DcaArgs a,
+                                                                                  BatchLaunch BL)
 {
+    if constexpr (BATCH) {
+        // a batch: this CTA serves one event (CTAs apportioned to the events by their size) and
+        // takes that event's 32-seed groups from the event's own counter
+        const int e = BL.dca_map[blockIdx.x];
+        if (e < 0) return;
+        a = BL.ev[e].dca;
+        a.counter = BL.counters + e;
+    }
     const PLayout L = p_layout(a.W, (int)sizeof(T));
     extern __shared__ __align__(128) unsigned char sm[];
     uint64_t *bar = (uint64_t *)sm;
@@ -697,11 +707,11 @@ static cudaError_t dca_launch(const F &fld, const DcaArgs &a, cudaStream_t st)
 {
     if (a.W <= kPersistMaxW && a.counter) {
         const PLayout L = p_layout(a.W, (int)sizeof(T));
-        cudaError_t e = cudaFuncSetAttribute(dca_persistent_kernel<T, F>,
+        cudaError_t e = cudaFuncSetAttribute(dca_persistent_kernel<T, F, false>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
         if (e != cudaSuccess) return e;
         int per_sm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dca_persistent_kernel<T, F>,
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dca_persistent_kernel<T, F, false>,
                                                           kThreads, L.total);
         if (e != cudaSuccess) return e;
         per_sm = per_sm < 1 ? 1 : per_sm;
@@ -711,7 +721,7 @@ static cudaError_t dca_launch(const F &fld, const DcaArgs &a, cudaStream_t st)
         nb = nb < cap ? nb : cap;
         e = cudaMemsetAsync(a.counter, 0, sizeof(int32_t), st);
         if (e != cudaSuccess) return e;
-        dca_persistent_kernel<T, F><<<(unsigned)nb, kThreads, L.total, st>>>(fld, a);
+        dca_persistent_kernel<T, F, false><<<(unsigned)nb, kThreads, L.total, st>>>(fld, a, BatchLaunch{});
         return cudaGetLastError();
     }
     using L = Smem<T>;
@@ -757,6 +767,71 @@ void dca_segments(int n_rec, int *G0, int *G1)
     if ((g0 + g1 - 1) / g1 > kN1Max) g1 = (g0 + kN1Max - 1) / kN1Max;
     *G0 = g0;
     *G1 = g1 > g0 ? g0 : g1;
+}
+
+template <typename T, class F>
+static cudaError_t dca_batch_launch(const F &fld, const BatchLaunch &BL, cudaStream_t st)
+{
+    // (the shared-memory attribute for W_max was set when the batch was prepared: nothing here but
+    // stream work, so that the launch can be captured)
+    const PLayout L = p_layout(BL.W_max, (int)sizeof(T));
+    cudaError_t e = cudaMemsetAsync(BL.counters, 0, sizeof(int32_t) * (size_t)BL.B, st);
+    if (e != cudaSuccess) return e;
+    if (BL.dca_ctas == 0) return cudaSuccess;
+    dca_persistent_kernel<T, F, true><<<BL.dca_ctas, kThreads, L.total, st>>>(fld, DcaArgs{}, BL);
+    return cudaGetLastError();
+}
+
+template <typename T, class F>
+static int dca_ctas_per_sm_t(int W)
+{
+    const PLayout L = p_layout(W, (int)sizeof(T));
+    if (cudaFuncSetAttribute(dca_persistent_kernel<T, F, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)L.total) != cudaSuccess)
+        return 0;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dca_persistent_kernel<T, F, true>, kThreads,
+                                                      L.total) != cudaSuccess)
+        return 0;
+    return per_sm;
+}
+
+template <typename T>
+static int dca_ctas_per_sm_field(const comet_field &f, int W)
+{
+    switch (field_kind(f)) {
+    case FieldKind::Axial: return dca_ctas_per_sm_t<T, FieldAxial<T>>(W);
+    case FieldKind::Uniform: return dca_ctas_per_sm_t<T, FieldUniform<T>>(W);
+    default: return dca_ctas_per_sm_t<T, FieldTable<T>>(W);
+    }
+}
+
+int dca_persistent_ctas_per_sm(comet_dtype dt, const comet_field &f, int W)
+{
+    return dt == COMET_F32 ? dca_ctas_per_sm_field<float>(f, W) : dca_ctas_per_sm_field<double>(f, W);
+}
+
+int device_sm_count() { return sm_count(); }
+
+template <typename T>
+static cudaError_t dca_batch_dispatch(const comet_field &f, const BatchLaunch &BL, cudaStream_t st)
+{
+    switch (field_kind(f)) {
+    case FieldKind::Axial:
+        return dca_batch_launch<T>(FieldAxial<T>{(T)f.b[2]}, BL, st);
+    case FieldKind::Uniform:
+        return dca_batch_launch<T>(FieldUniform<T>{(T)f.b[0], (T)f.b[1], (T)f.b[2]}, BL, st);
+    case FieldKind::Table:
+    default:
+        return dca_batch_launch<T>(FieldTable<T>{(const float *)f.table, f.nx, f.ny, f.nz, (T)f.origin[0],
+                                                 (T)f.origin[1], (T)f.origin[2], (T)(1.0 / f.spacing)},
+                                   BL, st);
+    }
+}
+
+cudaError_t launch_dca_batch(comet_dtype dt, const comet_field &f, const BatchLaunch &BL, cudaStream_t st)
+{
+    return dt == COMET_F32 ? dca_batch_dispatch<float>(f, BL, st) : dca_batch_dispatch<double>(f, BL, st);
 }
 
 cudaError_t launch_dca(comet_dtype dt, const comet_field &f, const DcaArgs &a, cudaStream_t st)

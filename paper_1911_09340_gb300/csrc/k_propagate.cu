@@ -38,15 +38,28 @@ constexpr int kLatTab = 512;   // node values tabulated per block when the four 
 // there is one lattice centred at a.centre; otherwise lattice k is centred at refs[k'] (4 doubles:
 // z0, phi, pz, pt), k' = k while k < *n_refs, else 0 (a repeat of the first, so that the seed count
 // stays fixed whatever the number of references found).
-template <typename T>
+// BATCH: one launch for the lattices of a batch of events; block b belongs to the event that
+// batch_find gives (refs unused).
+template <typename T, bool BATCH>
 __global__ void __launch_bounds__(256) lattice_kernel(LatArgs a, const double *__restrict__ refs,
                                                       const int32_t *__restrict__ n_refs,
-                                                      T *__restrict__ seeds, int64_t S1, int64_t S)
+                                                      T *__restrict__ seeds, int64_t S1, int64_t S,
+                                                      BatchLaunch L)
 {
     // every node value (and cos / sin of every phi node) once per block, in shared memory
     __shared__ double nodes[kLatTab];
     __shared__ double cphi[kLatTab], sphi[kLatTab];
-    const int64_t kb = blockIdx.y;
+    int64_t bx = blockIdx.x;
+    if constexpr (BATCH) {
+        int e;
+        int64_t lb;
+        if (!batch_find(L.lat_start, L.B, blockIdx.x, e, lb)) return;
+        a = L.ev[e].lat;
+        seeds = (T *)L.ev[e].seeds;
+        S1 = S = L.ev[e].S;
+        bx = lb;
+    }
+    const int64_t kb = BATCH ? 0 : blockIdx.y;
     if (refs) {
         const int64_t kr = kb < (int64_t)*n_refs ? kb : 0;
 #pragma unroll
@@ -67,7 +80,7 @@ __global__ void __launch_bounds__(256) lattice_kernel(LatArgs a, const double *_
         }
         __syncthreads();
     }
-    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t s = bx * blockDim.x + threadIdx.x;
     if (s >= S1) return;
     int b[4];
     b[0] = a.counts[0] % 2 == 0 ? 2 : 1;
@@ -253,10 +266,19 @@ __device__ __forceinline__ void advance_interval(const F &f, const PropArgs &a, 
     }
 }
 
-template <typename T, class F, int STRIDE>
-__global__ void __launch_bounds__(128) propagate_kernel(F f, PropArgs a)
+// BATCH: one launch for a batch of events; block b belongs to the event that batch_find gives.
+template <typename T, class F, int STRIDE, bool BATCH>
+__global__ void __launch_bounds__(128) propagate_kernel(F f, PropArgs a, BatchLaunch L)
 {
-    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t bx = blockIdx.x;
+    if constexpr (BATCH) {
+        int e;
+        int64_t lb;
+        if (!batch_find(L.prop_start, L.B, blockIdx.x, e, lb)) return;
+        a = L.ev[e].prop;
+        bx = lb;
+    }
+    const int64_t s = bx * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     const bool valid = s < a.S;
     const bool wb = a.bounds != nullptr;   // whole warps then stay in the loop (warp reductions)
@@ -387,51 +409,80 @@ cudaError_t launch_lattice_refined(comet_dtype dt, const LatArgs &a, const doubl
     const int nt = 256;
     const int64_t S1 = S / K;
     const dim3 grid((unsigned)((S1 + nt - 1) / nt), (unsigned)K);
+    const BatchLaunch none{};
     if (dt == COMET_F32)
-        lattice_kernel<float><<<grid, nt, 0, st>>>(a, refs, n_refs, (float *)seeds, S1, S);
+        lattice_kernel<float, false><<<grid, nt, 0, st>>>(a, refs, n_refs, (float *)seeds, S1, S, none);
     else
-        lattice_kernel<double><<<grid, nt, 0, st>>>(a, refs, n_refs, (double *)seeds, S1, S);
+        lattice_kernel<double, false><<<grid, nt, 0, st>>>(a, refs, n_refs, (double *)seeds, S1, S, none);
     return cudaGetLastError();
 }
 
-template <typename T, class F>
-static void prop_launch(const F &fld, const PropArgs &a, cudaStream_t st)
+cudaError_t launch_lattice_batch(comet_dtype dt, const BatchLaunch &L, cudaStream_t st)
+{
+    if (L.lat_blocks == 0) return cudaSuccess;
+    const LatArgs none{};
+    if (dt == COMET_F32)
+        lattice_kernel<float, true><<<L.lat_blocks, 256, 0, st>>>(none, nullptr, nullptr, nullptr, 0, 0, L);
+    else
+        lattice_kernel<double, true><<<L.lat_blocks, 256, 0, st>>>(none, nullptr, nullptr, nullptr, 0, 0, L);
+    return cudaGetLastError();
+}
+
+template <typename T, class F, bool BATCH>
+static void prop_launch(const F &fld, const PropArgs &a, int stride, unsigned nb, const BatchLaunch &L,
+                        cudaStream_t st)
 {
     const int nt = 128;
-    const unsigned nb = (unsigned)((a.S + nt - 1) / nt);
-    switch (a.stride) {
-    case 1: propagate_kernel<T, F, 1><<<nb, nt, 0, st>>>(fld, a); break;
-    case 2: propagate_kernel<T, F, 2><<<nb, nt, 0, st>>>(fld, a); break;
-    case 4: propagate_kernel<T, F, 4><<<nb, nt, 0, st>>>(fld, a); break;
-    case 8: propagate_kernel<T, F, 8><<<nb, nt, 0, st>>>(fld, a); break;
-    default: propagate_kernel<T, F, 0><<<nb, nt, 0, st>>>(fld, a); break;
+    switch (stride) {
+    case 1: propagate_kernel<T, F, 1, BATCH><<<nb, nt, 0, st>>>(fld, a, L); break;
+    case 2: propagate_kernel<T, F, 2, BATCH><<<nb, nt, 0, st>>>(fld, a, L); break;
+    case 4: propagate_kernel<T, F, 4, BATCH><<<nb, nt, 0, st>>>(fld, a, L); break;
+    case 8: propagate_kernel<T, F, 8, BATCH><<<nb, nt, 0, st>>>(fld, a, L); break;
+    default: propagate_kernel<T, F, 0, BATCH><<<nb, nt, 0, st>>>(fld, a, L); break;
     }
 }
 
-template <typename T>
-static void prop_dispatch(const comet_field &f, const PropArgs &a, cudaStream_t st)
+template <typename T, bool BATCH>
+static void prop_dispatch(const comet_field &f, const PropArgs &a, int stride, unsigned nb,
+                          const BatchLaunch &L, cudaStream_t st)
 {
     switch (field_kind(f)) {
     case FieldKind::Axial:
-        prop_launch<T>(FieldAxial<T>{(T)f.b[2]}, a, st);
+        prop_launch<T, FieldAxial<T>, BATCH>(FieldAxial<T>{(T)f.b[2]}, a, stride, nb, L, st);
         break;
     case FieldKind::Uniform:
-        prop_launch<T>(FieldUniform<T>{(T)f.b[0], (T)f.b[1], (T)f.b[2]}, a, st);
+        prop_launch<T, FieldUniform<T>, BATCH>(FieldUniform<T>{(T)f.b[0], (T)f.b[1], (T)f.b[2]}, a,
+                                               stride, nb, L, st);
         break;
     case FieldKind::Table:
-        prop_launch<T>(FieldTable<T>{(const float *)f.table, f.nx, f.ny, f.nz, (T)f.origin[0],
-                                     (T)f.origin[1], (T)f.origin[2], (T)(1.0 / f.spacing)},
-                       a, st);
+        prop_launch<T, FieldTable<T>, BATCH>(FieldTable<T>{(const float *)f.table, f.nx, f.ny, f.nz,
+                                                           (T)f.origin[0], (T)f.origin[1],
+                                                           (T)f.origin[2], (T)(1.0 / f.spacing)},
+                                             a, stride, nb, L, st);
         break;
     }
 }
 
 cudaError_t launch_propagate(comet_dtype dt, const comet_field &f, const PropArgs &a, cudaStream_t st)
 {
+    const unsigned nb = (unsigned)((a.S + 127) / 128);
+    const BatchLaunch none{};
     if (dt == COMET_F32)
-        prop_dispatch<float>(f, a, st);
+        prop_dispatch<float, false>(f, a, a.stride, nb, none, st);
     else
-        prop_dispatch<double>(f, a, st);
+        prop_dispatch<double, false>(f, a, a.stride, nb, none, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_propagate_batch(comet_dtype dt, const comet_field &f, int stride, const BatchLaunch &L,
+                                   cudaStream_t st)
+{
+    if (L.prop_blocks == 0) return cudaSuccess;
+    const PropArgs none{};
+    if (dt == COMET_F32)
+        prop_dispatch<float, true>(f, none, stride, L.prop_blocks, L, st);
+    else
+        prop_dispatch<double, true>(f, none, stride, L.prop_blocks, L, st);
     return cudaGetLastError();
 }
 

@@ -116,7 +116,57 @@ __global__ void __launch_bounds__(kSelThreads) select_pass2(const T *__restrict_
     }
 }
 
+// A batch: pass 1 block b serves the chunk batch_find gives inside its event; pass 2 block e serves
+// event e.  Each event's partial results live at its SelArgs.scratch (ids first, then values).
+template <typename T>
+__global__ void __launch_bounds__(kSelThreads) select_pass1_batch(BatchLaunch L)
+{
+    int e;
+    int64_t lb;
+    if (!batch_find(L.sel_start, L.B, blockIdx.x, e, lb)) return;
+    const SelArgs a = L.ev[e].sel;
+    int64_t *pi = (int64_t *)a.scratch;
+    T *pv = (T *)(pi + (int64_t)a.n_blocks * a.k);
+    const T *__restrict__ rss = (const T *)a.rss;
+    const int64_t b0 = lb * kChunk;
+    const int64_t n = min((int64_t)kChunk, a.S - b0);
+    block_topk<T>(n, a.k, [&](int64_t j) { return Key<T>{rss[b0 + j], b0 + j}; }, pv + lb * a.k,
+                  pi + lb * a.k);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kSelThreads) select_pass2_batch(BatchLaunch L)
+{
+    if ((int)blockIdx.x >= L.B) return;
+    const SelArgs a = L.ev[blockIdx.x].sel;
+    if (a.S <= 0) return;
+    const int64_t *pi = (const int64_t *)a.scratch;
+    const T *pv = (const T *)(pi + (int64_t)a.n_blocks * a.k);
+    __shared__ T ov[64];
+    __shared__ int64_t oi[64];
+    block_topk<T>((int64_t)a.n_blocks * a.k, a.k, [&](int64_t j) { return Key<T>{pv[j], pi[j]}; }, ov, oi);
+    for (int r = threadIdx.x; r < a.k; r += blockDim.x) {
+        a.idx_out[r] = oi[r];
+        if (a.rss_out) ((T *)a.rss_out)[r] = ov[r];
+    }
+}
+
 } // namespace
+
+cudaError_t launch_select_batch(comet_dtype dt, const BatchLaunch &L, cudaStream_t st)
+{
+    if (L.B == 0) return cudaSuccess;
+    if (dt == COMET_F32) {
+        if (L.sel_blocks) select_pass1_batch<float><<<L.sel_blocks, kSelThreads, 0, st>>>(L);
+        select_pass2_batch<float><<<(unsigned)L.B, kSelThreads, 0, st>>>(L);
+    } else {
+        if (L.sel_blocks) select_pass1_batch<double><<<L.sel_blocks, kSelThreads, 0, st>>>(L);
+        select_pass2_batch<double><<<(unsigned)L.B, kSelThreads, 0, st>>>(L);
+    }
+    return cudaGetLastError();
+}
+
+int select_chunk() { return kChunk; }
 
 size_t select_scratch_bytes(comet_dtype dt, int64_t S, int k, int *n_blocks)
 {

@@ -494,6 +494,40 @@ def multi_turn_event(i: int, chamber: Optional[Chamber] = None, counts=(16, 16, 
     return make_event_random(ch, workload_rng(2, i), counts=counts)
 
 
+BATCH_COUNTS = {1: (4, 4, 16, 16), 2: (4, 8, 16, 16), 3: (8, 8, 16, 16), 4: (8, 8, 32, 32),
+                5: (16, 8, 32, 32), 6: (16, 16, 32, 32)}   # 2^12, 2^13, 2^14, 2^16, 2^17, 2^18 seeds
+
+
+def batch_event(i: int, chamber: Optional[Chamber] = None, counts_scale: int = 0) -> Event:
+    """Event i of the batching workload: 1-6 turns, p ~ U(100, 105) MeV/c, seeds per partition by
+    turn count (BATCH_COUNTS; ``counts_scale`` halves the two fastest dimensions that many times for
+    small test lattices), fired signal wires log-uniform over 20-400: a target bin of 16 log-spaced
+    bins is drawn first and the turn count is redrawn until an event lands in it (rejection to a
+    16-bin log histogram; a bin no turn count reaches in 12 draws falls back to 20-400)."""
+    ch = chamber or make_chamber()
+    rng = workload_rng(5, i)
+    edges = np.geomspace(20.0, 400.0, 17)
+    b = int(rng.integers(0, 16))
+    lo, hi = int(math.ceil(edges[b])), int(math.floor(edges[b + 1]))
+
+    def counts_for(n_t):
+        c = list(BATCH_COUNTS[n_t])
+        for _ in range(counts_scale):
+            c[2] = max(2, c[2] // 2)
+            c[3] = max(2, c[3] // 2)
+        return tuple(c)
+
+    for _ in range(12):
+        n_t = int(rng.integers(1, 7))
+        try:
+            return make_event_random(ch, rng, turns=(n_t, n_t), counts=counts_for(n_t),
+                                     hits_window=(lo, max(lo, hi)), max_tries=6)
+        except RuntimeError:
+            continue
+    n_t = int(rng.integers(1, 7))
+    return make_event_random(ch, rng, turns=(n_t, n_t), counts=counts_for(n_t), hits_window=(20, 400))
+
+
 def table_field_event(i: int, field: Field, chamber: Optional[Chamber] = None,
                       counts=(16, 16, 32, 32)) -> Event:
     """Event i of the non-uniform-field workload: p from the DIO-shaped sampler, field from the
