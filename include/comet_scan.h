@@ -292,7 +292,9 @@ comet_status comet_scan_gn_step(comet_ctx *ctx, double *theta, int64_t S, const 
  * An update waits for the previous batch's descriptor copy to leave the staging buffer before it
  * rewrites it.  Calling comet_scan_batch with events packs them first (an update); with events =
  * NULL and B = 0 it enqueues the last packed batch.  The first update with new caps allocates the
- * staging buffers (and synchronises the device): make it before capturing. */
+ * staging buffers (and synchronises the device): make it before capturing.  An update whose caps or
+ * dtype differ from the previous one frees and reallocates the staging buffers, so a graph captured
+ * before it copies from freed memory: such a graph must not be replayed again (capture anew). */
 typedef struct {
     int32_t max_events;        /* event slots per batch, 1 .. the resident DCA CTAs (~1000) */
     int64_t max_seeds;         /* seeds of one event */

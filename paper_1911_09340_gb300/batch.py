@@ -49,13 +49,14 @@ class BatchScanner:
                  max_wires: int = 512, max_hits: int = 2048, max_n_steps: int = 2400,
                  graph: bool = True, field: Optional[synth.Field] = None, dca_ctas_per_sm: int = 0):
         self.ctx, self.dtype, self.stride, self.lam = ctx, dtype, stride, lam
-        self.slots = slots
+        self.slots = self.slots_alloc = slots
         self.max_hits = max_hits
         self.field = B.DeviceField.from_synth(field or synth.uniform_field(1.0))
         self.params = B.ScanParams(n_steps=max_n_steps, stride=stride, lam=lam,
                                    tol=1e-12 if dtype == torch.float64 else 1e-6, max_iter=16)
-        self.caps = B.BatchCaps(slots, max_seeds, max_total_seeds, max_wires, slots * max_wires,
-                                dca_ctas_per_sm)
+        self.max_seeds, self.max_total_seeds, self.max_wires = max_seeds, max_total_seeds, max_wires
+        self.dca_ctas_per_sm = dca_ctas_per_sm
+        self.caps = self._caps(slots, dca_ctas_per_sm)
         self.n_rec_max = max_n_steps // stride + 1
         dev = dict(device="cuda")
         es = torch.tensor([], dtype=dtype).element_size()
@@ -80,9 +81,32 @@ class BatchScanner:
         self.s_best_rss = torch.zeros(slots, dtype=dtype, **dev)
         self.s_unconv = torch.zeros(slots, dtype=torch.int32, **dev)
         self.desc = (B.BatchEvent * slots)()
-        self.graph = None
+        self.graphs = {}                 # captured rounds, per caps
         self.use_graph = graph
         self.stream = torch.cuda.Stream()
+
+    def _caps(self, slots: int, dca_ctas_per_sm: int) -> B.BatchCaps:
+        return B.BatchCaps(slots, self.max_seeds, self.max_total_seeds, self.max_wires,
+                           slots * self.max_wires, dca_ctas_per_sm)
+
+    def configure(self, slots: Optional[int] = None, dca_ctas_per_sm: Optional[int] = None,
+                  graph: Optional[bool] = None):
+        """Events in flight (at most the slots allocated), DCA CTAs per SM and graph use of the next
+        runs (the knobs the autotuner turns)."""
+        if slots is not None:
+            if slots > self.slots_alloc:
+                raise ValueError("more slots than allocated")
+            self.slots = slots
+        if dca_ctas_per_sm is not None:
+            self.dca_ctas_per_sm = dca_ctas_per_sm
+        if graph is not None:
+            self.use_graph = graph
+        caps = self._caps(self.slots, self.dca_ctas_per_sm)
+        if (caps.max_events, caps.dca_ctas_per_sm) != (self.caps.max_events, self.caps.dca_ctas_per_sm):
+            # the next update reallocates the context's staging buffers that captured graphs copy
+            # from: a graph captured before must never be replayed again
+            self.graphs.clear()
+        self.caps = caps
 
     # ---- slots -----------------------------------------------------------------------------------
     def _load(self, slot: int, ev):
@@ -203,17 +227,33 @@ class BatchScanner:
             B.comet_scan_batch(self.ctx, self.dtype, self.field, self.params, self.caps,
                                stream=self.stream)
             return
-        if self.graph is None:
+        key = (self.caps.max_events, self.caps.dca_ctas_per_sm)   # at most one entry (see configure)
+        g = self.graphs.get(key)
+        if g is None:
             g = torch.cuda.CUDAGraph()
             with torch.cuda.graph(g, stream=self.stream):
                 B.comet_scan_batch(self.ctx, self.dtype, self.field, self.params, self.caps,
                                    stream=torch.cuda.current_stream())
-            self.graph = g
-        self.graph.replay()
+            self.graphs[key] = g
+        g.replay()
 
 
-def batch_counts(n_turns: int):
-    """Seed lattice of a turn partition for an event of n_turns turns: 2^12, 2^13, 2^14, 2^16, 2^17,
-    2^18 seeds for 1..6 turns."""
-    return {1: (4, 4, 16, 16), 2: (4, 8, 16, 16), 3: (8, 8, 16, 16), 4: (8, 8, 32, 32),
-            5: (16, 8, 32, 32), 6: (16, 16, 32, 32)}[int(n_turns)]
+def autotune(scanner: BatchScanner, events, slots_options=(32, 64, 128, 256), ctas_options=(0, 4, 2),
+             graph_options=(True, False)):
+    """Measures events/s of each (events in flight, DCA CTAs per SM, CUDA graph) on ``events`` (a
+    sample of the workload; one warm run and one timed run each) and leaves the scanner configured
+    with the fastest.  Returns (best, table)."""
+    table = []
+    for g in graph_options:
+        for sl in slots_options:
+            if sl > scanner.slots_alloc:
+                continue
+            for c in ctas_options:
+                scanner.configure(slots=sl, dca_ctas_per_sm=c, graph=g)
+                scanner.run(events)
+                r = scanner.run(events)
+                table.append({"slots": sl, "dca_ctas_per_sm": c, "graph": g,
+                              "events_per_s": len(events) / (r["gpu_ms"] * 1e-3), "gpu_ms": r["gpu_ms"]})
+    best = max(table, key=lambda t: t["events_per_s"])
+    scanner.configure(slots=best["slots"], dca_ctas_per_sm=best["dca_ctas_per_sm"], graph=best["graph"])
+    return best, table

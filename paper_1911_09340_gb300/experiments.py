@@ -4,6 +4,7 @@
     python -m paper_1911_09340_gb300.experiments backward [--events N] [--stride s]
     python -m paper_1911_09340_gb300.experiments iterative [--events N] [--stride s]
     python -m paper_1911_09340_gb300.experiments gauss-newton [--events N] [--lambda-mm 0.8]
+    python -m paper_1911_09340_gb300.experiments batch [--events N]
 
 * ``lambda-sweep``: hit-classification efficiency and purity (metrics.py) of the first stage and of
   all stages as the cutoff lambda runs over 0.5-1.2 mm in 0.1 mm steps (the range of the paper's
@@ -16,6 +17,8 @@
   references, finer lattices around them) of a 2^14 coarse grid refined twice.
 * ``gauss-newton``: the dense grid against Gauss-Newton on the smoothed RSS (comet_scan_jacobian,
   comet_scan_gn_step) started from the top 16 seeds of a 2^14 grid.
+* ``batch``: events/s and per-event latency of many uneven events, per-event path against
+  continuous batching (batch.py) under the autotuned configuration.
 
 Every scan runs through the library's kernels (scan.scan_partition); only the metrics are computed
 on the host from the copied-back hit classes.  One JSON line per result.
@@ -295,9 +298,76 @@ def gn_study(n_events: int = 32, stride: int = 16, lam: float = 8e-4, iters: int
              "gn_top16_of_2^14": summ(gn), "coarse_2^14_best": summ(coarse_only)}]
 
 
+def generate_batch_events(n: int, workers: int = 0):
+    """Events 0..n-1 of the batching workload (synth.batch_event), generated in a spawn process
+    pool (the generator is NumPy only)."""
+    import multiprocessing as mp
+    import os
+    workers = workers or min(16, os.cpu_count() or 1)
+    if workers <= 1:
+        return [synth.batch_event(i) for i in range(n)]
+    with mp.get_context("spawn").Pool(workers) as pool:
+        return pool.map(synth.batch_event, range(n), chunksize=4)
+
+
+def batch_study(n_events: int = 512, stride: int = 16, lam: float = 1e-2, tune_events: int = 128,
+                dtype=torch.float32, max_total_seeds: int = 1 << 24):
+    """Events/s and per-event latency of the batching workload (1-6 turns, 2^12-2^18 seeds per
+    partition by turn count, uneven hit counts): the per-event path (one partition at a time, six
+    launches each) against continuous batching (comet_scan_batch rounds replayed from a CUDA graph,
+    configured by the autotuner on the first ``tune_events`` events)."""
+    from . import batch as BT
+    events = generate_batch_events(n_events)
+    ctx = B.Context(torch.cuda.current_device())
+    field = B.DeviceField.from_synth(synth.uniform_field(1.0))
+    # per-event path
+    S = max(sp.n_seeds for ev in events for sp in ev.partitions)
+    n_rec = max(n // stride + 1 for ev in events for n in ev.n_steps)
+    ws = scan.Workspace(S, n_rec, max(ev.n_hits for ev in events), dtype)
+    devs = [scan.DeviceEvent.from_event(ev, dtype) for ev in events]
+    for ev, dev in zip(events[:8], devs[:8]):
+        scan.scan_event(ctx, field, ev, dev, ws, dtype, stride, lam)
+    torch.cuda.synchronize()
+    lat = []
+    t_all0 = torch.cuda.Event(enable_timing=True)
+    t_all0.record()
+    for ev, dev in zip(events, devs):
+        dev.mask.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        scan.scan_event(ctx, field, ev, dev, ws, dtype, stride, lam)
+        b.record()
+        lat.append((a, b))
+    t_all1 = torch.cuda.Event(enable_timing=True)
+    t_all1.record()
+    torch.cuda.synchronize()
+    seq_ms = t_all0.elapsed_time(t_all1)
+    seq_lat = np.array([a.elapsed_time(b) for a, b in lat])
+    del ws, devs
+    torch.cuda.empty_cache()
+    # batched path
+    sc = BT.BatchScanner(ctx, dtype, stride, lam, slots=256, max_total_seeds=max_total_seeds,
+                         max_wires=max(512, max(ev.n_wires for ev in events)),
+                         max_hits=max(2048, max(ev.n_hits for ev in events)))
+    best, table = BT.autotune(sc, events[:tune_events])
+    sc.run(events[:tune_events])
+    r = sc.run(events)
+    wires = np.array([ev.n_wires for ev in events])
+    turns = np.bincount([len(ev.partitions) for ev in events], minlength=7)[1:]
+    ctx.close()
+    pct = lambda x: {"p50": float(np.percentile(x, 50)), "p99": float(np.percentile(x, 99))}
+    return [{"study": "batch", "events": n_events, "stride": stride, "lambda_mm": lam * 1e3,
+             "turns_1_to_6": turns.tolist(), "wires_min_median_max": [int(wires.min()), int(np.median(wires)),
+                                                                      int(wires.max())],
+             "per_event_path": {"events_per_s": n_events / (seq_ms * 1e-3), "latency_ms": pct(seq_lat)},
+             "batched": {"events_per_s": n_events / (r["gpu_ms"] * 1e-3), "latency_ms": pct(r["latency_ms"]),
+                         "rounds": r["rounds"], "config": best},
+             "autotune": table}]
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("study", choices=["lambda-sweep", "backward", "iterative", "gauss-newton"])
+    ap.add_argument("study", choices=["lambda-sweep", "backward", "iterative", "gauss-newton", "batch"])
     ap.add_argument("--events", type=int, default=32)
     ap.add_argument("--stride", type=int, default=16)
     ap.add_argument("--lambda-mm", type=float, default=10.0, help="cutoff (backward, iterative, gn)")
@@ -307,6 +377,8 @@ def main(argv=None):
         rows = lambda_sweep(args.events, stride=args.stride)
     elif args.study == "iterative":
         rows = iterative_study(args.events, args.stride, args.lambda_mm * 1e-3)
+    elif args.study == "batch":
+        rows = batch_study(args.events, args.stride, args.lambda_mm * 1e-3)
     elif args.study == "gauss-newton":
         rows = gn_study(args.events, args.stride, args.lambda_mm * 1e-3, tau=args.tau_mm * 1e-3)
     else:

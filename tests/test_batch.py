@@ -48,3 +48,23 @@ def test_batch_equals_per_event_scan(ctx, dtype_name, graph, budget):
             assert res.best_rss[p] == part["rss"]
             assert np.array_equal(res.hit_class[p], part["hit_class"])
     assert np.all(r["latency_ms"] > 0) and r["rounds"] >= max(len(ev.partitions) for ev in events)
+
+
+def test_autotune_then_run_matches_per_event_scan(ctx):
+    """The autotuner cycles through configurations (new caps reallocate the context's staging, and
+    graphs captured before must be dropped); the configured run afterwards still reproduces the
+    per-event scan exactly."""
+    import torch
+    from paper_1911_09340_gb300 import batch
+    events = _events(6)
+    ref = _reference(ctx, events, torch.float32, 16)
+    bs = batch.BatchScanner(ctx, torch.float32, stride=16, lam=1e-2, slots=4, max_seeds=4096,
+                            max_total_seeds=1 << 16, max_wires=512, max_hits=1024)
+    best, table = batch.autotune(bs, events[:3], slots_options=(2, 4), ctas_options=(0, 2),
+                                 graph_options=(True, False))
+    assert len(table) == 8 and best in table
+    r = bs.run(events, collect=True)
+    for rr, res in zip(ref, r["results"]):
+        for p, part in enumerate(rr):
+            assert res.best_idx[p] == part["idx"] and res.best_rss[p] == part["rss"]
+            assert np.array_equal(res.hit_class[p], part["hit_class"])
