@@ -280,9 +280,10 @@ comet_status comet_scan_gn_step(comet_ctx *ctx, double *theta, int64_t S, const 
  * One turn partition of up to caps.max_events events: for each active event its lattice, track
  * recording, DCA and RSS, selection (k = 1) and classification with the mask update, exactly as the
  * single-event calls with the same arguments compute them, but each step one launch for the whole
- * batch.  A launch's blocks are apportioned to the events by their sizes (the persistent DCA launch
- * binds each of its CTAs to one event, at least one per event, the rest in proportion to the
- * event's 32-seed groups).  Shared by the batch: dtype, field and params except n_steps; W <= 1024.
+ * batch.  A launch's blocks are apportioned to the events by their sizes; the persistent DCA
+ * launch's CTAs take chunks of 16 32-seed groups from one counter over all events, restaging an
+ * event's wires when they move to it.  Shared by the batch: dtype, field and params except n_steps;
+ * W <= 1024.
  *
  * comet_scan_batch_update (host work only) validates the events and packs their descriptors into
  * the context's pinned staging buffer; comet_scan_batch enqueues one copy of that buffer to the
@@ -296,7 +297,7 @@ comet_status comet_scan_gn_step(comet_ctx *ctx, double *theta, int64_t S, const 
  * dtype differ from the previous one frees and reallocates the staging buffers, so a graph captured
  * before it copies from freed memory: such a graph must not be replayed again (capture anew). */
 typedef struct {
-    int32_t max_events;        /* event slots per batch, 1 .. the resident DCA CTAs (~1000) */
+    int32_t max_events;        /* event slots per batch, 1 .. 65536 */
     int64_t max_seeds;         /* seeds of one event */
     int64_t max_total_seeds;   /* seeds of all events of a batch */
     int32_t max_wires;         /* wires of one event, <= 1024 */

@@ -23,8 +23,6 @@ namespace {
 using comet::BatchEvent;
 using comet::BatchLaunch;
 
-constexpr int kDcaGroupsPerWarp = 1;
-
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 struct Layout {
@@ -57,11 +55,11 @@ Layout make_layout(const comet_batch_caps &c, comet_dtype dt, unsigned dca_ctas)
     o = round_up(o + sizeof(int64_t) * (L.E + 1), 256);
     L.cls = o;
     o = round_up(o + sizeof(int64_t) * (L.E + 1), 256);
-    L.map = o;
-    o = round_up(o + sizeof(int32_t) * L.dca_ctas, 256);
+    L.map = o;                               // DCA chunk prefix
+    o = round_up(o + sizeof(int64_t) * (L.E + 1), 256);
     L.host_bytes = o;                        // copied host -> device on every batch
-    L.counters = o;
-    o = round_up(o + sizeof(int32_t) * L.E, 256);
+    L.counters = o;                          // the DCA chunk counter
+    o = round_up(o + sizeof(unsigned long long), 256);
     L.scratch_per_event = round_up((size_t)L.nb_sel * (sizeof(int64_t) + (dt == COMET_F32 ? 4 : 8)), 256);
     L.scratch = o;
     o += L.scratch_per_event * L.E;
@@ -107,9 +105,6 @@ comet_status comet_scan_batch_update(comet_ctx *ctx, comet_dtype dtype, const co
     if (caps->dca_ctas_per_sm < 0) return fail(COMET_ERR_INVALID_ARG, "caps.dca_ctas_per_sm must be >= 0");
     if (caps->dca_ctas_per_sm > 0 && caps->dca_ctas_per_sm < per_sm) per_sm = caps->dca_ctas_per_sm;
     const unsigned dca_ctas = (unsigned)(per_sm * comet::device_sm_count());
-    if ((unsigned)caps->max_events > dca_ctas)
-        return fail(COMET_ERR_INVALID_ARG, "caps.max_events (%d) exceeds the resident DCA CTAs (%u)",
-                    caps->max_events, dca_ctas);
     const Layout L = make_layout(*caps, dtype, dca_ctas);
 
     // (re)allocate the staging buffers when the caps or the dtype change
@@ -144,13 +139,13 @@ comet_status comet_scan_batch_update(comet_ctx *ctx, comet_dtype dtype, const co
     BatchEvent *ev = (BatchEvent *)(H + L.ev);
     int64_t *lat = (int64_t *)(H + L.lat), *prop = (int64_t *)(H + L.prop);
     int64_t *sel = (int64_t *)(H + L.sel), *cls = (int64_t *)(H + L.cls);
-    int32_t *map = (int32_t *)(H + L.map);
+    int64_t *dstart = (int64_t *)(H + L.map);
     std::memset(H, 0, L.host_bytes);
 
     const size_t es = esize(dtype);
-    int64_t tot_seeds = 0, tot_wires = 0, tot_groups = 0;
+    int64_t tot_seeds = 0, tot_wires = 0;
     std::vector<int64_t> groups(L.E, 0);
-    lat[0] = prop[0] = sel[0] = cls[0] = 0;
+    lat[0] = prop[0] = sel[0] = cls[0] = dstart[0] = 0;
     for (int e = 0; e < L.E; ++e) {
         BatchEvent &be = ev[e];
         const comet_batch_event *x = e < B ? &events[e] : nullptr;
@@ -189,7 +184,7 @@ comet_status comet_scan_batch_update(comet_ctx *ctx, comet_dtype dtype, const co
         sel[e + 1] = sel[e] + (S + comet::select_chunk() - 1) / comet::select_chunk();
         cls[e + 1] = cls[e] + (W > 0 && S > 0 ? (W + 7) / 8 : 0);
         groups[e] = (S + 31) / 32;
-        tot_groups += groups[e];
+        dstart[e + 1] = dstart[e] + (groups[e] + comet::kDcaBatchChunk - 1) / comet::kDcaBatchChunk;
         if (!S) continue;
 
         comet_scan_params p = *params;
@@ -219,33 +214,14 @@ comet_status comet_scan_batch_update(comet_ctx *ctx, comet_dtype dtype, const co
     if (tot_seeds > caps->max_total_seeds) return fail(COMET_ERR_INVALID_ARG, "batch has %lld seeds > caps.max_total_seeds", (long long)tot_seeds);
     if (tot_wires > caps->max_total_wires) return fail(COMET_ERR_INVALID_ARG, "batch has %lld wires > caps.max_total_wires", (long long)tot_wires);
 
-    // persistent DCA CTAs: one per active event, the rest in proportion to the 32-seed groups
-    int n_active = 0;
-    for (int e = 0; e < L.E; ++e) n_active += groups[e] > 0;
-    std::vector<int64_t> cta(L.E, 0);
-    int64_t used = 0;
-    const int64_t spare = (int64_t)dca_ctas - n_active;
-    for (int e = 0; e < L.E; ++e) {
-        if (!groups[e]) continue;
-        int64_t want = 1 + (tot_groups ? spare * groups[e] / tot_groups : 0);
-        const int64_t useful = (groups[e] + comet::kDcaWarpsPerCta * kDcaGroupsPerWarp - 1) /
-                               (comet::kDcaWarpsPerCta * kDcaGroupsPerWarp);
-        cta[e] = std::max<int64_t>(1, std::min(want, useful));
-        used += cta[e];
-    }
-    int64_t c = 0;
-    for (int e = 0; e < L.E; ++e)
-        for (int64_t j = 0; j < cta[e]; ++j) map[c++] = e;
-    for (; c < (int64_t)dca_ctas; ++c) map[c] = -1;
-    (void)used;
     bs.B = L.E;
     bs.launch.ev = (const BatchEvent *)(D + L.ev);
     bs.launch.lat_start = (const int64_t *)(D + L.lat);
     bs.launch.prop_start = (const int64_t *)(D + L.prop);
     bs.launch.sel_start = (const int64_t *)(D + L.sel);
     bs.launch.cls_start = (const int64_t *)(D + L.cls);
-    bs.launch.dca_map = (const int32_t *)(D + L.map);
-    bs.launch.counters = (int32_t *)(D + L.counters);
+    bs.launch.dca_start = (const int64_t *)(D + L.map);
+    bs.launch.chunk_counter = (unsigned long long *)(D + L.counters);
     bs.launch.B = L.E;
     bs.launch.lat_blocks = L.lat_blocks;
     bs.launch.prop_blocks = L.prop_blocks;

@@ -136,6 +136,7 @@ struct JacArgs {
 cudaError_t launch_jacobian(const JacArgs &a, cudaStream_t st);
 
 constexpr int kDcaWarpsPerCta = 4;   // warps of a persistent DCA CTA (128 threads)
+constexpr int kDcaBatchChunk = 16;   // 32-seed groups per chunk of the batched DCA launch
 
 // ---- batches of events (one turn partition each) in single launches ---------------------------
 // Every batched launch has a fixed grid; block b finds its event e and its block index inside the
@@ -156,8 +157,8 @@ struct BatchLaunch {
     const int64_t *prop_start;       // device [B + 1] prefix of propagate blocks (128 seeds)
     const int64_t *sel_start;        // device [B + 1] prefix of select pass-1 blocks
     const int64_t *cls_start;        // device [B + 1] prefix of classify blocks (8 wires)
-    const int32_t *dca_map;          // device [dca_ctas]: event of each persistent DCA CTA (-1: none)
-    int32_t *counters;               // device [B]: 32-seed group counters of the DCA launch
+    const int64_t *dca_start;        // device [B + 1] prefix of DCA chunks (16 groups of 32 seeds)
+    unsigned long long *chunk_counter;  // device [1]: next DCA chunk
     int B;
     unsigned lat_blocks, prop_blocks, sel_blocks, cls_blocks, dca_ctas;
     int W_max;                       // largest W of the caps (shared-memory layout of the DCA CTAs)

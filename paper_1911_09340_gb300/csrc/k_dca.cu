@@ -459,18 +459,9 @@ __host__ __device__ inline PLayout p_layout(int W, int es)
 
 constexpr int kPersistMaxW = 1024;
 
-template <typename T, class F, bool BATCH>
-__global__ void __launch_bounds__(kThreads, COMET_DCA_MINB) dca_persistent_kernel(F f, DcaArgs a,
-                                                                                  BatchLaunch BL)
+template <typename T, class F>
+__global__ void __launch_bounds__(kThreads, COMET_DCA_MINB) dca_persistent_kernel(F f, DcaArgs a)
 {
-    if constexpr (BATCH) {
-        // a batch: this CTA serves one event (CTAs apportioned to the events by their size) and
-        // takes that event's 32-seed groups from the event's own counter
-        const int e = BL.dca_map[blockIdx.x];
-        if (e < 0) return;
-        a = BL.ev[e].dca;
-        a.counter = BL.counters + e;
-    }
     const PLayout L = p_layout(a.W, (int)sizeof(T));
     extern __shared__ __align__(128) unsigned char sm[];
     uint64_t *bar = (uint64_t *)sm;
@@ -707,11 +698,11 @@ static cudaError_t dca_launch(const F &fld, const DcaArgs &a, cudaStream_t st)
 {
     if (a.W <= kPersistMaxW && a.counter) {
         const PLayout L = p_layout(a.W, (int)sizeof(T));
-        cudaError_t e = cudaFuncSetAttribute(dca_persistent_kernel<T, F, false>,
+        cudaError_t e = cudaFuncSetAttribute(dca_persistent_kernel<T, F>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
         if (e != cudaSuccess) return e;
         int per_sm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dca_persistent_kernel<T, F, false>,
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dca_persistent_kernel<T, F>,
                                                           kThreads, L.total);
         if (e != cudaSuccess) return e;
         per_sm = per_sm < 1 ? 1 : per_sm;
@@ -721,7 +712,7 @@ static cudaError_t dca_launch(const F &fld, const DcaArgs &a, cudaStream_t st)
         nb = nb < cap ? nb : cap;
         e = cudaMemsetAsync(a.counter, 0, sizeof(int32_t), st);
         if (e != cudaSuccess) return e;
-        dca_persistent_kernel<T, F, false><<<(unsigned)nb, kThreads, L.total, st>>>(fld, a, BatchLaunch{});
+        dca_persistent_kernel<T, F><<<(unsigned)nb, kThreads, L.total, st>>>(fld, a);
         return cudaGetLastError();
     }
     using L = Smem<T>;
@@ -769,16 +760,172 @@ void dca_segments(int n_rec, int *G0, int *G1)
     *G1 = g1 > g0 ? g0 : g1;
 }
 
+// ------------------------------------------------------------------------------------------------
+// Batch of events: persistent CTAs take chunks of kBatchChunk 32-seed groups from ONE counter over
+// all events (chunks numbered event by event, BL.dca_start the prefix), so the load balances across
+// events as it does across groups in the single-event kernel.  A CTA restages wires and hits only
+// when its next chunk belongs to another event (a few KB by bulk copy).  Shared memory is laid out
+// for the batch's largest W.
+// ------------------------------------------------------------------------------------------------
+constexpr int kBatchChunk = kDcaBatchChunk;
+
+#ifndef COMET_DCA_BATCH_MINB
+#define COMET_DCA_BATCH_MINB 6   // the event's arguments come from a table, not the parameter bank
+#endif
+
+template <typename T, class F>
+__global__ void __launch_bounds__(kThreads, COMET_DCA_BATCH_MINB) dca_batch_kernel(F f, BatchLaunch BL)
+{
+    const PLayout L = p_layout(BL.W_max, (int)sizeof(T));
+    extern __shared__ __align__(128) unsigned char sm[];
+    uint64_t *bar = (uint64_t *)sm;
+    __shared__ int64_t s_chunk;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    float4 *sph0 = (float4 *)(sm + L.sph0) + warp * kN0Max;
+    float4 *sph1 = (float4 *)(sm + L.sph1) + warp * kN0Max * kN1Max;
+    T *wrow = (T *)(sm + L.wrow);
+    int32_t *orow = (int32_t *)(sm + L.orow);
+    T *capv = (T *)(sm + L.cap);
+    T *frm = (T *)(sm + L.frame);
+    T *dsm = (T *)(sm + L.drift);
+    uint8_t *msm = (uint8_t *)(sm + L.mask);
+    const int rcap = L.wcap + 32;
+    if (tid == 0) mbar_init(bar, 1);
+    __syncthreads();
+
+    const int64_t n_chunks = BL.dca_start[BL.B];
+    uint32_t parity = 0;
+    bool timed_out = false;
+    int cur = -1;
+    // the current event's arguments and staged tile live in shared memory (they change only on a
+    // restage): registers stay free for the group loop
+    __shared__ DcaArgs s_a;
+    __shared__ Tile<T> s_tl;
+    const DcaArgs &a = s_a;
+    const Tile<T> &tl = s_tl;
+    int nunc = 0;
+    for (;;) {
+        if (tid == 0) s_chunk = (int64_t)atomicAdd((unsigned long long *)BL.chunk_counter, 1ull);
+        __syncthreads();
+        const int64_t chunk = s_chunk;
+        if (chunk >= n_chunks) break;
+        int e;
+        int64_t lc;
+        batch_find(BL.dca_start, BL.B, chunk, e, lc);
+        if (e != cur) {
+            // flush this CTA's unconverged count to the event it leaves
+            if (cur >= 0 && a.n_unconv) {
+                int t = nunc;
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+                if (lane == 0 && t) atomicAdd(a.n_unconv, t);
+            }
+            nunc = 0;
+            // every thread is past its last use of s_a / s_tl (the barrier closing the chunk)
+            if (tid == 0) s_a = BL.ev[e].dca;
+            __syncthreads();
+            cur = e;
+            const T *__restrict__ Wg = (const T *)a.wires;
+            const T *__restrict__ Dg = (const T *)a.drift;
+            const int W = a.W;
+            const int H = W > 0 ? a.offs[W] : 0;
+            const bool hits_sm = H <= kHitMax;
+            // every thread's earlier shared-memory accesses before the bulk copies overwrite them
+            fence_proxy_async_smem();
+            __syncthreads();
+            uint32_t bytes = 0;
+            int woff[6] = {0, 0, 0, 0, 0, 0};
+            int ooff = 0, doff = 0, moff = 0;
+            if (W > 0) {
+                bytes = stage_bytes<int32_t>(a.offs, W + 1);
+#pragma unroll
+                for (int r = 0; r < 6; ++r) bytes += stage_bytes<T>(Wg + (size_t)r * a.ldw, W);
+                if (hits_sm && H > 0) bytes += stage_bytes<T>(Dg, H) + stage_bytes<uint8_t>(a.mask, H);
+                if (tid == 0 && bytes > 0) mbar_arrive_expect_tx(bar, bytes);
+#pragma unroll
+                for (int r = 0; r < 6; ++r)
+                    woff[r] = stage_issue<T>(wrow + r * rcap, Wg + (size_t)r * a.ldw, W, bar, tid == 0);
+                ooff = stage_issue<int32_t>(orow, a.offs, W + 1, bar, tid == 0);
+                if (hits_sm && H > 0) {
+                    doff = stage_issue<T>(dsm, Dg, H, bar, tid == 0);
+                    moff = stage_issue<uint8_t>(msm, a.mask, H, bar, tid == 0);
+                }
+            }
+            const bool to = finish_stage(bar, parity, bytes);
+            if (to && W > 0) {
+#pragma unroll
+                for (int r = 0; r < 6; ++r) stage_fallback<T>(wrow + r * rcap, Wg + (size_t)r * a.ldw, W);
+                stage_fallback<int32_t>(orow, a.offs, W + 1);
+                if (hits_sm && H > 0) {
+                    stage_fallback<T>(dsm, Dg, H);
+                    stage_fallback<uint8_t>(msm, a.mask, H);
+                }
+            }
+            if (to) {
+                // a timed-out copy may still land: wait for it (bounded) before anything reuses
+                // the buffers, and report it
+                timed_out = true;
+                if (tid == 0 && a.status) atomicOr(a.status, 1);
+                mbar_wait(bar, parity ^ 1u, kWaitNs);
+            }
+            if (tid == 0) {
+                s_tl.ax = wrow + 0 * rcap + woff[0];
+                s_tl.ay = wrow + 1 * rcap + woff[1];
+                s_tl.az = wrow + 2 * rcap + woff[2];
+                s_tl.ux = wrow + 3 * rcap + woff[3];
+                s_tl.uy = wrow + 4 * rcap + woff[4];
+                s_tl.uz = wrow + 5 * rcap + woff[5];
+                s_tl.frm = frm;
+                s_tl.fs = L.wcap;
+                s_tl.cap = capv;
+                s_tl.offs = orow + ooff;
+                s_tl.dsm = hits_sm ? dsm + doff : Dg;
+                s_tl.msm = hits_sm ? msm + moff : a.mask;
+                s_tl.w0 = 0;
+                s_tl.wn = W;
+            }
+            __syncthreads();
+            for (int i = tid; i < W; i += kThreads) tile_wire_setup<T>(tl, i, in_prec<T>(a.lambda, a.lambda_f), capv, frm);
+            __syncthreads();
+        }
+        // the chunk's groups, one warp at a time
+        const int64_t n_groups = (a.S + 31) / 32;
+        const int64_t g0 = lc * kBatchChunk;
+        const int64_t g1 = min(g0 + kBatchChunk, n_groups);
+        for (int64_t g = g0 + warp; g < g1; g += kWarps) {
+            const Group<T> gr = load_group<T>(a, g, lane);
+            build_spheres<T>(a, gr, lane, sph0, sph1, g);
+            Acc<T> acc;
+            int nin = 0;
+            group_wires<T, F>(f, a, gr, tl, sph0, sph1, lane, acc, nin, nunc);
+            if (gr.valid) {
+                ((T *)a.rss)[gr.s] = acc.value();
+                a.n_in[gr.s] = nin;
+            }
+            __syncwarp();
+        }
+        __syncthreads();   // every warp done with this chunk before a restage or the next s_chunk
+    }
+    if (cur >= 0 && a.n_unconv) {
+        int t = nunc;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+        if (lane == 0 && t) atomicAdd(a.n_unconv, t);
+    }
+    (void)timed_out;
+}
+
 template <typename T, class F>
 static cudaError_t dca_batch_launch(const F &fld, const BatchLaunch &BL, cudaStream_t st)
 {
     // (the shared-memory attribute for W_max was set when the batch was prepared: nothing here but
     // stream work, so that the launch can be captured)
     const PLayout L = p_layout(BL.W_max, (int)sizeof(T));
-    cudaError_t e = cudaMemsetAsync(BL.counters, 0, sizeof(int32_t) * (size_t)BL.B, st);
+    cudaError_t e = cudaMemsetAsync(BL.chunk_counter, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
     if (BL.dca_ctas == 0) return cudaSuccess;
-    dca_persistent_kernel<T, F, true><<<BL.dca_ctas, kThreads, L.total, st>>>(fld, DcaArgs{}, BL);
+    dca_batch_kernel<T, F><<<BL.dca_ctas, kThreads, L.total, st>>>(fld, BL);
     return cudaGetLastError();
 }
 
@@ -786,11 +933,11 @@ template <typename T, class F>
 static int dca_ctas_per_sm_t(int W)
 {
     const PLayout L = p_layout(W, (int)sizeof(T));
-    if (cudaFuncSetAttribute(dca_persistent_kernel<T, F, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(dca_batch_kernel<T, F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)L.total) != cudaSuccess)
         return 0;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dca_persistent_kernel<T, F, true>, kThreads,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dca_batch_kernel<T, F>, kThreads,
                                                       L.total) != cudaSuccess)
         return 0;
     return per_sm;

@@ -311,7 +311,7 @@ def generate_batch_events(n: int, workers: int = 0):
 
 
 def batch_study(n_events: int = 512, stride: int = 16, lam: float = 1e-2, tune_events: int = 128,
-                dtype=torch.float32, max_total_seeds: int = 1 << 24):
+                dtype=torch.float32, max_total_seeds: int = 1 << 25):
     """Events/s and per-event latency of the batching workload (1-6 turns, 2^12-2^18 seeds per
     partition by turn count, uneven hit counts): the per-event path (one partition at a time, six
     launches each) against continuous batching (comet_scan_batch rounds replayed from a CUDA graph,
@@ -350,8 +350,9 @@ def batch_study(n_events: int = 512, stride: int = 16, lam: float = 1e-2, tune_e
                          max_wires=max(512, max(ev.n_wires for ev in events)),
                          max_hits=max(2048, max(ev.n_hits for ev in events)))
     best, table = BT.autotune(sc, events[:tune_events])
-    sc.run(events[:tune_events])
-    r = sc.run(events)
+    pinned = sc.pin(events)
+    sc.run(events[:tune_events], pinned=pinned[:tune_events])
+    r = sc.run(events, pinned=pinned)
     wires = np.array([ev.n_wires for ev in events])
     turns = np.bincount([len(ev.partitions) for ev in events], minlength=7)[1:]
     ctx.close()
@@ -361,7 +362,8 @@ def batch_study(n_events: int = 512, stride: int = 16, lam: float = 1e-2, tune_e
                                                                       int(wires.max())],
              "per_event_path": {"events_per_s": n_events / (seq_ms * 1e-3), "latency_ms": pct(seq_lat)},
              "batched": {"events_per_s": n_events / (r["gpu_ms"] * 1e-3), "latency_ms": pct(r["latency_ms"]),
-                         "rounds": r["rounds"], "config": best},
+                         "rounds": r["rounds"], "host_wall_ms": r["wall_ms"], "gpu_ms": r["gpu_ms"],
+                         "config": best},
              "autotune": table}]
 
 
