@@ -253,13 +253,15 @@ comet_status comet_scan_lattice_refined(comet_ctx *ctx, comet_dtype dtype, const
  *   at fixed lengths (at the point of closest approach the distance is stationary along the track).
  *   For each wire with an unmasked hit: e = min_j |D - r_j|, w = 1 / (1 + exp(-(lambda - e)/tau)),
  *   term = w e^2 + (1 - w) lambda^2 (Eq. 1 with a smooth cap; tau > 0, in metres).
- *   work       [S][W][9] double device scratch.
+ *   work       [S][W][11] double device scratch.
  *   srss_out   out, [S] double: sum of the terms in ascending wire order (the smoothed RSS).
  *   grad_out   out, [S][4] double: its gradient in theta.
  *   jtj_out    out, [S][4][4] double: sum over wires of w J J^T (J = dD/dtheta);
  *   jtr_out    out, [S][4] double: sum of w J (D - r_j*), the Gauss-Newton normal equations with
  *              the weights held fixed.
  *   dca_out    optional out, [S][W] double: D.   jac_out optional out, [S][W][4] double: dD/dtheta.
+ *   grad6_out  optional out, [S][6] double: the gradient of the smoothed RSS in the Cartesian seed
+ *              (x, y, z, px, py, pz) -- the vertex (x, y) enters the recorded positions additively.
  *   n_unconverged optional [1] int32 device, incremented for refinements that did not converge. */
 comet_status comet_scan_jacobian(comet_ctx *ctx, comet_dtype dtype, const comet_field *field,
                                  const comet_scan_params *params, const double *theta, int64_t S,
@@ -268,7 +270,7 @@ comet_status comet_scan_jacobian(comet_ctx *ctx, comet_dtype dtype, const comet_
                                  const uint8_t *hit_mask, double tau, double *work,
                                  double *srss_out, double *grad_out, double *jtj_out,
                                  double *jtr_out, double *dca_out, double *jac_out,
-                                 int32_t *n_unconverged, comet_stream stream);
+                                 double *grad6_out, int32_t *n_unconverged, comet_stream stream);
 
 /* theta[s] += delta with (JTJ + mu diag(JTJ)) delta = -JTR (Cholesky; a seed whose matrix is not
  * positive definite keeps its theta).  theta [S][4], jtj [S][4][4], jtr [S][4]: double device, as

@@ -286,7 +286,13 @@ def smoothed_rss(field, params: Params, theta, vx, vy, q, wires, hit_offsets, dr
     """Eq. 1 with a smooth cap, for Gauss-Newton refinement of the best seeds: for every wire with an
     unmasked hit, e = min_j |D - r_j| (D from this oracle's scan), w = 1 / (1 + exp(-(lam - e)/tau)),
     term = w e^2 + (1 - w) lam^2; summed in ascending wire order.  Returns (srss [S], dca [S][W])."""
-    seeds = seeds_from_theta(theta, vx, vy)
+    return smoothed_rss_seeds(field, params, seeds_from_theta(theta, vx, vy), q, wires, hit_offsets,
+                              drift, mask, tau)
+
+
+def smoothed_rss_seeds(field, params: Params, seeds, q, wires, hit_offsets, drift, mask, tau):
+    """smoothed_rss of Cartesian seeds (AoS [S][6])."""
+    seeds = np.asarray(seeds, dtype=np.float64).reshape(-1, 6)
     r = scan(field, params, seeds, q, wires, hit_offsets, drift, mask, want_dca=True)
     D = r["dca"]
     offs = np.asarray(hit_offsets)

@@ -86,7 +86,7 @@ SIGNATURES = {
                                    _vp],
     "comet_scan_jacobian": [_vp, C.c_int, C.POINTER(_Field), C.POINTER(_Params), _vp, _i64, C.c_double,
                             C.c_double, _i32, _vp, _i32, _i32, _vp, _vp, _vp, C.c_double, _vp, _vp,
-                            _vp, _vp, _vp, _vp, _vp, _vp, _vp],
+                            _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "comet_scan_gn_step": [_vp, _vp, _i64, _vp, _vp, C.c_double, _vp],
     "comet_scan_batch_update": [_vp, C.c_int, C.POINTER(_Field), C.POINTER(_Params),
                                 C.POINTER(BatchCaps), C.POINTER(BatchEvent), _i32],
@@ -308,13 +308,13 @@ def comet_scan_lattice_refined(ctx: Context, shape_spec, refs, n_refs, K: int, s
                                             seeds.shape[-1], _stream(stream)))
 
 
-JAC_WORK_PER_PAIR = 9    # doubles of comet_scan_jacobian scratch per (seed, wire)
+JAC_WORK_PER_PAIR = 11   # doubles of comet_scan_jacobian scratch per (seed, wire)
 
 
 def comet_scan_jacobian(ctx: Context, field: DeviceField, params: ScanParams, theta, vx: float,
                         vy: float, charge: int, wires, hit_offsets, drift, hit_mask, tau: float, work,
                         srss, grad, jtj, jtr, dca_out=None, jac_out=None, n_unconverged=None,
-                        n_wires: Optional[int] = None, stream=None):
+                        n_wires: Optional[int] = None, stream=None, grad6=None):
     """Smoothed RSS, its gradient and the Gauss-Newton normal equations of seeds theta [S, 4]
     (float64 device; z0, phi, pz, pT); see include/comet_scan.h."""
     f64 = torch.float64
@@ -327,7 +327,8 @@ def comet_scan_jacobian(ctx: Context, field: DeviceField, params: ScanParams, th
                                      _ptr(drift, f64), _ptr(hit_mask, torch.uint8), float(tau),
                                      _ptr(work, f64), _ptr(srss, f64), _ptr(grad, f64), _ptr(jtj, f64),
                                      _ptr(jtr, f64), _ptr(dca_out, f64), _ptr(jac_out, f64),
-                                     _ptr(n_unconverged, torch.int32), _stream(stream)))
+                                     _ptr(grad6, f64), _ptr(n_unconverged, torch.int32),
+                                     _stream(stream)))
 
 
 def comet_scan_gn_step(ctx: Context, theta, jtj, jtr, mu: float = 0.0, stream=None):

@@ -405,7 +405,7 @@ comet_status comet_scan_jacobian(comet_ctx *ctx, comet_dtype dtype, const comet_
                                  const uint8_t *hit_mask, double tau, double *work,
                                  double *srss_out, double *grad_out, double *jtj_out,
                                  double *jtr_out, double *dca_out, double *jac_out,
-                                 int32_t *n_unconverged, comet_stream stream)
+                                 double *grad6_out, int32_t *n_unconverged, comet_stream stream)
 {
     if (!ctx) return fail(COMET_ERR_INVALID_ARG, "ctx is NULL");
     CHECK(check_dtype(dtype));
@@ -424,8 +424,9 @@ comet_status comet_scan_jacobian(comet_ctx *ctx, comet_dtype dtype, const comet_
     if (W > 0 && (!wires || !hit_offsets || !drift || !hit_mask || !aligned(wires, 8) || !aligned(drift, 8) ||
                   !aligned(hit_offsets, 4)))
         return fail(COMET_ERR_INVALID_ARG, "wires / hits NULL or misaligned");
-    if ((dca_out && !aligned(dca_out, 8)) || (jac_out && !aligned(jac_out, 8)))
-        return fail(COMET_ERR_INVALID_ARG, "dca_out / jac_out misaligned");
+    if ((dca_out && !aligned(dca_out, 8)) || (jac_out && !aligned(jac_out, 8)) ||
+        (grad6_out && !aligned(grad6_out, 8)))
+        return fail(COMET_ERR_INVALID_ARG, "dca_out / jac_out / grad6_out misaligned");
     if (charge < -128 || charge > 127) return fail(COMET_ERR_INVALID_ARG, "charge must fit int8");
     DeviceGuard g(ctx->device);
     if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
@@ -460,6 +461,7 @@ comet_status comet_scan_jacobian(comet_ctx *ctx, comet_dtype dtype, const comet_
     a.jtr_out = jtr_out;
     a.dca_out = dca_out;
     a.jac_out = jac_out;
+    a.grad6_out = grad6_out;
     a.n_unconv = n_unconverged;
     cudaError_t e = comet::launch_jacobian(a, (cudaStream_t)stream);
     return e == cudaSuccess ? COMET_OK : cuda_fail(e, "jacobian launch");

@@ -128,8 +128,9 @@ struct JacArgs {
     const int32_t *offs;
     const double *drift;
     const uint8_t *mask;
-    double *work;          // [S][W][9]
+    double *work;          // [S][W][11]
     double *srss_out, *grad_out, *jtj_out, *jtr_out;
+    double *grad6_out;     // optional [S][6]: gradient in the Cartesian seed (x, y, z, px, py, pz)
     double *dca_out, *jac_out;
     int32_t *n_unconv;
 };

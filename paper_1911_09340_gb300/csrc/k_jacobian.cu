@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(32) jacobian_kernel(JacArgs a)
     if (tid >= a.S * a.W) return;
     const int64_t s = tid / a.W;
     const int i = (int)(tid % a.W);
-    double *out = a.work + tid * 9;   // flag, term, dterm, w, rho, J[0..3]
+    double *out = a.work + tid * 11;   // flag, term, dterm, w, rho, J[0..3], nhat_x, nhat_y
     const int hb = a.offs[i], he = a.offs[i + 1];
     bool any = false;
     for (int j = hb; j < he; ++j) any = any || !a.mask[j];
@@ -338,6 +338,8 @@ __global__ void __launch_bounds__(32) jacobian_kernel(JacArgs a)
     }
 #pragma unroll
     for (int j = 0; j < 4; ++j) out[5 + j] = J[j];
+    out[9] = ex * inv;    // dD/dx0 and dD/dy0: the recorded X_k depend on (x0, y0) additively
+    out[10] = ey * inv;
     if (!conv && any && a.n_unconv) atomicAdd(a.n_unconv, 1);
 }
 
@@ -346,14 +348,16 @@ __global__ void jacobian_reduce_kernel(JacArgs a)
 {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= a.S) return;
-    double srss = 0.0, g[4] = {0, 0, 0, 0}, jtj[16], jtr[4] = {0, 0, 0, 0};
+    double srss = 0.0, g[4] = {0, 0, 0, 0}, jtj[16], jtr[4] = {0, 0, 0, 0}, gxy[2] = {0, 0};
     for (int q = 0; q < 16; ++q) jtj[q] = 0.0;
     for (int i = 0; i < a.W; ++i) {
         const int64_t t = s * a.W + i;
-        const double *o = a.work + t * 9;
+        const double *o = a.work + t * 11;
         if (o[0] == 0.0) continue;
         const double *J = o + 5;
         srss += o[1];
+        gxy[0] += o[2] * o[9];
+        gxy[1] += o[2] * o[10];
         for (int j = 0; j < 4; ++j) {
             g[j] += o[2] * J[j];
             jtr[j] += o[3] * o[4] * J[j];
@@ -366,6 +370,18 @@ __global__ void jacobian_reduce_kernel(JacArgs a)
         a.jtr_out[s * 4 + j] = jtr[j];
     }
     for (int q = 0; q < 16; ++q) a.jtj_out[s * 16 + q] = jtj[q];
+    if (a.grad6_out) {
+        // (x0, y0, z0, px, py, pz): phi = atan2(py, px) and pT = hypot(px, py), by the chain rule
+        const double phi = a.theta[s * 4 + 1], pt = a.theta[s * 4 + 3];
+        const double cp = cos(phi), sp = sin(phi);
+        double *o = a.grad6_out + s * 6;
+        o[0] = gxy[0];
+        o[1] = gxy[1];
+        o[2] = g[0];
+        o[3] = -g[1] * sp / pt + g[3] * cp;
+        o[4] = g[1] * cp / pt + g[3] * sp;
+        o[5] = g[2];
+    }
 }
 
 // theta += delta, (J^T W J + mu diag(J^T W J)) delta = -J^T W rho, by Cholesky; a seed whose

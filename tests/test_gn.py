@@ -116,3 +116,37 @@ def test_gauss_newton_improves_a_seed_half_a_step_off(ctx):
     dp_start = np.abs(np.hypot(start[:, 2], start[:, 3]) - p_true)
     dp_end = np.abs(np.hypot(th[:, 2], th[:, 3]) - p_true)
     assert np.all(dp_end < dp_start)
+
+
+@pytest.mark.gpu
+def test_gradient_in_the_six_cartesian_seed_components(ctx):
+    """d(smoothed RSS)/d(x, y, z, px, py, pz) of the seed against central finite differences of the
+    oracle's smoothed RSS of Cartesian seeds (rel 1e-4)."""
+    import torch
+    from paper_1911_09340_gb300 import binding as B
+    from paper_1911_09340_gb300 import scan
+    ev = synth.single_event_fp64()
+    t0 = _truth_theta(ev)
+    theta = np.stack([t0, t0 + [0.002, -0.002, 0.3, -0.4]])
+    lam, tau, stride = 8e-4, 1e-3, 16
+    f64 = dict(dtype=torch.float64, device="cuda")
+    dev = scan.DeviceEvent.from_event(ev, torch.float64)
+    p = B.ScanParams(n_steps=ev.n_steps[0], stride=stride, lam=lam, tol=1e-12)
+    S, W = theta.shape[0], dev.W
+    th = torch.as_tensor(theta, **f64).contiguous()
+    outs = [torch.empty(S * W * B.JAC_WORK_PER_PAIR, **f64), torch.empty(S, **f64), torch.empty((S, 4), **f64),
+            torch.empty((S, 16), **f64), torch.empty((S, 4), **f64)]
+    g6 = torch.empty((S, 6), **f64)
+    B.comet_scan_jacobian(ctx, B.DeviceField.from_synth(UNIFORM), p, th, ev.vertex[0], ev.vertex[1], -1,
+                          dev.wires, dev.hit_offsets, dev.drift, dev.mask, tau, *outs, n_wires=W, grad6=g6)
+    g6 = g6.cpu().numpy()
+    P = O.Params(n_steps=ev.n_steps[0], stride=stride, lam=lam, tol=1e-12)
+    args = (-1, O.wires_aos(ev.wires), ev.hit_offsets, ev.drift, np.zeros(ev.n_hits, np.uint8), tau)
+    seeds = O.seeds_from_theta(theta, ev.vertex[0], ev.vertex[1])
+    eps = [1e-6, 1e-6, 1e-6, 1e-4, 1e-4, 1e-4]
+    for k in range(6):
+        sp, sm = seeds.copy(), seeds.copy()
+        sp[:, k] += eps[k]
+        sm[:, k] -= eps[k]
+        fd = (O.smoothed_rss_seeds(UNIFORM, P, sp, *args)[0] - O.smoothed_rss_seeds(UNIFORM, P, sm, *args)[0]) / (2 * eps[k])
+        assert np.allclose(g6[:, k], fd, rtol=1e-4, atol=1e-4 * np.abs(fd).max() + 1e-15), (k, g6[:, k], fd)
