@@ -383,8 +383,9 @@ __device__ __forceinline__ int refine_dca(const F &f, T c, T ip, T y[6], T ax, T
     int conv = 0;
     T sigma = T(0);
     for (int it = 0;; ++it) {
-        const T rp = rsqrt_t<T>(y[3] * y[3] + y[4] * y[4] + y[5] * y[5]);
-        const T tx = y[3] * rp, ty = y[4] * rp, tz = y[5] * rp;
+        // t = p / P0: |p| stays P0 in a magnetic field, and the plane and its zero do not depend on
+        // the norm of t (n is normalised below), only the Newton step length, by rounding
+        const T tx = y[3] * ip, ty = y[4] * ip, tz = y[5] * ip;
         const T tu = tx * ux + ty * uy + tz * uz;
         const T nx = tx - tu * ux, ny = ty - tu * uy, nz = tz - tu * uz;
         const T nn2 = nx * nx + ny * ny + nz * nz;

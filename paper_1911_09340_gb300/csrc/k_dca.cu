@@ -62,7 +62,7 @@ struct Smem {
     static constexpr size_t orow = align16(wrow + sizeof(T) * 6 * kWireCap);
     static constexpr size_t cap = align16(orow + sizeof(int32_t) * (kWireCap + 8));
     static constexpr size_t frame = align16(cap + sizeof(T) * kWireTile);
-    static constexpr size_t drift = align16(frame + sizeof(T) * 8 * kWireTile);
+    static constexpr size_t drift = align16(frame + sizeof(T) * 16 * kWireTile);
     static constexpr size_t mask = align16(drift + sizeof(T) * kHitCap);
     static constexpr size_t total = align16(mask + kHitCap);
 };
@@ -235,12 +235,18 @@ __device__ __forceinline__ void build_spheres(const DcaArgs &a, const Group<T> &
     __syncwarp();
 }
 
+// Per-wire record of a staged tile, four of them per wire: (v, a.v), (w, a.w), (a, capture radius),
+// (u, 0) -- one 16-byte-aligned load each (two for double).
+template <typename T>
+struct alignas(16) Q4 {
+    T x, y, z, w;
+};
+
 // A staged range of wires [w0, w0 + wn) in shared memory.
 template <typename T>
 struct Tile {
     const T *ax, *ay, *az, *ux, *uy, *uz;   // wire point and direction, element i = wire w0 + i
-    const T *frm;                            // frames [8][fs]: v, w, a.v, a.w
-    int fs;
+    const Q4<T> *rec;                        // [wire][4]: (v, a.v), (w, a.w), (a, cap), (u, 0)
     const T *cap;                            // capture radius (< 0: no unmasked hit)
     const int32_t *offs;                     // CSR offsets, element i = wire w0 + i
     const T *dsm;                            // drifts / masks: staged (global hit index) or global
@@ -248,24 +254,23 @@ struct Tile {
     int w0, wn;
 };
 
-// Capture radius and frame of wire i of a staged tile (one thread per wire).
+// Capture radius and frame of wire i of a staged tile (one thread per wire), packed with its
+// point and direction into the wire's four records.
 template <typename T>
-__device__ __forceinline__ void tile_wire_setup(const Tile<T> &tl, int i, T lam, T *capv, T *frm)
+__device__ __forceinline__ void tile_wire_setup(const Tile<T> &tl, int i, T lam, T *capv, Q4<T> *rec)
 {
     const int hb = tl.offs[i], he = tl.offs[i + 1];
     T mr = T(-1);
     for (int j = hb; j < he; ++j)
         if (!tl.msm[j] && tl.dsm[j] > mr) mr = tl.dsm[j];
-    capv[i] = mr >= T(0) ? mr + lam : T(-1);
-    const WireFrame<T> fr = wire_frame<T>(tl.ax[i], tl.ay[i], tl.az[i], tl.ux[i], tl.uy[i], tl.uz[i]);
-    frm[0 * tl.fs + i] = fr.vx;
-    frm[1 * tl.fs + i] = fr.vy;
-    frm[2 * tl.fs + i] = fr.vz;
-    frm[3 * tl.fs + i] = fr.wx;
-    frm[4 * tl.fs + i] = fr.wy;
-    frm[5 * tl.fs + i] = fr.wz;
-    frm[6 * tl.fs + i] = fr.av;
-    frm[7 * tl.fs + i] = fr.aw;
+    const T cap = mr >= T(0) ? mr + lam : T(-1);
+    capv[i] = cap;
+    const T ax = tl.ax[i], ay = tl.ay[i], az = tl.az[i], ux = tl.ux[i], uy = tl.uy[i], uz = tl.uz[i];
+    const WireFrame<T> fr = wire_frame<T>(ax, ay, az, ux, uy, uz);
+    rec[4 * i + 0] = Q4<T>{fr.vx, fr.vy, fr.vz, fr.av};
+    rec[4 * i + 1] = Q4<T>{fr.wx, fr.wy, fr.wz, fr.aw};
+    rec[4 * i + 2] = Q4<T>{ax, ay, az, cap};
+    rec[4 * i + 3] = Q4<T>{ux, uy, uz, T(0)};
 }
 
 // The wires of one tile for one 32-seed group: accumulates d_i^2, n_in and unconverged counts.
@@ -285,8 +290,7 @@ __device__ __forceinline__ void group_wires(const F &f, const DcaArgs &a, const 
             half_rec = in_prec<T>(a.half_rec, a.half_rec_f), h_rec = in_prec<T>(a.h_rec, a.h_rec_f);
     const int G0 = a.G0, G1 = a.G1;
     const int N1 = (G0 + G1 - 1) / G1;
-    const int fs = tl.fs;
-    const T *frm = tl.frm;
+    const Q4<T> *rec = tl.rec;
     constexpr int kU = COMET_DCA_U2;
 
     for (int base = 0; base < tl.wn; base += 32) {
@@ -300,28 +304,29 @@ __device__ __forceinline__ void group_wires(const F &f, const DcaArgs &a, const 
                 mask0 = 1u;
             } else if (capw >= T(0)) {
                 const T lim = capw + half_rec;
+                const Q4<T> r0 = rec[4 * iw + 0], r1 = rec[4 * iw + 1], r2 = rec[4 * iw + 2],
+                            r3 = rec[4 * iw + 3];
                 for (int j = 0; j < gr.n0w; ++j)
-                    if (sphere_within<T>(sph0[j], frm[0 * fs + iw], frm[1 * fs + iw], frm[2 * fs + iw],
-                                         frm[6 * fs + iw], frm[3 * fs + iw], frm[4 * fs + iw],
-                                         frm[5 * fs + iw], frm[7 * fs + iw], tl.ax[iw], tl.ay[iw],
-                                         tl.az[iw], tl.ux[iw], tl.uy[iw], tl.uz[iw], lim))
+                    if (sphere_within<T>(sph0[j], r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w, r2.x,
+                                         r2.y, r2.z, r3.x, r3.y, r3.z, lim))
                         mask0 |= 1u << j;
             }
         }
         for (int t = 0; t < clen; ++t) {
             const int ii = base + t;
             const uint32_t m0 = __shfl_sync(0xffffffffu, mask0, t);
-            const T cap = tl.cap[ii];
+            const Q4<T> r2 = rec[4 * ii + 2];
+            const T cap = r2.w;
             if (m0 == 0u) {
                 // beyond every seed's capture radius (or no unmasked hit): lambda^2 if in the sum
                 if (valid && cap >= T(0)) acc.add(lam * lam);
                 continue;
             }
-            const T ax = tl.ax[ii], ay = tl.ay[ii], az = tl.az[ii];
-            const T ux = tl.ux[ii], uy = tl.uy[ii], uz = tl.uz[ii];
-            const T fvx = frm[0 * fs + ii], fvy = frm[1 * fs + ii], fvz = frm[2 * fs + ii],
-                    fwx = frm[3 * fs + ii], fwy = frm[4 * fs + ii], fwz = frm[5 * fs + ii],
-                    fav = frm[6 * fs + ii], faw = frm[7 * fs + ii];
+            const Q4<T> r0 = rec[4 * ii + 0], r1 = rec[4 * ii + 1], r3 = rec[4 * ii + 3];
+            const T ax = r2.x, ay = r2.y, az = r2.z;
+            const T ux = r3.x, uy = r3.y, uz = r3.z;
+            const T fvx = r0.x, fvy = r0.y, fvz = r0.z, fav = r0.w;
+            const T fwx = r1.x, fwy = r1.y, fwz = r1.z, faw = r1.w;
 #if COMET_SEARCH_FRAME
             auto sd2 = [&](T x, T y, T z) {
                 return frame_dist2<T>(x, y, z, fvx, fvy, fvz, fav, fwx, fwy, fwz, faw);
@@ -451,7 +456,7 @@ __host__ __device__ inline PLayout p_layout(int W, int es)
     L.orow = align16(L.wrow + (size_t)es * 6 * (wc + 32));
     L.cap = align16(L.orow + (size_t)4 * (wc + 40));
     L.frame = align16(L.cap + (size_t)es * wc);
-    L.drift = align16(L.frame + (size_t)es * 8 * wc);
+    L.drift = align16(L.frame + (size_t)es * 16 * wc);
     L.mask = align16(L.drift + (size_t)es * kHitCap);
     L.total = align16(L.mask + kHitCap);
     return L;
@@ -472,7 +477,7 @@ __global__ void __launch_bounds__(kThreads, COMET_DCA_MINB) dca_persistent_kerne
     T *wrow = (T *)(sm + L.wrow);
     int32_t *orow = (int32_t *)(sm + L.orow);
     T *capv = (T *)(sm + L.cap);
-    T *frm = (T *)(sm + L.frame);
+    Q4<T> *frm = (Q4<T> *)(sm + L.frame);
     T *dsm = (T *)(sm + L.drift);
     uint8_t *msm = (uint8_t *)(sm + L.mask);
     const int rcap = L.wcap + 32;
@@ -527,8 +532,7 @@ __global__ void __launch_bounds__(kThreads, COMET_DCA_MINB) dca_persistent_kerne
     tl.ux = wrow + 3 * rcap + woff[3];
     tl.uy = wrow + 4 * rcap + woff[4];
     tl.uz = wrow + 5 * rcap + woff[5];
-    tl.frm = frm;
-    tl.fs = L.wcap;
+    tl.rec = frm;
     tl.cap = capv;
     tl.offs = orow + ooff;
     tl.dsm = hits_sm ? dsm + doff : Dg;
@@ -586,7 +590,7 @@ __global__ void __launch_bounds__(kThreads, COMET_DCA_MINB) dca_tiled_kernel(F f
     T *wrow = (T *)(sm + L::wrow);
     int32_t *orow = (int32_t *)(sm + L::orow);
     T *capv = (T *)(sm + L::cap);
-    T *frm = (T *)(sm + L::frame);
+    Q4<T> *frm = (Q4<T> *)(sm + L::frame);
     T *dsm = (T *)(sm + L::drift);
     uint8_t *msm = (uint8_t *)(sm + L::mask);
     const T *__restrict__ Wg = (const T *)a.wires;
@@ -652,8 +656,7 @@ __global__ void __launch_bounds__(kThreads, COMET_DCA_MINB) dca_tiled_kernel(F f
         tl.ux = wrow + 3 * kWireCap + woff[3];
         tl.uy = wrow + 4 * kWireCap + woff[4];
         tl.uz = wrow + 5 * kWireCap + woff[5];
-        tl.frm = frm;
-        tl.fs = kWireTile;
+        tl.rec = frm;
         tl.cap = capv;
         tl.offs = orow + ooff;
         tl.dsm = hits_sm ? dsm + doff : Dg;
@@ -787,7 +790,7 @@ __global__ void __launch_bounds__(kThreads, COMET_DCA_BATCH_MINB) dca_batch_kern
     T *wrow = (T *)(sm + L.wrow);
     int32_t *orow = (int32_t *)(sm + L.orow);
     T *capv = (T *)(sm + L.cap);
-    T *frm = (T *)(sm + L.frame);
+    Q4<T> *frm = (Q4<T> *)(sm + L.frame);
     T *dsm = (T *)(sm + L.drift);
     uint8_t *msm = (uint8_t *)(sm + L.mask);
     const int rcap = L.wcap + 32;
@@ -876,8 +879,7 @@ __global__ void __launch_bounds__(kThreads, COMET_DCA_BATCH_MINB) dca_batch_kern
                 s_tl.ux = wrow + 3 * rcap + woff[3];
                 s_tl.uy = wrow + 4 * rcap + woff[4];
                 s_tl.uz = wrow + 5 * rcap + woff[5];
-                s_tl.frm = frm;
-                s_tl.fs = L.wcap;
+                s_tl.rec = frm;
                 s_tl.cap = capv;
                 s_tl.offs = orow + ooff;
                 s_tl.dsm = hits_sm ? dsm + doff : Dg;
