@@ -387,8 +387,9 @@ DCA_FLOPS_PER_WIRE = 201
 DCA_FLOPS_PER_HIT = 8
 PROP_BYTES_PER_REC = 24
 
-# DRAM bytes (read + write) per launch of the two main kernels on this workload at stride 16, from
-# the ncu launch list in profiles/launches_multi_turn_2e18_stride16.md (mean over its 80 launches).
+# DRAM bytes (read + write) per launch of the two main kernels on this workload at stride 16, from a
+# one-pass ncu launch list of `python bench.py` (dram__bytes_read.sum + dram__bytes_write.sum, mean
+# over its 80 launches of each kernel).
 # Valid only for the kernel sources they were measured on (SHA-1 of the package's csrc/ files);
 # reported as null once those change.
 NCU_TRAFFIC = {"csrc_sha1": "97d6be73e52b2631f9ff257f1bbac17ac5a09afb", "stride": 16,
