@@ -172,28 +172,36 @@ class ScanParams:
 
 
 class DeviceField:
-    """Mirror of comet_field.  ``table`` (if given) is copied to the device as float32."""
+    """Mirror of comet_field.  ``table`` [3][nz][ny][nx] (if given) is copied to the device as
+    float32, component-major (kind 1) or, with ``interleaved``, as [nz][ny][nx][4] (kind 2: one
+    16-byte load per grid node; identical results)."""
 
     def __init__(self, kind: int = 0, b=(0.0, 0.0, 1.0), table=None, origin=(0.0, 0.0, 0.0),
-                 spacing: float = 0.0, device="cuda"):
+                 spacing: float = 0.0, device="cuda", interleaved: bool = False):
         self.kind = kind
         self.b = tuple(float(x) for x in b)
         self.table = None
         self.origin = tuple(float(x) for x in origin)
         self.spacing = float(spacing)
-        if kind == 1:
-            t = torch.as_tensor(table)
-            self.table = t.to(device=device, dtype=torch.float32).contiguous()
+        if kind in (1, 2):
+            t = torch.as_tensor(table).to(dtype=torch.float32)
+            self.shape = tuple(t.shape[1:])          # (nz, ny, nx)
+            if interleaved or kind == 2:
+                self.kind = 2
+                t4 = torch.zeros(self.shape + (4,), dtype=torch.float32)
+                t4[..., :3] = t.permute(1, 2, 3, 0)
+                t = t4
+            self.table = t.to(device=device).contiguous()
 
     @classmethod
-    def from_synth(cls, f, device="cuda"):
-        return cls(f.kind, f.b, f.table, f.origin, f.spacing, device)
+    def from_synth(cls, f, device="cuda", interleaved: bool = False):
+        return cls(f.kind, f.b, f.table, f.origin, f.spacing, device, interleaved)
 
     def c(self) -> _Field:
         if self.kind == 0:
             return _Field(0, (C.c_double * 3)(*self.b), None, 0, 0, 0, (C.c_double * 3)(0, 0, 0), 0.0)
-        nz, ny, nx = self.table.shape[1:]
-        return _Field(1, (C.c_double * 3)(*self.b), self.table.data_ptr(), nx, ny, nz,
+        nz, ny, nx = self.shape
+        return _Field(self.kind, (C.c_double * 3)(*self.b), self.table.data_ptr(), nx, ny, nz,
                       (C.c_double * 3)(*self.origin), self.spacing)
 
 

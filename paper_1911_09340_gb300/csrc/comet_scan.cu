@@ -71,9 +71,11 @@ comet_status check_field(const comet_field *f)
             if (!std::isfinite(f->b[i])) return fail(COMET_ERR_INVALID_ARG, "field.b must be finite");
         return COMET_OK;
     }
-    if (f->kind != 1) return fail(COMET_ERR_INVALID_ARG, "field.kind must be 0 (uniform) or 1 (table)");
+    if (f->kind != 1 && f->kind != 2)
+        return fail(COMET_ERR_INVALID_ARG, "field.kind must be 0 (uniform), 1 (table) or 2 (interleaved table)");
     if (!f->table) return fail(COMET_ERR_INVALID_ARG, "field.table is NULL");
-    if (!aligned(f->table, 4)) return fail(COMET_ERR_INVALID_ARG, "field.table must be 4-byte aligned");
+    if (!aligned(f->table, f->kind == 2 ? 16 : 4))
+        return fail(COMET_ERR_INVALID_ARG, "field.table must be %d-byte aligned", f->kind == 2 ? 16 : 4);
     if (f->nx < 2 || f->ny < 2 || f->nz < 2) return fail(COMET_ERR_INVALID_ARG, "field table needs >= 2 nodes per axis");
     if (!(f->spacing > 0.0) || !std::isfinite(f->spacing)) return fail(COMET_ERR_INVALID_ARG, "field.spacing must be > 0");
     for (int i = 0; i < 3; ++i)

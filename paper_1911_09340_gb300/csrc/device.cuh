@@ -54,6 +54,7 @@ struct FieldTable {
     const float *__restrict__ tab;
     int nx, ny, nz;
     T ox, oy, oz, inv_sp;
+    int il;   // layout: 0 = [3][nz][ny][nx], 1 = [nz][ny][nx][4] (one 16-byte load per node)
 
     __device__ __forceinline__ static void cell(T g, int n, int &i, T &t)
     {
@@ -76,6 +77,26 @@ struct FieldTable {
         const size_t base = ((size_t)iz * ny + iy) * nx + ix;
         const size_t sy = (size_t)nx, sz = (size_t)nx * ny;
         T out[3];
+        if (il) {
+            const float4 *q = (const float4 *)tab + base;
+            const float4 n000 = __ldg(q), n001 = __ldg(q + 1), n010 = __ldg(q + sy), n011 = __ldg(q + sy + 1);
+            const float4 n100 = __ldg(q + sz), n101 = __ldg(q + sz + 1), n110 = __ldg(q + sz + sy),
+                         n111 = __ldg(q + sz + sy + 1);
+            auto lerp3 = [&](float v000, float v001, float v010, float v011, float v100, float v101,
+                             float v110, float v111) {
+                const T a00 = (T)v000 + tx * ((T)v001 - (T)v000);
+                const T a01 = (T)v010 + tx * ((T)v011 - (T)v010);
+                const T a10 = (T)v100 + tx * ((T)v101 - (T)v100);
+                const T a11 = (T)v110 + tx * ((T)v111 - (T)v110);
+                const T b0 = a00 + ty * (a01 - a00);
+                const T b1 = a10 + ty * (a11 - a10);
+                return b0 + tz * (b1 - b0);
+            };
+            bx = lerp3(n000.x, n001.x, n010.x, n011.x, n100.x, n101.x, n110.x, n111.x);
+            by = lerp3(n000.y, n001.y, n010.y, n011.y, n100.y, n101.y, n110.y, n111.y);
+            bz = lerp3(n000.z, n001.z, n010.z, n011.z, n100.z, n101.z, n110.z, n111.z);
+            return;
+        }
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const float *p = tab + c * plane + base;
@@ -96,6 +117,13 @@ struct FieldTable {
         bz = out[2];
     }
 };
+
+template <typename T>
+inline FieldTable<T> make_table(const comet_field &f)
+{
+    return FieldTable<T>{(const float *)f.table, f.nx, f.ny, f.nz, (T)f.origin[0], (T)f.origin[1],
+                         (T)f.origin[2], (T)(1.0 / f.spacing), f.kind == 2 ? 1 : 0};
+}
 
 // ------------------------------------------------------------------------------------------------
 // RK4

@@ -212,7 +212,7 @@ cudaError_t launch_classify(comet_dtype dt, const comet_field &f, const ClsArgs 
 enum class FieldKind { Axial, Uniform, Table };
 inline FieldKind field_kind(const comet_field &f)
 {
-    if (f.kind == 1) return FieldKind::Table;
+    if (f.kind == 1 || f.kind == 2) return FieldKind::Table;
     return (f.b[0] == 0.0 && f.b[1] == 0.0) ? FieldKind::Axial : FieldKind::Uniform;
 }
 

@@ -112,8 +112,7 @@ static void cls_dispatch(const comet_field &f, const ClsArgs &a, unsigned nb, co
         break;
     case FieldKind::Table:
         classify_kernel<T, FieldTable<T>, BATCH><<<nb, nt, 0, st>>>(
-            FieldTable<T>{(const float *)f.table, f.nx, f.ny, f.nz, (T)f.origin[0], (T)f.origin[1],
-                          (T)f.origin[2], (T)(1.0 / f.spacing)},
+            make_table<T>(f),
             a, L);
         break;
     }

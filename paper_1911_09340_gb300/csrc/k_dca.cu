@@ -737,8 +737,7 @@ static cudaError_t dca_dispatch(const comet_field &f, const DcaArgs &a, cudaStre
         return dca_launch<T>(FieldUniform<T>{(T)f.b[0], (T)f.b[1], (T)f.b[2]}, a, st);
     case FieldKind::Table:
     default:
-        return dca_launch<T>(FieldTable<T>{(const float *)f.table, f.nx, f.ny, f.nz, (T)f.origin[0],
-                                           (T)f.origin[1], (T)f.origin[2], (T)(1.0 / f.spacing)},
+        return dca_launch<T>(make_table<T>(f),
                              a, st);
     }
 }
@@ -972,8 +971,7 @@ static cudaError_t dca_batch_dispatch(const comet_field &f, const BatchLaunch &B
         return dca_batch_launch<T>(FieldUniform<T>{(T)f.b[0], (T)f.b[1], (T)f.b[2]}, BL, st);
     case FieldKind::Table:
     default:
-        return dca_batch_launch<T>(FieldTable<T>{(const float *)f.table, f.nx, f.ny, f.nz, (T)f.origin[0],
-                                                 (T)f.origin[1], (T)f.origin[2], (T)(1.0 / f.spacing)},
+        return dca_batch_launch<T>(make_table<T>(f),
                                    BL, st);
     }
 }

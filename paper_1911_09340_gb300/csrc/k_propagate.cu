@@ -455,9 +455,7 @@ static void prop_dispatch(const comet_field &f, const PropArgs &a, int stride, u
                                                stride, nb, L, st);
         break;
     case FieldKind::Table:
-        prop_launch<T, FieldTable<T>, BATCH>(FieldTable<T>{(const float *)f.table, f.nx, f.ny, f.nz,
-                                                           (T)f.origin[0], (T)f.origin[1],
-                                                           (T)f.origin[2], (T)(1.0 / f.spacing)},
+        prop_launch<T, FieldTable<T>, BATCH>(make_table<T>(f),
                                              a, stride, nb, L, st);
         break;
     }

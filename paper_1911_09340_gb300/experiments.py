@@ -5,6 +5,7 @@
     python -m paper_1911_09340_gb300.experiments iterative [--events N] [--stride s]
     python -m paper_1911_09340_gb300.experiments gauss-newton [--events N] [--lambda-mm 0.8]
     python -m paper_1911_09340_gb300.experiments batch [--events N]
+    python -m paper_1911_09340_gb300.experiments table-field [--events N]
 
 * ``lambda-sweep``: hit-classification efficiency and purity (metrics.py) of the first stage and of
   all stages as the cutoff lambda runs over 0.5-1.2 mm in 0.1 mm steps (the range of the paper's
@@ -19,6 +20,8 @@
   comet_scan_gn_step) started from the top 16 seeds of a 2^14 grid.
 * ``batch``: events/s and per-event latency of many uneven events, per-event path against
   continuous batching (batch.py) under the autotuned configuration.
+* ``table-field``: evaluations/s on the non-uniform (tabulated solenoid) field workload, with the
+  uniform-field path on the same events beside it.
 
 Every scan runs through the library's kernels (scan.scan_partition); only the metrics are computed
 on the host from the copied-back hit classes.  One JSON line per result.
@@ -367,9 +370,57 @@ def batch_study(n_events: int = 512, stride: int = 16, lam: float = 1e-2, tune_e
              "autotune": table}]
 
 
+def table_field_study(n_events: int = 8, stride: int = 16, lam: float = 1e-2, dtype=torch.float32):
+    """Seed x hit DCA evaluations/s on the non-uniform-field workload (DIO-shaped momenta 50-105
+    MeV/c, the tabulated solenoid model, 2^18 seeds per partition): every RK4 step of the track
+    recording and of the refinement evaluates the trilinear table.  The same events scanned in the
+    uniform 1 T field (the closed-form axial map) are timed beside them."""
+    fld = synth.table_field()
+    events = [synth.table_field_event(i, fld) for i in range(n_events)]
+    ctx = B.Context(torch.cuda.current_device())
+    out = {"study": "table-field", "events": n_events, "stride": stride, "lambda_mm": lam * 1e3,
+           "momenta_MeV": [round(float(np.hypot(ev.pt, ev.pz)), 1) for ev in events]}
+    for name, field, il in (("table", fld, False), ("table_interleaved", fld, True),
+                            ("uniform", synth.uniform_field(1.0), False)):
+        dfield = B.DeviceField.from_synth(field, interleaved=il)
+        S = max(sp.n_seeds for ev in events for sp in ev.partitions)
+        n_rec = max(n // stride + 1 for ev in events for n in ev.n_steps)
+        ws = scan.Workspace(S, n_rec, max(ev.n_hits for ev in events), dtype)
+        devs = [scan.DeviceEvent.from_event(ev, dtype) for ev in events]
+        scan.scan_event(ctx, dfield, events[0], devs[0], ws, dtype, stride, lam)
+        evals = 0
+        timer = scan.KernelTimer()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        t0.record()
+        classes = []
+        for ev, dev in zip(events, devs):
+            dev.mask.zero_()
+            cl = []
+            for spec, p in zip(ev.partitions, scan.event_params(ev, dtype, stride, lam)):
+                scan.scan_partition(ctx, dfield, p, spec, dev, ws, timer=timer)
+                cl.append(ws.hit_class[: max(ev.n_hits, 1)].clone())
+            classes.append(cl)
+        t1.record()
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1)
+        for ev, cl in zip(events, classes):
+            masked = np.zeros(ev.n_hits, bool)
+            for spec, c in zip(ev.partitions, cl):
+                evals += spec.n_seeds * int((~masked).sum())
+                masked |= c.cpu().numpy()[: ev.n_hits].astype(bool)
+        out[name] = {"evals_per_s": evals / (ms * 1e-3), "ms_per_event": ms / n_events,
+                     "kernel_ms": {k: round(v[0], 3) for k, v in timer.totals().items()}}
+        del ws, devs
+        torch.cuda.empty_cache()
+    ctx.close()
+    return [out]
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("study", choices=["lambda-sweep", "backward", "iterative", "gauss-newton", "batch"])
+    ap.add_argument("study", choices=["lambda-sweep", "backward", "iterative", "gauss-newton", "batch",
+                                      "table-field"])
     ap.add_argument("--events", type=int, default=32)
     ap.add_argument("--stride", type=int, default=16)
     ap.add_argument("--lambda-mm", type=float, default=10.0, help="cutoff (backward, iterative, gn)")
@@ -379,6 +430,8 @@ def main(argv=None):
         rows = lambda_sweep(args.events, stride=args.stride)
     elif args.study == "iterative":
         rows = iterative_study(args.events, args.stride, args.lambda_mm * 1e-3)
+    elif args.study == "table-field":
+        rows = table_field_study(args.events, args.stride, args.lambda_mm * 1e-3)
     elif args.study == "batch":
         rows = batch_study(args.events, args.stride, args.lambda_mm * 1e-3)
     elif args.study == "gauss-newton":

@@ -199,15 +199,30 @@ def test_unconverged_count_matches_oracle(ctx):
     assert np.abs(g["dca"] - r["dca"]).max() <= 1e-9
 
 
-def test_table_field_dca(ctx):
+@pytest.mark.parametrize("interleaved", [False, True])
+def test_table_field_dca(ctx, interleaved):
     field = synth.table_field(spacing=0.02)
     ev = synth.single_event_fp64()
     seeds = O.lattice(ev.partitions[0])[::33]
     op, bp = both_params(n_steps=ev.n_steps[0])
     mask = np.zeros(ev.n_hits, np.uint8)
-    g = gpu_dca(ctx, B.DeviceField.from_synth(field), bp, seeds, -1, ev.wires, ev.hit_offsets,
-                ev.drift, mask, torch.float64, want_dca=True)
+    g = gpu_dca(ctx, B.DeviceField.from_synth(field, interleaved=interleaved), bp, seeds, -1, ev.wires,
+                ev.hit_offsets, ev.drift, mask, torch.float64, want_dca=True)
     r = O.scan(field, op, seeds, -1, O.wires_aos(ev.wires), ev.hit_offsets, ev.drift, mask,
                want_dca=True)
     assert np.abs(g["dca"] - r["dca"]).max() <= 1e-9
     assert np.allclose(g["rss"], r["rss"], rtol=1e-10, atol=0)
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_interleaved_table_is_bit_identical(ctx, dtype):
+    """Field kind 2 ([nz][ny][nx][4]) interpolates the same values in the same order as kind 1."""
+    field = synth.table_field(spacing=0.02)
+    ev = synth.single_event_fp64()
+    seeds = O.lattice(ev.partitions[0])[::17]
+    _, bp = both_params(n_steps=ev.n_steps[0], stride=4)
+    mask = np.zeros(ev.n_hits, np.uint8)
+    outs = [gpu_dca(ctx, B.DeviceField.from_synth(field, interleaved=il), bp, seeds, -1, ev.wires,
+                    ev.hit_offsets, ev.drift, mask, dtype, want_dca=True) for il in (False, True)]
+    for k in ("rss", "dca", "n_in"):
+        assert np.array_equal(outs[0][k], outs[1][k]), k
