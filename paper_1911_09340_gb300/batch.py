@@ -166,20 +166,18 @@ class BatchScanner:
         seed, its RSS and the hit classes of each partition), per-event latency in ms (from the end
         of the round before its first partition to the end of its last) and the total GPU time.
         ``pinned`` = self.pin(events), made once (else made here, untimed)."""
-        pinned = pinned if pinned is not None else self.pin(events)
+        return run_interleaved([self], events, collect, [pinned] if pinned is not None else None)
+
+    def rounds(self, events, pinned, results, collect: bool):
+        """Generator: packs and launches one round per step (on this scanner's stream) and yields
+        the CUDA event recorded after it; fills ``results`` (start/end rounds, and the outputs when
+        ``collect``)."""
         queue = deque(range(len(events)))
         state = [None] * self.slots          # (event index, next partition)
-        results = [EventResult([], [], []) for _ in events]
-        marks: List[torch.cuda.Event] = []
         rnd = 0
         start = 0
-        torch.cuda.synchronize()
-        import time
-        w0 = time.perf_counter()
-        with torch.cuda.stream(self.stream):
-            t0 = torch.cuda.Event(enable_timing=True)
-            t0.record()
-            while queue or any(s is not None for s in state):
+        while queue or any(s is not None for s in state):
+            with torch.cuda.stream(self.stream):
                 for slot in range(self.slots):
                     if state[slot] is None and queue:
                         i = queue.popleft()
@@ -207,34 +205,25 @@ class BatchScanner:
                 self._launch()
                 e = torch.cuda.Event(enable_timing=True)
                 e.record()
-                marks.append(e)
                 if collect:
                     self.stream.synchronize()
                     best = self.s_best.cpu().numpy()
                     best_rss = self.s_best_rss.double().cpu().numpy()
                     cls = self.s_class.cpu().numpy()
-                for slot in members:
-                    i, p = state[slot]
-                    if collect:
-                        ev = events[i]
-                        results[i].best_idx.append(int(best[slot]))
-                        results[i].best_rss.append(float(best_rss[slot]))
-                        results[i].hit_class.append(cls[slot, : ev.n_hits].copy())
-                    if p + 1 == len(events[i].partitions):
-                        results[i].end_round = rnd
-                        state[slot] = None
-                    else:
-                        state[slot] = (i, p + 1)
-                rnd += 1
-            self.stream.synchronize()
-        wall_ms = (time.perf_counter() - w0) * 1e3
-        ms_round = [t0.elapsed_time(m) for m in marks]
-        lat = []
-        for r in results:
-            begin = 0.0 if r.start_round == 0 else ms_round[r.start_round - 1]
-            lat.append(ms_round[r.end_round] - begin)
-        return {"results": results, "latency_ms": np.array(lat), "gpu_ms": ms_round[-1] if ms_round else 0.0,
-                "rounds": rnd, "wall_ms": wall_ms}
+            for slot in members:
+                i, p = state[slot]
+                if collect:
+                    ev = events[i]
+                    results[i].best_idx.append(int(best[slot]))
+                    results[i].best_rss.append(float(best_rss[slot]))
+                    results[i].hit_class.append(cls[slot, : ev.n_hits].copy())
+                if p + 1 == len(events[i].partitions):
+                    results[i].end_round = rnd
+                    state[slot] = None
+                else:
+                    state[slot] = (i, p + 1)
+            rnd += 1
+            yield e
 
     def _launch(self):
         B.comet_scan_batch_update(self.ctx, self.dtype, self.field, self.params, self.caps, self.desc,
@@ -252,6 +241,49 @@ class BatchScanner:
                                    stream=torch.cuda.current_stream())
             self.graphs[key] = g
         g.replay()
+
+
+def run_interleaved(scanners, events, collect: bool = False, pinned=None) -> Dict:
+    """Scans ``events`` with one or more scanners (each with its own context and stream): event i
+    goes to scanner i mod n, and the scanners' rounds are launched alternately, so that the rounds
+    of different scanners overlap on the GPU (one scanner's kernel tails are filled by another's
+    work).  Same results as one scanner; latency and GPU time as in BatchScanner.run."""
+    import time
+    n = len(scanners)
+    parts = [list(range(k, len(events), n)) for k in range(n)]
+    sub = [[events[i] for i in part] for part in parts]
+    pins = pinned if pinned is not None else [sc.pin(ev) for sc, ev in zip(scanners, sub)]
+    res = [[EventResult([], [], []) for _ in ev] for ev in sub]
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    gens = [sc.rounds(ev, pn, r, collect) for sc, ev, pn, r in zip(scanners, sub, pins, res)]
+    marks = [[] for _ in scanners]
+    live = list(range(n))
+    while live:
+        for k in list(live):
+            try:
+                marks[k].append(next(gens[k]))
+            except StopIteration:
+                live.remove(k)
+    torch.cuda.synchronize()
+    wall_ms = (time.perf_counter() - w0) * 1e3
+    results = [None] * len(events)
+    lat = np.zeros(len(events))
+    gpu_ms = 0.0
+    rounds = 0
+    for k in range(n):
+        ms = [t0.elapsed_time(m) for m in marks[k]]
+        rounds = max(rounds, len(ms))
+        if ms:
+            gpu_ms = max(gpu_ms, ms[-1])
+        for j, i in enumerate(parts[k]):
+            r = res[k][j]
+            results[i] = r
+            begin = 0.0 if r.start_round <= 0 else ms[r.start_round - 1]
+            lat[i] = ms[r.end_round] - begin
+    return {"results": results, "latency_ms": lat, "gpu_ms": gpu_ms, "rounds": rounds, "wall_ms": wall_ms}
 
 
 def autotune(scanner: BatchScanner, events, slots_options=(32, 64, 128, 256), ctas_options=(0, 4, 2),

@@ -356,6 +356,20 @@ def batch_study(n_events: int = 512, stride: int = 16, lam: float = 1e-2, tune_e
     pinned = sc.pin(events)
     sc.run(events[:tune_events], pinned=pinned[:tune_events])
     r = sc.run(events, pinned=pinned)
+    # two scanners (two contexts and streams) with the tuned configuration, rounds interleaved
+    half = max(1, max_total_seeds // 2)
+    ctx2 = B.Context(torch.cuda.current_device())
+    del sc
+    torch.cuda.empty_cache()
+    pair = [BT.BatchScanner(c, dtype, stride, lam, slots=best["slots"], max_total_seeds=half,
+                            max_wires=max(512, max(ev.n_wires for ev in events)),
+                            max_hits=max(2048, max(ev.n_hits for ev in events)),
+                            graph=best["graph"], dca_ctas_per_sm=best["dca_ctas_per_sm"])
+            for c in (ctx, ctx2)]
+    BT.run_interleaved(pair, events[:tune_events])
+    r2 = BT.run_interleaved(pair, events)
+    del pair
+    ctx2.close()
     wires = np.array([ev.n_wires for ev in events])
     turns = np.bincount([len(ev.partitions) for ev in events], minlength=7)[1:]
     ctx.close()
@@ -367,6 +381,8 @@ def batch_study(n_events: int = 512, stride: int = 16, lam: float = 1e-2, tune_e
              "batched": {"events_per_s": n_events / (r["gpu_ms"] * 1e-3), "latency_ms": pct(r["latency_ms"]),
                          "rounds": r["rounds"], "host_wall_ms": r["wall_ms"], "gpu_ms": r["gpu_ms"],
                          "config": best},
+             "batched_two_streams": {"events_per_s": n_events / (r2["gpu_ms"] * 1e-3),
+                                     "latency_ms": pct(r2["latency_ms"]), "rounds": r2["rounds"]},
              "autotune": table}]
 
 

@@ -68,3 +68,29 @@ def test_autotune_then_run_matches_per_event_scan(ctx):
         for p, part in enumerate(rr):
             assert res.best_idx[p] == part["idx"] and res.best_rss[p] == part["rss"]
             assert np.array_equal(res.hit_class[p], part["hit_class"])
+
+
+def test_two_interleaved_scanners_match_per_event_scan(ctx):
+    """Two scanners, each with its own context and stream, take alternate events and launch their
+    rounds alternately: every event's results are still those of the per-event scan."""
+    import torch
+    from paper_1911_09340_gb300 import batch
+    from paper_1911_09340_gb300 import binding as B
+    events = _events(7)
+    ref = _reference(ctx, events, torch.float32, 16)
+    ctx2 = B.Context(torch.cuda.current_device())
+    try:
+        pair = [batch.BatchScanner(c, torch.float32, stride=16, lam=1e-2, slots=3, max_seeds=4096,
+                                   max_total_seeds=1 << 15, max_wires=512, max_hits=1024, graph=g)
+                for c, g in ((ctx, True), (ctx2, False))]
+        r = batch.run_interleaved(pair, events, collect=True)
+        for ev, rr, res in zip(events, ref, r["results"]):
+            assert len(res.best_idx) == len(ev.partitions)
+            for p, part in enumerate(rr):
+                assert res.best_idx[p] == part["idx"] and res.best_rss[p] == part["rss"]
+                assert np.array_equal(res.hit_class[p], part["hit_class"])
+        assert np.all(r["latency_ms"] > 0)
+        del pair
+        torch.cuda.synchronize()
+    finally:
+        ctx2.close()
