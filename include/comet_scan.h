@@ -172,12 +172,15 @@ comet_status comet_scan_propagate(comet_ctx *ctx, comet_dtype dtype, const comet
  *   rss          out, [S] T: RSS = sum over wires with an unmasked hit of d_i^2, where
  *                d_i = min(min_j |D_i - r_ij|, lambda) and D_i is the DCA of the track to wire i
  *                (Eq. 1; the left and right hits of drift r sit at +-r across the wire, so
- *                min(d^L, d^R) = |D - r|).  Accumulated in double, summed in ascending wire order.
+ *                min(d^L, d^R) = |D - r|).  Summed in ascending wire order within chunks of at
+ *                most 32 wires (FP32 as a compensated TwoSum pair, FP64 plainly), the chunk sums
+ *                then in chunk order: deterministic, independent of the GPU's scheduling.
  *   n_in         out, [S] int32: wires whose capped residual is below lambda.
  *   dca_out      optional out, [W][S] T (NULL to skip): D_i of every (wire, seed).  Requesting it
  *                computes the exact DCA of every wire; without it, a wire the track never comes
- *                within (max drift + lambda + half a recording interval) of is known to contribute
- *                lambda^2 and is not refined.
+ *                within (max drift + lambda + half a recording interval; a whole interval at the
+ *                first and the last recorded state, which the refinement can move beyond) of is
+ *                known to contribute lambda^2 and is not refined.
  *   n_unconverged optional, device [1] int32 (NULL to skip): incremented by the number of
  *                (seed, wire) refinements that reached max_iter or met a track parallel to the wire.
  *                The caller zeroes it.
@@ -187,7 +190,9 @@ comet_status comet_scan_propagate(comet_ctx *ctx, comet_dtype dtype, const comet
  * |d| < tol (Algorithm 2's loop; the Newton step length is the reading of "the distance").
  * The closest recorded state is found exactly by a bounded search over the recorded states (recorded
  * states one recording interval apart are at most that arc length apart).  The kernel takes a
- * device work counter from the context: dca calls of one context must not overlap on the GPU. */
+ * device work counter from the context: dca calls of one context must not overlap on the GPU.
+ * With more than 32 wires the context also keeps per-chunk partial sums and per-group counters for
+ * the kernel (grown on demand, at least twofold: a call that grows them allocates device memory). */
 comet_status comet_scan_dca(comet_ctx *ctx, comet_dtype dtype, const comet_field *field,
                             const comet_scan_params *params, const void *points,
                             const int32_t *n_valid, const int8_t *charge, int64_t S,

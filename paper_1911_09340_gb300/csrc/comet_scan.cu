@@ -117,16 +117,19 @@ int n_rec_of(const comet_scan_params *p) { return p->n_steps / p->stride + 1; }
 // Segmentation and reaches of the closest-state search: identical for propagate (which writes the
 // segment bounding spheres) and dca (which reads them).  Consecutive recorded states are at most
 // stride*h apart along the track (|dx/ds| = |p|/P0 = 1 up to rounding); the margins cover the
-// rounding of the distances in the working precision.
+// rounding of the distances in the working precision.  The refinement reaches up to h_rec beyond
+// the first and the last recorded state, half an interval more than between states: R0 (and R1
+// when segments hold several states) include that half interval; for one-state segments the DCA
+// kernel adds it to its threshold where the state may be a track end.
 SearchGeometry search_geometry(comet_dtype dtype, const comet_scan_params *p)
 {
     SearchGeometry g;
     comet::dca_segments(n_rec_of(p), &g.G0, &g.G1);
     g.h_rec = p->h * p->stride;
     const double margin = dtype == COMET_F32 ? 4e-6 : 1e-9;
-    g.R0 = (g.G0 / 2) * g.h_rec * (1.0 + 1e-4) + margin;
-    g.R1 = (g.G1 / 2) * g.h_rec * (1.0 + 1e-4) + margin;
     g.half_rec = 0.5 * g.h_rec * (1.0 + 1e-4) + margin;
+    g.R0 = (g.G0 / 2) * g.h_rec * (1.0 + 1e-4) + margin + g.half_rec;
+    g.R1 = (g.G1 / 2) * g.h_rec * (1.0 + 1e-4) + margin + (g.G1 > 1 ? g.half_rec : 0.0);
     return g;
 }
 
@@ -212,6 +215,9 @@ void fill_dca(comet_ctx *ctx, comet_dtype, const comet_scan_params *p, const Sea
     a->h_rec_f = (float)a->h_rec;
     a->bounds = bounds;
     a->exact_all = dca_out != nullptr;
+    a->n_chunks = comet::dca_wire_chunks(W);
+    a->part = nullptr;
+    a->arrive = nullptr;
 }
 
 void fill_cls(comet_ctx *ctx, comet_dtype, const comet_scan_params *p, const void *points,
@@ -287,6 +293,8 @@ void comet_ctx_destroy(comet_ctx *ctx)
         cudaDeviceSynchronize();
         if (ctx->scratch) cudaFree(ctx->scratch);
         if (ctx->status) cudaFree(ctx->status);
+        if (ctx->dca_part) cudaFree(ctx->dca_part);
+        if (ctx->dca_arrive) cudaFree(ctx->dca_arrive);
         ctx->batch.release();
     }
     delete ctx;
@@ -531,6 +539,40 @@ comet_status comet_scan_dca(comet_ctx *ctx, comet_dtype dtype, const comet_field
     comet::DcaArgs a;
     fill_dca(ctx, dtype, params, search_geometry(dtype, params), points, n_valid, charge, S, bounds, wires,
              W, ldw, hit_offsets, drift, hit_mask, rss, n_in, dca_out, n_unconverged, &a);
+    if (a.n_chunks > 1) {
+        // per-chunk partial sums and per-group arrival counters, grown on demand; the counters are
+        // zeroed once here and left zero by every launch
+        // sized at first for the chunks of max(W, 256) wires, so that events of up to 256 wires
+        // never reallocate
+        const int nc_alloc = comet::dca_wire_chunks(W > 256 ? W : 256);
+        const size_t need = (size_t)(a.n_chunks > nc_alloc ? a.n_chunks : nc_alloc) * (size_t)S * (2 * esize(dtype) + 4);
+        const size_t groups = (size_t)((S + 31) / 32);
+        if (need > ctx->dca_part_bytes) {
+            // grown at least twofold, so that calls with more wires or seeds rarely reallocate
+            const size_t want = need > 2 * ctx->dca_part_bytes ? need : 2 * ctx->dca_part_bytes;
+            if (ctx->dca_part) cudaFree(ctx->dca_part);
+            ctx->dca_part = nullptr;
+            ctx->dca_part_bytes = 0;
+            cudaError_t e = cudaMalloc(&ctx->dca_part, want);
+            if (e != cudaSuccess)
+                return e == cudaErrorMemoryAllocation ? fail(COMET_ERR_NO_MEMORY, "cudaMalloc(dca partial sums, %zu B)", want) : cuda_fail(e, "cudaMalloc");
+            ctx->dca_part_bytes = want;
+        }
+        if (groups > ctx->dca_arrive_n) {
+            const size_t n = groups > 2 * ctx->dca_arrive_n ? groups : 2 * ctx->dca_arrive_n;
+            if (ctx->dca_arrive) cudaFree(ctx->dca_arrive);
+            ctx->dca_arrive = nullptr;
+            ctx->dca_arrive_n = 0;
+            cudaError_t e = cudaMalloc(&ctx->dca_arrive, n * 4);
+            if (e != cudaSuccess)
+                return e == cudaErrorMemoryAllocation ? fail(COMET_ERR_NO_MEMORY, "cudaMalloc(dca counters, %zu B)", n * 4) : cuda_fail(e, "cudaMalloc");
+            e = cudaMemsetAsync(ctx->dca_arrive, 0, n * 4, (cudaStream_t)stream);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+            ctx->dca_arrive_n = n;
+        }
+        a.part = ctx->dca_part;
+        a.arrive = ctx->dca_arrive;
+    }
     cudaError_t e = comet::launch_dca(dtype, *field, a, (cudaStream_t)stream);
     return e == cudaSuccess ? COMET_OK : cuda_fail(e, "dca launch");
 }

@@ -68,7 +68,19 @@ struct DcaArgs {
     int G0;                // recorded states per super-segment
     int G1;                // recorded states per level-1 segment
     int exact_all;         // refine every wire (dca_out requested)
+    // The wires are cut into n_chunks chunks (dca_wire_chunks(W)); a seed's RSS is the sum of its
+    // per-chunk compensated partial sums, added in chunk order.  With `part` and `arrive` given,
+    // the persistent kernel schedules (group, chunk) items across warps: partial sums go to part
+    // ([n_chunks][S] hi, [n_chunks][S] lo in T, then [n_chunks][S] int32 n_in) and the last warp
+    // to finish a group (arrive[group] counts, reset to 0 afterwards) adds them up.  Without them a
+    // warp does all chunks of its group itself, with the same arithmetic.
+    int n_chunks;
+    void *part;
+    uint32_t *arrive;
 };
+
+// Wire chunks of the DCA's per-seed sums for W wires (W <= 1024; 1 otherwise).
+int dca_wire_chunks(int W);
 
 struct SelArgs {
     const void *rss;
@@ -137,7 +149,10 @@ struct JacArgs {
 cudaError_t launch_jacobian(const JacArgs &a, cudaStream_t st);
 
 constexpr int kDcaWarpsPerCta = 4;   // warps of a persistent DCA CTA (128 threads)
-constexpr int kDcaBatchChunk = 16;   // 32-seed groups per chunk of the batched DCA launch
+#ifndef COMET_DCA_BATCH_CHUNK
+#define COMET_DCA_BATCH_CHUNK 16
+#endif
+constexpr int kDcaBatchChunk = COMET_DCA_BATCH_CHUNK;   // 32-seed groups per chunk of the batched DCA launch
 
 // ---- batches of events (one turn partition each) in single launches ---------------------------
 // Every batched launch has a fixed grid; block b finds its event e and its block index inside the

@@ -18,11 +18,15 @@
 // h_rec/2) are scanned state by state, each lane its own seed's states, keeping the lexicographic
 // (distance, index) minimum.  If a seed's closest state is within the capture radius it lies in a
 // scanned segment, so the minimum is exact; if not, every residual of the wire is at least lambda
-// and the wire adds exactly lambda^2 to the RSS, with or without a refinement.  With dca_out every
-// state is scanned (exact DCA for every wire).
+// and the wire adds exactly lambda^2 to the RSS, with or without a refinement.  Beyond the first
+// and the last recorded state the refinement reaches up to h_rec (not h_rec/2) from the nearest
+// recorded state, so segments that may hold a track end are tested, and an end state refined,
+// within capture radius + h_rec.  With dca_out every state is scanned (exact DCA for
+// every wire).
 //
-// RSS: each thread sums its wires' d_i^2 in ascending wire order (FP32 as a TwoSum pair, FP64
-// plainly).  No atomics: the result does not depend on scheduling (the paper's GPU kernel used
+// RSS: each thread sums its wires' d_i^2 in ascending wire order within each wire chunk (FP32 as a
+// TwoSum pair, FP64 plainly), then the chunks' sums in chunk order.  Atomics only hand out work
+// and count arrivals: the result does not depend on scheduling (the paper's GPU kernel summed with
 // atomics and was not deterministic, Sec. 4.1).
 #include <float.h>
 
@@ -36,6 +40,10 @@
 #endif
 #ifndef COMET_DCA_U2
 #define COMET_DCA_U2 4
+#endif
+// wires per chunk of the per-seed sums (the persistent kernel's finest work item)
+#ifndef COMET_DCA_CHUNK_W
+#define COMET_DCA_CHUNK_W 32
 #endif
 
 namespace comet {
@@ -154,6 +162,7 @@ struct Group {
     bool valid;
     int nv;          // recorded states of the seed
     int n0w;         // super-segments of the longest track of the warp
+    int elo, ehi;    // smallest and largest last state index over the warp's tracks
     T c, ip;         // KAPPA q / P0, 1 / P0
 };
 
@@ -178,6 +187,8 @@ __device__ __forceinline__ Group<T> load_group(const DcaArgs &a, int64_t g, int 
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) n0w = max(n0w, __shfl_xor_sync(0xffffffffu, n0w, off));
     gr.n0w = n0w;
+    gr.elo = (int)__reduce_min_sync(0xffffffffu, (unsigned)(gr.valid ? gr.nv - 1 : 0x7fffffff));
+    gr.ehi = (int)__reduce_max_sync(0xffffffffu, (unsigned)(gr.valid ? gr.nv - 1 : 0));
     return gr;
 }
 
@@ -273,12 +284,12 @@ __device__ __forceinline__ void tile_wire_setup(const Tile<T> &tl, int i, T lam,
     rec[4 * i + 3] = Q4<T>{ux, uy, uz, T(0)};
 }
 
-// The wires of one tile for one 32-seed group: accumulates d_i^2, n_in and unconverged counts.
+// Wires [wb, we) of one tile for one 32-seed group: accumulates d_i^2, n_in and unconverged counts.
 template <typename T, class F>
 __device__ __forceinline__ void group_wires(const F &f, const DcaArgs &a, const Group<T> &gr,
                                             const Tile<T> &tl, const float4 *sph0,
                                             const float4 *sph1, int lane, Acc<T> &acc, int &nin,
-                                            int &nunc)
+                                            int &nunc, int wb, int we)
 {
     const T *__restrict__ P = (const T *)a.points;
     const int64_t S = a.S;
@@ -293,8 +304,8 @@ __device__ __forceinline__ void group_wires(const F &f, const DcaArgs &a, const 
     const Q4<T> *rec = tl.rec;
     constexpr int kU = COMET_DCA_U2;
 
-    for (int base = 0; base < tl.wn; base += 32) {
-        const int clen = min(32, tl.wn - base);
+    for (int base = wb; base < we; base += 32) {
+        const int clen = min(32, we - base);
         // lane t: which super-segments can bring wire base + t within its capture radius
         uint32_t mask0 = 0;
         if (lane < clen) {
@@ -372,11 +383,15 @@ __device__ __forceinline__ void group_wires(const F &f, const DcaArgs &a, const 
                 while (u0) {
                     const int j = __ffs(u0) - 1;
                     u0 &= u0 - 1;
-                    // lane m tests level-1 segment m of super-segment j
+                    // lane m tests level-1 segment m of super-segment j; a one-state segment
+                    // that may hold a track end (the first state, or between the warp's smallest
+                    // and largest last state) gets the refinement's extra half interval there
+                    const int k1 = j * G0 + lane;
+                    const bool end1 = G1 == 1 && (k1 == 0 || (k1 >= gr.elo && k1 <= gr.ehi));
                     const bool hit1 = lane < N1 &&
                                       sphere_within<T>(sph1[j * kN1Max + lane], fvx, fvy, fvz, fav,
                                                        fwx, fwy, fwz, faw, ax, ay, az, ux, uy, uz,
-                                                       capth);
+                                                       end1 ? capth + half_rec : capth);
                     const uint32_t u1 = __ballot_sync(0xffffffffu, hit1);
                     if (u1) {
                         // one contiguous range from the first to the last candidate level-1
@@ -389,9 +404,12 @@ __device__ __forceinline__ void group_wires(const F &f, const DcaArgs &a, const 
                 }
             }
 
-            // refinement from the closest recorded state (only when it can matter)
-            // (compared squared: capth carries margins far above the rounding of the square)
-            const bool refine = want && bk != 0x7fffffff && (a.exact_all || bd <= capth * capth);
+            // refinement from the closest recorded state, only where it can bring the wire within
+            // its capture radius: within half an interval of a recorded state, within a whole one
+            // beyond either end of the recorded track (compared squared: capth carries margins far
+            // above the rounding of the square)
+            const T th = (bk == 0 || bk == nv - 1) ? capth + half_rec : capth;
+            const bool refine = want && bk != 0x7fffffff && (a.exact_all || bd <= th * th);
             T D = T(INFINITY);
             if (refine) {
                 T yv[6];
@@ -418,6 +436,29 @@ __device__ __forceinline__ void group_wires(const F &f, const DcaArgs &a, const 
                 acc.add(d * d);
             }
         }
+    }
+}
+
+// Wire chunk c of n over W wires: [c * wc, min((c + 1) * wc, W)), wc = ceil(W / n).
+__device__ __forceinline__ int2 chunk_range(int W, int n, int c)
+{
+    const int wc = (W + n - 1) / n;
+    return make_int2(min(c * wc, W), min((c + 1) * wc, W));
+}
+
+// All wire chunks of one group in this warp: each chunk's partial sum, added in chunk order (the
+// arithmetic the cross-warp schedule of the persistent kernel reproduces).
+template <typename T, class F>
+__device__ __forceinline__ void group_all_chunks(const F &f, const DcaArgs &a, const Group<T> &gr,
+                                                 const Tile<T> &tl, const float4 *sph0,
+                                                 const float4 *sph1, int lane, Acc<T> &acc,
+                                                 int &nin, int &nunc)
+{
+    for (int c = 0; c < a.n_chunks; ++c) {
+        const int2 r = chunk_range(tl.wn, a.n_chunks, c);
+        Acc<T> part;
+        group_wires<T, F>(f, a, gr, tl, sph0, sph1, lane, part, nin, nunc, r.x, r.y);
+        acc.add_pair(part.hi, part.lo);
     }
 }
 
@@ -546,28 +587,68 @@ __global__ void __launch_bounds__(kThreads, COMET_DCA_MINB) dca_persistent_kerne
     for (int i = tid; i < W; i += kThreads) tile_wire_setup<T>(tl, i, in_prec<T>(a.lambda, a.lambda_f), capv, frm);
     __syncthreads();
 
-    // ---- 32-seed groups, taken dynamically by each warp
+    // ---- work items taken dynamically by each warp: 32-seed groups, or (group, wire chunk) pairs
+    // when partial sums can be parked in `part` (finer items balance the warps' loads)
     const int64_t n_groups = (a.S + 31) / 32;
+    const bool split = a.n_chunks > 1 && a.part && a.arrive;
+    const int nc = split ? a.n_chunks : 1;
+    const int64_t n_items = n_groups * nc;
     int nunc = 0;
     for (;;) {
-        unsigned int g = 0;
-        if (lane == 0) g = atomicAdd((unsigned int *)a.counter, 1u);
-        g = __shfl_sync(0xffffffffu, g, 0);
-        if ((int64_t)g >= n_groups) break;
-        const Group<T> gr = load_group<T>(a, (int64_t)g, lane);
+        unsigned int it = 0;
+        if (lane == 0) it = atomicAdd((unsigned int *)a.counter, 1u);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if ((int64_t)it >= n_items) break;
+        const int64_t g = (int64_t)(it / (unsigned)nc);
+        const int c = (int)(it % (unsigned)nc);
+        const Group<T> gr = load_group<T>(a, g, lane);
         const float4 *s0 = sph0, *s1 = sph1;
         if (sph_smem) {
-            build_spheres<T>(a, gr, lane, sph0, sph1, (int64_t)g);
+            build_spheres<T>(a, gr, lane, sph0, sph1, g);
         } else if (a.bounds) {
-            s0 = (const float4 *)a.bounds + (int64_t)g * kBoundsPerGroup;   // read in place
+            s0 = (const float4 *)a.bounds + g * kBoundsPerGroup;   // read in place
             s1 = s0 + kN0Max;
         }
         Acc<T> acc;
         int nin = 0;
-        group_wires<T, F>(f, a, gr, tl, s0, s1, lane, acc, nin, nunc);
-        if (gr.valid) {
-            ((T *)a.rss)[gr.s] = acc.value();
-            a.n_in[gr.s] = nin;
+        if (!split) {
+            group_all_chunks<T, F>(f, a, gr, tl, s0, s1, lane, acc, nin, nunc);
+            if (gr.valid) {
+                ((T *)a.rss)[gr.s] = acc.value();
+                a.n_in[gr.s] = nin;
+            }
+        } else {
+            const int2 r = chunk_range(W, nc, c);
+            group_wires<T, F>(f, a, gr, tl, s0, s1, lane, acc, nin, nunc, r.x, r.y);
+            T *ph = (T *)a.part;
+            T *pl = ph + (size_t)nc * a.S;
+            int32_t *pn = (int32_t *)(pl + (size_t)nc * a.S);
+            if (gr.valid) {
+                ph[(int64_t)c * a.S + gr.s] = acc.hi;
+                pl[(int64_t)c * a.S + gr.s] = acc.lo;
+                pn[(int64_t)c * a.S + gr.s] = nin;
+            }
+            __threadfence();
+            __syncwarp();
+            unsigned int done = 0;
+            if (lane == 0) done = atomicAdd(a.arrive + g, 1u);
+            done = __shfl_sync(0xffffffffu, done, 0);
+            if (done == (unsigned)(nc - 1)) {
+                // the group's last chunk: add the partial sums in chunk order
+                __threadfence();
+                if (gr.valid) {
+                    Acc<T> tot;
+                    int nt = 0;
+                    for (int k = 0; k < nc; ++k) {
+                        const int64_t o = (int64_t)k * a.S + gr.s;
+                        tot.add_pair(__ldcg(ph + o), __ldcg(pl + o));
+                        nt += __ldcg(pn + o);
+                    }
+                    ((T *)a.rss)[gr.s] = tot.value();
+                    a.n_in[gr.s] = nt;
+                }
+                if (lane == 0) a.arrive[g] = 0u;   // left zero for the next launch
+            }
         }
         __syncwarp();   // the next group's spheres overwrite this warp's slot
     }
@@ -675,7 +756,7 @@ __global__ void __launch_bounds__(kThreads, COMET_DCA_MINB) dca_tiled_kernel(F f
         tl.wn = wn;
         for (int i = tid; i < wn; i += kThreads) tile_wire_setup<T>(tl, i, in_prec<T>(a.lambda, a.lambda_f), capv, frm);
         __syncthreads();
-        group_wires<T, F>(f, a, gr, tl, sph0, sph1, lane, acc, nin, nunc);
+        group_wires<T, F>(f, a, gr, tl, sph0, sph1, lane, acc, nin, nunc, 0, wn);
         if (w0 + kWireTile < W) __syncthreads();   // tile consumed before the next staging
     }
 
@@ -719,8 +800,8 @@ static cudaError_t dca_launch(const F &fld, const DcaArgs &a, cudaStream_t st)
                                                           kThreads, L.total);
         if (e != cudaSuccess) return e;
         per_sm = per_sm < 1 ? 1 : per_sm;
-        const int64_t groups = (a.S + 31) / 32;
-        int64_t nb = (groups + kWarps - 1) / kWarps;
+        const int64_t items = (a.S + 31) / 32 * ((a.part && a.arrive) ? a.n_chunks : 1);
+        int64_t nb = (items + kWarps - 1) / kWarps;
         const int64_t cap = (int64_t)per_sm * sm_count();
         nb = nb < cap ? nb : cap;
         e = cudaMemsetAsync(a.counter, 0, sizeof(int32_t), st);
@@ -750,6 +831,12 @@ static cudaError_t dca_dispatch(const comet_field &f, const DcaArgs &a, cudaStre
         return dca_launch<T>(make_table<T>(f),
                              a, st);
     }
+}
+
+int dca_wire_chunks(int W)
+{
+    if (W <= 0 || W > kPersistMaxW) return 1;
+    return (W + COMET_DCA_CHUNK_W - 1) / COMET_DCA_CHUNK_W;
 }
 
 void dca_segments(int n_rec, int *G0, int *G1)
@@ -908,7 +995,7 @@ __global__ void __launch_bounds__(kThreads, COMET_DCA_BATCH_MINB) dca_batch_kern
             const float4 *s0 = (const float4 *)a.bounds + g * kBoundsPerGroup;   // read in place
             Acc<T> acc;
             int nin = 0;
-            group_wires<T, F>(f, a, gr, tl, s0, s0 + kN0Max, lane, acc, nin, nunc);
+            group_all_chunks<T, F>(f, a, gr, tl, s0, s0 + kN0Max, lane, acc, nin, nunc);
             if (gr.valid) {
                 ((T *)a.rss)[gr.s] = acc.value();
                 a.n_in[gr.s] = nin;

@@ -81,5 +81,9 @@ struct comet_ctx {
     void *scratch = nullptr;     // comet_scan_select's per-block partial results
     size_t scratch_bytes = 0;
     int32_t *status = nullptr;   // device status word (bit 0: bulk-copy timeout, bit 1: bad seed index)
+    void *dca_part = nullptr;    // comet_scan_dca's per-chunk partial sums
+    size_t dca_part_bytes = 0;
+    uint32_t *dca_arrive = nullptr;   // per-group arrival counters (kept zero between launches)
+    size_t dca_arrive_n = 0;
     comet::detail::BatchState batch;
 };

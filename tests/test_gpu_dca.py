@@ -226,3 +226,29 @@ def test_interleaved_table_is_bit_identical(ctx, dtype):
                     ev.hit_offsets, ev.drift, mask, dtype, want_dca=True) for il in (False, True)]
     for k in ("rss", "dca", "n_in"):
         assert np.array_equal(outs[0][k], outs[1][k]), k
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("use_bounds", [True, False])
+def test_pruned_search_keeps_wires_beyond_the_track_ends(ctx, dtype, use_bounds):
+    """Wires crossing the track's extension 0.875 of an interval past its last recorded state and
+    before its first: the refinement from the end state reaches them (DCA ~0.4-1 mm), although the
+    closest recorded state is ~14 mm away, beyond cap + h_rec/2.  The pruned path (segment spheres
+    from propagate or built by the DCA kernel) must still refine those pairs."""
+    from gpu_util import per_wire_residual, rss_bound
+    from track_ends import end_case
+    seeds, wires, offs, drift, n = end_case(UNIFORM)
+    lam = 2e-3
+    f64 = dtype == torch.float64
+    op, bp = both_params(n_steps=n, stride=16, lam=lam, tol=1e-12 if f64 else 1e-6)
+    mask = np.zeros(3, np.uint8)
+    g = gpu_dca(ctx, B.DeviceField.from_synth(UNIFORM), bp, seeds, -1, wires, offs, drift, mask, dtype,
+                want_dca=False, use_bounds=use_bounds)
+    r = O.scan(UNIFORM, op, seeds, -1, O.wires_aos(wires), offs, drift, mask, want_dca=True)
+    assert (np.abs(r["dca"][:, :2] - drift[:2]) < lam).all()   # the end wires are inliers in the oracle
+    if f64:
+        assert np.allclose(g["rss"], r["rss"], rtol=1e-10, atol=0)
+    else:
+        e = per_wire_residual(r["dca"], offs, drift, mask)
+        assert (np.abs(g["rss"] - r["rss"]) <= rss_bound(e, lam, 2e-6) + 1e-12).all()
+    assert np.array_equal(g["n_in"], r["n_in"])

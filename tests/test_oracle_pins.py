@@ -484,3 +484,28 @@ def test_backward_seed_retraces_the_turn():
     assert back.centre[0] - spec.centre[0] == pytest.approx(dz_turn, abs=1e-12)
     assert math.cos(back.centre[1] - spec.centre[1]) == pytest.approx(-1.0, abs=1e-12)
     assert back.centre[2] == -spec.centre[2] and back.centre[3] == spec.centre[3]
+
+
+def test_refinement_reaches_beyond_the_recorded_track():
+    """A wire crossing the track 0.875 of an interval past its last recorded state (or before its
+    first): the oracle's DCA equals the brute-force minimum of the distance over the track propagated
+    in 10 um steps (the refinement moves up to one interval from the closest recorded state)."""
+    from track_ends import end_case
+    U = synth.uniform_field(1.0)
+    seeds, wires, offs, drift, n = end_case(U, S=3)
+    P = O.Params(n_steps=n, stride=16, lam=2e-3, tol=1e-12)
+    wa = O.wires_aos(wires)
+    r = O.scan(U, P, seeds, -1, wa, offs, drift, np.zeros(3, np.uint8), want_dca=True)
+    fine = O.Params(h=1e-5, n_steps=200 * 100, stride=1)
+    for s in range(3):
+        for back in (False, True):
+            sd = seeds[s] * ([1, 1, 1, -1, -1, -1] if back else 1)
+            pts, nv = O.propagate(U, fine, sd[None], 1 if back else -1)
+            i = 1 if back else 0
+            lo = 150 * 100 if not back else 0
+            x = pts[0, lo: lo + 40 * 100, :3]
+            d = x - wa[i, :3]
+            d = d - (d @ wa[i, 3:])[:, None] * wa[i, 3:]
+            brute = np.sqrt((d * d).sum(1)).min()
+            assert abs(r["dca"][s, i] - brute) <= 1e-7, (s, i, r["dca"][s, i], brute)
+            assert brute < 1.5e-3
