@@ -29,7 +29,7 @@ struct Layout {
     int E;                   // event slots = caps.max_events
     int64_t nb_sel;          // select pass-1 blocks per event at most
     unsigned lat_blocks, prop_blocks, sel_blocks, cls_blocks, dca_ctas;
-    size_t ev, lat, prop, sel, cls, map, host_bytes, counters, scratch, dev_bytes;
+    size_t ev, lat, prop, sel, cls, map, host_bytes, counters, part, scratch, dev_bytes;
     size_t scratch_per_event;
 };
 
@@ -58,8 +58,10 @@ Layout make_layout(const comet_batch_caps &c, comet_dtype dt, unsigned dca_ctas)
     L.map = o;                               // DCA chunk prefix
     o = round_up(o + sizeof(int64_t) * (L.E + 1), 256);
     L.host_bytes = o;                        // copied host -> device on every batch
-    L.counters = o;                          // the DCA chunk counter
+    L.counters = o;                          // the DCA item counter
     o = round_up(o + sizeof(unsigned long long), 256);
+    L.part = o;                              // the DCA CTAs' partial sums
+    o = round_up(o + (size_t)dca_ctas * comet::kDcaBatchSub * 32 * (2 * (dt == COMET_F32 ? 4 : 8) + 4), 256);
     L.scratch_per_event = round_up((size_t)L.nb_sel * (sizeof(int64_t) + (dt == COMET_F32 ? 4 : 8)), 256);
     L.scratch = o;
     o += L.scratch_per_event * L.E;
@@ -184,7 +186,10 @@ comet_status comet_scan_batch_update(comet_ctx *ctx, comet_dtype dtype, const co
         sel[e + 1] = sel[e] + (S + comet::select_chunk() - 1) / comet::select_chunk();
         cls[e + 1] = cls[e] + (W > 0 && S > 0 ? (W + 7) / 8 : 0);
         groups[e] = (S + 31) / 32;
-        dstart[e + 1] = dstart[e] + (groups[e] + comet::kDcaBatchChunk - 1) / comet::kDcaBatchChunk;
+        {
+            const int gpi = comet::dca_batch_groups(comet::dca_wire_chunks(W));
+            dstart[e + 1] = dstart[e] + (groups[e] + gpi - 1) / gpi;
+        }
         if (!S) continue;
 
         comet_scan_params p = *params;
@@ -222,6 +227,7 @@ comet_status comet_scan_batch_update(comet_ctx *ctx, comet_dtype dtype, const co
     bs.launch.cls_start = (const int64_t *)(D + L.cls);
     bs.launch.dca_start = (const int64_t *)(D + L.map);
     bs.launch.chunk_counter = (unsigned long long *)(D + L.counters);
+    bs.launch.dca_part = D + L.part;
     bs.launch.B = L.E;
     bs.launch.lat_blocks = L.lat_blocks;
     bs.launch.prop_blocks = L.prop_blocks;

@@ -149,10 +149,14 @@ struct JacArgs {
 cudaError_t launch_jacobian(const JacArgs &a, cudaStream_t st);
 
 constexpr int kDcaWarpsPerCta = 4;   // warps of a persistent DCA CTA (128 threads)
-#ifndef COMET_DCA_BATCH_CHUNK
-#define COMET_DCA_BATCH_CHUNK 16
-#endif
-constexpr int kDcaBatchChunk = COMET_DCA_BATCH_CHUNK;   // 32-seed groups per chunk of the batched DCA launch
+// Batched DCA: a CTA takes one item of an event -- dca_batch_groups(n_chunks) consecutive 32-seed
+// groups, i.e. at most kDcaBatchSub (group, wire chunk) sub-items, which its warps share out.
+constexpr int kDcaBatchSub = 64;
+__host__ __device__ inline int dca_batch_groups(int n_chunks)
+{
+    const int g = kDcaBatchSub / (n_chunks > 0 ? n_chunks : 1);
+    return g > 0 ? g : 1;
+}
 
 // ---- batches of events (one turn partition each) in single launches ---------------------------
 // Every batched launch has a fixed grid; block b finds its event e and its block index inside the
@@ -173,8 +177,9 @@ struct BatchLaunch {
     const int64_t *prop_start;       // device [B + 1] prefix of propagate blocks (128 seeds)
     const int64_t *sel_start;        // device [B + 1] prefix of select pass-1 blocks
     const int64_t *cls_start;        // device [B + 1] prefix of classify blocks (8 wires)
-    const int64_t *dca_start;        // device [B + 1] prefix of DCA chunks (16 groups of 32 seeds)
-    unsigned long long *chunk_counter;  // device [1]: next DCA chunk
+    const int64_t *dca_start;        // device [B + 1] prefix of DCA items (dca_batch_groups groups)
+    unsigned long long *chunk_counter;  // device [1]: next DCA item
+    void *dca_part;                  // device: per DCA CTA, kDcaBatchSub x 32 partial sums (hi, lo in T; n_in int32)
     int B;
     unsigned lat_blocks, prop_blocks, sel_blocks, cls_blocks, dca_ctas;
     int W_max;                       // largest W of the caps (shared-memory layout of the DCA CTAs)

@@ -860,13 +860,15 @@ void dca_segments(int n_rec, int *G0, int *G1)
 }
 
 // ------------------------------------------------------------------------------------------------
-// Batch of events: persistent CTAs take chunks of kBatchChunk 32-seed groups from ONE counter over
-// all events (chunks numbered event by event, BL.dca_start the prefix), so the load balances across
-// events as it does across groups in the single-event kernel.  A CTA restages wires and hits only
-// when its next chunk belongs to another event (a few KB by bulk copy).  Shared memory is laid out
-// for the batch's largest W.
+// Batch of events: persistent CTAs take items -- dca_batch_groups(n_chunks) consecutive 32-seed
+// groups of one event -- from ONE counter over all events (items numbered event by event,
+// BL.dca_start the prefix), so the load balances across events as it does in the single-event
+// kernel.  Inside an item the warps share out its (group, wire chunk) sub-items from a shared
+// counter, park the partial sums in the CTA's slice of BL.dca_part, and add them per seed in chunk
+// order once the item is done (the single-event kernel's arithmetic).  A CTA restages wires and
+// hits only when its next item belongs to another event (a few KB by bulk copy).  Shared memory is
+// laid out for the batch's largest W.
 // ------------------------------------------------------------------------------------------------
-constexpr int kBatchChunk = kDcaBatchChunk;
 
 #ifndef COMET_DCA_BATCH_MINB
 #define COMET_DCA_BATCH_MINB 6   // the event's arguments come from a table, not the parameter bank
@@ -879,6 +881,7 @@ __global__ void __launch_bounds__(kThreads, COMET_DCA_BATCH_MINB) dca_batch_kern
     extern __shared__ __align__(128) unsigned char sm[];
     uint64_t *bar = (uint64_t *)sm;
     __shared__ int64_t s_chunk;
+    __shared__ int s_sub;
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const int warp = tid >> 5;
@@ -904,7 +907,10 @@ __global__ void __launch_bounds__(kThreads, COMET_DCA_BATCH_MINB) dca_batch_kern
     const Tile<T> &tl = s_tl;
     int nunc = 0;
     for (;;) {
-        if (tid == 0) s_chunk = (int64_t)atomicAdd((unsigned long long *)BL.chunk_counter, 1ull);
+        if (tid == 0) {
+            s_chunk = (int64_t)atomicAdd((unsigned long long *)BL.chunk_counter, 1ull);
+            s_sub = 0;
+        }
         __syncthreads();
         const int64_t chunk = s_chunk;
         if (chunk >= n_chunks) break;
@@ -986,23 +992,48 @@ __global__ void __launch_bounds__(kThreads, COMET_DCA_BATCH_MINB) dca_batch_kern
             for (int i = tid; i < W; i += kThreads) tile_wire_setup<T>(tl, i, in_prec<T>(a.lambda, a.lambda_f), capv, frm);
             __syncthreads();
         }
-        // the chunk's groups, one warp at a time
+        // the item's (group, wire chunk) sub-items, taken by the warps as they come free
+        const int nc = a.n_chunks;
         const int64_t n_groups = (a.S + 31) / 32;
-        const int64_t g0 = lc * kBatchChunk;
-        const int64_t g1 = min(g0 + kBatchChunk, n_groups);
-        for (int64_t g = g0 + warp; g < g1; g += kWarps) {
+        const int64_t g0 = lc * dca_batch_groups(nc);
+        const int ng = (int)min((int64_t)dca_batch_groups(nc), n_groups - g0);
+        const int n_sub = ng * nc;
+        T *ph = (T *)((unsigned char *)BL.dca_part +
+                      (size_t)blockIdx.x * kDcaBatchSub * 32 * (2 * sizeof(T) + 4));
+        T *pl = ph + kDcaBatchSub * 32;
+        int32_t *pn = (int32_t *)(pl + kDcaBatchSub * 32);
+        for (;;) {
+            int k = 0;
+            if (lane == 0) k = atomicAdd(&s_sub, 1);
+            k = __shfl_sync(0xffffffffu, k, 0);
+            if (k >= n_sub) break;
+            const int64_t g = g0 + k / nc;
             const Group<T> gr = load_group<T>(a, g, lane);
             const float4 *s0 = (const float4 *)a.bounds + g * kBoundsPerGroup;   // read in place
             Acc<T> acc;
             int nin = 0;
-            group_all_chunks<T, F>(f, a, gr, tl, s0, s0 + kN0Max, lane, acc, nin, nunc);
-            if (gr.valid) {
-                ((T *)a.rss)[gr.s] = acc.value();
-                a.n_in[gr.s] = nin;
-            }
-            __syncwarp();
+            const int2 r = chunk_range(a.W, nc, k % nc);
+            group_wires<T, F>(f, a, gr, tl, s0, s0 + kN0Max, lane, acc, nin, nunc, r.x, r.y);
+            ph[k * 32 + lane] = acc.hi;
+            pl[k * 32 + lane] = acc.lo;
+            pn[k * 32 + lane] = nin;
         }
-        __syncthreads();   // every warp done with this chunk before a restage or the next s_chunk
+        __syncthreads();   // every sub-item of the item done (and its partial sums visible)
+        for (int gi = warp; gi < ng; gi += kWarps) {
+            const int64_t s = (g0 + gi) * 32 + lane;
+            if (s < a.S) {
+                Acc<T> tot;
+                int nt = 0;
+                for (int c = 0; c < nc; ++c) {
+                    const int k = (gi * nc + c) * 32 + lane;
+                    tot.add_pair(ph[k], pl[k]);
+                    nt += pn[k];
+                }
+                ((T *)a.rss)[s] = tot.value();
+                a.n_in[s] = nt;
+            }
+        }
+        __syncthreads();   // every warp done with this item before a restage or the next s_chunk
     }
     if (cur >= 0 && a.n_unconv) {
         int t = nunc;
