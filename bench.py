@@ -387,7 +387,7 @@ DCA_FLOPS_PER_WIRE = 201
 DCA_FLOPS_PER_HIT = 8
 PROP_BYTES_PER_REC = 24
 
-# DRAM bytes (read + write) per launch of the two main kernels on this workload at stride 16, from a
+# DRAM bytes (read + write) per launch of the two main kernels on this workload at stride 32, from a
 # one-pass ncu launch list of `python bench.py` (dram__bytes_read.sum + dram__bytes_write.sum, mean
 # over its 80 DCA launches and 108 propagate launches: the bench re-runs lattice + propagate once
 # per partition, untimed, to count the recorded states).
@@ -451,7 +451,7 @@ def main():
     ap.add_argument("--steps", type=int, default=8)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--stride", type=int, default=16,
+    ap.add_argument("--stride", type=int, default=32,
                     help="record every stride-th RK4 state (h = 1 mm is unchanged)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-seconds", type=float, default=8.0)

@@ -41,6 +41,11 @@
 #ifndef COMET_DCA_U2
 #define COMET_DCA_U2 4
 #endif
+// 1: the candidate scan loads each state's momentum with its position and keeps the closest
+// state, so that the refinement starts without a second dependent load
+#ifndef COMET_DCA_SCAN_P
+#define COMET_DCA_SCAN_P 1
+#endif
 // wires per chunk of the per-seed sums (the persistent kernel's finest work item)
 #ifndef COMET_DCA_CHUNK_W
 #define COMET_DCA_CHUNK_W 32
@@ -349,27 +354,58 @@ __device__ __forceinline__ void group_wires(const F &f, const DcaArgs &a, const 
             const T capth = a.exact_all ? T(INFINITY) : cap + half_rec;
             T bd = T(INFINITY);
             int bk = 0x7fffffff;
+#if COMET_DCA_SCAN_P
+            // the closest state so far, loaded with the scan (no second round trip to refine)
+            T by[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+#endif
             // scans states [k0, k1) of this lane's seed, kU at a time (span is warp-uniform)
             auto scan = [&](int k0, int k1, int span) {
                 // one 64-bit multiply per range; states are S elements apart
                 const T *q0 = P + ((int64_t)k0 * S + s);
                 for (int t0 = 0; t0 < span; t0 += kU, q0 += kU * S) {
                     T xs[kU], ys[kU], zs[kU];
+#if COMET_DCA_SCAN_P
+                    T pxs[kU], pys[kU], pzs[kU];
+#endif
 #pragma unroll
                     for (int u = 0; u < kU; ++u) {
                         const int k = k0 + t0 + u;
                         xs[u] = ys[u] = zs[u] = T(0);
+#if COMET_DCA_SCAN_P
+                        pxs[u] = pys[u] = pzs[u] = T(0);
+#endif
                         if (want && k < k1) {
                             const T *q = q0 + u * S;
                             xs[u] = q[0];
                             ys[u] = q[plane];
                             zs[u] = q[2 * plane];
+#if COMET_DCA_SCAN_P
+                            pxs[u] = q[3 * plane];
+                            pys[u] = q[4 * plane];
+                            pzs[u] = q[5 * plane];
+#endif
                         }
                     }
 #pragma unroll
                     for (int u = 0; u < kU; ++u) {
                         const int k = k0 + t0 + u;
-                        if (want && k < k1) lex_min<T>(bd, bk, sd2(xs[u], ys[u], zs[u]), k);
+                        if (want && k < k1) {
+#if COMET_DCA_SCAN_P
+                            const T d = sd2(xs[u], ys[u], zs[u]);
+                            if (d < bd || (d == bd && k < bk)) {
+                                bd = d;
+                                bk = k;
+                                by[0] = xs[u];
+                                by[1] = ys[u];
+                                by[2] = zs[u];
+                                by[3] = pxs[u];
+                                by[4] = pys[u];
+                                by[5] = pzs[u];
+                            }
+#else
+                            lex_min<T>(bd, bk, sd2(xs[u], ys[u], zs[u]), k);
+#endif
+                        }
                     }
                 }
             };
@@ -413,9 +449,14 @@ __device__ __forceinline__ void group_wires(const F &f, const DcaArgs &a, const 
             T D = T(INFINITY);
             if (refine) {
                 T yv[6];
+#if COMET_DCA_SCAN_P
+#pragma unroll
+                for (int cc = 0; cc < 6; ++cc) yv[cc] = by[cc];
+#else
                 const int64_t o = (int64_t)bk * S + s;
 #pragma unroll
                 for (int cc = 0; cc < 6; ++cc) yv[cc] = P[cc * plane + o];
+#endif
                 const int conv = refine_dca<T, F>(f, gr.c, gr.ip, yv, ax, ay, az, ux, uy, uz, tol,
                                                   a.max_iter, h_rec, D);
                 if (cap >= T(0)) nunc += 1 - conv;

@@ -77,7 +77,7 @@ def _fp32_check(g, r, ev_offs, drift, mask, lam, delta=2e-6):
     assert np.array_equal(g["n_in"][sel], r["n_in"][sel])
 
 
-@pytest.mark.parametrize("stride", [1, 4, 16])
+@pytest.mark.parametrize("stride", [1, 4, 16, 24, 32])
 def test_fp32_matches_oracle_multi_turn_event(ctx, stride):
     ev = synth.multi_turn_event(0)
     seeds = O.lattice(ev.partitions[0])[::64].astype(np.float32).astype(np.float64)  # 4096 seeds

@@ -58,7 +58,7 @@ def test_fp64_points_match_oracle_single_event(ctx):
         assert np.abs(got[s, :n, 3:] - ref[s, :n, 3:]).max() <= 1e-9 * 105
 
 
-@pytest.mark.parametrize("stride", [1, 16])
+@pytest.mark.parametrize("stride", [1, 16, 24])
 def test_fp32_points_within_1um_over_three_turns(ctx, stride):
     """The compensated FP32 state (and, in an axial field, the per-seed interval map formed in
     float-float) stays within 1 um and 2e-6 relative momentum of the FP64 oracle over ~6,700 steps
@@ -134,7 +134,7 @@ def test_general_uniform_field_and_zero_charge(ctx):
 
 
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
-@pytest.mark.parametrize("stride", [1, 4, 16])
+@pytest.mark.parametrize("stride", [1, 4, 16, 24, 32])
 def test_search_bounds_contain_every_recorded_state(ctx, dtype, stride):
     """The segment spheres propagate writes for each 32-seed group contain every recorded state of
     the segment, for every seed of the group, including tracks stopped by the target region."""

@@ -43,7 +43,7 @@ def test_single_event_fp64_all_partitions(ctx):
         omask = r["mask"]
 
 
-@pytest.mark.parametrize("stride", [1, 4, 16])
+@pytest.mark.parametrize("stride", [1, 4, 16, 24, 32])
 def test_multi_turn_event_fp32_full_size_sampled(ctx, stride):
     ev = synth.multi_turn_event(4)
     spec = ev.partitions[0]

@@ -251,7 +251,7 @@ def test_dca_same_for_every_recording_stride(chamber):
     wires = O.wires_aos(ev.wires)
     mask = np.zeros(ev.n_hits, np.uint8)
     out = []
-    for stride in (1, 3, 8, 16, 24):
+    for stride in (1, 3, 8, 16, 24, 32):
         P = O.Params(n_steps=ev.n_steps[0], stride=stride)
         out.append(O.scan(synth.uniform_field(1.0), P, seeds, -1, wires, ev.hit_offsets, ev.drift,
                           mask, want_dca=True))
