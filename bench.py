@@ -393,8 +393,8 @@ PROP_BYTES_PER_REC = 24
 # per partition, untimed, to count the recorded states).
 # Valid only for the kernel sources they were measured on (SHA-1 of the package's csrc/ files);
 # reported as null once those change.
-NCU_TRAFFIC = {"csrc_sha1": "d6590ad1f1e39d2299edd30017819b2d62c0e537", "stride": 16,
-               "dca": 299012646.4, "propagate": 839353728.0}
+NCU_TRAFFIC = {"csrc_sha1": "4c2d35b62a3c2da130b0b0ec80bd384926dd665d", "stride": 32,
+               "dca": 206264620.8, "propagate": 402366836.1}
 
 
 def csrc_sha1() -> str:
