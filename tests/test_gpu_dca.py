@@ -252,3 +252,49 @@ def test_pruned_search_keeps_wires_beyond_the_track_ends(ctx, dtype, use_bounds)
         e = per_wire_residual(r["dca"], offs, drift, mask)
         assert (np.abs(g["rss"] - r["rss"]) <= rss_bound(e, lam, 2e-6) + 1e-12).all()
     assert np.array_equal(g["n_in"], r["n_in"])
+
+
+def _wires_case(n_wires, hits_per_wire=3, seed=7):
+    """The event's own wires first, then random chamber wires, n_wires in all; random drifts."""
+    ch = synth.make_chamber()
+    ev = synth.single_event_fp64(ch)
+    rng = np.random.default_rng(seed)
+    own = np.sort(np.asarray(ev.wire_ids))
+    if n_wires <= own.size:
+        ids = own[:n_wires]
+    else:
+        rest = np.setdiff1d(np.arange(ch.n_wires), own)
+        ids = np.concatenate([own, rng.choice(rest, size=n_wires - own.size, replace=False)])
+    wires = np.concatenate([ch.a[:, ids], ch.u[:, ids]], axis=0)
+    offs = np.arange(ids.size + 1, dtype=np.int32) * hits_per_wire
+    drift = rng.uniform(0, 8e-3, size=offs[-1])
+    mask = (rng.uniform(size=offs[-1]) < 0.2).astype(np.uint8)
+    return ev, wires, offs, drift, mask
+
+
+@pytest.mark.parametrize("n_wires", [1, 32, 33, 64, 65, 1024, 1025])
+def test_wire_chunk_boundaries(ctx, n_wires):
+    """Each seed's sum is cut into chunks of at most 32 wires, one work item per (32-seed group,
+    chunk), the chunk sums added in chunk order; W = 1025 takes the tiled kernel instead.  At the
+    chunk boundaries: FP64 RSS within the bound that the 1e-9 m DCA bar implies term by term (a
+    single small residual makes any relative bar meaningless) plus the summation order, n_in equal
+    away from the cutoff, pruned and exact paths; and FP32 sums bit-identical from run to run (no
+    dependence on which warp finishes a group last)."""
+    ev, wires, offs, drift, mask = _wires_case(n_wires)
+    assert wires.shape[1] == n_wires
+    seeds = O.lattice(ev.partitions[0])[::7].astype(np.float32).astype(np.float64)   # 586 seeds
+    f = B.DeviceField.from_synth(UNIFORM)
+    lam = 0.01
+    op, bp = both_params(n_steps=ev.n_steps[0], stride=16, lam=lam, tol=1e-12)
+    r = O.scan(UNIFORM, op, seeds, -1, O.wires_aos(wires), offs, drift, mask, want_dca=True)
+    e = per_wire_residual(r["dca"], offs, drift, mask)
+    bound = rss_bound(e, lam, 1e-9, fp32=False) + 1e-14 * r["rss"]
+    edge = (np.abs(e - lam) < 1e-9).any(1)
+    for want in (True, False):
+        g = gpu_dca(ctx, f, bp, seeds, -1, wires, offs, drift, mask, torch.float64, want_dca=want)
+        assert (np.abs(g["rss"] - r["rss"]) <= bound).all()
+        assert np.array_equal(g["n_in"][~edge], r["n_in"][~edge])
+    _, bp32 = both_params(n_steps=ev.n_steps[0], stride=16, lam=0.01, tol=1e-6)
+    a = gpu_dca(ctx, f, bp32, seeds, -1, wires, offs, drift, mask, torch.float32, want_dca=False)
+    b = gpu_dca(ctx, f, bp32, seeds, -1, wires, offs, drift, mask, torch.float32, want_dca=False)
+    assert np.array_equal(a["rss"], b["rss"]) and np.array_equal(a["n_in"], b["n_in"])
