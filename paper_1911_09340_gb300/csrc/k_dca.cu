@@ -39,7 +39,7 @@
 #define COMET_DCA_MINB 8
 #endif
 #ifndef COMET_DCA_U2
-#define COMET_DCA_U2 4
+#define COMET_DCA_U2 2
 #endif
 // 1: the candidate scan loads each state's momentum with its position and keeps the closest
 // state, so that the refinement starts without a second dependent load
