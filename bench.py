@@ -393,8 +393,8 @@ PROP_BYTES_PER_REC = 24
 # per partition, untimed, to count the recorded states).
 # Valid only for the kernel sources they were measured on (SHA-1 of the package's csrc/ files);
 # reported as null once those change.
-NCU_TRAFFIC = {"csrc_sha1": "4c2d35b62a3c2da130b0b0ec80bd384926dd665d", "stride": 32,
-               "dca": 206264620.8, "propagate": 402366836.1}
+NCU_TRAFFIC = {"csrc_sha1": "dacf632c29cc13ea48ff1fd71abb064d0b51e8d0", "stride": 32,
+               "dca": 206326204.8, "propagate": 402080974.2}
 
 
 def csrc_sha1() -> str:
