@@ -150,3 +150,47 @@ def test_gradient_in_the_six_cartesian_seed_components(ctx):
         sm[:, k] -= eps[k]
         fd = (O.smoothed_rss_seeds(UNIFORM, P, sp, *args)[0] - O.smoothed_rss_seeds(UNIFORM, P, sm, *args)[0]) / (2 * eps[k])
         assert np.allclose(g6[:, k], fd, rtol=1e-4, atol=1e-4 * np.abs(fd).max() + 1e-15), (k, g6[:, k], fd)
+
+
+@pytest.mark.gpu
+def test_smoothed_rss_autograd_functions(ctx):
+    """torch.autograd through the smoothed RSS: backward of SmoothedRSS gives the kernel's gradient
+    in theta (scaled by the incoming gradient), SmoothedRSSCartesian the six-component one, and the
+    latter equals central finite differences of the oracle's smoothed RSS of Cartesian seeds."""
+    import torch
+    from paper_1911_09340_gb300 import autodiff as A
+    from paper_1911_09340_gb300 import binding as B
+    from paper_1911_09340_gb300 import scan
+    ev = synth.single_event_fp64()
+    t0 = _truth_theta(ev)
+    theta_np = np.stack([t0, t0 + [0.002, -0.002, 0.3, -0.4], t0 + [-0.001, 0.001, -0.2, 0.2]])
+    lam, tau, stride = 8e-4, 1e-3, 16
+    spec = A.SmoothedRSSSpec(ctx, B.DeviceField.from_synth(UNIFORM),
+                             B.ScanParams(n_steps=ev.n_steps[0], stride=stride, lam=lam, tol=1e-12),
+                             scan.DeviceEvent.from_event(ev, torch.float64), -1, tau)
+    theta = torch.tensor(theta_np, dtype=torch.float64, device="cuda", requires_grad=True)
+    s = A.SmoothedRSS.apply(theta, spec, ev.vertex[0], ev.vertex[1])
+    w = torch.tensor([1.0, -2.0, 0.5], dtype=torch.float64, device="cuda")
+    (s * w).sum().backward()
+    srss, grad, grad6 = A._evaluate(spec, theta.detach(), ev.vertex[0], ev.vertex[1])
+    assert torch.equal(s.detach(), srss)
+    assert torch.equal(theta.grad, w[:, None] * grad)
+
+    seeds_np = O.seeds_from_theta(theta_np, ev.vertex[0], ev.vertex[1])
+    seeds = torch.tensor(seeds_np, dtype=torch.float64, device="cuda", requires_grad=True)
+    s6 = A.SmoothedRSSCartesian.apply(seeds, spec)
+    s6.sum().backward()
+    assert torch.allclose(s6.detach(), srss, rtol=1e-12, atol=0)
+    g6 = seeds.grad.cpu().numpy()
+    P = O.Params(n_steps=ev.n_steps[0], stride=stride, lam=lam, tol=1e-12)
+    args = (-1, O.wires_aos(ev.wires), ev.hit_offsets, ev.drift, np.zeros(ev.n_hits, np.uint8), tau)
+    eps = [1e-6, 1e-6, 1e-6, 1e-4, 1e-4, 1e-4]
+    for k in range(6):
+        sp, sm = seeds_np.copy(), seeds_np.copy()
+        sp[:, k] += eps[k]
+        sm[:, k] -= eps[k]
+        fd = (O.smoothed_rss_seeds(UNIFORM, P, sp, *args)[0] - O.smoothed_rss_seeds(UNIFORM, P, sm, *args)[0]) / (2 * eps[k])
+        assert np.allclose(g6[:, k], fd, rtol=1e-4, atol=1e-4 * np.abs(fd).max() + 1e-15), (k, g6[:, k], fd)
+    with pytest.raises(ValueError):
+        A.SmoothedRSSCartesian.apply(seeds.detach() + torch.tensor([0.0, 1e-3, 0, 0, 0, 0], device="cuda",
+                                                                    dtype=torch.float64) * torch.arange(3, device="cuda", dtype=torch.float64)[:, None], spec)
