@@ -1,28 +1,30 @@
 // DCA finding and RSS (Algorithm 2, Eq. 1, Sec. 2.2.2).
 //
-// Layout of the work: one thread per seed, 128 seeds per CTA, all wires per seed.  The wire
-// geometry, the CSR hit offsets and (when they fit) the drift distances and masks are staged in
-// shared memory with the bulk-copy engine (cp.async.bulk + mbarrier), in tiles of 128 wires.
+// Layout of the work: one thread per seed, a warp per 32-seed group.  The persistent kernel (up to
+// 1024 wires) stages every wire's geometry, the CSR hit offsets and (when they fit) the drift
+// distances and masks once per CTA in shared memory with the bulk-copy engine (cp.async.bulk +
+// mbarrier), and its warps take (group, wire chunk) items; the tiled kernel (more wires) stages
+// them in tiles of 256 wires per 128-seed CTA.
 //
 // Closest recorded state of a (seed, wire) pair, found exactly without visiting every state.  The
 // recorded states of each seed are cut into at most 8 super-segments of G0 states, each cut into at
 // most 24 level-1 segments of G1 states.  Because the seed lattice numbers neighbouring nodes
 // consecutively, the 32 tracks of a warp are close, and one bounding sphere per segment covers all
-// 32 of them: its centre is one lane's segment centre C, its radius the largest distance from C to
-// any lane's segment centre plus (g/2) h_rec (a recorded state within g/2 recording intervals of a
-// centre is at most that far from it along the track).  Every recorded state x of that segment of
-// every seed of the warp then satisfies dist(x, wire) >= dist(C, wire) - radius.  The spheres live
-// in shared memory.  For each wire, the lanes test the spheres in parallel (lane t: wire t against
-// the super-segment spheres; then lane m: level-1 sphere m of a candidate super-segment) and only
-// segments whose bound does not exceed the wire's capture radius (largest unmasked drift + lambda +
-// h_rec/2) are scanned state by state, each lane its own seed's states, keeping the lexicographic
-// (distance, index) minimum.  If a seed's closest state is within the capture radius it lies in a
+// 32 of them: its centre is the midpoint of the first and the last lane's segment centres, its
+// radius the largest distance from it to any lane's segment centre plus (g/2) h_rec (a recorded
+// state within g/2 recording intervals of a centre is at most that far from it along the track).
+// Every recorded state x of that segment of every seed of the warp then satisfies
+// dist(x, wire) >= dist(C, wire) - radius.  The spheres are read in place from the table the
+// recording kernel wrote (or built in shared memory when no table is given).  For each wire, the
+// lanes test the spheres in parallel (lane t: wire t against the super-segment spheres; then lane
+// m: level-1 sphere m of a candidate super-segment) and only segments whose bound does not exceed
+// the wire's capture radius (largest unmasked drift + lambda + h_rec/2) are scanned state by
+// state, each lane its own seed's states, keeping the lexicographic (distance, index) minimum.  If a seed's closest state is within the capture radius it lies in a
 // scanned segment, so the minimum is exact; if not, every residual of the wire is at least lambda
 // and the wire adds exactly lambda^2 to the RSS, with or without a refinement.  Beyond the first
 // and the last recorded state the refinement reaches up to h_rec (not h_rec/2) from the nearest
 // recorded state, so segments that may hold a track end are tested, and an end state refined,
-// within capture radius + h_rec.  With dca_out every state is scanned (exact DCA for
-// every wire).
+// within capture radius + h_rec.  With dca_out every state is scanned (exact DCA for every wire).
 //
 // RSS: each thread sums its wires' d_i^2 in ascending wire order within each wire chunk (FP32 as a
 // TwoSum pair, FP64 plainly), then the chunks' sums in chunk order.  Atomics only hand out work
@@ -517,8 +519,9 @@ __device__ __forceinline__ bool finish_stage(uint64_t *bar, uint32_t &parity, ui
 
 // ------------------------------------------------------------------------------------------------
 // Persistent kernel: all wires fit one shared-memory tile (the common case).  Each CTA stages the
-// wires and hits once; each warp then takes 32-seed groups from a device counter until none is left,
-// with no CTA-wide barrier between groups.
+// wires and hits once; each warp then takes work items -- (32-seed group, wire chunk) pairs, or
+// whole groups when no partial-sum scratch is given -- from a device counter until none is left,
+// with no CTA-wide barrier between items.
 // ------------------------------------------------------------------------------------------------
 
 struct PLayout {
