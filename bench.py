@@ -393,8 +393,8 @@ PROP_BYTES_PER_REC = 24
 # per partition, untimed, to count the recorded states).
 # Valid only for the kernel sources they were measured on (SHA-1 of the package's csrc/ files);
 # reported as null once those change.
-NCU_TRAFFIC = {"csrc_sha1": "dacf632c29cc13ea48ff1fd71abb064d0b51e8d0", "stride": 32,
-               "dca": 206326204.8, "propagate": 402080974.2}
+NCU_TRAFFIC = {"csrc_sha1": "3db314dd2473bf2a33c88b838cccc0d8ce729ee8", "stride": 32,
+               "dca": 206332217.6, "propagate": 402410285.0}
 
 
 def csrc_sha1() -> str:
