@@ -509,3 +509,41 @@ def test_refinement_reaches_beyond_the_recorded_track():
             brute = np.sqrt((d * d).sum(1)).min()
             assert abs(r["dca"][s, i] - brute) <= 1e-7, (s, i, r["dca"][s, i], brute)
             assert brute < 1.5e-3
+
+
+def _golden(name):
+    import os
+    vals = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", name)) as f:
+        for line in f:
+            line = line.split("#", 1)[0].split()
+            if len(line) == 2:
+                vals[line[0]] = float(line[1])
+    return vals
+
+
+def test_helix_radius_and_pitch_follow_eq3():
+    """The recorded track of a 104.97 MeV/c electron with p_T = 101 MeV/c in 1 T (tests/golden/
+    helix_curvature.txt, Eq. 3): the circle through its transverse positions has radius
+    p_T / (0.3 B) mm to the rounding of Eq. 3's 0.3 (7e-4 relative), p_T / (kappa B) to 1e-9 m with
+    the exact kappa, and the track advances 2 pi R p_z / p_T along z per turn."""
+    g = _golden("helix_curvature.txt")
+    pT, p, B = g["pT_MeV"], g["p_MeV"], g["B_T"]
+    pz = math.sqrt(p * p - pT * pT)
+    R_eq3 = pT / (g["kappa_eq3"] * B) * 1e-3          # m
+    R_exact = pT / (299.792458 * B)
+    n = 2200
+    seed = np.array([[0.0, 0.0, 0.0, pT, 0.0, pz]])
+    pts, nv = O.propagate(synth.uniform_field(B), O.Params(n_steps=n, **OPEN), seed, -1)
+    x, y, z = pts[0, : nv[0], 0], pts[0, : nv[0], 1], pts[0, : nv[0], 2]
+    # algebraic circle fit x^2 + y^2 + D x + E y + F = 0 (least squares)
+    A = np.stack([x, y, np.ones_like(x)], axis=1)
+    D, E, F = np.linalg.lstsq(A, -(x * x + y * y), rcond=None)[0]
+    R = math.sqrt(D * D / 4 + E * E / 4 - F)
+    assert abs(R - R_eq3) / R_eq3 < 1e-3
+    assert abs(R - R_exact) < 1e-9
+    # z advance per turn: z(s) = (p_z / p) s, one turn is s = 2 pi R p / p_T
+    s_turn = 2 * math.pi * R_exact * p / pT
+    k = int(round(s_turn / 1e-3))
+    assert abs(z[k] - pz / p * k * 1e-3) < 1e-12
+    assert abs(math.hypot(x[k], y[k])) < 2e-3           # back near the start after one turn
