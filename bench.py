@@ -393,8 +393,8 @@ PROP_BYTES_PER_REC = 24
 # per partition, untimed, to count the recorded states).
 # Valid only for the kernel sources they were measured on (SHA-1 of the package's csrc/ files);
 # reported as null once those change.
-NCU_TRAFFIC = {"csrc_sha1": "3db314dd2473bf2a33c88b838cccc0d8ce729ee8", "stride": 32,
-               "dca": 206332217.6, "propagate": 402410285.0}
+NCU_TRAFFIC = {"csrc_sha1": "98b517e64c36932de778f78442187d9ccc6d7dc4", "stride": 32,
+               "dca": 206323827.2, "propagate": 402434688.0}
 
 
 def csrc_sha1() -> str:

@@ -197,6 +197,7 @@ comet_status comet_scan_batch_update(comet_ctx *ctx, comet_dtype dtype, const co
         const SearchGeometry sg = search_geometry(dtype, &p);
         // lattice
         fill_lat(x->lattice, x->charge, &be.lat);
+        fill_lat_table(be.lat, &be.lat_tab);
         be.seeds = x->seeds;
         // propagate
         fill_prop(dtype, &p, sg, x->seeds, x->charge, S, x->points, x->n_valid, x->bounds, &be.prop);

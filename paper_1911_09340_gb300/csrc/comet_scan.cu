@@ -148,6 +148,37 @@ void fill_lat(const comet_lattice &lat, int8_t *charge_out, LatArgs *a)
     a->charge_out = charge_out;
 }
 
+// Node i of n of one lattice dimension: centre + half_width (2 i / (n - 1) - 1), each operation
+// rounded on its own (no fused multiply-add), the same arithmetic as the oracle's lattice.
+static double host_lattice_node(double centre, double half_width, int n, int i)
+{
+    if (n == 1) return centre;
+    volatile double q = (2.0 * i) / (double)(n - 1);
+    volatile double t = q - 1.0;
+    volatile double u = half_width * t;
+    return centre + u;
+}
+
+void fill_lat_table(const LatArgs &a, LatTable *t)
+{
+    t->use = 0;
+    int tot = 0;
+    for (int d = 0; d < 4; ++d) tot += a.counts[d];
+    if (tot > kLatParamNodes || a.counts[1] > kLatParamPhi) return;
+    int o = 0;
+    for (int d = 0; d < 4; ++d) {
+        for (int k = 0; k < a.counts[d]; ++k)
+            t->node[o + k] = host_lattice_node(a.centre[d], a.half_width[d], a.counts[d], k);
+        o += a.counts[d];
+    }
+    for (int k = 0; k < a.counts[1]; ++k) {
+        const double v = t->node[a.counts[0] + k];
+        t->cphi[k] = std::cos(v);
+        t->sphi[k] = std::sin(v);
+    }
+    t->use = 1;
+}
+
 void fill_prop(comet_dtype, const comet_scan_params *p, const SearchGeometry &sg, const void *seeds,
                const int8_t *charge, int64_t S, void *points, int32_t *n_valid, void *bounds, PropArgs *a)
 {
@@ -333,7 +364,9 @@ comet_status comet_scan_lattice(comet_ctx *ctx, comet_dtype dtype, const comet_l
     if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
     comet::LatArgs a;
     fill_lat(*lat, charge_out, &a);
-    cudaError_t e = comet::launch_lattice(dtype, a, seeds, S, (cudaStream_t)stream);
+    comet::LatTable t;
+    fill_lat_table(a, &t);
+    cudaError_t e = comet::launch_lattice(dtype, a, t, seeds, S, (cudaStream_t)stream);
     return e == cudaSuccess ? COMET_OK : cuda_fail(e, "lattice launch");
 }
 

@@ -22,6 +22,17 @@ struct LatArgs {
     int8_t *charge_out;
 };
 
+// Node values of a lattice's four dimensions and cos / sin of its phi nodes, computed once on the
+// host (per block on the device they cost double divisions and sincos in every block); use = 0
+// when the counts exceed the table (the kernel then tabulates per block).
+constexpr int kLatParamNodes = 128;
+constexpr int kLatParamPhi = 64;
+struct LatTable {
+    int use;
+    double node[kLatParamNodes];
+    double cphi[kLatParamPhi], sphi[kLatParamPhi];
+};
+
 struct PropArgs {
     const void *seeds;
     const int8_t *charge;
@@ -112,7 +123,8 @@ struct ClsArgs {
     int update_mask;
 };
 
-cudaError_t launch_lattice(comet_dtype dt, const LatArgs &a, void *seeds, int64_t S, cudaStream_t st);
+cudaError_t launch_lattice(comet_dtype dt, const LatArgs &a, const LatTable &t, void *seeds, int64_t S,
+                           cudaStream_t st);
 cudaError_t launch_lattice_refined(comet_dtype dt, const LatArgs &a, const double *refs,
                                    const int32_t *n_refs, int K, void *seeds, int64_t S,
                                    cudaStream_t st);
@@ -163,6 +175,7 @@ __host__ __device__ inline int dca_batch_groups(int n_chunks)
 // event from a prefix array start[0..B] (start[e] <= b < start[e+1]); blocks past start[B] exit.
 struct BatchEvent {
     LatArgs lat;
+    LatTable lat_tab;
     void *seeds;
     int64_t S;
     PropArgs prop;

@@ -41,20 +41,25 @@ constexpr int kLatTab = 512;   // node values tabulated per block when the four 
 // BATCH: one launch for the lattices of a batch of events; block b belongs to the event that
 // batch_find gives (refs unused).
 template <typename T, bool BATCH>
-__global__ void __launch_bounds__(256) lattice_kernel(LatArgs a, const double *__restrict__ refs,
+__global__ void __launch_bounds__(256) lattice_kernel(LatArgs a, const __grid_constant__ LatTable lt,
+                                                      const double *__restrict__ refs,
                                                       const int32_t *__restrict__ n_refs,
                                                       T *__restrict__ seeds, int64_t S1, int64_t S,
                                                       BatchLaunch L)
 {
-    // every node value (and cos / sin of every phi node) once per block, in shared memory
+    // the host's table of node values and phi-node cos / sin when there is one (lt, read in place,
+    // or the batch event's copy); otherwise every node value (and cos / sin of every phi node)
+    // once per block, in shared memory
     __shared__ double nodes[kLatTab];
     __shared__ double cphi[kLatTab], sphi[kLatTab];
     int64_t bx = blockIdx.x;
+    const LatTable *tp = (!BATCH && lt.use && !refs) ? &lt : nullptr;
     if constexpr (BATCH) {
         int e;
         int64_t lb;
         if (!batch_find(L.lat_start, L.B, blockIdx.x, e, lb)) return;
         a = L.ev[e].lat;
+        tp = L.ev[e].lat_tab.use ? &L.ev[e].lat_tab : nullptr;
         seeds = (T *)L.ev[e].seeds;
         S1 = S = L.ev[e].S;
         bx = lb;
@@ -69,7 +74,7 @@ __global__ void __launch_bounds__(256) lattice_kernel(LatArgs a, const double *_
     off[0] = 0;
     for (int d = 1; d < 4; ++d) off[d] = off[d - 1] + a.counts[d - 1];
     const int tot = off[3] + a.counts[3];
-    const bool tab = tot <= kLatTab;
+    const bool tab = !tp && tot <= kLatTab;
     if (tab) {
         for (int i = threadIdx.x; i < tot; i += blockDim.x) {
             const int d = i < off[1] ? 0 : (i < off[2] ? 1 : (i < off[3] ? 2 : 3));
@@ -100,7 +105,12 @@ __global__ void __launch_bounds__(256) lattice_kernel(LatArgs a, const double *_
         ii[d] = i_bl * b[d] + i_in;
     }
     double v[4], sp, cp;
-    if (tab) {
+    if (tp) {
+#pragma unroll
+        for (int d = 0; d < 4; ++d) v[d] = tp->node[off[d] + ii[d]];
+        sp = tp->sphi[ii[1]];
+        cp = tp->cphi[ii[1]];
+    } else if (tab) {
 #pragma unroll
         for (int d = 0; d < 4; ++d) v[d] = nodes[off[d] + ii[d]];
         sp = sphi[ii[1]];
@@ -397,34 +407,47 @@ __global__ void __launch_bounds__(128) propagate_kernel(F f, PropArgs a, BatchLa
     if (valid) a.n_valid[s] = n;
 }
 
-cudaError_t launch_lattice(comet_dtype dt, const LatArgs &a, void *seeds, int64_t S, cudaStream_t st)
-{
-    return launch_lattice_refined(dt, a, nullptr, nullptr, 1, seeds, S, st);
-}
-
-cudaError_t launch_lattice_refined(comet_dtype dt, const LatArgs &a, const double *refs,
-                                   const int32_t *n_refs, int K, void *seeds, int64_t S,
-                                   cudaStream_t st)
+static cudaError_t lattice_launch(comet_dtype dt, const LatArgs &a, const LatTable &t,
+                                  const double *refs, const int32_t *n_refs, int K, void *seeds,
+                                  int64_t S, cudaStream_t st)
 {
     const int nt = 256;
     const int64_t S1 = S / K;
     const dim3 grid((unsigned)((S1 + nt - 1) / nt), (unsigned)K);
     const BatchLaunch none{};
     if (dt == COMET_F32)
-        lattice_kernel<float, false><<<grid, nt, 0, st>>>(a, refs, n_refs, (float *)seeds, S1, S, none);
+        lattice_kernel<float, false><<<grid, nt, 0, st>>>(a, t, refs, n_refs, (float *)seeds, S1, S, none);
     else
-        lattice_kernel<double, false><<<grid, nt, 0, st>>>(a, refs, n_refs, (double *)seeds, S1, S, none);
+        lattice_kernel<double, false><<<grid, nt, 0, st>>>(a, t, refs, n_refs, (double *)seeds, S1, S, none);
     return cudaGetLastError();
+}
+
+cudaError_t launch_lattice(comet_dtype dt, const LatArgs &a, const LatTable &t, void *seeds, int64_t S,
+                           cudaStream_t st)
+{
+    return lattice_launch(dt, a, t, nullptr, nullptr, 1, seeds, S, st);
+}
+
+cudaError_t launch_lattice_refined(comet_dtype dt, const LatArgs &a, const double *refs,
+                                   const int32_t *n_refs, int K, void *seeds, int64_t S,
+                                   cudaStream_t st)
+{
+    // the centres are the references on the device: tabulated per block
+    LatTable none;
+    none.use = 0;
+    return lattice_launch(dt, a, none, refs, n_refs, K, seeds, S, st);
 }
 
 cudaError_t launch_lattice_batch(comet_dtype dt, const BatchLaunch &L, cudaStream_t st)
 {
     if (L.lat_blocks == 0) return cudaSuccess;
     const LatArgs none{};
+    LatTable no_tab;
+    no_tab.use = 0;
     if (dt == COMET_F32)
-        lattice_kernel<float, true><<<L.lat_blocks, 256, 0, st>>>(none, nullptr, nullptr, nullptr, 0, 0, L);
+        lattice_kernel<float, true><<<L.lat_blocks, 256, 0, st>>>(none, no_tab, nullptr, nullptr, nullptr, 0, 0, L);
     else
-        lattice_kernel<double, true><<<L.lat_blocks, 256, 0, st>>>(none, nullptr, nullptr, nullptr, 0, 0, L);
+        lattice_kernel<double, true><<<L.lat_blocks, 256, 0, st>>>(none, no_tab, nullptr, nullptr, nullptr, 0, 0, L);
     return cudaGetLastError();
 }
 

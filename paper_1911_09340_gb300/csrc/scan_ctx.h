@@ -61,6 +61,7 @@ SearchGeometry search_geometry(comet_dtype dtype, const comet_scan_params *p);
 
 // Argument blocks of the kernels, from validated arguments.
 void fill_lat(const comet_lattice &lat, int8_t *charge_out, LatArgs *a);
+void fill_lat_table(const LatArgs &a, LatTable *t);
 void fill_prop(comet_dtype dtype, const comet_scan_params *p, const SearchGeometry &sg, const void *seeds,
                const int8_t *charge, int64_t S, void *points, int32_t *n_valid, void *bounds, PropArgs *a);
 void fill_dca(comet_ctx *ctx, comet_dtype dtype, const comet_scan_params *p, const SearchGeometry &sg,
