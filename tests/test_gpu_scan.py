@@ -131,3 +131,41 @@ def test_stage_metrics_from_gpu_equal_oracle_at_0_8_mm(ctx):
     for a, b in zip(g, o):
         assert np.array_equal(a, b)
     assert M.event_metrics(g, ev.hit_turn) == M.event_metrics(o, ev.hit_turn)
+
+
+def test_sixteen_million_seed_partition_needs_64bit_offsets(ctx):
+    """2^24 seeds (a 64^4 lattice) at stride 32: the track points hold 6 x 70 x 2^24 = 7.0e9 values
+    (28 GB), so offsets into them, into the search bounds and into the partial sums exceed 32 bits.
+    Sampled seeds -- among them the last one, at the highest offsets -- and the selected seed
+    against the oracle within the bound the FP32 DCAs imply; the selection is the argmin of the
+    RSS the GPU computed."""
+    ev = synth.multi_turn_event(4, counts=(64, 64, 64, 64))
+    spec = ev.partitions[0]
+    S = spec.n_seeds
+    assert S == 1 << 24
+    f = B.DeviceField.from_synth(UNIFORM)
+    dev = scan.DeviceEvent.from_event(ev, torch.float32)
+    bp = scan.event_params(ev, torch.float32, stride=32)[0]
+    assert 6 * bp.n_rec * S > 1 << 32
+    ws = scan.Workspace(S, bp.n_rec, ev.n_hits, torch.float32)
+    scan.scan_partition(ctx, f, bp, spec, dev, ws)
+    torch.cuda.synchronize()
+    g_rss = ws.rss[:S].double().cpu().numpy()
+    g_idx = int(ws.idx[0])
+    assert g_rss[g_idx] == g_rss.min() and g_idx == int(np.flatnonzero(g_rss == g_rss.min())[0])
+    assert np.all(g_rss >= 0) and np.all(np.isfinite(g_rss))
+    del ws
+    torch.cuda.empty_cache()
+    seeds = O.lattice(spec).astype(np.float32).astype(np.float64)
+    rng = np.random.default_rng(1)
+    sample = np.unique(np.concatenate([rng.choice(S, 256, replace=False), [g_idx, S - 1, S - 33]]))
+    op = O.Params(n_steps=bp.n_steps, stride=bp.stride, lam=bp.lam, tol=1e-12)
+    mask = np.zeros(ev.n_hits, np.uint8)
+    r = O.scan(UNIFORM, op, seeds[sample], -1, O.wires_aos(ev.wires), ev.hit_offsets, ev.drift,
+               mask, want_dca=True)
+    e = per_wire_residual(r["dca"], ev.hit_offsets, ev.drift, mask)
+    bound = rss_bound(e, bp.lam, 2e-6)
+    ok = np.abs(g_rss[sample] - r["rss"]) <= bound + 1e-12
+    assert ok.mean() >= 0.99 and ok[np.searchsorted(sample, [S - 1])].all()
+    r_best = r["rss"][np.searchsorted(sample, g_idx)]
+    assert r_best <= r["rss"].min() * (1 + 1e-5)
