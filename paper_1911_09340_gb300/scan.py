@@ -185,7 +185,16 @@ class HostEventRunner:
         return dict(w=w.pin_memory(), o=torch.as_tensor(ev.hit_offsets, dtype=torch.int32).pin_memory(),
                     d=torch.as_tensor(ev.drift, dtype=dtype).pin_memory(), W=W, H=ev.n_hits)
 
-    def run(self, ev, pinned, stride: int = 1, lam: float = 1e-2):
+    def result_slots(self):
+        """Pinned host buffers for one event's results (best seed index and RSS per partition, the
+        final hit mask), so that results of events in flight are not overwritten."""
+        return (torch.zeros(16, dtype=torch.int64).pin_memory(), torch.zeros(16, dtype=self.dtype).pin_memory(),
+                torch.zeros(self.h_mask.numel(), dtype=torch.uint8).pin_memory())
+
+    def run(self, ev, pinned, stride: int = 1, lam: float = 1e-2, out=None):
+        """Enqueues the event on the current stream (copies in, every partition, copies out) and
+        returns (bytes in, bytes out); the results land in ``out`` (``result_slots()``) or in the
+        runner's own buffers once the stream reaches them."""
         W, H = pinned["W"], pinned["H"]
         ldw = pinned["w"].shape[1]
         w = self.dev_w.view(-1)[: 6 * ldw].view(6, ldw)
@@ -201,8 +210,9 @@ class HostEventRunner:
             scan_partition(self.ctx, self.field, p, spec, dev, self.ws)
             self.res_idx[i:i + 1].copy_(self.ws.idx[:1])
             self.res_rss[i:i + 1].copy_(self.ws.best[:1])
-        self.h_idx[:n].copy_(self.res_idx[:n], non_blocking=True)
-        self.h_rss[:n].copy_(self.res_rss[:n], non_blocking=True)
-        self.h_mask[:H].copy_(self.dev_m[:H], non_blocking=True)
+        h_idx, h_rss, h_mask = out if out is not None else (self.h_idx, self.h_rss, self.h_mask)
+        h_idx[:n].copy_(self.res_idx[:n], non_blocking=True)
+        h_rss[:n].copy_(self.res_rss[:n], non_blocking=True)
+        h_mask[:H].copy_(self.dev_m[:H], non_blocking=True)
         d2h = n * (8 + self.res_rss.element_size()) + H
         return h2d, d2h
