@@ -6,6 +6,7 @@
     python -m paper_1911_09340_gb300.experiments gauss-newton [--events N] [--lambda-mm 0.8]
     python -m paper_1911_09340_gb300.experiments batch [--events N]
     python -m paper_1911_09340_gb300.experiments table-field [--events N]
+    python -m paper_1911_09340_gb300.experiments single-event [--reps N] [--stride s]
 
 * ``lambda-sweep``: hit-classification efficiency and purity (metrics.py) of the first stage and of
   all stages as the cutoff lambda runs over 0.5-1.2 mm in 0.1 mm steps (the range of the paper's
@@ -22,6 +23,8 @@
   continuous batching (batch.py) under the autotuned configuration.
 * ``table-field``: evaluations/s on the non-uniform (tabulated solenoid) field workload, with the
   uniform-field path on the same events beside it.
+* ``single-event``: the small single-event configuration (2 partitions of 8^4 seeds) in FP64 and
+  FP32: time per event and the DCA kernel's algorithmic flop rate against the FP64 and FP32 rates.
 
 Every scan runs through the library's kernels (scan.scan_partition); only the metrics are computed
 on the host from the copied-back hit classes.  One JSON line per result.
@@ -433,10 +436,63 @@ def table_field_study(n_events: int = 8, stride: int = 16, lam: float = 1e-2, dt
     return [out]
 
 
+def single_event_study(reps: int = 50, stride: int = 16, lam: float = 1e-2):
+    """The single-event configuration (p = 104 MeV/c at 80 degrees, 2 turn partitions of 8^4 seeds,
+    131 hits on 106 wires) in FP64 and in FP32: per-kernel GPU time per event, seed x hit
+    evaluations/s, and the DCA kernel's algorithmic flop rate (201 flops per seed x wire with an
+    unmasked hit + 8 per seed x unmasked hit) against the nominal FP64 rate of this part
+    (1.25 TFLOP/s, not measured here) and the derived FP32 peak (80.5 TFLOP/s).  At 4096 seeds per
+    partition the launches are latency-bound: the fractions say how little of the part such a
+    small scan uses, not how fast the kernels are."""
+    ev = synth.single_event_fp64()
+    out = {"study": "single-event", "reps": reps, "stride": stride, "lambda_mm": lam * 1e3,
+           "seeds_per_partition": ev.partitions[0].n_seeds, "partitions": len(ev.partitions),
+           "hits": ev.n_hits, "wires": ev.n_wires}
+    offs = np.asarray(ev.hit_offsets)
+    for name, dtype, peak in (("fp64", torch.float64, 1.25), ("fp32", torch.float32, 80.54784)):
+        ctx, field, ws = _setup([ev], dtype, stride)
+        dev = scan.DeviceEvent.from_event(ev, dtype)
+        params = scan.event_params(ev, dtype, stride, lam)
+        classes = [torch.zeros(max(ev.n_hits, 1), dtype=torch.uint8, device="cuda") for _ in ev.partitions]
+
+        def run(timer=None):
+            dev.mask.zero_()
+            for p, (spec, bp) in enumerate(zip(ev.partitions, params)):
+                scan.scan_partition(ctx, field, bp, spec, dev, ws, hit_class=classes[p], timer=timer)
+
+        for _ in range(3):
+            run()
+        timer = scan.KernelTimer()
+        torch.cuda.synchronize()
+        for _ in range(reps):
+            run(timer)
+        torch.cuda.synchronize()
+        kt = {k: v[0] / reps for k, v in timer.totals().items()}
+        masked = np.zeros(ev.n_hits, bool)
+        hits = wires = 0
+        for spec, cls in zip(ev.partitions, classes):
+            live = ~masked
+            per_wire = np.add.reduceat(live.astype(np.int64), offs[:-1])
+            per_wire[offs[:-1] == offs[1:]] = 0
+            hits += spec.n_seeds * int(live.sum())
+            wires += spec.n_seeds * int((per_wire > 0).sum())
+            masked |= cls[: ev.n_hits].cpu().numpy().astype(bool)
+        ms = sum(kt.values())
+        flops = 201 * wires + 8 * hits
+        out[name] = {"ms_per_event": ms, "kernel_ms": {k: round(v, 4) for k, v in kt.items()},
+                     "evals_per_s": hits / (ms * 1e-3),
+                     "dca_tflops": flops / (kt["dca"] * 1e-3) / 1e12,
+                     "dca_frac": flops / (kt["dca"] * 1e-3) / 1e12 / peak,
+                     "peak_tflops": peak, "peak_source": "nominal" if name == "fp64" else "derived"}
+        ctx.close()
+    return [out]
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("study", choices=["lambda-sweep", "backward", "iterative", "gauss-newton", "batch",
-                                      "table-field"])
+                                      "table-field", "single-event"])
+    ap.add_argument("--reps", type=int, default=50, help="timed repetitions (single-event)")
     ap.add_argument("--events", type=int, default=32)
     ap.add_argument("--stride", type=int, default=16)
     ap.add_argument("--lambda-mm", type=float, default=10.0, help="cutoff (backward, iterative, gn)")
@@ -446,6 +502,8 @@ def main(argv=None):
         rows = lambda_sweep(args.events, stride=args.stride)
     elif args.study == "iterative":
         rows = iterative_study(args.events, args.stride, args.lambda_mm * 1e-3)
+    elif args.study == "single-event":
+        rows = single_event_study(args.reps, args.stride, args.lambda_mm * 1e-3)
     elif args.study == "table-field":
         rows = table_field_study(args.events, args.stride, args.lambda_mm * 1e-3)
     elif args.study == "batch":
