@@ -26,8 +26,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "seed x hit DCA evals/s"
-WORKLOAD = ("multi-turn electron events, 2^18 seeds per turn partition (16x16x32x32), FP32, "
-            "uniform 1 T, 18-layer stereo chamber")
+WORKLOAD = ("multi-turn electron events (2-5 turns, 100-105 MeV/c), 2^18 seeds per turn partition "
+            "(16x16x32x32), uniform 1 T, 18-layer stereo chamber")
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -147,8 +147,8 @@ def pairs_of(ev, classes):
     for spec, cls in zip(ev.partitions, classes):
         live = ~masked
         hits += spec.n_seeds * int(live.sum())
-        per_wire = np.add.reduceat(live.astype(np.int64), offs[:-1]) if H else np.zeros(0)
-        per_wire[offs[:-1] == offs[1:]] = 0
+        csum = np.concatenate([[0], np.cumsum(live.astype(np.int64))])
+        per_wire = csum[offs[1:]] - csum[offs[:-1]]          # unmasked hits of each wire
         wires += spec.n_seeds * int((per_wire > 0).sum())
         masked |= cls[:H].astype(bool)
     return hits, wires
@@ -186,10 +186,12 @@ def oracle_rate(ev, target_s: float = 10.0, nthreads=None, stride: int = 16):
                                 f"{ev.n_hits} hits, stride {stride}, FP64 oracle, {dt:.1f} s"
 
 
-def workload_config(args):
-    """The workload keys both arms report."""
+def workload_config(args, arithmetic: str):
+    """The workload keys both arms report; ``arithmetic`` names the precision the arm computes in
+    (the events, lattice and parameters are the same)."""
     counts = args.lattice or (16, 16, 32, 32)
-    return {"workload": WORKLOAD, "seeds_per_partition": int(np.prod(counts)), "stride": args.stride,
+    return {"workload": WORKLOAD, "arithmetic": arithmetic,
+            "seeds_per_partition": int(np.prod(counts)), "stride": args.stride,
             "lambda_m": 0.01, "rk4_step_m": 1e-3}
 
 
@@ -208,7 +210,7 @@ def run_reference(args, rank, world):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": dict(workload_config(args), parallelism=f"host threads ({cores})"),
+        "config": dict(workload_config(args, "FP64 CPU oracle"), parallelism=f"host threads ({cores})"),
         "cpu_baseline": {"value": value, "unit": "evals/s", "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -364,7 +366,7 @@ def run_ours(args, rank, world):
         "events_per_s": events_all / t_max,
         "event_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
                      "max": max(step_ms)},
-        "config": dict(workload_config(args), events=events_all, partitions=n_parts * world,
+        "config": dict(workload_config(args, "FP32 GPU"), events=events_all, partitions=n_parts * world,
                        l2="256 MiB buffer written between timed steps; track points (~0.9 GB per "
                           "partition) also exceed L2",
                        parallelism=f"replicas: {world} GPU(s), disjoint events"),
@@ -382,8 +384,148 @@ def run_ours(args, rank, world):
         out["cpu_baseline"] = {"value": cpu[0], "unit": "evals/s", "cores": cpu[1], "kind": "oracle",
                                "sample": cpu[2], "value_1_thread": cpu1[0],
                                "sample_1_thread": cpu1[2]}
+    if not args.no_legs:
+        del ws, devs
+        torch.cuda.empty_cache()
+        out["legs"] = {
+            "single_event_fp64": leg_single_event_fp64(ctx, reps=args.fp64_reps),
+            "table_field_fp32": leg_table_field_fp32(ctx, 2, args.table_events, args.stride),
+        }
     print(json.dumps(out), flush=True)
     ctx.close()
+
+
+# ------------------------------------------------------------------------------------------------
+# Extra legs: the paper's precision on the single-event configuration, and the tabulated field
+# ------------------------------------------------------------------------------------------------
+
+def _time_events(run_event, n_warm: int, n_timed: int):
+    """Runs n_warm untimed then n_timed timed events (CUDA events around each on the current
+    stream); returns per-event ms and the KernelTimer totals of one more pass over the timed ones."""
+    import torch
+
+    from paper_1911_09340_gb300 import scan
+    for i in range(n_warm):
+        run_event(i, None)
+    torch.cuda.synchronize()
+    st = [torch.cuda.Event(enable_timing=True) for _ in range(n_timed)]
+    en = [torch.cuda.Event(enable_timing=True) for _ in range(n_timed)]
+    for j in range(n_timed):
+        st[j].record()
+        run_event(n_warm + j, None)
+        en[j].record()
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in zip(st, en)]
+    timer = scan.KernelTimer()
+    for j in range(n_timed):
+        run_event(n_warm + j, timer)
+    torch.cuda.synchronize()
+    return ms, timer.totals()
+
+
+def leg_single_event_fp64(ctx, reps: int, stride: int = 1):
+    """The paper's precision (FP64, Sec. 2.2) on the single-event configuration: one 104 MeV/c
+    electron at 80 degrees to the axis making 2 turns in a uniform 1 T field, 8^4 seeds per turn
+    partition, RK4 step 1 mm, every state recorded (Algorithm 1), lambda = 1 cm.  The event is
+    repeated `reps` times (the mask reset before each); per-event CUDA-event times."""
+    import torch
+
+    from paper_1911_09340_gb300 import binding as B
+    from paper_1911_09340_gb300 import scan, synth
+    dt = torch.float64
+    ev = synth.single_event_fp64()
+    field = B.DeviceField.from_synth(synth.uniform_field(1.0))
+    dev = scan.DeviceEvent.from_event(ev, dt)
+    params = scan.event_params(ev, dt, stride=stride)
+    ws = scan.Workspace(ev.partitions[0].n_seeds, max(p.n_rec for p in params), ev.n_hits, dt)
+    classes = torch.zeros((len(ev.partitions), max(ev.n_hits, 1)), dtype=torch.uint8, device="cuda")
+
+    def run_event(_i, t):
+        dev.mask.zero_()
+        for p, (spec, bp) in enumerate(zip(ev.partitions, params)):
+            scan.scan_partition(ctx, field, bp, spec, dev, ws, hit_class=classes[p], timer=t)
+
+    ms, kt = _time_events(run_event, 3, reps)
+    hits, wires = pairs_of(ev, classes.cpu().numpy())
+    mean_ms = sum(ms) / len(ms)
+    n_parts = len(ev.partitions)
+    dca_ms = kt["dca"][0] / kt["dca"][1]
+    flops = (DCA_FLOPS_PER_WIRE * wires + DCA_FLOPS_PER_HIT * hits) / n_parts
+    tf = flops / (dca_ms * 1e-3) / 1e12
+    return {
+        "config": "one 104 MeV/c electron at 80 deg, 2 turns, uniform 1 T; 8^4 seeds per turn "
+                  f"partition; RK4 step 1 mm, stride {stride}; lambda 1 cm; {ev.n_hits} hits on "
+                  f"{ev.n_wires} wires",
+        "dtype": "f64", "events": reps, "evals_per_s": hits / (mean_ms * 1e-3),
+        "events_per_s": 1e3 / mean_ms,
+        "event_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))},
+        "kernel_ms_per_event": {k: round(v[0] / reps, 4) for k, v in kt.items()},
+        "gpu_launches_per_event": scan.LAUNCHES_PER_PARTITION * n_parts,
+        "roofline": {"kernel": "dca", "bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": tf / FP64_PEAK_TFLOPS, "traffic": None,
+                     "peak_source": "nominal FP64 rate of the part (not measured)",
+                     "flops_per_launch": flops, "avg_launch_ms": dca_ms},
+    }
+
+
+def leg_table_field_fp32(ctx, n_warm: int, n_timed: int, stride: int):
+    """The non-uniform field (FP32): events with the DIO-shaped momentum spectrum (50-105 MeV/c),
+    the harmonic solenoid model (1 T centre, 5% gradients) tabulated on a 5 mm grid and
+    interpolated trilinearly at every RK4 stage, 2^18 seeds per turn partition."""
+    import torch
+
+    from paper_1911_09340_gb300 import binding as B
+    from paper_1911_09340_gb300 import scan, synth
+    dt = torch.float32
+    fld = synth.table_field()
+    events = [synth.table_field_event(i, fld) for i in range(n_warm + n_timed)]
+    field = B.DeviceField.from_synth(fld, interleaved=True)
+    S = max(sp.n_seeds for ev in events for sp in ev.partitions)
+    params = [scan.event_params(ev, dt, stride=stride) for ev in events]
+    ws = scan.Workspace(S, max(p.n_rec for ps in params for p in ps), max(ev.n_hits for ev in events), dt)
+    devs = [scan.DeviceEvent.from_event(ev, dt) for ev in events]
+    classes = [torch.zeros((len(ev.partitions), max(ev.n_hits, 1)), dtype=torch.uint8, device="cuda")
+               for ev in events]
+
+    def run_event(i, t):
+        devs[i].mask.zero_()
+        for p, (spec, bp) in enumerate(zip(events[i].partitions, params[i])):
+            scan.scan_partition(ctx, field, bp, spec, devs[i], ws, hit_class=classes[i][p], timer=t)
+
+    ms, kt = _time_events(run_event, n_warm, n_timed)
+    hits = n_parts = 0
+    steps = 0
+    for i in range(n_warm, n_warm + n_timed):
+        hits += pairs_of(events[i], classes[i].cpu().numpy())[0]
+        n_parts += len(events[i].partitions)
+        # RK4 steps the recording took: (states recorded - 1) x stride per seed
+        for spec, bp in zip(events[i].partitions, params[i]):
+            seeds, charge, pts, nv, _, _ = ws.views(spec.n_seeds, bp.n_rec)
+            B.comet_scan_lattice(ctx, spec, seeds, charge)
+            B.comet_scan_propagate(ctx, field, bp, seeds, charge, pts, nv)
+            steps += int((nv.long() - 1).sum().item()) * bp.stride
+    tot_ms = sum(ms)
+    prop_ms = kt["propagate"][0] / kt["propagate"][1]
+    flops = TABLE_FLOPS_PER_STEP * steps / n_parts
+    tf = flops / (prop_ms * 1e-3) / 1e12
+    peak = fp32_peak_tflops(_peaks())
+    return {
+        "config": "DIO-shaped momenta 50-105 MeV/c, tabulated solenoid field (5 mm grid, trilinear, "
+                  f"[nz][ny][nx][4] float32), 2^18 seeds per turn partition, stride {stride}, "
+                  "lambda 1 cm",
+        "dtype": "f32", "events": n_timed, "partitions": n_parts,
+        "momenta_MeV": [round(float(np.hypot(events[i].pt, events[i].pz)), 1)
+                        for i in range(n_warm, n_warm + n_timed)],
+        "evals_per_s": hits / (tot_ms * 1e-3), "events_per_s": n_timed / (tot_ms * 1e-3),
+        "event_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))},
+        "kernel_ms": {k: round(v[0], 3) for k, v in kt.items()},
+        "gpu_launches": scan.LAUNCHES_PER_PARTITION * n_parts,
+        "roofline": {"kernel": "propagate", "bound": "alu", "achieved": tf, "peak": peak,
+                     "unit": "TFLOP/s", "frac": tf / peak, "traffic": None,
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
+                     "flops_per_launch": flops, "flops_per_rk4_step": TABLE_FLOPS_PER_STEP,
+                     "avg_launch_ms": prop_ms},
+    }
 
 
 # Algorithmic work of the kernels (counted from the formulas; FMA = 2 flops):
@@ -393,9 +535,16 @@ def run_ours(args, rank, world):
 #    square and accumulate of Eq. 1 = 8 flops.  The closest-state search is not counted;
 #  - the recording of one state: 6 FP32 stores = 24 bytes (the propagate kernel is store-bound),
 #    counted over the states actually recorded (sum of n_valid), plus 24 bytes per seed read.
+#  - one RK4 step in a tabulated field: 4 trilinear lookups x (cell coordinates and weights 9 +
+#    3 components x 7 linear interpolations x 3 flops = 72) + 4 derivative evaluations x 15
+#    (dx/ds 3, p x B 9, scale 3) + 3 intermediate states x 6 FMA (36) + the combination
+#    k1 + 2 k2 + 2 k3 + k4 of 6 components (54) = 438 FP32 flops;
+#  - FP64 peak: the part's nominal FP64 rate (1.25 TFLOP/s), not measured.
 DCA_FLOPS_PER_WIRE = 201
 DCA_FLOPS_PER_HIT = 8
 PROP_BYTES_PER_REC = 24
+TABLE_FLOPS_PER_STEP = 438
+FP64_PEAK_TFLOPS = 1.25
 
 # DRAM bytes (read + write) per launch of the two main kernels on this workload at stride 32, from a
 # one-pass ncu launch list of `python bench.py` (dram__bytes_read.sum + dram__bytes_write.sum, mean
@@ -455,6 +604,37 @@ def roofline_entry(kernel, avg_ms, prop_bytes_per_launch, clocks, peaks, dca_flo
             "frac": None, "traffic": None, "avg_launch_ms": avg_ms}
 
 
+def run_dry(args, rank, world):
+    """--dry-run: the launch, sharding and reduction logic without CUDA (gloo ranks on the CPU):
+    each rank takes its events as in a real run, and rank 0 prints one line with what every rank
+    reported."""
+    from paper_1911_09340_gb300 import multi
+    idx = multi.event_indices(args.warmup + args.steps, rank, world)
+    mine = {"rank": rank, "events": idx[args.warmup:], "local_rank": int(os.environ.get("LOCAL_RANK", "0"))}
+    if world > 1:
+        import torch.distributed as dist
+        got = [None] * world
+        dist.all_gather_object(got, mine)
+    else:
+        got = [mine]
+    total = sum_over_ranks(float(len(mine["events"])), world)
+    if rank == 0:
+        print(json.dumps({"metric": METRIC, "dry_run": True, "n_gpus": world, "steps": args.steps,
+                          "warmup": args.warmup, "events_timed": total, "ranks": got}), flush=True)
+
+
+def spawn_ranks(n: int) -> int:
+    """`--gpus N` without a launcher: start N ranks of this script (one per GPU) under
+    torch.distributed.run on this node and return its exit status; rank 0 prints the line."""
+    import socket
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={n}",
+           "--master-addr=127.0.0.1", f"--master-port={port}", os.path.abspath(__file__)] + sys.argv[1:]
+    return subprocess.call(cmd)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -467,12 +647,22 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=8.0)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling)")
+    ap.add_argument("--no-legs", action="store_true",
+                    help="skip the single-event FP64 and table-field legs")
+    ap.add_argument("--fp64-reps", type=int, default=20, help="timed events of the FP64 leg")
+    ap.add_argument("--table-events", type=int, default=3, help="timed events of the table-field leg")
+    ap.add_argument("--dry-run", action="store_true",
+                    help="no CUDA: exercise the rank launch, sharding and reductions on the CPU")
     ap.add_argument("--lattice", type=lambda s: [int(x) for x in s.split(",")],
                     default=[16, 16, 32, 32], help="seed lattice counts (z0,phi,pz,pt); "
                     "the workload is 16,16,32,32, smaller lattices are for profiling only")
     args = ap.parse_args()
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        sys.exit(spawn_ranks(args.gpus))
     rank, world = dist_setup(args.gpus)
-    if args.impl == "reference":
+    if args.dry_run:
+        run_dry(args, rank, world)
+    elif args.impl == "reference":
         run_reference(args, rank, world)
     else:
         run_ours(args, rank, world)

@@ -121,13 +121,25 @@ typedef struct {
  * frees the context's device memory and the context; NULL is a no-op.  A context may be used from
  * one host thread at a time.
  * comet_ctx_status: synchronises the device and copies the status word to *flags (host pointer):
- *   bit 0  a kernel's wait for a shared-memory bulk copy exceeded its time limit (2 s); the kernel
- *          then re-read the data with plain loads, so its results are still valid;
+ *   bit 0  a kernel's wait for a shared-memory bulk copy exceeded its time limit (2 s unless
+ *          comet_ctx_set_copy_wait changed it); the kernel then re-read the data with plain loads,
+ *          so its results are still valid;
  *   bit 1  comet_scan_classify was given a seed index outside [0, S); its hit_class was zeroed.
+ * comet_ctx_set_copy_wait: the longest (ns >= 0, in nanoseconds) that a kernel launched with this
+ *   context waits for a shared-memory bulk copy before it gives up, re-reads the data with plain
+ *   loads and sets status bit 0 (default 2e9).  0 makes every such wait give up at once, so that the
+ *   plain-load path runs on every launch: a way to test it.  A copy that was given up on is still
+ *   waited for (up to 2 s) before the kernel reuses or releases the shared memory it writes.
+ *   Host-side setting; takes effect for calls enqueued after it.
+ * comet_kernel_arch: writes to *sm_version (host pointer) the SM version the library's device code
+ *   was compiled for, as major * 10 + minor (103 for sm_103a), read from a kernel's attributes on
+ *   the current device.
  * comet_last_error: message of the calling thread's last non-OK status (static storage). */
 comet_status comet_ctx_create(int device, comet_ctx **out);
 void comet_ctx_destroy(comet_ctx *ctx);
 comet_status comet_ctx_status(comet_ctx *ctx, int32_t *flags);
+comet_status comet_ctx_set_copy_wait(comet_ctx *ctx, int64_t ns);
+comet_status comet_kernel_arch(int32_t *sm_version);
 const char *comet_last_error(void);
 
 /* ---- a1: seed lattice -------------------------------------------------------------------------
@@ -183,7 +195,9 @@ comet_status comet_scan_propagate(comet_ctx *ctx, comet_dtype dtype, const comet
  *                known to contribute lambda^2 and is not refined.
  *   n_unconverged optional, device [1] int32 (NULL to skip): incremented by the number of
  *                (seed, wire) refinements that reached max_iter or met a track parallel to the wire.
- *                The caller zeroes it.
+ *                The caller zeroes it.  Non-convergence is reported only here, never through the
+ *                return status: the count exists on the device once the kernel has run, and
+ *                returning it would need a host synchronisation in every call.
  * D_i: start from the recorded state closest to the wire line (ties: lowest index), then step along
  * the track by -d/|n| with one RK4 step, where n is the part of the unit direction perpendicular to
  * the wire and d the distance to the plane that contains the wire axis with normal n, until
@@ -355,8 +369,11 @@ comet_status comet_scan_batch(comet_ctx *ctx, comet_dtype dtype, const comet_fie
  *   the process exits.  A call needs ceil(S / 2048) * k * (sizeof(T) + 8) + 64 bytes of it and is
  *   rejected with COMET_ERR_INVALID_ARG beyond 1 MiB (k = 1: S up to about 134 million FP64 or
  *   178 million FP32 seeds; k = 64: about 2.09 million FP64 or 2.79 million FP32).
+ *   The arrays must be device memory of the current device (else COMET_ERR_INVALID_ARG).
  *   The first call on a device looks the array's device address up (cudaGetSymbolAddress, with that
- *   device current); make that first call before any stream capture.
+ *   device current) and keeps it for the rest of the process; make that first call before any
+ *   stream capture.  The kept address does not survive a reset of the device's primary context
+ *   (cudaDeviceReset): do not call this function after such a reset in the same process.
  *   Every call shares the array and it keeps the last call's contents; nothing in it needs to start
  *   at zero (each call writes every entry it reads).  Calls that overlap on the GPU (other streams,
  *   other host threads) race on the array: serialise them. */

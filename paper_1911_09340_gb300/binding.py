@@ -72,6 +72,8 @@ SIGNATURES = {
     "comet_ctx_create": [C.c_int, C.POINTER(C.c_void_p)],
     "comet_ctx_destroy": [_vp],
     "comet_ctx_status": [_vp, C.POINTER(C.c_int32)],
+    "comet_ctx_set_copy_wait": [_vp, _i64],
+    "comet_kernel_arch": [C.POINTER(C.c_int32)],
     "comet_last_error": [],
     "comet_scan_lattice": [_vp, C.c_int, C.POINTER(_Lattice), _vp, _vp, _i64, _vp],
     "comet_scan_propagate": [_vp, C.c_int, C.POINTER(_Field), C.POINTER(_Params), _vp, _vp, _i64,
@@ -219,6 +221,10 @@ class Context:
         _check(lib().comet_ctx_status(self.handle, C.byref(v)))
         return v.value
 
+    def set_copy_wait(self, ns: int):
+        """Limit (ns) of a kernel's wait for a staging bulk copy; 0 forces the plain-load path."""
+        _check(lib().comet_ctx_set_copy_wait(self.handle, int(ns)))
+
     def close(self):
         if self.handle:
             lib().comet_ctx_destroy(self.handle)
@@ -289,10 +295,23 @@ def comet_scan_select(ctx: Context, rss, k: int, idx_out, rss_out=None, stream=N
 
 def comet_scan_select_noalloc(rss, k: int, idx_out, rss_out=None, stream=None):
     """comet_scan_select without a context and without device allocation (static scratch on the
-    current device; see include/comet_scan.h for its size limit and sharing rules)."""
-    _check(lib().comet_scan_select_noalloc(_dtype_code(rss), _ptr(rss), rss.shape[0], int(k),
-                                           _ptr(idx_out, torch.int64), _ptr(rss_out, rss.dtype),
-                                           _stream(stream)))
+    device that holds ``rss``; see include/comet_scan.h for its size limit and sharing rules).  Runs
+    with that device current, on its current stream unless ``stream`` is given."""
+    for t in (idx_out, rss_out):
+        if t is not None and t.device != rss.device:
+            raise ValueError("rss, idx_out and rss_out must be on one device")
+    with torch.cuda.device(rss.device):
+        st = stream if stream is not None else torch.cuda.current_stream(rss.device)
+        _check(lib().comet_scan_select_noalloc(_dtype_code(rss), _ptr(rss), rss.shape[0], int(k),
+                                               _ptr(idx_out, torch.int64), _ptr(rss_out, rss.dtype),
+                                               st.cuda_stream))
+
+
+def kernel_arch() -> int:
+    """SM version of the library's device code (major * 10 + minor) on the current device."""
+    v = C.c_int32(0)
+    _check(lib().comet_kernel_arch(C.byref(v)))
+    return v.value
 
 
 def comet_scan_refine_refs(ctx: Context, seeds, idx, half_width, K: int, refs_out, n_refs_out,

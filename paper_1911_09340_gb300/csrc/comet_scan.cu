@@ -231,6 +231,7 @@ void fill_dca(comet_ctx *ctx, comet_dtype, const comet_scan_params *p, const Sea
     a->n_unconv = n_unconverged;
     a->status = ctx->status;
     a->counter = ctx->status + 16;
+    a->wait_ns = ctx->copy_wait_ns;
     a->lambda = p->lambda;
     a->tol = p->tol;
     a->max_iter = p->max_iter;
@@ -340,6 +341,24 @@ comet_status comet_ctx_status(comet_ctx *ctx, int32_t *flags)
     if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
     e = cudaMemcpy(flags, ctx->status, sizeof(int32_t), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(status)");
+    return COMET_OK;
+}
+
+comet_status comet_ctx_set_copy_wait(comet_ctx *ctx, int64_t ns)
+{
+    if (!ctx) return fail(COMET_ERR_INVALID_ARG, "ctx is NULL");
+    if (ns < 0) return fail(COMET_ERR_INVALID_ARG, "the copy wait limit must be >= 0 ns");
+    ctx->copy_wait_ns = (uint64_t)ns;
+    return COMET_OK;
+}
+
+comet_status comet_kernel_arch(int32_t *sm_version)
+{
+    if (!sm_version) return fail(COMET_ERR_INVALID_ARG, "sm_version is NULL");
+    int v = 0;
+    cudaError_t e = comet::kernel_binary_version(&v);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncGetAttributes");
+    *sm_version = v;
     return COMET_OK;
 }
 
@@ -656,6 +675,23 @@ comet_status comet_scan_select_noalloc(comet_dtype dtype, const void *rss, int64
     if (!rss || !idx_out) return fail(COMET_ERR_INVALID_ARG, "rss and idx_out are required");
     if (!aligned(rss, esize(dtype)) || !aligned(idx_out, 8) || (rss_out && !aligned(rss_out, esize(dtype))))
         return fail(COMET_ERR_INVALID_ARG, "an array is misaligned for its element type");
+    // the arrays must live on the current device, where the kernels and the scratch are
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    const void *arrays[3] = {rss, idx_out, rss_out};
+    for (const void *q : arrays) {
+        if (!q) continue;
+        cudaPointerAttributes at;
+        e = cudaPointerGetAttributes(&at, q);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(COMET_ERR_INVALID_ARG, "rss / idx_out / rss_out is not a device pointer");
+        }
+        if ((at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) || at.device != dev)
+            return fail(COMET_ERR_INVALID_ARG,
+                        "rss / idx_out / rss_out must be device memory of the current device (%d)", dev);
+    }
     comet::SelArgs a;
     a.rss = rss;
     a.S = S;
@@ -667,7 +703,7 @@ comet_status comet_scan_select_noalloc(comet_dtype dtype, const void *rss, int64
         return fail(COMET_ERR_INVALID_ARG,
                     "S = %lld with k = %d needs %zu bytes of scratch; the static scratch holds %zu",
                     (long long)S, k, need, comet::kStaticSelectScratchBytes);
-    cudaError_t e = comet::static_select_scratch(&a.scratch);
+    e = comet::static_select_scratch(&a.scratch);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(select scratch)");
     e = comet::launch_select(dtype, a, (cudaStream_t)stream);
     return e == cudaSuccess ? COMET_OK : cuda_fail(e, "select launch");

@@ -67,6 +67,7 @@ struct DcaArgs {
     int32_t *n_unconv;
     int32_t *status;       // device status word of the context (bit 0: a bulk-copy wait timed out)
     int32_t *counter;      // device work counter (context-owned; zeroed before each launch)
+    uint64_t wait_ns;      // limit of a wait for a staging bulk copy (0: give up at once)
     double lambda, tol;
     double R0;             // super-segment radius (m), margins included
     double R1;             // level-1 segment radius (m), margins included
@@ -122,6 +123,9 @@ struct ClsArgs {
     int max_iter;
     int update_mask;
 };
+
+// SM version (major * 10 + minor) of the library's device code, read from a kernel's attributes.
+cudaError_t kernel_binary_version(int *version);
 
 cudaError_t launch_lattice(comet_dtype dt, const LatArgs &a, const LatTable &t, void *seeds, int64_t S,
                            cudaStream_t st);

@@ -64,7 +64,7 @@ constexpr int kWireTile = 256;
 constexpr int kWireCap = kWireTile + 32;     // elements per staged row (room for the 16-B shift)
 constexpr int kHitMax = 1024;                // hits staged in shared memory when H <= kHitMax
 constexpr int kHitCap = kHitMax + 32;
-constexpr uint64_t kWaitNs = 2000000000ull;  // bulk-copy wait limit (2 s)
+constexpr uint64_t kWaitNs = 2000000000ull;  // limit of the wait for an abandoned copy (2 s)
 
 __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
@@ -505,13 +505,16 @@ __device__ __forceinline__ void group_all_chunks(const F &f, const DcaArgs &a, c
     }
 }
 
-// Stages n_arrays arrays with one bulk-copy transaction (thread 0 issues, everyone waits).  Returns
-// true if the wait timed out anywhere in the CTA (the caller then re-reads with plain loads).
-__device__ __forceinline__ bool finish_stage(uint64_t *bar, uint32_t &parity, uint32_t bytes)
+// Waits for a staging transaction of `bytes` (thread 0 issued it; everyone waits) for at most
+// wait_ns; wait_ns = 0 gives up at once without waiting (the context's test setting).  Returns true
+// if the wait gave up anywhere in the CTA: the caller then re-reads the data with plain loads and,
+// before its shared memory or barrier is used again, waits (up to kWaitNs) for the abandoned copy.
+__device__ __forceinline__ bool finish_stage(uint64_t *bar, uint32_t &parity, uint32_t bytes,
+                                             uint64_t wait_ns)
 {
     bool to = false;
     if (bytes > 0) {
-        to = !mbar_wait(bar, parity, kWaitNs);
+        to = wait_ns == 0 ? true : !mbar_wait(bar, parity, wait_ns);
         parity ^= 1u;
     }
     return __syncthreads_or(to);
@@ -603,7 +606,7 @@ __global__ void __launch_bounds__(kThreads, COMET_DCA_MINB) dca_persistent_kerne
             moff = stage_issue<uint8_t>(msm, a.mask, H, bar, tid == 0);
         }
     }
-    const bool any_timeout = finish_stage(bar, parity, bytes);
+    const bool any_timeout = finish_stage(bar, parity, bytes, a.wait_ns);
     if (any_timeout && W > 0) {
 #pragma unroll
         for (int r = 0; r < 6; ++r) stage_fallback<T>(wrow + r * rcap, Wg + (size_t)r * a.ldw, W);
@@ -752,10 +755,12 @@ __global__ void __launch_bounds__(kThreads, COMET_DCA_MINB) dca_tiled_kernel(F f
         }
         doff = stage_issue<T>(dsm, Dg, H, bar, tid == 0);
         moff = stage_issue<uint8_t>(msm, a.mask, H, bar, tid == 0);
-        if (finish_stage(bar, parity, bytes)) {
+        if (finish_stage(bar, parity, bytes, a.wait_ns)) {
             any_timeout = true;
             stage_fallback<T>(dsm, Dg, H);
             stage_fallback<uint8_t>(msm, a.mask, H);
+            // the barrier is reused by the wire tiles: let the abandoned copy land first (bounded)
+            mbar_wait(bar, parity ^ 1u, kWaitNs);
         }
         __syncthreads();
     }
@@ -776,12 +781,15 @@ __global__ void __launch_bounds__(kThreads, COMET_DCA_MINB) dca_tiled_kernel(F f
         for (int r = 0; r < 6; ++r)
             woff[r] = stage_issue<T>(wrow + r * kWireCap, Wg + (size_t)r * a.ldw + w0, wn, bar, tid == 0);
         const int ooff = stage_issue<int32_t>(orow, a.offs + w0, wn + 1, bar, tid == 0);
-        if (finish_stage(bar, parity, bytes)) {
+        if (finish_stage(bar, parity, bytes, a.wait_ns)) {
             any_timeout = true;
 #pragma unroll
             for (int r = 0; r < 6; ++r)
                 stage_fallback<T>(wrow + r * kWireCap, Wg + (size_t)r * a.ldw + w0, wn);
             stage_fallback<int32_t>(orow, a.offs + w0, wn + 1);
+            // the next tile reuses these buffers and the barrier: let the abandoned copy land
+            // first (bounded)
+            mbar_wait(bar, parity ^ 1u, kWaitNs);
         }
         __syncthreads();
         Tile<T> tl;
@@ -814,10 +822,7 @@ __global__ void __launch_bounds__(kThreads, COMET_DCA_MINB) dca_tiled_kernel(F f
         for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
         if (lane == 0 && t) atomicAdd(a.n_unconv, t);
     }
-    if (any_timeout) {
-        if (tid == 0 && a.status) atomicOr(a.status, 1);
-        mbar_wait(bar, parity ^ 1u, kWaitNs);
-    }
+    if (any_timeout && tid == 0 && a.status) atomicOr(a.status, 1);
 }
 
 static int sm_count()
@@ -1000,7 +1005,7 @@ __global__ void __launch_bounds__(kThreads, COMET_DCA_BATCH_MINB) dca_batch_kern
                     moff = stage_issue<uint8_t>(msm, a.mask, H, bar, tid == 0);
                 }
             }
-            const bool to = finish_stage(bar, parity, bytes);
+            const bool to = finish_stage(bar, parity, bytes, a.wait_ns);
             if (to && W > 0) {
 #pragma unroll
                 for (int r = 0; r < 6; ++r) stage_fallback<T>(wrow + r * rcap, Wg + (size_t)r * a.ldw, W);

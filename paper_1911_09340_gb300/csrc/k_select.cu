@@ -213,6 +213,14 @@ cudaError_t static_select_scratch(void **ptr)
     return cudaSuccess;
 }
 
+cudaError_t kernel_binary_version(int *version)
+{
+    cudaFuncAttributes fa;
+    const cudaError_t e = cudaFuncGetAttributes(&fa, select_pass1<float>);
+    if (e == cudaSuccess) *version = fa.binaryVersion;
+    return e;
+}
+
 cudaError_t launch_select(comet_dtype dt, const SelArgs &a, cudaStream_t st)
 {
     if (dt == COMET_F32)

@@ -82,6 +82,7 @@ struct comet_ctx {
     void *scratch = nullptr;     // comet_scan_select's per-block partial results
     size_t scratch_bytes = 0;
     int32_t *status = nullptr;   // device status word (bit 0: bulk-copy timeout, bit 1: bad seed index)
+    uint64_t copy_wait_ns = 2000000000ull;   // limit of a kernel's wait for a staging bulk copy
     void *dca_part = nullptr;    // comet_scan_dca's per-chunk partial sums
     size_t dca_part_bytes = 0;
     uint32_t *dca_arrive = nullptr;   // per-group arrival counters (kept zero between launches)

@@ -7,6 +7,23 @@ import oracle as O
 from paper_1911_09340_gb300 import binding as B
 
 
+def seen(x, dtype):
+    """The values the device path receives for an input given in float64: rounded to float32 for the
+    FP32 path (and exactly representable in float64 again), unchanged for FP64.  Parity tests give
+    the oracle these same values, so that the comparison measures the arithmetic, not the input
+    rounding."""
+    x = np.asarray(x, np.float64)
+    return x.astype(np.float32).astype(np.float64) if dtype == torch.float32 else x
+
+
+# Bars of the FP32 path (FP64: 1e-9 m throughout).  DCA: the FP32 track points stay within 1 um of
+# FP64 over three turns (tested) and the distance arithmetic adds rounding of a few ulp of metres,
+# so 2 um per (seed, wire); the RSS bound follows from it term by term (rss_bound).  Classification:
+# bit-identical except hits whose residual |D - r| lies within 1 um of the cutoff.
+FP32_DCA_TOL = 2e-6
+CLASS_EDGE = {torch.float32: 1e-6, torch.float64: 1e-9}
+
+
 def both_params(**kw):
     return O.Params(**kw), B.ScanParams(**kw)
 

@@ -44,9 +44,18 @@ def test_binding_signatures_cover_the_header():
     assert set(binding.SIGNATURES) == set(declared_functions())
 
 
-def test_library_is_built_for_sm_103a(libpath):
-    out = subprocess.run(["cuobjdump", "--list-elf", libpath], capture_output=True, text=True).stdout
-    assert "sm_103a" in out
+def test_library_is_built_for_sm_103a():
+    """The build compiles every translation unit for sm_103a only (one -gencode)."""
+    from paper_1911_09340_gb300 import build
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+    assert "-gencode" not in build.FLAGS and not any("arch" in f for f in build.FLAGS)
+
+
+@pytest.mark.gpu
+def test_kernels_report_sm_103():
+    """The loaded library's kernels carry SM version 10.3 (read from a kernel's attributes)."""
+    from paper_1911_09340_gb300 import binding
+    assert binding.kernel_arch() == 103
 
 
 def test_header_compiles_as_c(tmp_path):

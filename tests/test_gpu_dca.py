@@ -2,8 +2,10 @@
 
 Bars: FP64 DCAs within 1e-9 m and RSS within 1e-10 relative (the paper's own CPU/GPU validation
 found < O(1e-12), Sec. 4.1); FP32 DCAs within 2 um (track points within 1 um over one turn plus the
-FP32 distance arithmetic) and RSS within the bound those DCAs imply; n_in identical where no
-residual sits within the DCA tolerance of the cutoff.  Covered: both dtypes, small and large seed
+FP32 distance arithmetic) and every RSS within the bound those DCAs imply; n_in identical where no
+residual sits within the DCA tolerance of the cutoff.  The oracle takes the inputs the device path
+receives (FP32: seeds, wires and drifts rounded to float32).  No statistical allowance: every
+compared value must meet its bar.  Covered: both dtypes, small and large seed
 counts, ragged seed counts, several wire tiles, hits beyond the shared-memory capacity, misaligned
 wire rows, W = 0, all hits masked, the pruned and exact paths.
 """
@@ -15,7 +17,7 @@ import oracle as O
 from paper_1911_09340_gb300 import binding as B
 from paper_1911_09340_gb300 import synth
 
-from gpu_util import both_params, gpu_dca, per_wire_residual, rss_bound
+from gpu_util import FP32_DCA_TOL, both_params, gpu_dca, per_wire_residual, rss_bound, seen
 
 pytestmark = pytest.mark.gpu
 
@@ -58,23 +60,18 @@ def test_fp64_pruned_path_equals_exact_path(ctx):
     assert np.allclose(b["rss"], r["rss"], rtol=1e-10, atol=0)
 
 
-def _fp32_check(g, r, ev_offs, drift, mask, lam, delta=2e-6):
-    # A wire the track passes twice at nearly equal distance may have its closest recorded state on
-    # the other pass in FP32 than in FP64; the two local minima then differ by up to ~(h_rec/2)^2/R.
-    # Such flips are counted and bounded; everything else must agree within delta.
+def _fp32_check(g, r, ev_offs, drift, mask, lam, delta=FP32_DCA_TOL):
+    """Every DCA of a wire within 3 cm within delta of the oracle's, every RSS within the bound
+    those DCAs imply, n_in identical for seeds with no residual within delta of the cutoff."""
     near = r["dca"] < 0.03
-    bad = (np.abs(g["dca"] - r["dca"]) > delta) & near
-    assert bad.mean() <= 1e-3, (bad.sum(), np.abs(g["dca"] - r["dca"])[near].max())
-    flip = bad.any(1)
-    assert flip.mean() <= 0.02, flip.mean()
+    dd = np.abs(g["dca"] - r["dca"])[near]
+    assert dd.max() <= delta, (int((dd > delta).sum()), dd.max())
     e = per_wire_residual(r["dca"], ev_offs, drift, mask)
     bound = rss_bound(e, lam, delta)
-    dev = np.abs(g["rss"] - r["rss"])
-    ok = dev <= bound + 1e-12
-    assert ok[~flip].all(), (dev / np.maximum(bound, 1e-30))[~flip].max()
+    excess = np.abs(g["rss"] - r["rss"]) - bound
+    assert excess.max() <= 1e-12, (int((excess > 1e-12).sum()), int(np.argmax(excess)))
     edge = (np.abs(e - lam) < delta).any(1)
-    sel = ~edge & ~flip
-    assert np.array_equal(g["n_in"][sel], r["n_in"][sel])
+    assert np.array_equal(g["n_in"][~edge], r["n_in"][~edge])
 
 
 @pytest.mark.parametrize("stride", [1, 4, 16, 24, 32])
@@ -84,11 +81,11 @@ def test_fp32_matches_oracle_multi_turn_event(ctx, stride):
     op, bp = both_params(n_steps=ev.n_steps[0], stride=stride, lam=0.01, tol=1e-6)
     op.tol = 1e-12
     mask = np.zeros(ev.n_hits, np.uint8)
+    w32, d32 = seen(ev.wires, torch.float32), seen(ev.drift, torch.float32)
     g = gpu_dca(ctx, B.DeviceField.from_synth(UNIFORM), bp, seeds, -1, ev.wires, ev.hit_offsets,
                 ev.drift, mask, torch.float32, want_dca=True)
-    r = O.scan(UNIFORM, op, seeds, -1, O.wires_aos(ev.wires), ev.hit_offsets, ev.drift, mask,
-               want_dca=True)
-    _fp32_check(g, r, ev.hit_offsets, ev.drift, mask, 0.01)
+    r = O.scan(UNIFORM, op, seeds, -1, O.wires_aos(w32), ev.hit_offsets, d32, mask, want_dca=True)
+    _fp32_check(g, r, ev.hit_offsets, d32, mask, 0.01)
     # the pruned path gives the same RSS as the exact path up to FP32 summation of equal terms
     p = gpu_dca(ctx, B.DeviceField.from_synth(UNIFORM), bp, seeds, -1, ev.wires, ev.hit_offsets,
                 ev.drift, mask, torch.float32, want_dca=False)
@@ -111,11 +108,13 @@ def test_fp32_large_seed_count_sampled(ctx):
     g = gpu_dca(ctx, B.DeviceField.from_synth(UNIFORM), bp, seeds, -1, ev.wires, ev.hit_offsets,
                 ev.drift, mask, torch.float32, want_dca=False)
     sample = np.unique(np.concatenate([np.arange(0, 65573, 61), [65572, int(np.argmin(g["rss"]))]]))
-    r = O.scan(UNIFORM, op, seeds[sample], -1, O.wires_aos(ev.wires), ev.hit_offsets, ev.drift,
-               mask, want_dca=True)
-    e = per_wire_residual(r["dca"], ev.hit_offsets, ev.drift, mask)
-    bound = rss_bound(e, 0.01, 2e-6)
-    assert (np.abs(g["rss"][sample] - r["rss"]) <= bound + 1e-12).mean() >= 0.999
+    w32, d32 = seen(ev.wires, torch.float32), seen(ev.drift, torch.float32)
+    r = O.scan(UNIFORM, op, seeds[sample], -1, O.wires_aos(w32), ev.hit_offsets, d32, mask,
+               want_dca=True)
+    e = per_wire_residual(r["dca"], ev.hit_offsets, d32, mask)
+    bound = rss_bound(e, 0.01, FP32_DCA_TOL)
+    excess = np.abs(g["rss"][sample] - r["rss"]) - bound
+    assert excess.max() <= 1e-12, (int((excess > 1e-12).sum()), sample[int(np.argmax(excess))])
 
 
 def _many_wires_case(n_wires=600, hits_per_wire=3, seed=5):
@@ -143,7 +142,8 @@ def test_many_wires_many_hits_misaligned(ctx, dtype, misalign):
     for want in (True, False):
         g = gpu_dca(ctx, B.DeviceField.from_synth(UNIFORM), bp, seeds, -1, wires, offs, drift, mask,
                     dtype, want_dca=want, misalign=misalign)
-        r = O.scan(UNIFORM, op, seeds, -1, O.wires_aos(wires), offs, drift, mask, want_dca=True)
+        r = O.scan(UNIFORM, op, seeds, -1, O.wires_aos(seen(wires, dtype)), offs, seen(drift, dtype),
+                   mask, want_dca=True)
         if dtype == torch.float64:
             if want:
                 # wires metres away whose closest recorded state is a track end: the refinement
@@ -154,9 +154,13 @@ def test_many_wires_many_hits_misaligned(ctx, dtype, misalign):
             assert np.allclose(g["rss"], r["rss"], rtol=1e-10, atol=0)
             assert np.array_equal(g["n_in"], r["n_in"])
         else:
-            e = per_wire_residual(r["dca"], offs, drift, mask)
-            bound = rss_bound(e, 0.01, 2e-6)
-            assert (np.abs(g["rss"] - r["rss"]) <= bound + 1e-12).mean() >= 0.999
+            if want:
+                near = r["dca"] < 0.05
+                assert np.abs(g["dca"] - r["dca"])[near].max() <= FP32_DCA_TOL
+            e = per_wire_residual(r["dca"], offs, seen(drift, dtype), mask)
+            bound = rss_bound(e, 0.01, FP32_DCA_TOL)
+            excess = np.abs(g["rss"] - r["rss"]) - bound
+            assert excess.max() <= 1e-12, (int((excess > 1e-12).sum()), int(np.argmax(excess)))
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
@@ -173,16 +177,21 @@ def test_degenerate_inputs(ctx, dtype):
     mask = np.ones(ev.n_hits, np.uint8)
     g = gpu_dca(ctx, f, bp, seeds, -1, ev.wires, ev.hit_offsets, ev.drift, mask, dtype, want_dca=True)
     assert np.all(g["rss"] == 0) and np.all(g["n_in"] == 0)
-    r = O.scan(UNIFORM, op, seeds, -1, O.wires_aos(ev.wires), ev.hit_offsets, ev.drift, mask,
-               want_dca=True)
-    tol = 1e-9 if dtype == torch.float64 else 2e-6
+    r = O.scan(UNIFORM, op, seeds, -1, O.wires_aos(seen(ev.wires, dtype)), ev.hit_offsets,
+               seen(ev.drift, dtype), mask, want_dca=True)
+    tol = 1e-9 if dtype == torch.float64 else FP32_DCA_TOL
     assert np.abs(g["dca"] - r["dca"])[r["dca"] < 0.03].max() <= tol
     # a single seed
     g = gpu_dca(ctx, f, bp, seeds[:1], -1, ev.wires, ev.hit_offsets, ev.drift,
                 np.zeros(ev.n_hits, np.uint8), dtype, want_dca=False)
-    r = O.scan(UNIFORM, op, seeds[:1], -1, O.wires_aos(ev.wires), ev.hit_offsets, ev.drift,
-               np.zeros(ev.n_hits, np.uint8))
-    assert np.allclose(g["rss"], r["rss"], rtol=1e-10 if dtype == torch.float64 else 1e-3)
+    z = np.zeros(ev.n_hits, np.uint8)
+    r = O.scan(UNIFORM, op, seeds[:1], -1, O.wires_aos(seen(ev.wires, dtype)), ev.hit_offsets,
+               seen(ev.drift, dtype), z, want_dca=True)
+    if dtype == torch.float64:
+        assert np.allclose(g["rss"], r["rss"], rtol=1e-10, atol=0)
+    else:
+        e = per_wire_residual(r["dca"], ev.hit_offsets, seen(ev.drift, dtype), z)
+        assert np.abs(g["rss"] - r["rss"]).max() <= rss_bound(e, op.lam, FP32_DCA_TOL).max() + 1e-12
 
 
 def test_unconverged_count_matches_oracle(ctx):
@@ -244,13 +253,14 @@ def test_pruned_search_keeps_wires_beyond_the_track_ends(ctx, dtype, use_bounds)
     mask = np.zeros(3, np.uint8)
     g = gpu_dca(ctx, B.DeviceField.from_synth(UNIFORM), bp, seeds, -1, wires, offs, drift, mask, dtype,
                 want_dca=False, use_bounds=use_bounds)
-    r = O.scan(UNIFORM, op, seeds, -1, O.wires_aos(wires), offs, drift, mask, want_dca=True)
+    r = O.scan(UNIFORM, op, seeds, -1, O.wires_aos(seen(wires, dtype)), offs, seen(drift, dtype),
+               mask, want_dca=True)
     assert (np.abs(r["dca"][:, :2] - drift[:2]) < lam).all()   # the end wires are inliers in the oracle
     if f64:
         assert np.allclose(g["rss"], r["rss"], rtol=1e-10, atol=0)
     else:
-        e = per_wire_residual(r["dca"], offs, drift, mask)
-        assert (np.abs(g["rss"] - r["rss"]) <= rss_bound(e, lam, 2e-6) + 1e-12).all()
+        e = per_wire_residual(r["dca"], offs, seen(drift, dtype), mask)
+        assert (np.abs(g["rss"] - r["rss"]) <= rss_bound(e, lam, FP32_DCA_TOL) + 1e-12).all()
     assert np.array_equal(g["n_in"], r["n_in"])
 
 
@@ -298,3 +308,30 @@ def test_wire_chunk_boundaries(ctx, n_wires):
     a = gpu_dca(ctx, f, bp32, seeds, -1, wires, offs, drift, mask, torch.float32, want_dca=False)
     b = gpu_dca(ctx, f, bp32, seeds, -1, wires, offs, drift, mask, torch.float32, want_dca=False)
     assert np.array_equal(a["rss"], b["rss"]) and np.array_equal(a["n_in"], b["n_in"])
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+@pytest.mark.parametrize("n_wires", [200, 1025])
+def test_copy_wait_give_up_falls_back_to_plain_loads(ctx, dtype, n_wires):
+    """With the context's copy wait set to 0, every bulk-copy wait of the DCA kernels gives up at
+    once: the kernel re-reads the staged arrays with plain loads, sets status bit 0, and waits
+    (bounded) for the abandoned copy before its shared memory is reused.  Results are bit-identical
+    to a normal run: 200 wires with 600 hits (persistent kernel, hits staged) and 1025 wires (tiled
+    kernel, staged tile by tile)."""
+    ev, wires, offs, drift, mask = _wires_case(n_wires)
+    seeds = O.lattice(ev.partitions[0])[::13].astype(np.float32).astype(np.float64)
+    f = B.DeviceField.from_synth(UNIFORM)
+    _, bp = both_params(n_steps=ev.n_steps[0], stride=16, lam=0.01,
+                        tol=1e-12 if dtype == torch.float64 else 1e-6)
+    ref = gpu_dca(ctx, f, bp, seeds, -1, wires, offs, drift, mask, dtype, want_dca=False)
+    c0 = B.Context(0)
+    try:
+        assert c0.status() == 0
+        c0.set_copy_wait(0)
+        got = gpu_dca(c0, f, bp, seeds, -1, wires, offs, drift, mask, dtype, want_dca=False)
+        assert c0.status() & 1
+        for k in ("rss", "n_in"):
+            assert np.array_equal(got[k], ref[k]), k
+        c0.set_copy_wait(2_000_000_000)
+    finally:
+        c0.close()

@@ -2,10 +2,11 @@
 mask) run through the package's scan driver, against the oracle's pipeline.
 
 Bars: the argmin seed identical, or its oracle RSS within 1e-5 relative of the oracle's minimum;
-classifications bit-identical except hits whose residual lies within the DCA tolerance of lambda.
-The full-size FP32 event (2^18 seeds per partition, the benchmark's launch configuration) is checked
-on a sample of seeds the oracle computes one by one, plus the property that the selected seed is at
-least as good as every sampled one.
+classifications bit-identical except hits whose residual lies within 1 um (FP32; 1e-9 m FP64) of
+lambda.  The benchmark's launch configuration (2^18 seeds per partition, FP32, stride 32) is checked
+against the oracle on every seed of every partition of three benchmark events; the other strides
+and the 2^24-seed partition on samples of seeds the oracle computes one by one.  No statistical
+allowance: every compared value must meet its bar.
 """
 import numpy as np
 import pytest
@@ -15,7 +16,7 @@ import oracle as O
 from paper_1911_09340_gb300 import binding as B
 from paper_1911_09340_gb300 import scan, synth
 
-from gpu_util import per_wire_residual, rss_bound
+from gpu_util import CLASS_EDGE, FP32_DCA_TOL, per_wire_residual, rss_bound, seen
 
 pytestmark = pytest.mark.gpu
 UNIFORM = synth.uniform_field(1.0)
@@ -43,8 +44,119 @@ def test_single_event_fp64_all_partitions(ctx):
         omask = r["mask"]
 
 
-@pytest.mark.parametrize("stride", [1, 4, 16, 24, 32])
+def _edge_hits(dca_wire, ev, drift, lam, band):
+    """Hits whose residual |D - r| (D: the oracle's DCA of the classified seed to the hit's wire)
+    lies within `band` of the cutoff: the only hits whose class may differ."""
+    wid = np.repeat(np.arange(ev.n_wires), np.diff(ev.hit_offsets))
+    return np.abs(np.abs(dca_wire[wid] - drift) - lam) < band
+
+
+def _check_selected_and_classified(g_rss, g_idx, g_cls, r_rss_of, seeds, ev, op, w32, d32, mask):
+    """The argmin rule and the classification rule for one partition.  ``r_rss_of(i)`` is the
+    oracle's RSS of seed i; returns the oracle's mask after classifying the selected seed."""
+    o_best_idx, o_best = r_rss_of(None)
+    # argmin seed identical, or its oracle RSS within 1e-5 relative of the oracle's minimum
+    assert g_idx == o_best_idx or r_rss_of(g_idx) <= o_best * (1 + 1e-5), (g_idx, o_best_idx)
+    # classification of the selected seed: bit-identical except within 1 um of the cutoff
+    cls, dwr, m2 = O.classify(UNIFORM, op, seeds[g_idx], -1, O.wires_aos(w32), ev.hit_offsets, d32,
+                              mask, update_mask=True)
+    edge = _edge_hits(dwr, ev, d32, op.lam, CLASS_EDGE[torch.float32])
+    diff = np.flatnonzero(g_cls != cls)
+    assert np.all(edge[diff]), ("hits classified differently away from the cutoff", diff[~edge[diff]])
+    return m2, int(edge.sum()), diff.size
+
+
+HEADLINE_EVENTS = (0, 1, 2)
+
+
+@pytest.mark.parametrize("event", HEADLINE_EVENTS)
+def test_benchmark_event_every_partition_full_oracle(ctx, event):
+    """The benchmark's launch configuration -- 2^18 seeds per turn partition, FP32, every 32nd state
+    recorded, uniform 1 T -- on every partition of a benchmark event, against the oracle run on all
+    2^18 seeds of each partition (same FP32-rounded seeds, wires and drifts), the hit mask carried
+    from each partition's classification to the next.
+
+    Per partition, through the scan driver (lattice -> propagate -> dca -> select -> classify, the
+    DCA on its pruned path as the benchmark runs it):
+      - every seed's RSS within the bound the 2 um DCA bar implies term by term, n_in identical
+        for every seed with no residual within 2 um of the cutoff;
+      - the selected seed identical to the oracle's argmin, or its oracle RSS within 1e-5 relative
+        of the oracle's minimum over the whole partition;
+      - the selected seed's hit classes bit-identical to the oracle's except hits whose residual
+        lies within 1 um of the cutoff, and the carried mask equal to the oracle's;
+    and, on the exact path (every DCA requested), every (seed, wire with an unmasked hit) DCA that
+    can give a residual below lambda within 2 um of the oracle's, the others beyond the wire's
+    capture radius on both sides."""
+    ev = synth.multi_turn_event(event)
+    S = ev.partitions[0].n_seeds
+    assert S == 1 << 18
+    f = B.DeviceField.from_synth(UNIFORM)
+    dev = scan.DeviceEvent.from_event(ev, torch.float32)
+    params = scan.event_params(ev, torch.float32, stride=32)
+    ws = scan.Workspace(S, max(p.n_rec for p in params), ev.n_hits, torch.float32)
+    w32, d32 = seen(ev.wires, torch.float32), seen(ev.drift, torch.float32)
+    omask = np.zeros(ev.n_hits, np.uint8)
+    dca = torch.empty((ev.n_wires, S), dtype=torch.float32, device="cuda")
+    for part, (spec, bp) in enumerate(zip(ev.partitions, params)):
+        assert np.array_equal(dev.mask[:ev.n_hits].cpu().numpy(), omask)
+        seeds = O.lattice(spec).astype(np.float32).astype(np.float64)
+        op = O.Params(n_steps=bp.n_steps, stride=bp.stride, lam=bp.lam, tol=1e-12)
+        r = O.scan(UNIFORM, op, seeds, -1, O.wires_aos(w32), ev.hit_offsets, d32, omask,
+                   want_dca=True)
+        e = per_wire_residual(r["dca"], ev.hit_offsets, d32, omask)
+        live = np.isfinite(e[0])
+        # exact path: every DCA of a wire that is in the sum
+        seeds_dev, charge, pts, nv, _, _ = ws.views(S, bp.n_rec)
+        B.comet_scan_lattice(ctx, spec, seeds_dev, charge)
+        B.comet_scan_propagate(ctx, f, bp, seeds_dev, charge, pts, nv)
+        rss_x = torch.empty(S, dtype=torch.float32, device="cuda")
+        nin_x = torch.empty(S, dtype=torch.int32, device="cuda")
+        B.comet_scan_dca(ctx, f, bp, pts, nv, charge, dev.wires, dev.hit_offsets, dev.drift,
+                         dev.mask, rss_x, nin_x, dca_out=dca, n_wires=ev.n_wires)
+        # every (seed, wire) whose DCA can give a residual below lambda -- the oracle's DCA within
+        # the wire's capture radius (largest unmasked drift + lambda) plus 1 mm -- agrees to 2 um;
+        # beyond it both sides lie beyond the capture radius (the wire adds lambda^2 either way:
+        # far from the track the closest recorded state may be a track end, where the extrapolated
+        # DCA depends on rounding)
+        g_dca = dca.double().cpu().numpy()                     # [W][S]
+        o_dca = r["dca"].T                                      # [W][S]
+        cap = np.array([max((d32[j] for j in range(ev.hit_offsets[i], ev.hit_offsets[i + 1])
+                             if not omask[j]), default=-1.0) for i in range(ev.n_wires)]) + bp.lam
+        rel = live[:, None] & (o_dca < cap[:, None] + 1e-3)
+        dd = np.abs(g_dca - o_dca)[rel]
+        assert dd.max() <= FP32_DCA_TOL, dd.max()
+        far = live[:, None] & ~rel
+        margin = g_dca[far] - np.broadcast_to(cap[:, None], far.shape)[far]
+        assert margin.min() >= 0.0, (margin.min(), int((margin < 0).sum()))
+        # pruned path, the benchmark's sequence
+        scan.scan_partition(ctx, f, bp, spec, dev, ws)
+        torch.cuda.synchronize()
+        g_rss = ws.rss[:S].double().cpu().numpy()
+        g_idx = int(ws.idx[0])
+        g_cls = ws.hit_class[:ev.n_hits].cpu().numpy()
+        assert g_rss[g_idx] == g_rss.min() and g_idx == int(np.flatnonzero(g_rss == g_rss.min())[0])
+        bound = rss_bound(e, bp.lam, FP32_DCA_TOL)
+        excess = np.abs(g_rss - r["rss"]) - bound
+        assert excess.max() <= 1e-12, (int((excess > 1e-12).sum()), int(np.argmax(excess)))
+        edge_s = (np.abs(e - bp.lam) < FP32_DCA_TOL).any(1)
+        assert np.array_equal(ws.n_in[:S].cpu().numpy()[~edge_s], r["n_in"][~edge_s])
+        o_idx, o_best = O.select(r["rss"], 1)
+        rss_of = lambda i: (int(o_idx[0]), float(o_best[0])) if i is None else float(r["rss"][i])
+        omask, n_edge, n_diff = _check_selected_and_classified(g_rss, g_idx, g_cls, rss_of, seeds, ev,
+                                                               op, w32, d32, omask)
+        print(f"event {event} partition {part}: {live.sum()} wires in the sum, {dd.size} (seed, "
+              f"wire) DCAs within reach, max |dDCA| {dd.max():.2e} m, selected {g_idx} (oracle "
+              f"{int(o_idx[0])}), {n_edge} hits within 1 um of the cutoff, {n_diff} hit classes "
+              f"differ")
+    assert np.array_equal(dev.mask[:ev.n_hits].cpu().numpy(), omask)
+
+
+@pytest.mark.parametrize("stride", [1, 4, 16, 24])
 def test_multi_turn_event_fp32_full_size_sampled(ctx, stride):
+    """2^18 seeds at the other pinned strides: a sample of seeds (random, the 64 of lowest GPU RSS and
+    the selected one) computed by the oracle one by one; every sampled RSS within the bound of the
+    2 um DCA bar, the selected seed at least as good (by the oracle) as every sampled seed, and the
+    selected seed's classification bit-identical except within 1 um of the cutoff."""
     ev = synth.multi_turn_event(4)
     spec = ev.partitions[0]
     S = spec.n_seeds
@@ -59,27 +171,23 @@ def test_multi_turn_event_fp32_full_size_sampled(ctx, stride):
     g_idx = int(ws.idx[0])
     assert g_rss[g_idx] == g_rss.min() and g_idx == int(np.flatnonzero(g_rss == g_rss.min())[0])
     g_cls = ws.hit_class[:ev.n_hits].cpu().numpy()
-
+    w32, d32 = seen(ev.wires, torch.float32), seen(ev.drift, torch.float32)
     seeds = O.lattice(spec).astype(np.float32).astype(np.float64)
     rng = np.random.default_rng(0)
     order = np.argsort(g_rss, kind="stable")
     sample = np.unique(np.concatenate([rng.choice(S, 384, replace=False), order[:64], [g_idx]]))
     op = O.Params(n_steps=bp.n_steps, stride=bp.stride, lam=bp.lam, tol=1e-12)
     mask = np.zeros(ev.n_hits, np.uint8)
-    r = O.scan(UNIFORM, op, seeds[sample], -1, O.wires_aos(ev.wires), ev.hit_offsets, ev.drift,
-               mask, want_dca=True)
-    e = per_wire_residual(r["dca"], ev.hit_offsets, ev.drift, mask)
-    bound = rss_bound(e, bp.lam, 2e-6)
-    assert (np.abs(g_rss[sample] - r["rss"]) <= bound + 1e-12).mean() >= 0.995
-    # the selected seed is, by the oracle too, at least as good as every sampled seed
+    r = O.scan(UNIFORM, op, seeds[sample], -1, O.wires_aos(w32), ev.hit_offsets, d32, mask,
+               want_dca=True)
+    e = per_wire_residual(r["dca"], ev.hit_offsets, d32, mask)
+    bound = rss_bound(e, bp.lam, FP32_DCA_TOL)
+    excess = np.abs(g_rss[sample] - r["rss"]) - bound
+    assert excess.max() <= 1e-12, (int((excess > 1e-12).sum()), sample[int(np.argmax(excess))])
     r_best = r["rss"][np.searchsorted(sample, g_idx)]
     assert r_best <= r["rss"].min() * (1 + 1e-5)
-    # classification of the selected seed
-    cls, dwr, _ = O.classify(UNIFORM, op, seeds[g_idx], -1, O.wires_aos(ev.wires), ev.hit_offsets,
-                             ev.drift, mask)
-    wid = np.repeat(np.arange(ev.n_wires), np.diff(ev.hit_offsets))
-    edge = np.abs(np.abs(dwr[wid] - ev.drift) - bp.lam) < 2e-6
-    assert np.array_equal(g_cls[~edge], cls[~edge]) or (g_cls != cls).sum() <= 2
+    rss_of = lambda i: (g_idx, r_best) if i is None else r_best
+    _check_selected_and_classified(g_rss, g_idx, g_cls, rss_of, seeds, ev, op, w32, d32, mask)
 
 
 def test_backward_partition_fp64_matches_oracle(ctx):
@@ -161,11 +269,12 @@ def test_sixteen_million_seed_partition_needs_64bit_offsets(ctx):
     sample = np.unique(np.concatenate([rng.choice(S, 256, replace=False), [g_idx, S - 1, S - 33]]))
     op = O.Params(n_steps=bp.n_steps, stride=bp.stride, lam=bp.lam, tol=1e-12)
     mask = np.zeros(ev.n_hits, np.uint8)
-    r = O.scan(UNIFORM, op, seeds[sample], -1, O.wires_aos(ev.wires), ev.hit_offsets, ev.drift,
-               mask, want_dca=True)
-    e = per_wire_residual(r["dca"], ev.hit_offsets, ev.drift, mask)
-    bound = rss_bound(e, bp.lam, 2e-6)
-    ok = np.abs(g_rss[sample] - r["rss"]) <= bound + 1e-12
-    assert ok.mean() >= 0.99 and ok[np.searchsorted(sample, [S - 1])].all()
+    w32, d32 = seen(ev.wires, torch.float32), seen(ev.drift, torch.float32)
+    r = O.scan(UNIFORM, op, seeds[sample], -1, O.wires_aos(w32), ev.hit_offsets, d32, mask,
+               want_dca=True)
+    e = per_wire_residual(r["dca"], ev.hit_offsets, d32, mask)
+    bound = rss_bound(e, bp.lam, FP32_DCA_TOL)
+    excess = np.abs(g_rss[sample] - r["rss"]) - bound
+    assert excess.max() <= 1e-12, (int((excess > 1e-12).sum()), sample[int(np.argmax(excess))])
     r_best = r["rss"][np.searchsorted(sample, g_idx)]
     assert r_best <= r["rss"].min() * (1 + 1e-5)
