@@ -208,7 +208,7 @@ void fill_prop(comet_dtype, const comet_scan_params *p, const SearchGeometry &sg
     a->n_rec = n_rec_of(p);
 }
 
-void fill_dca(comet_ctx *ctx, comet_dtype, const comet_scan_params *p, const SearchGeometry &sg,
+void fill_dca(comet_ctx *ctx, comet_dtype dtype, const comet_scan_params *p, const SearchGeometry &sg,
               const void *points, const int32_t *n_valid, const int8_t *charge, int64_t S,
               const void *bounds, const void *wires, int32_t W, int32_t ldw, const int32_t *offs,
               const void *drift, const uint8_t *mask, void *rss, int32_t *n_in, void *dca_out,
@@ -245,6 +245,8 @@ void fill_dca(comet_ctx *ctx, comet_dtype, const comet_scan_params *p, const Sea
     a->tol_f = (float)a->tol;
     a->half_rec_f = (float)a->half_rec;
     a->h_rec_f = (float)a->h_rec;
+    a->margin = dtype == COMET_F32 ? 4e-6 : 1e-9;
+    a->margin_f = (float)a->margin;
     a->bounds = bounds;
     a->exact_all = dca_out != nullptr;
     a->n_chunks = comet::dca_wire_chunks(W);

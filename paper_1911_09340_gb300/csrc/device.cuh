@@ -404,13 +404,22 @@ __device__ __forceinline__ void lex_min(T &bd, int &bk, T d, int k)
 // of the starting state's valley; a step is shortened to stay inside.  Returns 1 if |d| < tol was
 // reached within max_iter steps, 0 if not, if the track runs parallel to the wire, or if the state
 // is held at the edge of the interval.  D = distance of the final state to the wire line.
+// s0 != 0 takes a first step of that length (|s0| <= h_rec; it counts as one of the max_iter steps)
+// before the first evaluation: a better start than the recorded state, the same fixed point.
 template <typename T, class F>
 __device__ __forceinline__ int refine_dca(const F &f, T c, T ip, T y[6], T ax, T ay, T az, T ux,
-                                          T uy, T uz, T tol, int max_iter, T h_rec, T &D)
+                                          T uy, T uz, T tol, int max_iter, T h_rec, T &D,
+                                          T s0 = T(0))
 {
     int conv = 0;
     T sigma = T(0);
-    for (int it = 0;; ++it) {
+    int it0 = 0;
+    if (s0 != T(0)) {
+        rk4_step<T, F>(f, c, ip, y, s0);
+        sigma = s0;
+        it0 = 1;
+    }
+    for (int it = it0;; ++it) {
         // t = p / P0: |p| stays P0 in a magnetic field, and the plane and its zero do not depend on
         // the norm of t (n is normalised below), only the Newton step length, by rounding
         const T tx = y[3] * ip, ty = y[4] * ip, tz = y[5] * ip;

@@ -76,6 +76,9 @@ struct DcaArgs {
     // the four scalars above rounded to float on the host: the FP32 kernel reads these, so that
     // no double-to-float conversion is re-done inside its loops
     float lambda_f, tol_f, half_rec_f, h_rec_f;
+    // rounding margin of the closest-state search (m; 4e-6 FP32, 1e-9 FP64) and its float copy
+    double margin;
+    float margin_f;
     int max_iter;
     int G0;                // recorded states per super-segment
     int G1;                // recorded states per level-1 segment

@@ -310,6 +310,21 @@ __device__ __forceinline__ void group_wires(const F &f, const DcaArgs &a, const 
     const int N1 = (G0 + G1 - 1) / G1;
     const Q4<T> *rec = tl.rec;
     constexpr int kU = COMET_DCA_U2;
+    // Tighter reach of the refinement from an interior closest state (axial field): at a point of
+    // closest approach X* with distance D, the recorded state within delta <= h_rec/2 of it along the
+    // track is at most sqrt(D^2 + delta^2) + kappa delta^2 / 2 from the wire (the tangent line from
+    // X* moves away from the wire as sqrt(D^2 + delta^2 |t_perp|^2), the track leaves the tangent by
+    // at most kappa delta^2 / 2, kappa = |KAPPA q B / P0| its curvature).  So a closest recorded state
+    // farther than sqrt(cap^2 + (h_rec/2)^2) + kappa (h_rec/2)^2 / 2 cannot refine to D < cap: the
+    // wire adds lambda^2.  kq2 = the warp's largest kappa times (h_rec/2)^2 / 2, plus the margin.
+    T kq2 = T(INFINITY);
+    if constexpr (F::kAxial) {
+        T kap = fabs(gr.c * f.bz);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) kap = fmax(kap, __shfl_xor_sync(0xffffffffu, kap, off));
+        kq2 = T(0.5) * kap * half_rec * half_rec + in_prec<T>(a.margin, a.margin_f);
+    }
+    const T hq2 = half_rec * half_rec;
 
     for (int base = wb; base < we; base += 32) {
         const int clen = min(32, we - base);
@@ -354,11 +369,17 @@ __device__ __forceinline__ void group_wires(const F &f, const DcaArgs &a, const 
 #endif
             const bool want = valid && (cap >= T(0) || a.exact_all);
             const T capth = a.exact_all ? T(INFINITY) : cap + half_rec;
+            // interior reach (see kq2): never above capth
+            const T thin = a.exact_all ? T(INFINITY) : fmin(capth, sqrt(cap * cap + hq2) + kq2);
             T bd = T(INFINITY);
             int bk = 0x7fffffff;
 #if COMET_DCA_SCAN_P
             // the closest state so far, loaded with the scan (no second round trip to refine)
             T by[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+            // squared distances of the states scanned just before and after the closest one (for
+            // the first refinement step) and of the previous state scanned
+            T bdm = T(INFINITY), bdp = T(INFINITY), dprev = T(INFINITY);
+            int kprev = -2;
 #endif
             // scans states [k0, k1) of this lane's seed, kU at a time (span is warp-uniform)
             auto scan = [&](int k0, int k1, int span) {
@@ -395,6 +416,8 @@ __device__ __forceinline__ void group_wires(const F &f, const DcaArgs &a, const 
 #if COMET_DCA_SCAN_P
                             const T d = sd2(xs[u], ys[u], zs[u]);
                             if (d < bd || (d == bd && k < bk)) {
+                                bdm = k == kprev + 1 ? dprev : T(INFINITY);
+                                bdp = T(INFINITY);
                                 bd = d;
                                 bk = k;
                                 by[0] = xs[u];
@@ -403,7 +426,11 @@ __device__ __forceinline__ void group_wires(const F &f, const DcaArgs &a, const 
                                 by[3] = pxs[u];
                                 by[4] = pys[u];
                                 by[5] = pzs[u];
+                            } else if (k == bk + 1) {
+                                bdp = d;
                             }
+                            dprev = d;
+                            kprev = k;
 #else
                             lex_min<T>(bd, bk, sd2(xs[u], ys[u], zs[u]), k);
 #endif
@@ -426,10 +453,12 @@ __device__ __forceinline__ void group_wires(const F &f, const DcaArgs &a, const 
                     // and largest last state) gets the refinement's extra half interval there
                     const int k1 = j * G0 + lane;
                     const bool end1 = G1 == 1 && (k1 == 0 || (k1 >= gr.elo && k1 <= gr.ehi));
+                    // one-state segments away from the track ends need only the interior reach
+                    const T lim1 = G1 == 1 ? (end1 ? capth + half_rec : thin) : capth;
                     const bool hit1 = lane < N1 &&
                                       sphere_within<T>(sph1[j * kN1Max + lane], fvx, fvy, fvz, fav,
                                                        fwx, fwy, fwz, faw, ax, ay, az, ux, uy, uz,
-                                                       end1 ? capth + half_rec : capth);
+                                                       lim1);
                     const uint32_t u1 = __ballot_sync(0xffffffffu, hit1);
                     if (u1) {
                         // one contiguous range from the first to the last candidate level-1
@@ -443,24 +472,37 @@ __device__ __forceinline__ void group_wires(const F &f, const DcaArgs &a, const 
             }
 
             // refinement from the closest recorded state, only where it can bring the wire within
-            // its capture radius: within half an interval of a recorded state, within a whole one
-            // beyond either end of the recorded track (compared squared: capth carries margins far
-            // above the rounding of the square)
-            const T th = (bk == 0 || bk == nv - 1) ? capth + half_rec : capth;
+            // its capture radius: from an interior state within the interior reach thin, from the
+            // first or the last recorded state within a whole interval more than capth (the
+            // refinement may extrapolate h_rec beyond the track); compared squared: the thresholds
+            // carry margins far above the rounding of the square
+            const T th = (bk == 0 || bk == nv - 1) ? capth + half_rec : thin;
             const bool refine = want && bk != 0x7fffffff && (a.exact_all || bd <= th * th);
             T D = T(INFINITY);
             if (refine) {
                 T yv[6];
+                T s0 = T(0);
 #if COMET_DCA_SCAN_P
 #pragma unroll
                 for (int cc = 0; cc < 6; ++cc) yv[cc] = by[cc];
+                // first step to the vertex of the parabola through the squared distances of the
+                // closest state and its two neighbours (exact for a straight track, where the
+                // squared distance is quadratic in arc length); then Newton steps as usual.  Used
+                // when both neighbours were scanned and the step budget allows (max_iter >= 4).
+                if (a.max_iter >= 4 && bdm < T(INFINITY) && bdp < T(INFINITY)) {
+                    const T den = bdm - T(2) * bd + bdp;
+                    if (den > T(0)) {
+                        s0 = T(0.5) * h_rec * (bdm - bdp) / den;
+                        s0 = fmin(fmax(s0, -h_rec), h_rec);
+                    }
+                }
 #else
                 const int64_t o = (int64_t)bk * S + s;
 #pragma unroll
                 for (int cc = 0; cc < 6; ++cc) yv[cc] = P[cc * plane + o];
 #endif
                 const int conv = refine_dca<T, F>(f, gr.c, gr.ip, yv, ax, ay, az, ux, uy, uz, tol,
-                                                  a.max_iter, h_rec, D);
+                                                  a.max_iter, h_rec, D, s0);
                 if (cap >= T(0)) nunc += 1 - conv;
                 if (a.dca_out) ((T *)a.dca_out)[(int64_t)(tl.w0 + ii) * S + s] = D;
             }
@@ -528,22 +570,34 @@ __device__ __forceinline__ bool finish_stage(uint64_t *bar, uint32_t &parity, ui
 // ------------------------------------------------------------------------------------------------
 
 struct PLayout {
-    size_t sph0, sph1, wrow, orow, cap, frame, drift, mask, total;
+    size_t sph, wrow, orow, cap, frame, drift, mask, total;
     int wcap;
+    int nsph;    // float4 sphere entries per warp
 };
 
-// sph_smem: the warps' sphere tables live in shared memory (built here when no bounds table was
-// given); with the bounds table of the recording kernel the warps read it in place (L1-cached), and
-// the CTA's shared memory shrinks by 12.8 KB (more resident CTAs).
-__host__ __device__ inline PLayout p_layout(int W, int es, bool sph_smem)
+// Sphere entries each warp keeps in shared memory: the whole table (built here) when no bounds
+// table was given; with the recording kernel's table, the part a group can use -- its kN0Max
+// super-segment spheres and the level-1 spheres of the super-segments an n_rec-state track has --
+// copied in per work item (about 1.3 KB per warp at 70 recorded states, so that the per-wire
+// level-1 tests read shared memory, not L2); none when every state is scanned (dca_out requested).
+__host__ __device__ inline int p_sph_entries(const DcaArgs &a)
+{
+    if (a.exact_all) return 0;
+    if (a.bounds == nullptr) return kBoundsPerGroup;
+    int n0 = (a.n_rec + a.G0 - 1) / a.G0;
+    n0 = n0 < kN0Max ? n0 : kN0Max;
+    return kN0Max + n0 * kN1Max;
+}
+
+__host__ __device__ inline PLayout p_layout(int W, int es, int nsph)
 {
     PLayout L;
     int wc = ((W + 31) / 32) * 32;
     wc = wc < 32 ? 32 : wc;
     L.wcap = wc;
-    L.sph0 = 16;
-    L.sph1 = align16(L.sph0 + (sph_smem ? 16 * kWarps * kN0Max : 0));
-    L.wrow = align16(L.sph1 + (sph_smem ? (size_t)16 * kWarps * kN0Max * kN1Max : 0));
+    L.nsph = nsph;
+    L.sph = 16;
+    L.wrow = align16(L.sph + (size_t)16 * kWarps * nsph);
     L.orow = align16(L.wrow + (size_t)es * 6 * (wc + 32));
     L.cap = align16(L.orow + (size_t)4 * (wc + 40));
     L.frame = align16(L.cap + (size_t)es * wc);
@@ -559,13 +613,13 @@ template <typename T, class F>
 __global__ void __launch_bounds__(kThreads, COMET_DCA_MINB) dca_persistent_kernel(F f, DcaArgs a)
 {
     const bool sph_smem = a.bounds == nullptr && !a.exact_all;
-    const PLayout L = p_layout(a.W, (int)sizeof(T), sph_smem);
+    const PLayout L = p_layout(a.W, (int)sizeof(T), p_sph_entries(a));
     extern __shared__ __align__(128) unsigned char sm[];
     uint64_t *bar = (uint64_t *)sm;
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
-    float4 *sph0 = (float4 *)(sm + L.sph0) + warp * kN0Max;
-    float4 *sph1 = (float4 *)(sm + L.sph1) + warp * kN0Max * kN1Max;
+    float4 *sph0 = (float4 *)(sm + L.sph) + warp * L.nsph;
+    float4 *sph1 = sph0 + kN0Max;
     T *wrow = (T *)(sm + L.wrow);
     int32_t *orow = (int32_t *)(sm + L.orow);
     T *capv = (T *)(sm + L.cap);
@@ -649,13 +703,15 @@ __global__ void __launch_bounds__(kThreads, COMET_DCA_MINB) dca_persistent_kerne
         const int64_t g = (int64_t)(it / (unsigned)nc);
         const int c = (int)(it % (unsigned)nc);
         const Group<T> gr = load_group<T>(a, g, lane);
-        const float4 *s0 = sph0, *s1 = sph1;
         if (sph_smem) {
             build_spheres<T>(a, gr, lane, sph0, sph1, g);
-        } else if (a.bounds) {
-            s0 = (const float4 *)a.bounds + g * kBoundsPerGroup;   // read in place
-            s1 = s0 + kN0Max;
+        } else if (L.nsph > 0) {
+            // the usable part of this group's table from the recording kernel
+            const float4 *src = (const float4 *)a.bounds + g * kBoundsPerGroup;
+            for (int i = lane; i < L.nsph; i += 32) sph0[i] = __ldg(src + i);
+            __syncwarp();
         }
+        const float4 *s0 = sph0, *s1 = sph1;
         Acc<T> acc;
         int nin = 0;
         if (!split) {
@@ -840,7 +896,7 @@ template <typename T, class F>
 static cudaError_t dca_launch(const F &fld, const DcaArgs &a, cudaStream_t st)
 {
     if (a.W <= kPersistMaxW && a.counter) {
-        const PLayout L = p_layout(a.W, (int)sizeof(T), a.bounds == nullptr && !a.exact_all);
+        const PLayout L = p_layout(a.W, (int)sizeof(T), p_sph_entries(a));
         cudaError_t e = cudaFuncSetAttribute(dca_persistent_kernel<T, F>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
         if (e != cudaSuccess) return e;
@@ -926,7 +982,7 @@ void dca_segments(int n_rec, int *G0, int *G1)
 template <typename T, class F>
 __global__ void __launch_bounds__(kThreads, COMET_DCA_BATCH_MINB) dca_batch_kernel(F f, BatchLaunch BL)
 {
-    const PLayout L = p_layout(BL.W_max, (int)sizeof(T), false);   // batches always carry bounds
+    const PLayout L = p_layout(BL.W_max, (int)sizeof(T), 0);   // batches read their bounds in place
     extern __shared__ __align__(128) unsigned char sm[];
     uint64_t *bar = (uint64_t *)sm;
     __shared__ int64_t s_chunk;
@@ -1098,7 +1154,7 @@ static cudaError_t dca_batch_launch(const F &fld, const BatchLaunch &BL, cudaStr
 {
     // (the shared-memory attribute for W_max was set when the batch was prepared: nothing here but
     // stream work, so that the launch can be captured)
-    const PLayout L = p_layout(BL.W_max, (int)sizeof(T), false);
+    const PLayout L = p_layout(BL.W_max, (int)sizeof(T), 0);
     cudaError_t e = cudaMemsetAsync(BL.chunk_counter, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
     if (BL.dca_ctas == 0) return cudaSuccess;
@@ -1109,7 +1165,7 @@ static cudaError_t dca_batch_launch(const F &fld, const BatchLaunch &BL, cudaStr
 template <typename T, class F>
 static int dca_ctas_per_sm_t(int W)
 {
-    const PLayout L = p_layout(W, (int)sizeof(T), false);
+    const PLayout L = p_layout(W, (int)sizeof(T), 0);
     if (cudaFuncSetAttribute(dca_batch_kernel<T, F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)L.total) != cudaSuccess)
         return 0;
