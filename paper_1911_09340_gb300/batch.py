@@ -12,6 +12,12 @@ With ``graph=True`` the work comet_scan_batch enqueues is captured once in a CUD
 round replays it after comet_scan_batch_update has packed the round's descriptors (grid sizes
 depend on the caps only).
 
+Size-aware rounds (``solo_min_seeds``): a partition of that many seeds or more fills the GPU by
+itself, so it runs through the single-event calls (lattice, propagate, dca, select, classify on the
+slot's resident buffers) on a second stream, while the round's smaller partitions run as one batch
+on the first stream -- the big partitions keep the single-event kernels' efficiency, the small ones
+share launches, and each fills the other's kernel tails.  Both streams join at the end of a round.
+
 The host work per round is descriptor packing; every step of the scan runs in the library's
 kernels.
 """
@@ -47,7 +53,8 @@ class BatchScanner:
     def __init__(self, ctx: B.Context, dtype=torch.float32, stride: int = 16, lam: float = 1e-2,
                  slots: int = 128, max_seeds: int = 1 << 18, max_total_seeds: int = 1 << 24,
                  max_wires: int = 512, max_hits: int = 2048, max_n_steps: int = 2400,
-                 graph: bool = True, field: Optional[synth.Field] = None, dca_ctas_per_sm: int = 0):
+                 graph: bool = True, field: Optional[synth.Field] = None, dca_ctas_per_sm: int = 0,
+                 solo_min_seeds: Optional[int] = None, solo_lanes: int = 1):
         self.ctx, self.dtype, self.stride, self.lam = ctx, dtype, stride, lam
         self.slots = self.slots_alloc = slots
         self.max_hits = max_hits
@@ -84,15 +91,27 @@ class BatchScanner:
         self.graphs = {}                 # captured rounds, per caps
         self.use_graph = graph
         self.stream = torch.cuda.Stream()
+        # partitions of at least this many seeds run alone through the single-event calls, spread
+        # round-robin over `solo_lanes` lanes (a context, a stream and a workspace each: one
+        # context's DCA calls must not overlap on the GPU, those of different contexts may)
+        self.solo_min_seeds = solo_min_seeds
+        self.solo_lanes = solo_lanes
+        self._lanes = []                 # [(context, stream, workspace)], made on first use
+        self.solo_params = {}
 
     def _caps(self, slots: int, dca_ctas_per_sm: int) -> B.BatchCaps:
         return B.BatchCaps(slots, self.max_seeds, self.max_total_seeds, self.max_wires,
                            slots * self.max_wires, dca_ctas_per_sm)
 
     def configure(self, slots: Optional[int] = None, dca_ctas_per_sm: Optional[int] = None,
-                  graph: Optional[bool] = None):
-        """Events in flight (at most the slots allocated), DCA CTAs per SM and graph use of the next
-        runs (the knobs the autotuner turns)."""
+                  graph: Optional[bool] = None, solo_min_seeds=-1, solo_lanes: Optional[int] = None):
+        """Events in flight (at most the slots allocated), DCA CTAs per SM, graph use, the solo
+        threshold (None: every partition batched) and the number of solo lanes of the next runs
+        (the knobs the autotuner turns)."""
+        if solo_min_seeds != -1:
+            self.solo_min_seeds = solo_min_seeds
+        if solo_lanes is not None:
+            self.solo_lanes = max(1, int(solo_lanes))
         if slots is not None:
             if slots > self.slots_alloc:
                 raise ValueError("more slots than allocated")
@@ -160,6 +179,52 @@ class BatchScanner:
         d.n_unconverged = self.s_unconv[slot:].data_ptr()
         return S
 
+    def _lane(self, k: int):
+        while len(self._lanes) <= k:
+            c = self.ctx if not self._lanes else B.Context(self.ctx.device)
+            self._lanes.append((c, torch.cuda.Stream(),
+                                scan.Workspace(self.max_seeds, self.n_rec_max, 1, self.dtype)))
+        return self._lanes[k]
+
+    def close_lanes(self):
+        """Releases the extra contexts of the solo lanes (the first lane uses the scanner's)."""
+        torch.cuda.synchronize()
+        for c, _, _ in self._lanes[1:]:
+            c.close()
+        self._lanes = []
+
+    def _solo(self, lane, slot: int, ev, part: int):
+        """One partition of the event in ``slot`` through the single-event calls on a solo lane
+        (context, stream, workspace), reading and updating the slot's resident hits and mask and
+        writing its outputs."""
+        ctx, st, ws = lane
+        spec = ev.partitions[part]
+        S = spec.n_seeds
+        n = ev.n_steps[part]
+        key = n
+        bp = self.solo_params.get(key)
+        if bp is None:
+            bp = B.ScanParams(n_steps=n, stride=self.stride, lam=self.lam, tol=self.params.tol,
+                              max_iter=self.params.max_iter)
+            self.solo_params[key] = bp
+        seeds, charge, pts, nv, rss, n_in = ws.views(S, bp.n_rec)
+        W, H = ev.n_wires, ev.n_hits
+        wires = self.s_wires[slot]
+        offs = self.s_offs[slot, : W + 1]
+        drift = self.s_drift[slot, : max(H, 1)]
+        mask = self.s_mask[slot, : max(H, 1)]
+        bounds = ws.bounds[: (S + 31) // 32]
+        B.comet_scan_lattice(ctx, spec, seeds, charge, stream=st)
+        B.comet_scan_propagate(ctx, self.field, bp, seeds, charge, pts, nv, bounds=bounds, stream=st)
+        B.comet_scan_dca(ctx, self.field, bp, pts, nv, charge, wires, offs, drift, mask, rss, n_in,
+                         n_unconverged=self.s_unconv[slot:slot + 1], n_wires=W, bounds=bounds, stream=st)
+        B.comet_scan_select(ctx, rss, 1, self.s_best[slot:slot + 1], self.s_best_rss[slot:slot + 1],
+                            stream=st)
+        if W > 0:
+            B.comet_scan_classify(ctx, self.field, bp, pts, nv, charge, self.s_best[slot:slot + 1],
+                                  wires, offs, drift, mask, self.s_class[slot, : max(H, 1)],
+                                  update_mask=True, n_wires=W, stream=st)
+
     # ---- the run -----------------------------------------------------------------------------------
     def run(self, events, collect: bool = False, pinned=None) -> Dict:
         """Scans every partition of every event.  Returns per-event results (when ``collect``: best
@@ -185,7 +250,8 @@ class BatchScanner:
                         state[slot] = (i, 0)
                         results[i].start_round = rnd
                 o_s = o_b = w_tot = 0
-                members = []
+                members, solos = [], []
+                solo_min = self.solo_min_seeds
                 for k in range(self.slots):
                     slot = (start + k) % self.slots
                     st = state[slot]
@@ -194,6 +260,9 @@ class BatchScanner:
                         continue
                     ev = events[st[0]]
                     S = ev.partitions[st[1]].n_seeds
+                    if solo_min is not None and S >= solo_min:
+                        solos.append(slot)
+                        continue
                     if o_s + S > self.caps.max_total_seeds or w_tot + ev.n_wires > self.caps.max_total_wires:
                         continue                       # waits for the next round
                     self._fill(slot, ev, st[1], o_s, o_b)
@@ -202,7 +271,23 @@ class BatchScanner:
                     w_tot += ev.n_wires
                     members.append(slot)
                 start = (start + 1) % self.slots
-                self._launch()
+                lanes = [self._lane(k) for k in range(min(self.solo_lanes, len(solos)))]
+                if solos:
+                    # the solo lanes start after this round's loads and the previous round
+                    loaded = torch.cuda.Event()
+                    loaded.record(self.stream)
+                    for _, st_l, _ in lanes:
+                        st_l.wait_event(loaded)
+                    for n_s, slot in enumerate(solos):
+                        i, p = state[slot]
+                        self._solo(lanes[n_s % len(lanes)], slot, events[i], p)
+                if members:
+                    self._launch()
+                for _, st_l, _ in lanes:
+                    done = torch.cuda.Event()
+                    done.record(st_l)
+                    self.stream.wait_event(done)
+                members += solos
                 e = torch.cuda.Event(enable_timing=True)
                 e.record()
                 if collect:
@@ -287,22 +372,28 @@ def run_interleaved(scanners, events, collect: bool = False, pinned=None) -> Dic
 
 
 def autotune(scanner: BatchScanner, events, slots_options=(32, 64, 128, 256), ctas_options=(0, 4, 2),
-             graph_options=(True, False)):
-    """Measures events/s of each (events in flight, DCA CTAs per SM, CUDA graph) on ``events`` (a
-    sample of the workload; one warm run and one timed run each) and leaves the scanner configured
-    with the fastest.  Returns (best, table)."""
+             graph_options=(True, False), solo_options=(None,), lanes_options=(1,)):
+    """Measures events/s of each (events in flight, DCA CTAs per SM, CUDA graph, solo threshold,
+    solo lanes) on ``events`` (a sample of the workload; one warm run and one timed run each) and
+    leaves the scanner configured with the fastest.  Returns (best, table)."""
     table = []
     pinned = scanner.pin(events)
-    for g in graph_options:
-        for sl in slots_options:
-            if sl > scanner.slots_alloc:
-                continue
-            for c in ctas_options:
-                scanner.configure(slots=sl, dca_ctas_per_sm=c, graph=g)
-                scanner.run(events, pinned=pinned)
-                r = scanner.run(events, pinned=pinned)
-                table.append({"slots": sl, "dca_ctas_per_sm": c, "graph": g,
-                              "events_per_s": len(events) / (r["gpu_ms"] * 1e-3), "gpu_ms": r["gpu_ms"]})
+    for solo in solo_options:
+        for nl in (lanes_options if solo is not None else (1,)):
+            for g in graph_options:
+                for sl in slots_options:
+                    if sl > scanner.slots_alloc:
+                        continue
+                    for c in ctas_options:
+                        scanner.configure(slots=sl, dca_ctas_per_sm=c, graph=g, solo_min_seeds=solo,
+                                          solo_lanes=nl)
+                        scanner.run(events, pinned=pinned)
+                        r = scanner.run(events, pinned=pinned)
+                        table.append({"slots": sl, "dca_ctas_per_sm": c, "graph": g,
+                                      "solo_min_seeds": solo, "solo_lanes": nl,
+                                      "events_per_s": len(events) / (r["gpu_ms"] * 1e-3),
+                                      "gpu_ms": r["gpu_ms"]})
     best = max(table, key=lambda t: t["events_per_s"])
-    scanner.configure(slots=best["slots"], dca_ctas_per_sm=best["dca_ctas_per_sm"], graph=best["graph"])
+    scanner.configure(slots=best["slots"], dca_ctas_per_sm=best["dca_ctas_per_sm"], graph=best["graph"],
+                      solo_min_seeds=best["solo_min_seeds"], solo_lanes=best["solo_lanes"])
     return best, table

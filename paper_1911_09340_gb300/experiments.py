@@ -316,7 +316,7 @@ def generate_batch_events(n: int, workers: int = 0):
         return pool.map(synth.batch_event, range(n), chunksize=4)
 
 
-def batch_study(n_events: int = 512, stride: int = 16, lam: float = 1e-2, tune_events: int = 128,
+def batch_study(n_events: int = 512, stride: int = 32, lam: float = 1e-2, tune_events: int = 128,
                 dtype=torch.float32, max_total_seeds: int = 1 << 25):
     """Events/s and per-event latency of the batching workload (1-6 turns, 2^12-2^18 seeds per
     partition by turn count, uneven hit counts): the per-event path (one partition at a time, six
@@ -355,10 +355,13 @@ def batch_study(n_events: int = 512, stride: int = 16, lam: float = 1e-2, tune_e
     sc = BT.BatchScanner(ctx, dtype, stride, lam, slots=256, max_total_seeds=max_total_seeds,
                          max_wires=max(512, max(ev.n_wires for ev in events)),
                          max_hits=max(2048, max(ev.n_hits for ev in events)))
-    best, table = BT.autotune(sc, events[:tune_events])
+    best, table = BT.autotune(sc, events[:tune_events], slots_options=(64, 128, 256), ctas_options=(0, 4),
+                              graph_options=(True, False), solo_options=(None, 1 << 16, 1 << 17),
+                              lanes_options=(1, 2, 3, 4))
     pinned = sc.pin(events)
     sc.run(events[:tune_events], pinned=pinned[:tune_events])
     r = sc.run(events, pinned=pinned)
+    sc.close_lanes()
     # two scanners (two contexts and streams) with the tuned configuration, rounds interleaved
     half = max(1, max_total_seeds // 2)
     ctx2 = B.Context(torch.cuda.current_device())
@@ -367,10 +370,13 @@ def batch_study(n_events: int = 512, stride: int = 16, lam: float = 1e-2, tune_e
     pair = [BT.BatchScanner(c, dtype, stride, lam, slots=best["slots"], max_total_seeds=half,
                             max_wires=max(512, max(ev.n_wires for ev in events)),
                             max_hits=max(2048, max(ev.n_hits for ev in events)),
-                            graph=best["graph"], dca_ctas_per_sm=best["dca_ctas_per_sm"])
+                            graph=best["graph"], dca_ctas_per_sm=best["dca_ctas_per_sm"],
+                            solo_min_seeds=best["solo_min_seeds"], solo_lanes=best["solo_lanes"])
             for c in (ctx, ctx2)]
     BT.run_interleaved(pair, events[:tune_events])
     r2 = BT.run_interleaved(pair, events)
+    for sc2 in pair:
+        sc2.close_lanes()
     del pair
     ctx2.close()
     wires = np.array([ev.n_wires for ev in events])

@@ -268,9 +268,25 @@ class Event:
         return math.hypot(self.pt, self.pz)
 
 
-def _signal_hits(ch: Chamber, track, s_total, rng, max_dca=8e-3, sigma=150e-6, ds=1e-3):
-    """All (wire, pass) local minima of the truth-trajectory distance to a wire under ``max_dca``,
-    with the foot of the perpendicular inside the wire's extent.  Returns (wire, s_pca, dtrue, r)."""
+def fired_wire_bounds(ch: Chamber, track, s_total, max_dca=8e-3, ds=1e-3):
+    """Bounds (n_lo, n_hi) on the number of distinct wires _signal_hits fires, from the trajectory
+    sampled every ds alone (no minimisation, no random draws): along a run the true minimum distance
+    lies between the sampled minimum minus ds/2 and the sampled minimum, and the foot of the
+    perpendicular moves by less than ds along the wire between samples."""
+    s, pos, wid, sidx, run_id, n_runs = _hit_runs(ch, track, s_total, max_dca, ds)
+    if wid is None:
+        return 0, 0
+    d_all, t_all = _dist_to_wires(pos[:, sidx], ch.a[:, wid], ch.u[:, wid])
+    zf = np.abs(t_all * ch.u[2, wid])
+    sure = (d_all < max_dca) & (zf <= ch.half_length - ds)
+    maybe = (d_all < max_dca + 0.5 * ds) & (zf <= ch.half_length + ds)
+    return len(np.unique(wid[sure])), len(np.unique(wid[maybe]))
+
+
+def _hit_runs(ch: Chamber, track, s_total, max_dca, ds):
+    """The trajectory sampled every ds and the (wire, consecutive samples) runs within reach of a
+    wire.  Returns (s, pos, wire of each entry, sample of each entry, run id, number of runs), the
+    entries sorted by (wire, sample); wire is None when no sample is near any wire."""
     s = np.arange(0.0, s_total + 0.5 * ds, ds)
     pos, _ = track(s)
     rho = np.hypot(pos[0], pos[1])
@@ -294,10 +310,10 @@ def _signal_hits(ch: Chamber, track, s_total, rng, max_dca=8e-3, sigma=150e-6, d
             ok = d < max_dca + 1.5e-3
             wl.append(wid[ok])
             sl.append(sel[ok])
-    if not wl:
-        return (np.zeros(0, np.int64),) + (np.zeros(0),) * 3
-    wid = np.concatenate(wl)
-    sidx = np.concatenate(sl)
+    wid = np.concatenate(wl) if wl else np.zeros(0, np.int64)
+    sidx = np.concatenate(sl) if sl else np.zeros(0, np.int64)
+    if wid.size == 0:
+        return s, pos, None, None, None, 0
     # unique (wire, sample) then runs of consecutive samples per wire = passes
     key = np.unique(wid * (len(s) + 1) + sidx)
     wid = key // (len(s) + 1)
@@ -305,7 +321,15 @@ def _signal_hits(ch: Chamber, track, s_total, rng, max_dca=8e-3, sigma=150e-6, d
     new_run = np.ones(len(key), bool)
     new_run[1:] = (wid[1:] != wid[:-1]) | (sidx[1:] != sidx[:-1] + 1)
     run_id = np.cumsum(new_run) - 1
-    n_runs = run_id[-1] + 1
+    return s, pos, wid, sidx, run_id, run_id[-1] + 1
+
+
+def _signal_hits(ch: Chamber, track, s_total, rng, max_dca=8e-3, sigma=150e-6, ds=1e-3):
+    """All (wire, pass) local minima of the truth-trajectory distance to a wire under ``max_dca``,
+    with the foot of the perpendicular inside the wire's extent.  Returns (wire, s_pca, dtrue, r)."""
+    s, pos, wid, sidx, run_id, n_runs = _hit_runs(ch, track, s_total, max_dca, ds)
+    if wid is None:
+        return (np.zeros(0, np.int64),) + (np.zeros(0),) * 3
     d_all, _ = _dist_to_wires(pos[:, sidx], ch.a[:, wid], ch.u[:, wid])
     # argmin sample of every run
     order = np.lexsort((d_all, run_id))
@@ -431,7 +455,8 @@ def _make_event(ch, rng, vertex, pt, phi0, pz, q, bz, n_turns, counts, noise_fra
 
 def make_event_random(ch: Chamber, rng, p_range=(100.0, 105.0), turns=(2, 5), counts=(16, 16, 32, 32),
                       hits_window=(60, 250), noise_frac=0.10, q=-1, bz=1.0, h=1e-3,
-                      field: Optional[Field] = None, p_sampler=None, max_tries=200) -> Event:
+                      field: Optional[Field] = None, p_sampler=None, max_tries=200,
+                      prescreen: bool = False) -> Event:
     """One multi-turn event of the 1000-event workload.
 
     Vertex: one of 17 disks (z = -0.40 + 0.05 d m, d = 0..16) of 10 cm radius, uniform on the disk.
@@ -439,7 +464,10 @@ def make_event_random(ch: Chamber, rng, p_range=(100.0, 105.0), turns=(2, 5), co
     derived so that N_t turns span U(0.6, 0.95) of the chamber length in front of the vertex (a 40-70
     degree pitch cannot fit 2-5 turns in a 1.5 m chamber; this keeps the chamber and the turn count).
     Events whose number of signal fired wires falls outside ``hits_window`` are redrawn (the paper's
-    preselection counts fired wires, Sec. 3.3); 10% noise hits are then added on top."""
+    preselection counts fired wires, Sec. 3.3); 10% noise hits are then added on top.
+    ``prescreen`` (uniform field only) rejects a draw whose fired-wire bounds (fired_wire_bounds)
+    miss the window before its hits are simulated: fewer random numbers are drawn for it, so the
+    events differ from those without it (same distribution)."""
     for _ in range(max_tries):
         n_t = int(rng.integers(turns[0], turns[1] + 1))
         p = float(p_sampler(rng)) if p_sampler is not None else float(rng.uniform(*p_range))
@@ -455,6 +483,12 @@ def make_event_random(ch: Chamber, rng, p_range=(100.0, 105.0), turns=(2, 5), co
             continue
         pt = math.sqrt(p * p - pz * pz)
         phi0 = rng.uniform(0.0, 2.0 * math.pi)
+        if prescreen and (field is None or field.kind == 0):
+            s_tot = n_t * 2.0 * math.pi * math.hypot(pt, pz) / (KAPPA * abs(q) * bz)
+            n_lo, n_hi = fired_wire_bounds(
+                ch, lambda sv: helix_points(vertex, pt, phi0, pz, q, bz, sv), s_tot)
+            if n_hi < hits_window[0] or n_lo > hits_window[1]:
+                continue
         ev = _make_event(ch, rng, vertex, pt, phi0, pz, q, bz, n_t, counts, noise_frac, h, field)
         n_fired = len(np.unique(ev.wire_ids[np.repeat(np.arange(ev.n_wires), np.diff(ev.hit_offsets))]
                                 [ev.hit_turn >= 0]))
@@ -498,12 +532,19 @@ BATCH_COUNTS = {1: (4, 4, 16, 16), 2: (4, 8, 16, 16), 3: (8, 8, 16, 16), 4: (8, 
                 5: (16, 8, 32, 32), 6: (16, 16, 32, 32)}   # 2^12, 2^13, 2^14, 2^16, 2^17, 2^18 seeds
 
 
+# Fired signal wires that 100-105 MeV/c electrons of 1-6 turns give in this chamber (measured over
+# the workload's events): bins of the log-uniform target outside this range cannot be reached.
+BATCH_FIRED_REACH = (32, 237)
+
+
 def batch_event(i: int, chamber: Optional[Chamber] = None, counts_scale: int = 0) -> Event:
     """Event i of the batching workload: 1-6 turns, p ~ U(100, 105) MeV/c, seeds per partition by
     turn count (BATCH_COUNTS; ``counts_scale`` halves the two fastest dimensions that many times for
     small test lattices), fired signal wires log-uniform over 20-400: a target bin of 16 log-spaced
-    bins is drawn first and the turn count is redrawn until an event lands in it (rejection to a
-    16-bin log histogram; a bin no turn count reaches in 12 draws falls back to 20-400)."""
+    bins is drawn first, then events (turn count uniform in 1-6 and the rest of the 1000-event
+    workload's parameters) are drawn until one lands in the bin -- rejection sampling of the
+    workload conditioned on the bin, at most 72 draws.  A bin outside BATCH_FIRED_REACH, or one
+    that 72 draws miss, takes an event of the whole 20-400 window instead."""
     ch = chamber or make_chamber()
     rng = workload_rng(5, i)
     edges = np.geomspace(20.0, 400.0, 17)
@@ -517,13 +558,14 @@ def batch_event(i: int, chamber: Optional[Chamber] = None, counts_scale: int = 0
             c[3] = max(2, c[3] // 2)
         return tuple(c)
 
-    for _ in range(12):
-        n_t = int(rng.integers(1, 7))
-        try:
-            return make_event_random(ch, rng, turns=(n_t, n_t), counts=counts_for(n_t),
-                                     hits_window=(lo, max(lo, hi)), max_tries=6)
-        except RuntimeError:
-            continue
+    if hi >= BATCH_FIRED_REACH[0] and lo <= BATCH_FIRED_REACH[1]:
+        for _ in range(72):
+            n_t = int(rng.integers(1, 7))
+            try:
+                return make_event_random(ch, rng, turns=(n_t, n_t), counts=counts_for(n_t),
+                                         hits_window=(lo, max(lo, hi)), max_tries=1, prescreen=True)
+            except RuntimeError:
+                continue
     n_t = int(rng.integers(1, 7))
     return make_event_random(ch, rng, turns=(n_t, n_t), counts=counts_for(n_t), hits_window=(20, 400))
 

@@ -50,6 +50,32 @@ def test_batch_equals_per_event_scan(ctx, dtype_name, graph, budget):
     assert np.all(r["latency_ms"] > 0) and r["rounds"] >= max(len(ev.partitions) for ev in events)
 
 
+@pytest.mark.parametrize("dtype_name,solo_lanes", [("float32", 1), ("float32", 3), ("float64", 2)])
+def test_size_aware_rounds_equal_per_event_scan(ctx, dtype_name, solo_lanes):
+    """Partitions of at least 256 seeds run through the single-event calls on 1-3 solo lanes (each
+    with its own context and stream) while the smaller ones are batched: every partition's results
+    are still identical to the per-event scan."""
+    import torch
+    from paper_1911_09340_gb300 import batch
+    dtype = getattr(torch, dtype_name)
+    events = _events(9)
+    sizes = {sp.n_seeds for ev in events for sp in ev.partitions}
+    assert min(sizes) < 256 <= max(sizes)          # both kinds of partition occur
+    ref = _reference(ctx, events, dtype, 16)
+    bs = batch.BatchScanner(ctx, dtype, stride=16, lam=1e-2, slots=4, max_seeds=4096,
+                            max_total_seeds=1 << 16, max_wires=512, max_hits=1024, graph=True,
+                            solo_min_seeds=256, solo_lanes=solo_lanes)
+    try:
+        r = bs.run(events, collect=True)
+        for ev, rr, res in zip(events, ref, r["results"]):
+            assert len(res.best_idx) == len(ev.partitions)
+            for p, part in enumerate(rr):
+                assert res.best_idx[p] == part["idx"] and res.best_rss[p] == part["rss"]
+                assert np.array_equal(res.hit_class[p], part["hit_class"])
+    finally:
+        bs.close_lanes()
+
+
 def test_autotune_then_run_matches_per_event_scan(ctx):
     """The autotuner cycles through configurations (new caps reallocate the context's staging, and
     graphs captured before must be dropped); the configured run afterwards still reproduces the
@@ -94,3 +120,92 @@ def test_two_interleaved_scanners_match_per_event_scan(ctx):
         torch.cuda.synchronize()
     finally:
         ctx2.close()
+
+
+def _variant(ev, keep=None, extra_wires=0, seed=0):
+    """An event with only the wires ``keep`` (indices into ev's wires), or with ``extra_wires``
+    random chamber wires added, each with one noise hit (drift ~ U(0, 8 mm)); CSR order kept."""
+    import dataclasses
+    ch = synth.make_chamber()
+    rng = np.random.default_rng(seed)
+    offs = np.asarray(ev.hit_offsets)
+    ids = list(range(ev.n_wires)) if keep is None else list(keep)
+    hits = [np.arange(offs[i], offs[i + 1]) for i in ids]
+    wire_ids = [int(ev.wire_ids[i]) for i in ids]
+    cols = [ev.wires[:, i] for i in ids]
+    drift = [ev.drift[h] for h in hits]
+    turn = [ev.hit_turn[h] for h in hits]
+    dtrue = [ev.hit_dtrue[h] for h in hits]
+    if extra_wires:
+        new = rng.choice(np.setdiff1d(np.arange(ch.n_wires), ev.wire_ids), size=extra_wires, replace=False)
+        for w in new:
+            wire_ids.append(int(w))
+            cols.append(np.concatenate([ch.a[:, w], ch.u[:, w]]))
+            drift.append(rng.uniform(0, 8e-3, size=1))
+            turn.append(np.array([-1], np.int32))
+            dtrue.append(np.array([np.nan]))
+    order = np.argsort(wire_ids, kind="stable")
+    counts = np.array([len(drift[i]) for i in order])
+    o = np.zeros(len(order) + 1, np.int32)
+    o[1:] = np.cumsum(counts)
+    return dataclasses.replace(
+        ev, wire_ids=np.array(wire_ids, np.int32)[order], wires=np.stack([cols[i] for i in order], 1),
+        hit_offsets=o, drift=np.concatenate([drift[i] for i in order]),
+        hit_turn=np.concatenate([turn[i] for i in order]).astype(np.int32),
+        hit_dtrue=np.concatenate([dtrue[i] for i in order]))
+
+
+@pytest.mark.parametrize("dtype_name", ["float32", "float64"])
+def test_batch_matches_oracle(ctx, dtype_name):
+    """The batched path against the oracle, not only against the per-event path: events of 1-6 turns
+    (small lattices), among them one reduced to a single wire (W = 1) and one with 300 extra wires
+    (W > 256); every partition's selected seed by the argmin rule (identical, or oracle RSS within
+    1e-5 relative of the oracle's minimum over all seeds), its RSS (FP64 within 1e-10 relative; FP32
+    within the bound of the 2 um DCA bar), its hit classes bit-identical except within 1 um (FP32) /
+    1e-9 m (FP64) of the cutoff, and the mask carried from partition to partition."""
+    import torch
+
+    import oracle as O
+    from gpu_util import CLASS_EDGE, FP32_DCA_TOL, per_wire_residual, rss_bound, seen
+    from paper_1911_09340_gb300 import batch
+    dtype = getattr(torch, dtype_name)
+    evs = [synth.batch_event(i, counts_scale=3) for i in range(12)]
+    by_turns = {}
+    for ev in evs:
+        by_turns.setdefault(len(ev.partitions), ev)
+    events = [by_turns[k] for k in sorted(by_turns)]
+    events.append(_variant(events[0], keep=[int(np.argmax(np.diff(events[0].hit_offsets)))]))
+    events.append(_variant(events[-2], extra_wires=300, seed=3))
+    assert events[-2].n_wires == 1 and events[-1].n_wires > 256
+    assert len({len(ev.partitions) for ev in events}) >= 4
+    stride, lam = 32, 1e-2
+    bs = batch.BatchScanner(ctx, dtype, stride=stride, lam=lam, slots=4, max_seeds=1 << 12,
+                            max_total_seeds=1 << 14, max_wires=1024, max_hits=2048, graph=False)
+    r = bs.run(events, collect=True)
+    field = synth.uniform_field(1.0)
+    for ev, res in zip(events, r["results"]):
+        w, d = O.wires_aos(seen(ev.wires, dtype)), seen(ev.drift, dtype)
+        wid = np.repeat(np.arange(ev.n_wires), np.diff(ev.hit_offsets))
+        omask = np.zeros(ev.n_hits, np.uint8)
+        assert len(res.best_idx) == len(ev.partitions)
+        for p, spec in enumerate(ev.partitions):
+            seeds = seen(O.lattice(spec), dtype)
+            op = O.Params(n_steps=ev.n_steps[p], stride=stride, lam=lam, tol=1e-12)
+            o = O.scan(field, op, seeds, spec.charge, w, ev.hit_offsets, d, omask)
+            o_idx, o_best = O.select(o["rss"], 1)
+            g = res.best_idx[p]
+            assert g == int(o_idx[0]) or o["rss"][g] <= o_best[0] * (1 + 1e-5), (p, g, int(o_idx[0]))
+            one = O.scan(field, op, seeds[g:g + 1], spec.charge, w, ev.hit_offsets, d, omask,
+                         want_dca=True)
+            if dtype == torch.float64:
+                assert abs(res.best_rss[p] - one["rss"][0]) <= 1e-10 * one["rss"][0] + 1e-300
+            else:
+                e = per_wire_residual(one["dca"], ev.hit_offsets, d, omask)
+                assert abs(res.best_rss[p] - one["rss"][0]) <= rss_bound(e, lam, FP32_DCA_TOL)[0] + 1e-12
+            cls, dwr, m2 = O.classify(field, op, seeds[g], spec.charge, w, ev.hit_offsets, d, omask,
+                                      update_mask=True)
+            edge = np.abs(np.abs(dwr[wid] - d) - lam) < CLASS_EDGE[dtype]
+            diff = np.flatnonzero(res.hit_class[p] != cls)
+            assert np.all(edge[diff]), (p, diff[~edge[diff]])
+            omask = np.maximum(omask, res.hit_class[p].astype(np.uint8))
+            assert np.array_equal(omask[~edge], m2[~edge])
