@@ -300,6 +300,25 @@ comet_status comet_scan_jacobian(comet_ctx *ctx, comet_dtype dtype, const comet_
 comet_status comet_scan_gn_step(comet_ctx *ctx, double *theta, int64_t S, const double *jtj,
                                 const double *jtr, double mu, comet_stream stream);
 
+/* Levenberg-Marquardt with a per-seed accept/reject of each trial, all on the device (double device
+ * arrays, S in 1 .. 2^24):
+ *   theta [S][4], srss [S], jtj [S][4][4], jtr [S][4]: the current (accepted) seeds and
+ *       comet_scan_jacobian's outputs at them; replaced by the trial's where it is accepted;
+ *   theta_try [S][4]: the trial seeds; overwritten with the next trial;
+ *   srss_try, jtj_try, jtr_try: comet_scan_jacobian's outputs at theta_try (ignored, may be NULL,
+ *       when first != 0);
+ *   mu [S]: per-seed damping.
+ * Unless first != 0, each seed's trial is accepted when its smoothed RSS is below the current one
+ * (then mu *= down), else rejected (mu *= up); mu stays within [1e-12, 1e12].  Then the next trial
+ * is theta_try = theta + delta with (JTJ + mu diag(JTJ)) delta = -JTR (delta = 0 when that matrix
+ * is not positive definite).  up >= 1, 0 < down <= 1.  So the smoothed RSS of the current seeds
+ * never increases: Gauss-Newton steps with the safeguard that the smoothed RSS (whose cap makes it
+ * non-convex, Sec. 2.1) cannot climb. */
+comet_status comet_scan_lm_step(comet_ctx *ctx, int64_t S, double *theta, double *srss, double *jtj,
+                                double *jtr, double *theta_try, const double *srss_try,
+                                const double *jtj_try, const double *jtr_try, double *mu, double up,
+                                double down, int32_t first, comet_stream stream);
+
 /* ---- batches of events in single launches (many events at once) ---------------------------------
  * One turn partition of up to caps.max_events events: for each active event its lattice, track
  * recording, DCA and RSS, selection (k = 1) and classification with the mask update, exactly as the

@@ -90,6 +90,8 @@ SIGNATURES = {
                             C.c_double, _i32, _vp, _i32, _i32, _vp, _vp, _vp, C.c_double, _vp, _vp,
                             _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "comet_scan_gn_step": [_vp, _vp, _i64, _vp, _vp, C.c_double, _vp],
+    "comet_scan_lm_step": [_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.c_double,
+                           C.c_double, _i32, _vp],
     "comet_scan_batch_update": [_vp, C.c_int, C.POINTER(_Field), C.POINTER(_Params),
                                 C.POINTER(BatchCaps), C.POINTER(BatchEvent), _i32],
     "comet_scan_batch": [_vp, C.c_int, C.POINTER(_Field), C.POINTER(_Params), C.POINTER(BatchCaps),
@@ -362,6 +364,18 @@ def comet_scan_gn_step(ctx: Context, theta, jtj, jtr, mu: float = 0.0, stream=No
     f64 = torch.float64
     _check(lib().comet_scan_gn_step(ctx.handle, _ptr(theta, f64), theta.shape[0], _ptr(jtj, f64),
                                     _ptr(jtr, f64), float(mu), _stream(stream)))
+
+
+def comet_scan_lm_step(ctx: Context, theta, srss, jtj, jtr, theta_try, srss_try, jtj_try, jtr_try, mu,
+                       up: float = 3.0, down: float = 1.0 / 3.0, first: bool = False, stream=None):
+    """Levenberg-Marquardt accept/reject of the trial seeds and the next trial (see
+    include/comet_scan.h); every array float64 on the device, the trial's may be None when first."""
+    f64 = torch.float64
+    _check(lib().comet_scan_lm_step(ctx.handle, theta.shape[0], _ptr(theta, f64), _ptr(srss, f64),
+                                    _ptr(jtj, f64), _ptr(jtr, f64), _ptr(theta_try, f64),
+                                    _ptr(srss_try, f64), _ptr(jtj_try, f64), _ptr(jtr_try, f64),
+                                    _ptr(mu, f64), float(up), float(down), int(bool(first)),
+                                    _stream(stream)))
 
 
 def comet_scan_batch_update(ctx: Context, dtype, field: DeviceField, params: ScanParams, caps: BatchCaps,

@@ -545,6 +545,45 @@ comet_status comet_scan_gn_step(comet_ctx *ctx, double *theta, int64_t S, const 
     return e == cudaSuccess ? COMET_OK : cuda_fail(e, "gn_step launch");
 }
 
+comet_status comet_scan_lm_step(comet_ctx *ctx, int64_t S, double *theta, double *srss, double *jtj,
+                                double *jtr, double *theta_try, const double *srss_try,
+                                const double *jtj_try, const double *jtr_try, double *mu, double up,
+                                double down, int32_t first, comet_stream stream)
+{
+    if (!ctx) return fail(COMET_ERR_INVALID_ARG, "ctx is NULL");
+    if (S <= 0 || S > ((int64_t)1 << 24)) return fail(COMET_ERR_INVALID_ARG, "S must be in 1 .. 2^24");
+    const void *req[] = {theta, srss, jtj, jtr, theta_try, mu};
+    for (const void *q : req)
+        if (!q || !aligned(q, 8)) return fail(COMET_ERR_INVALID_ARG, "a required array is NULL or misaligned");
+    if (!first) {
+        const void *tr[] = {srss_try, jtj_try, jtr_try};
+        for (const void *q : tr)
+            if (!q || !aligned(q, 8)) return fail(COMET_ERR_INVALID_ARG, "the trial's arrays are NULL or misaligned");
+    }
+    if (!(up >= 1.0) || !std::isfinite(up) || !(down > 0.0) || !(down <= 1.0))
+        return fail(COMET_ERR_INVALID_ARG, "need up >= 1 and 0 < down <= 1");
+    DeviceGuard g(ctx->device);
+    if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+    comet::LmArgs a;
+    a.S = S;
+    a.theta = theta;
+    a.srss = srss;
+    a.jtj = jtj;
+    a.jtr = jtr;
+    a.theta_try = theta_try;
+    a.srss_try = srss_try;
+    a.jtj_try = jtj_try;
+    a.jtr_try = jtr_try;
+    a.mu = mu;
+    a.up = up;
+    a.down = down;
+    a.mu_min = 1e-12;
+    a.mu_max = 1e12;
+    a.first = first != 0;
+    cudaError_t e = comet::launch_lm_step(a, (cudaStream_t)stream);
+    return e == cudaSuccess ? COMET_OK : cuda_fail(e, "lm_step launch");
+}
+
 comet_status comet_scan_propagate(comet_ctx *ctx, comet_dtype dtype, const comet_field *field,
                                   const comet_scan_params *params, const void *seeds,
                                   const int8_t *charge, int64_t S, void *points, int32_t *n_valid,

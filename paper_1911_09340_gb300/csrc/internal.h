@@ -127,6 +127,18 @@ struct ClsArgs {
     int update_mask;
 };
 
+// Levenberg-Marquardt step over S seeds (comet_scan_lm_step).
+struct LmArgs {
+    int64_t S;
+    double *theta, *srss, *jtj, *jtr;
+    double *theta_try;
+    const double *srss_try, *jtj_try, *jtr_try;
+    double *mu;
+    double up, down, mu_min, mu_max;
+    int first;
+};
+cudaError_t launch_lm_step(const LmArgs &a, cudaStream_t st);
+
 // SM version (major * 10 + minor) of the library's device code, read from a kernel's attributes.
 cudaError_t kernel_binary_version(int *version);
 

@@ -384,22 +384,20 @@ __global__ void jacobian_reduce_kernel(JacArgs a)
     }
 }
 
-// theta += delta, (J^T W J + mu diag(J^T W J)) delta = -J^T W rho, by Cholesky; a seed whose
-// matrix is not positive definite keeps its theta
-__global__ void gn_step_kernel(double *theta, int64_t S, const double *jtj, const double *jtr, double mu)
+// Solves (J^T W J + mu diag(J^T W J)) x = -J^T W rho for one seed by Cholesky; returns false (x
+// untouched) when the damped matrix is not positive definite.
+__device__ bool damped_normal_solve(const double *jtj, const double *jtr, double mu, double x[4])
 {
-    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= S) return;
     double A[4][4], L[4][4] = {}, r[4];
     for (int j = 0; j < 4; ++j) {
-        for (int k = 0; k < 4; ++k) A[j][k] = jtj[s * 16 + j * 4 + k];
+        for (int k = 0; k < 4; ++k) A[j][k] = jtj[j * 4 + k];
         A[j][j] *= 1.0 + mu;
-        r[j] = -jtr[s * 4 + j];
+        r[j] = -jtr[j];
     }
     for (int j = 0; j < 4; ++j) {
         double d = A[j][j];
         for (int k = 0; k < j; ++k) d -= L[j][k] * L[j][k];
-        if (!(d > 0.0)) return;
+        if (!(d > 0.0)) return false;
         L[j][j] = sqrt(d);
         for (int i = j + 1; i < 4; ++i) {
             double v = A[i][j];
@@ -407,7 +405,7 @@ __global__ void gn_step_kernel(double *theta, int64_t S, const double *jtj, cons
             L[i][j] = v / L[j][j];
         }
     }
-    double z[4], x[4];
+    double z[4];
     for (int j = 0; j < 4; ++j) {
         double v = r[j];
         for (int k = 0; k < j; ++k) v -= L[j][k] * z[k];
@@ -418,7 +416,44 @@ __global__ void gn_step_kernel(double *theta, int64_t S, const double *jtj, cons
         for (int k = j + 1; k < 4; ++k) v -= L[k][j] * x[k];
         x[j] = v / L[j][j];
     }
+    return true;
+}
+
+// theta += delta, (J^T W J + mu diag(J^T W J)) delta = -J^T W rho, by Cholesky; a seed whose
+// matrix is not positive definite keeps its theta
+__global__ void gn_step_kernel(double *theta, int64_t S, const double *jtj, const double *jtr, double mu)
+{
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    double x[4];
+    if (!damped_normal_solve(jtj + s * 16, jtr + s * 4, mu, x)) return;
     for (int j = 0; j < 4; ++j) theta[s * 4 + j] += x[j];
+}
+
+// Levenberg-Marquardt bookkeeping of one seed: judge the trial (accept it when its smoothed RSS is
+// lower: it becomes the current seed with its normal equations, and the damping shrinks; else the
+// damping grows), then form the next trial from the current seed.
+__global__ void lm_step_kernel(LmArgs a)
+{
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= a.S) return;
+    double mu = a.mu[s];
+    if (!a.first) {
+        const double ft = a.srss_try[s];
+        if (ft < a.srss[s]) {
+            a.srss[s] = ft;
+            for (int j = 0; j < 4; ++j) a.theta[s * 4 + j] = a.theta_try[s * 4 + j];
+            for (int j = 0; j < 4; ++j) a.jtr[s * 4 + j] = a.jtr_try[s * 4 + j];
+            for (int j = 0; j < 16; ++j) a.jtj[s * 16 + j] = a.jtj_try[s * 16 + j];
+            mu = fmax(mu * a.down, a.mu_min);
+        } else {
+            mu = fmin(mu * a.up, a.mu_max);
+        }
+        a.mu[s] = mu;
+    }
+    double x[4] = {0.0, 0.0, 0.0, 0.0};
+    damped_normal_solve(a.jtj + s * 16, a.jtr + s * 4, mu, x);
+    for (int j = 0; j < 4; ++j) a.theta_try[s * 4 + j] = a.theta[s * 4 + j] + x[j];
 }
 
 } // namespace
@@ -440,6 +475,12 @@ cudaError_t launch_gn_step(double *theta, int64_t S, const double *jtj, const do
                            cudaStream_t st)
 {
     gn_step_kernel<<<(unsigned)((S + 63) / 64), 64, 0, st>>>(theta, S, jtj, jtr, mu);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lm_step(const LmArgs &a, cudaStream_t st)
+{
+    lm_step_kernel<<<(unsigned)((a.S + 63) / 64), 64, 0, st>>>(a);
     return cudaGetLastError();
 }
 

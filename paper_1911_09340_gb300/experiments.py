@@ -255,6 +255,34 @@ class GaussNewton:
             B.comet_scan_gn_step(self.ctx, self.theta, self.jtj, self.jtr, mu)
         self.evaluate()
 
+    def _eval_at(self, theta, srss, grad, jtj, jtr, tau=None):
+        B.comet_scan_jacobian(self.ctx, self.field, self.params, theta, self.spec.vxy[0],
+                              self.spec.vxy[1], self.spec.charge, self.dev.wires, self.dev.hit_offsets,
+                              self.dev.drift, self.dev.mask, self.tau if tau is None else tau, self.work,
+                              srss, grad, jtj, jtr, n_wires=self.dev.W)
+
+    def run_lm(self, iters: int = 10, mu0: float = 1e-3):
+        """Levenberg-Marquardt: each iteration evaluates the trial seeds (one comet_scan_jacobian)
+        and comet_scan_lm_step accepts a seed's trial only if its smoothed RSS is lower (the
+        damping adapts per seed) and forms the next trial; theta ends at the accepted seeds."""
+        if not hasattr(self, "t_theta"):
+            f64 = dict(dtype=torch.float64, device="cuda")
+            K = self.K
+            self.t_theta = torch.empty((K, 4), **f64)
+            self.t_srss = torch.empty(K, **f64)
+            self.t_grad = torch.empty((K, 4), **f64)
+            self.t_jtj = torch.empty((K, 16), **f64)
+            self.t_jtr = torch.empty((K, 4), **f64)
+            self.mu = torch.empty(K, **f64)
+        self.mu.fill_(mu0)
+        self.evaluate()
+        B.comet_scan_lm_step(self.ctx, self.theta, self.srss, self.jtj, self.jtr, self.t_theta, None, None,
+                             None, self.mu, first=True)
+        for _ in range(iters):
+            self._eval_at(self.t_theta, self.t_srss, self.t_grad, self.t_jtj, self.t_jtr)
+            B.comet_scan_lm_step(self.ctx, self.theta, self.srss, self.jtj, self.jtr, self.t_theta,
+                                 self.t_srss, self.t_jtj, self.t_jtr, self.mu)
+
     def hard_rss(self):
         """srss <- Eq. 1's capped RSS of the current seeds (the smooth cap at tau -> 0)."""
         self.evaluate(tau=1e-12)
@@ -264,9 +292,10 @@ def gn_study(n_events: int = 32, stride: int = 16, lam: float = 8e-4, iters: int
              tau: float = 1e-3):
     """The dense 2^18 grid (FP32) against Gauss-Newton on the top K of a 2^14 grid (FP32 scan, then
     FP64 Gauss-Newton on the smoothed RSS; the seed of lowest capped RSS is kept): momentum error of
-    the selected seed against the truth and warm GPU time.  Also the coarse grid's own best seed."""
+    the selected seed against the truth and warm GPU time.  Also the coarse grid's own best seed, and
+    Levenberg-Marquardt with per-seed accept/reject (comet_scan_lm_step) from the same start."""
     ctx = B.Context(torch.cuda.current_device())
-    dense, gn, coarse_only = [], [], []
+    dense, gn, coarse_only, lm = [], [], [], []
     for i in range(n_events):
         ev = synth.multi_turn_event(i)
         p_true = float(np.hypot(ev.pt, ev.pz))
@@ -293,6 +322,20 @@ def gn_study(n_events: int = 32, stride: int = 16, lam: float = 8e-4, iters: int
         b = int(np.argmin(np.where(np.isfinite(srss), srss, np.inf)))
         gn.append((abs(float(np.hypot(theta[b, 2], theta[b, 3])) - p_true), ms))
         coarse_only.append((abs(float(np.hypot(th0[2], th0[3])) - p_true), 0.0))
+        for rep in range(2):                                     # second run timed (warm)
+            t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t0.record()
+            c = refine_partition(ctx, ev, 0, torch.float32, stride, lam, coarse=(8, 8, 16, 16),
+                                 levels=0, M=64, K=1, keep_top=K)
+            B.comet_scan_refine_refs(ctx, c["seeds"], c["idx"], [0.0] * 4, K, G.theta, c["nref"])
+            G.run_lm(iters)
+            G.hard_rss()
+            t1.record()
+            t1.synchronize()
+            res = (G.srss.cpu().numpy(), G.theta.cpu().numpy(), t0.elapsed_time(t1))
+        srss, theta, ms = res
+        b = int(np.argmin(np.where(np.isfinite(srss), srss, np.inf)))
+        lm.append((abs(float(np.hypot(theta[b, 2], theta[b, 3])) - p_true), ms))
     ctx.close()
 
     def summ(a):
@@ -301,7 +344,8 @@ def gn_study(n_events: int = 32, stride: int = 16, lam: float = 8e-4, iters: int
                 "mean_ms": float(a[:, 1].mean())}
     return [{"study": "gauss-newton", "events": n_events, "stride": stride, "lambda_mm": lam * 1e3,
              "tau_mm": tau * 1e3, "iterations": iters, "K": K, "dense_16x16x32x32": summ(dense),
-             "gn_top16_of_2^14": summ(gn), "coarse_2^14_best": summ(coarse_only)}]
+             "gn_top16_of_2^14": summ(gn), "lm_top16_of_2^14": summ(lm),
+             "coarse_2^14_best": summ(coarse_only)}]
 
 
 def generate_batch_events(n: int, workers: int = 0):

@@ -119,6 +119,82 @@ def test_gauss_newton_improves_a_seed_half_a_step_off(ctx):
 
 
 @pytest.mark.gpu
+def test_lm_step_accepts_lower_trials_and_solves_the_damped_system(ctx):
+    """comet_scan_lm_step on hand-made normal equations: a trial of lower smoothed RSS replaces the
+    current seed (theta, srss, JTJ, JTR) and shrinks mu, a higher one is rejected and grows mu; the
+    next trial solves (JTJ + mu diag JTJ) delta = -JTR (numpy), and a seed whose matrix is not
+    positive definite gets delta = 0."""
+    import torch
+    from paper_1911_09340_gb300 import binding as B
+    rng = np.random.default_rng(4)
+    S = 3
+    f64 = dict(dtype=torch.float64, device="cuda")
+    M = rng.normal(size=(S, 4, 4))
+    jtj = np.einsum("sij,skj->sik", M, M) + 0.1 * np.eye(4)
+    jtj_t = np.einsum("sij,skj->sik", M[::-1], M[::-1]) + 0.2 * np.eye(4)
+    jtj_t[2] = -np.eye(4)                                   # seed 2's trial: not positive definite
+    theta, theta_t = rng.normal(size=(S, 4)), rng.normal(size=(S, 4))
+    jtr, jtr_t = rng.normal(size=(S, 4)), rng.normal(size=(S, 4))
+    srss = np.array([1.0, 1.0, 1.0])
+    srss_t = np.array([0.5, 2.0, 0.25])                     # accept, reject, accept
+    mu = np.array([1e-3, 1e-3, 1e-3])
+    d = {k: torch.as_tensor(np.ascontiguousarray(v), **f64) for k, v in dict(
+        theta=theta, srss=srss, jtj=jtj.reshape(S, 16), jtr=jtr, theta_t=theta_t, srss_t=srss_t,
+        jtj_t=jtj_t.reshape(S, 16), jtr_t=jtr_t, mu=mu).items()}
+    B.comet_scan_lm_step(ctx, d["theta"], d["srss"], d["jtj"], d["jtr"], d["theta_t"], d["srss_t"],
+                         d["jtj_t"], d["jtr_t"], d["mu"], up=4.0, down=0.25)
+    acc = srss_t < srss
+    cur_theta = np.where(acc[:, None], theta_t, theta)
+    cur_jtj = np.where(acc[:, None, None], jtj_t, jtj)
+    cur_jtr = np.where(acc[:, None], jtr_t, jtr)
+    new_mu = np.where(acc, mu * 0.25, mu * 4.0)
+    assert np.array_equal(d["srss"].cpu().numpy(), np.minimum(srss, srss_t))
+    assert np.array_equal(d["theta"].cpu().numpy(), cur_theta)
+    assert np.allclose(d["mu"].cpu().numpy(), new_mu, rtol=1e-15)
+    nxt = d["theta_t"].cpu().numpy()
+    for s in range(S):
+        A = cur_jtj[s] + new_mu[s] * np.diag(np.diag(cur_jtj[s]))
+        if np.all(np.linalg.eigvalsh(A) > 0):
+            want = cur_theta[s] + np.linalg.solve(A, -cur_jtr[s])
+        else:
+            want = cur_theta[s]
+        assert np.allclose(nxt[s], want, rtol=1e-10, atol=1e-12), s
+    with pytest.raises(B.CometError):
+        B.comet_scan_lm_step(ctx, d["theta"], d["srss"], d["jtj"], d["jtr"], d["theta_t"], None, None,
+                             None, d["mu"], up=0.5)
+
+
+@pytest.mark.gpu
+def test_levenberg_marquardt_never_raises_the_smoothed_rss(ctx):
+    """Levenberg-Marquardt from seeds half and a whole lattice step off: the smoothed RSS of the kept
+    seeds never increases from iteration to iteration, ends below its start, and the momentum error
+    of a seed half a step off shrinks."""
+    import torch
+    from paper_1911_09340_gb300 import binding as B
+    from paper_1911_09340_gb300 import experiments as X
+    ev = synth.single_event_fp64()
+    spec = ev.partitions[0]
+    step = np.array([2 * h / (n - 1) for h, n in zip(spec.half_width, spec.counts)])
+    t0 = _truth_theta(ev)
+    start = np.stack([t0 + 0.5 * step * [1, -1, 1, 1], t0 + step * [-1, 1, 1, -1]])
+    G = X.GaussNewton(ctx, ev, 0, stride=16, lam=8e-4, tau=1e-3, K=2)
+    G.theta.copy_(torch.as_tensor(start))
+    G.run_lm(iters=0)
+    hist = [G.srss.cpu().numpy().copy()]
+    for _ in range(8):
+        G._eval_at(G.t_theta, G.t_srss, G.t_grad, G.t_jtj, G.t_jtr)
+        B.comet_scan_lm_step(ctx, G.theta, G.srss, G.jtj, G.jtr, G.t_theta, G.t_srss, G.t_jtj, G.t_jtr,
+                             G.mu)
+        hist.append(G.srss.cpu().numpy().copy())
+    hist = np.array(hist)
+    assert np.all(np.diff(hist, axis=0) <= 0)
+    assert np.all(hist[-1] < hist[0])
+    th = G.theta.cpu().numpy()
+    p_true = math.hypot(ev.pt, ev.pz)
+    assert abs(math.hypot(th[0, 2], th[0, 3]) - p_true) < abs(math.hypot(start[0, 2], start[0, 3]) - p_true)
+
+
+@pytest.mark.gpu
 def test_gradient_in_the_six_cartesian_seed_components(ctx):
     """d(smoothed RSS)/d(x, y, z, px, py, pz) of the seed against central finite differences of the
     oracle's smoothed RSS of Cartesian seeds (rel 1e-4)."""

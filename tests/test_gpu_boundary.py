@@ -223,6 +223,16 @@ def test_lattice_refine_jacobian_gn_validation(ctx, bufs):
             args = list(good)
             args[i] = v
             _expect_invalid(L.comet_scan_gn_step(*args))
+    t = f64(b["theta"])
+    good = [ctx.handle, 1, t, t, t, t, t, t, t, t, t, 3.0, 0.5, 0, None]
+    bad = {0: [None], 1: [0, (1 << 24) + 1], 2: [None, _odd(b["theta"])], 3: [None], 4: [None], 5: [None],
+           6: [None], 7: [None], 8: [None], 9: [None], 10: [None], 11: [0.5, float("inf")],
+           12: [0.0, 1.5, float("nan")]}
+    for i, vals in bad.items():
+        for v in vals:
+            args = list(good)
+            args[i] = v
+            _expect_invalid(L.comet_scan_lm_step(*args))
     _untouched(b)
 
 

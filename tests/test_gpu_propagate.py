@@ -109,6 +109,27 @@ def test_stride_and_target_region(ctx, dtype, tol):
         assert np.abs(got[s, :n, :3] - ref[s, :n, :3]).max() <= tol
 
 
+@pytest.mark.parametrize("interleaved", [False, True])
+def test_fp32_table_field_points_within_5um_over_three_turns(ctx, interleaved):
+    """The tabulated solenoid field of the non-uniform workload (5 mm grid, trilinear; both table
+    layouts): FP32 track points within 5 um of the FP64 oracle over three turns (~6,900 RK4 steps),
+    every state recorded every 16 steps, the same number of recorded states."""
+    field = synth.table_field()
+    ev = synth.single_event_fp64()
+    seeds = O.lattice(ev.partitions[0])[::67].astype(np.float32).astype(np.float64)
+    n = 3 * 2300 // 16 * 16
+    op, bp = both_params(n_steps=n, stride=16, **OPEN)
+    _, _, pts, nv = gpu_propagate(ctx, B.DeviceField.from_synth(field, interleaved=interleaved), bp,
+                                  seeds, -1, torch.float32)
+    ref, rnv = O.propagate(field, op, seeds, -1)
+    got = to_aos_points(pts)
+    assert np.array_equal(nv.cpu().numpy(), rnv)
+    assert (rnv == op.n_rec()).all()
+    err = max(np.abs(got[s, :rnv[s], :3] - ref[s, :rnv[s], :3]).max() for s in range(seeds.shape[0]))
+    print(f"max |dx| over three turns in the table field: {err:.2e} m")
+    assert err <= 5e-6, err
+
+
 @pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-9), (torch.float32, 5e-6)])
 def test_table_field_points(ctx, dtype, tol):
     field = synth.table_field(spacing=0.02)
