@@ -240,16 +240,28 @@ def run_ours(args, rank, world):
     max_h = max(ev.n_hits for ev in events)
     max_w = max(ev.n_wires for ev in events)
     S = events[0].partitions[0].n_seeds
-    ws = scan.Workspace(S, max_rec, max_h, dtype)
+    pipelined = not args.sequential
+    if pipelined:
+        # the next partition's lattice + propagate on a second stream beside the current
+        # partition's dca / select / classify (two workspaces; identical results)
+        pipe = scan.PipelinedScanner(ctx, field, S, max_rec, max_h, dtype)
+        ws = pipe.ws[0]
+    else:
+        pipe = None
+        ws = scan.Workspace(S, max_rec, max_h, dtype)
     devs = [scan.DeviceEvent.from_event(ev, dtype) for ev in events]
     classes = [torch.zeros((len(ev.partitions), max(ev.n_hits, 1)), dtype=torch.uint8, device="cuda")
                for ev in events]
     params = [scan.event_params(ev, dtype, stride=args.stride) for ev in events]
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     timer = scan.KernelTimer()
+    rec_timer = scan.KernelTimer()
 
-    def step(i, t=None):
+    def step(i, t=None, rt=None):
         ev, dev = events[i], devs[i]
+        if pipe is not None:
+            pipe.event(ev, dev, params[i], classes=classes[i], rec_timer=rt, timer=t)
+            return
         for p, (spec, bp) in enumerate(zip(ev.partitions, params[i])):
             scan.scan_partition(ctx, field, bp, spec, dev, ws, hit_class=classes[i][p], timer=t)
 
@@ -259,19 +271,34 @@ def run_ours(args, rank, world):
     barrier(world)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    t0 = torch.cuda.Event(enable_timing=True)
     gpu = torch.cuda.current_device()
     with ClockSampler(gpu) as clk:
         torch.cuda.synchronize()
         wall0 = time.perf_counter()
-        for j in range(args.steps):
-            flush.fill_(j & 0xFF)                     # evict L2 between steps (not timed)
-            starts[j].record()
-            step(args.warmup + j, timer)
-            ends[j].record()
+        if pipe is not None:
+            # back to back: the timed region is one interval on the stream; the recording stream
+            # starts inside it (the track points, 0.44 GB per partition, exceed L2)
+            t0.record()
+            pipe.rec.wait_event(t0)
+            for j in range(args.steps):
+                step(args.warmup + j, timer, rec_timer)
+                ends[j].record()
+        else:
+            for j in range(args.steps):
+                flush.fill_(j & 0xFF)                     # evict L2 between steps (not timed)
+                starts[j].record()
+                step(args.warmup + j, timer)
+                ends[j].record()
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
     barrier(world)
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    if pipe is not None:
+        # per event: completion to completion (the events overlap on the recording stream)
+        marks = [t0] + ends
+        step_ms = [a.elapsed_time(b) for a, b in zip(marks[:-1], marks[1:])]
+    else:
+        step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     dev_s = sum(step_ms) / 1e3
     evals = 0
     wire_pairs = 0
@@ -284,7 +311,8 @@ def run_ours(args, rank, world):
         evals += e_h
         wire_pairs += e_w
         n_parts += len(ev.partitions)
-    kt = timer.totals()
+    kt = dict(timer.totals())
+    kt.update(rec_timer.totals())
     t_max = max_over_ranks(dev_s, world)
     evals_all = sum_over_ranks(float(evals), world)
     events_all = args.steps * world
@@ -301,7 +329,7 @@ def run_ours(args, rank, world):
     # Like the device leg, the host enqueues event after event and synchronises once at the end;
     # each event's timed region holds its host->device copies, its partitions and the
     # device->host copy of its results into its own pinned slots.
-    runner = scan.HostEventRunner(ctx, field, ws, max_w, max_h, dtype)
+    runner = scan.HostEventRunner(ctx, field, ws, max_w, max_h, dtype, pipeline=pipe)
     pinned = [runner.pin(ev, dtype) for ev in events]
     slots = [runner.result_slots() for _ in range(args.steps)]
     for i in range(args.warmup):
@@ -311,16 +339,24 @@ def run_ours(args, rank, world):
     e_starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     e_ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     h2d = d2h = 0
+    e0 = torch.cuda.Event(enable_timing=True)
+    if pipe is not None:
+        e0.record()
+        pipe.rec.wait_event(e0)
     for j in range(args.steps):
         i = args.warmup + j
-        flush.fill_(j & 0xFF)                     # evict L2 between events (not timed)
-        e_starts[j].record()
+        if pipe is None:
+            flush.fill_(j & 0xFF)                     # evict L2 between events (not timed)
+            e_starts[j].record()
         b_in, b_out = runner.run(events[i], pinned[i], stride=args.stride, out=slots[j])
         e_ends[j].record()
         h2d += b_in
         d2h += b_out
     torch.cuda.synchronize()
-    e2e_ms = sum(a.elapsed_time(b) for a, b in zip(e_starts, e_ends))
+    if pipe is not None:
+        e2e_ms = e0.elapsed_time(e_ends[-1])
+    else:
+        e2e_ms = sum(a.elapsed_time(b) for a, b in zip(e_starts, e_ends))
     for j in range(args.steps):
         # the results read back are the device leg's: the final mask holds every classified hit
         i = args.warmup + j
@@ -352,6 +388,29 @@ def run_ours(args, rank, world):
     prop_bytes = (PROP_BYTES_PER_REC * recorded + 24 * S * n_parts) / max(n_parts, 1)
     roof = roofline_entry(dom, dom_ms / dom_launches, prop_bytes, clocks, peaks, dca_flops,
                           args.stride)
+    survey = survey_count_entry(kt["dca"][0] / kt["dca"][1], evals / max(n_parts, 1), clocks, peaks)
+    # the same kernels once more, one partition at a time on one stream (not part of `value`): the
+    # DCA kernel's duration without the recording kernels of the next partition beside it
+    seq_roof = None
+    if pipe is not None:
+        seq_timer = scan.KernelTimer()
+        for j in range(args.steps):
+            i = args.warmup + j
+            devs[i].mask.zero_()
+            for p, (spec, bp) in enumerate(zip(events[i].partitions, params[i])):
+                flush.fill_((i + p) & 0xFF)
+                scan.scan_partition(ctx, field, bp, spec, devs[i], ws, timer=seq_timer)
+        torch.cuda.synchronize()
+        skt = seq_timer.totals()
+        seq_roof = {"dca": roofline_entry("dca", skt["dca"][0] / skt["dca"][1], prop_bytes, clocks, peaks,
+                                          dca_flops, args.stride),
+                    "dca_survey_count": survey_count_entry(skt["dca"][0] / skt["dca"][1],
+                                                           evals / max(n_parts, 1), clocks, peaks),
+                    "propagate": roofline_entry("propagate", skt["propagate"][0] / skt["propagate"][1],
+                                                prop_bytes, clocks, peaks, dca_flops, args.stride),
+                    "kernel_ms": {k: round(v[0], 3) for k, v in skt.items()},
+                    "note": "the timed events once more, one partition at a time on one stream, "
+                            "a 256 MiB buffer written before each partition; not part of value"}
     second = "propagate" if dom != "propagate" else "dca"
     roof_prop = roofline_entry(second, kt[second][0] / kt[second][1], prop_bytes, clocks, peaks,
                                dca_flops, args.stride)
@@ -367,14 +426,22 @@ def run_ours(args, rank, world):
         "event_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
                      "max": max(step_ms)},
         "config": dict(workload_config(args, "FP32 GPU"), events=events_all, partitions=n_parts * world,
-                       l2="256 MiB buffer written between timed steps; track points (~0.9 GB per "
-                          "partition) also exceed L2",
+                       l2=("inputs larger than L2: the track points of each partition (0.44 GB; "
+                           "two workspaces alternate) are written and read inside every step"
+                           if pipe is not None else
+                           "256 MiB buffer written between timed steps; track points (~0.44 GB "
+                           "per partition) also exceed L2"),
+                       schedule=("pipelined: lattice + propagate of partition p+1 on a second stream "
+                                 "beside partition p's dca / select / classify"
+                                 if pipe is not None else "sequential: one partition at a time"),
                        parallelism=f"replicas: {world} GPU(s), disjoint events"),
         "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": h2d // args.steps,
                 "d2h_bytes_per_step": d2h // args.steps},
         "gpu_launches": scan.LAUNCHES_PER_PARTITION * n_parts,
         "kernel_ms": {k: round(v[0], 3) for k, v in kt.items()},
         "roofline": roof,
+        "roofline_survey_count": survey,
+        "roofline_sequential": seq_roof,
         "roofline_other": roof_prop,
         "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"],
                    "reasons": clocks["reasons"]},
@@ -385,7 +452,10 @@ def run_ours(args, rank, world):
                                "sample": cpu[2], "value_1_thread": cpu1[0],
                                "sample_1_thread": cpu1[2]}
     if not args.no_legs:
-        del ws, devs
+        del ws, devs, runner
+        if pipe is not None:
+            pipe.close()
+            del pipe
         torch.cuda.empty_cache()
         out["legs"] = {
             "single_event_fp64": leg_single_event_fp64(ctx, reps=args.fp64_reps),
@@ -544,6 +614,7 @@ DCA_FLOPS_PER_WIRE = 201
 DCA_FLOPS_PER_HIT = 8
 PROP_BYTES_PER_REC = 24
 TABLE_FLOPS_PER_STEP = 438
+SURVEY_INSTR_PER_EVAL = 285
 FP64_PEAK_TFLOPS = 1.25
 
 # DRAM bytes (read + write) per launch of the two main kernels on this workload at stride 32, from a
@@ -574,6 +645,20 @@ def measured_traffic(kernel: str, stride: int):
     except OSError:
         ok = False
     return NCU_TRAFFIC.get(kernel) if ok else None
+
+
+def survey_count_entry(avg_ms, evals_per_launch, clocks, peaks):
+    """The DCA kernel against the FP32 instruction peak by the scope table's own count: 285 FP32
+    instructions (the middle of its 250-320 estimate: 2-3 Newton iterations of an RK4 partial step
+    and the plane and distance arithmetic, plus min / cap / square) per DCA evaluation, i.e. per
+    (seed, unmasked hit) pair, against 152 SMs x 128 FP32 lanes x the maximum SM clock."""
+    instr = SURVEY_INSTR_PER_EVAL * evals_per_launch
+    rate = instr / (avg_ms * 1e-3)
+    peak = 152 * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6
+    return {"kernel": "dca", "bound": "alu", "achieved": rate / 1e12, "peak": peak / 1e12,
+            "unit": "T FP32 instr/s", "frac": rate / peak, "instr_per_eval": SURVEY_INSTR_PER_EVAL,
+            "evals_per_launch": evals_per_launch, "avg_launch_ms": avg_ms,
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x max SM clock"}
 
 
 def fp32_peak_tflops(peaks):
@@ -651,6 +736,8 @@ def main():
                     help="skip the single-event FP64 and table-field legs")
     ap.add_argument("--fp64-reps", type=int, default=20, help="timed events of the FP64 leg")
     ap.add_argument("--table-events", type=int, default=3, help="timed events of the table-field leg")
+    ap.add_argument("--sequential", action="store_true",
+                    help="one partition at a time on one stream (no recording beside the DCA)")
     ap.add_argument("--dry-run", action="store_true",
                     help="no CUDA: exercise the rank launch, sharding and reductions on the CPU")
     ap.add_argument("--lattice", type=lambda s: [int(x) for x in s.split(",")],

@@ -131,6 +131,10 @@ typedef struct {
  *   plain-load path runs on every launch: a way to test it.  A copy that was given up on is still
  *   waited for (up to 2 s) before the kernel reuses or releases the shared memory it writes.
  *   Host-side setting; takes effect for calls enqueued after it.
+ * comet_ctx_set_dca_ctas_per_sm: at most n (1 .. 64; 0 = as many as fit, the default) resident CTAs
+ *   per SM for comet_scan_dca's persistent launch with this context: leaves room on every SM for
+ *   kernels of other streams (for example the next turn partition's track recording) to run beside
+ *   it.  Results do not depend on it.  Host-side setting; takes effect for calls enqueued after it.
  * comet_kernel_arch: writes to *sm_version (host pointer) the SM version the library's device code
  *   was compiled for, as major * 10 + minor (103 for sm_103a), read from a kernel's attributes on
  *   the current device.
@@ -139,6 +143,7 @@ comet_status comet_ctx_create(int device, comet_ctx **out);
 void comet_ctx_destroy(comet_ctx *ctx);
 comet_status comet_ctx_status(comet_ctx *ctx, int32_t *flags);
 comet_status comet_ctx_set_copy_wait(comet_ctx *ctx, int64_t ns);
+comet_status comet_ctx_set_dca_ctas_per_sm(comet_ctx *ctx, int32_t n);
 comet_status comet_kernel_arch(int32_t *sm_version);
 const char *comet_last_error(void);
 

@@ -73,6 +73,7 @@ SIGNATURES = {
     "comet_ctx_destroy": [_vp],
     "comet_ctx_status": [_vp, C.POINTER(C.c_int32)],
     "comet_ctx_set_copy_wait": [_vp, _i64],
+    "comet_ctx_set_dca_ctas_per_sm": [_vp, _i32],
     "comet_kernel_arch": [C.POINTER(C.c_int32)],
     "comet_last_error": [],
     "comet_scan_lattice": [_vp, C.c_int, C.POINTER(_Lattice), _vp, _vp, _i64, _vp],
@@ -226,6 +227,10 @@ class Context:
     def set_copy_wait(self, ns: int):
         """Limit (ns) of a kernel's wait for a staging bulk copy; 0 forces the plain-load path."""
         _check(lib().comet_ctx_set_copy_wait(self.handle, int(ns)))
+
+    def set_dca_ctas_per_sm(self, n: int):
+        """Cap of the persistent DCA launch's resident CTAs per SM (0: as many as fit)."""
+        _check(lib().comet_ctx_set_dca_ctas_per_sm(self.handle, int(n)))
 
     def close(self):
         if self.handle:

@@ -232,6 +232,7 @@ void fill_dca(comet_ctx *ctx, comet_dtype dtype, const comet_scan_params *p, con
     a->status = ctx->status;
     a->counter = ctx->status + 16;
     a->wait_ns = ctx->copy_wait_ns;
+    a->max_ctas_per_sm = ctx->dca_ctas_per_sm;
     a->lambda = p->lambda;
     a->tol = p->tol;
     a->max_iter = p->max_iter;
@@ -351,6 +352,14 @@ comet_status comet_ctx_set_copy_wait(comet_ctx *ctx, int64_t ns)
     if (!ctx) return fail(COMET_ERR_INVALID_ARG, "ctx is NULL");
     if (ns < 0) return fail(COMET_ERR_INVALID_ARG, "the copy wait limit must be >= 0 ns");
     ctx->copy_wait_ns = (uint64_t)ns;
+    return COMET_OK;
+}
+
+comet_status comet_ctx_set_dca_ctas_per_sm(comet_ctx *ctx, int32_t n)
+{
+    if (!ctx) return fail(COMET_ERR_INVALID_ARG, "ctx is NULL");
+    if (n < 0 || n > 64) return fail(COMET_ERR_INVALID_ARG, "CTAs per SM must be in 0 .. 64");
+    ctx->dca_ctas_per_sm = n;
     return COMET_OK;
 }
 

@@ -68,6 +68,7 @@ struct DcaArgs {
     int32_t *status;       // device status word of the context (bit 0: a bulk-copy wait timed out)
     int32_t *counter;      // device work counter (context-owned; zeroed before each launch)
     uint64_t wait_ns;      // limit of a wait for a staging bulk copy (0: give up at once)
+    int max_ctas_per_sm;   // persistent launch: at most this many CTAs per SM (0: as many as fit)
     double lambda, tol;
     double R0;             // super-segment radius (m), margins included
     double R1;             // level-1 segment radius (m), margins included

@@ -905,6 +905,7 @@ static cudaError_t dca_launch(const F &fld, const DcaArgs &a, cudaStream_t st)
                                                           kThreads, L.total);
         if (e != cudaSuccess) return e;
         per_sm = per_sm < 1 ? 1 : per_sm;
+        if (a.max_ctas_per_sm > 0 && a.max_ctas_per_sm < per_sm) per_sm = a.max_ctas_per_sm;
         const int64_t items = (a.S + 31) / 32 * ((a.part && a.arrive) ? a.n_chunks : 1);
         int64_t nb = (items + kWarps - 1) / kWarps;
         const int64_t cap = (int64_t)per_sm * sm_count();

@@ -159,14 +159,86 @@ def scan_event(ctx: B.Context, field: B.DeviceField, ev, dev: DeviceEvent, ws: W
     return out
 
 
+class PipelinedScanner:
+    """Scans turn partitions with the track recording of the next partition (lattice, propagate:
+    they do not read the hit mask) on a second stream, beside the current partition's DCA,
+    selection and classification (which read and update the mask, in partition order on the
+    caller's stream).  Two workspaces alternate: a partition's recording waits only until the
+    partition two back has been classified.  Every kernel is the single-event path's; the results
+    are identical to scan_partition's.  With ``dca_ctas_per_sm`` the context's DCA launches leave
+    room on each SM for the recording kernels to run beside them."""
+
+    def __init__(self, ctx: B.Context, field: B.DeviceField, S: int, n_rec: int, H: int,
+                 dtype=torch.float32, dca_ctas_per_sm: int = 0):
+        self.ctx, self.field, self.dtype = ctx, field, dtype
+        self.ws = [Workspace(S, n_rec, H, dtype) for _ in range(2)]
+        self.rec = torch.cuda.Stream()
+        self.free = [None, None]     # event: the workspace's last consumer (classify) finished
+        self.k = 0
+        ctx.set_dca_ctas_per_sm(dca_ctas_per_sm)
+
+    def partition(self, params: B.ScanParams, spec, ev: DeviceEvent, hit_class=None,
+                  rec_timer=None, timer=None, update_mask: bool = True):
+        """Enqueues one partition (recording on the second stream, the rest on the current
+        stream); returns its workspace (idx, best, rss, n_in, hit_class valid once the current
+        stream reaches them)."""
+        b = self.k
+        self.k ^= 1
+        ws = self.ws[b]
+        main = torch.cuda.current_stream()
+        S = spec.n_seeds
+        seeds, charge, pts, nv, rss, n_in = ws.views(S, params.n_rec)
+        bounds = ws.bounds[: (S + 31) // 32]
+        with torch.cuda.stream(self.rec):
+            if self.free[b] is not None:
+                self.rec.wait_event(self.free[b])
+            mark = rec_timer.mark if rec_timer is not None else (lambda name: None)
+            mark("lattice")
+            B.comet_scan_lattice(self.ctx, spec, seeds, charge)
+            mark("propagate")
+            B.comet_scan_propagate(self.ctx, self.field, params, seeds, charge, pts, nv, bounds=bounds)
+            mark(None)
+            ready = torch.cuda.Event()
+            ready.record(self.rec)
+        main.wait_event(ready)
+        mark = timer.mark if timer is not None else (lambda name: None)
+        mark("dca")
+        B.comet_scan_dca(self.ctx, self.field, params, pts, nv, charge, ev.wires, ev.hit_offsets,
+                         ev.drift, ev.mask, rss, n_in, n_unconverged=ws.n_unconv, n_wires=ev.W,
+                         bounds=bounds)
+        mark("select")
+        B.comet_scan_select(self.ctx, rss, 1, ws.idx[:1], ws.best[:1])
+        mark("classify")
+        hc = ws.hit_class[: max(ev.H, 1)] if hit_class is None else hit_class
+        B.comet_scan_classify(self.ctx, self.field, params, pts, nv, charge, ws.idx, ev.wires,
+                              ev.hit_offsets, ev.drift, ev.mask, hc, update_mask=update_mask,
+                              n_wires=ev.W)
+        mark(None)
+        done = torch.cuda.Event()
+        done.record(main)
+        self.free[b] = done
+        return ws
+
+    def event(self, ev, dev: DeviceEvent, params, classes=None, rec_timer=None, timer=None):
+        """Every partition of an event, in order (``params`` from event_params)."""
+        for p, (spec, bp) in enumerate(zip(ev.partitions, params)):
+            self.partition(bp, spec, dev, hit_class=None if classes is None else classes[p],
+                           rec_timer=rec_timer, timer=timer)
+
+    def close(self):
+        self.ctx.set_dca_ctas_per_sm(0)
+
+
 class HostEventRunner:
     """End-to-end path from host buffers: copies an event's wires, offsets and drifts from pinned
-    host memory to the device, scans every partition, and copies back the per-partition best seed
-    index, its RSS and the final hit mask.  Counts the bytes moved each way."""
+    host memory to the device, scans every partition (one at a time, or through a PipelinedScanner),
+    and copies back the per-partition best seed index, its RSS and the final hit mask.  Counts the
+    bytes moved each way."""
 
     def __init__(self, ctx: B.Context, field: B.DeviceField, ws: Workspace, max_w: int, max_h: int,
-                 dtype=torch.float32):
+                 dtype=torch.float32, pipeline: Optional["PipelinedScanner"] = None):
         self.ctx, self.field, self.ws, self.dtype = ctx, field, ws, dtype
+        self.pipeline = pipeline
         self.dev_w = torch.zeros((6, _pad4(max_w)), dtype=dtype, device="cuda")
         self.dev_o = torch.zeros(max_w + 1, dtype=torch.int32, device="cuda")
         self.dev_d = torch.zeros(max(max_h, 1), dtype=dtype, device="cuda")
@@ -207,9 +279,12 @@ class HostEventRunner:
             pinned["d"].numel() * pinned["d"].element_size()
         n = len(ev.partitions)
         for i, (spec, p) in enumerate(zip(ev.partitions, event_params(ev, self.dtype, stride, lam))):
-            scan_partition(self.ctx, self.field, p, spec, dev, self.ws)
-            self.res_idx[i:i + 1].copy_(self.ws.idx[:1])
-            self.res_rss[i:i + 1].copy_(self.ws.best[:1])
+            if self.pipeline is not None:
+                ws = self.pipeline.partition(p, spec, dev)
+            else:
+                ws = scan_partition(self.ctx, self.field, p, spec, dev, self.ws)
+            self.res_idx[i:i + 1].copy_(ws.idx[:1])
+            self.res_rss[i:i + 1].copy_(ws.best[:1])
         h_idx, h_rss, h_mask = out if out is not None else (self.h_idx, self.h_rss, self.h_mask)
         h_idx[:n].copy_(self.res_idx[:n], non_blocking=True)
         h_rss[:n].copy_(self.res_rss[:n], non_blocking=True)

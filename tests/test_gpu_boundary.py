@@ -246,6 +246,9 @@ def test_context_validation():
     _expect_invalid(L.comet_ctx_set_copy_wait(None, 0))
     c = B.Context(0)
     _expect_invalid(L.comet_ctx_set_copy_wait(c.handle, -1))
+    _expect_invalid(L.comet_ctx_set_dca_ctas_per_sm(None, 1))
+    _expect_invalid(L.comet_ctx_set_dca_ctas_per_sm(c.handle, -1))
+    _expect_invalid(L.comet_ctx_set_dca_ctas_per_sm(c.handle, 65))
     _expect_invalid(L.comet_ctx_status(c.handle, None))
     _expect_invalid(L.comet_kernel_arch(None))
     c.close()

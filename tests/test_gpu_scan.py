@@ -190,6 +190,48 @@ def test_multi_turn_event_fp32_full_size_sampled(ctx, stride):
     _check_selected_and_classified(g_rss, g_idx, g_cls, rss_of, seeds, ev, op, w32, d32, mask)
 
 
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_pipelined_scanner_equals_partition_by_partition(ctx, dtype):
+    """PipelinedScanner (the next partition's recording on a second stream beside the current
+    partition's DCA, two workspaces) gives bit-identical RSS, best seeds, hit classes and masks to
+    scan_partition one partition at a time, over several events back to back."""
+    evs = [synth.multi_turn_event(i, counts=(8, 8, 16, 16)) for i in range(3)]
+    f = B.DeviceField.from_synth(UNIFORM)
+    S = evs[0].partitions[0].n_seeds
+    n_rec = max(bp.n_rec for ev in evs for bp in scan.event_params(ev, dtype, stride=32))
+    H = max(ev.n_hits for ev in evs)
+    ref = []
+    ws = scan.Workspace(S, n_rec, H, dtype)
+    for ev in evs:
+        dev = scan.DeviceEvent.from_event(ev, dtype)
+        out = []
+        for spec, bp in zip(ev.partitions, scan.event_params(ev, dtype, stride=32)):
+            scan.scan_partition(ctx, f, bp, spec, dev, ws)
+            out.append((ws.rss[:S].cpu().numpy().copy(), int(ws.idx[0]),
+                        ws.hit_class[:ev.n_hits].cpu().numpy().copy()))
+        ref.append((out, dev.mask[:ev.n_hits].cpu().numpy().copy()))
+    pipe = scan.PipelinedScanner(ctx, f, S, n_rec, H, dtype)
+    try:
+        devs = [scan.DeviceEvent.from_event(ev, dtype) for ev in evs]
+        got = []
+        for ev, dev in zip(evs, devs):
+            cls = torch.zeros((len(ev.partitions), max(ev.n_hits, 1)), dtype=torch.uint8, device="cuda")
+            rs = []
+            for p, (spec, bp) in enumerate(zip(ev.partitions, scan.event_params(ev, dtype, stride=32))):
+                w = pipe.partition(bp, spec, dev, hit_class=cls[p])
+                rs.append((w.rss[:S].clone(), w.idx[:1].clone()))
+            got.append((rs, cls))
+        torch.cuda.synchronize()
+        for (out, mask), (rs, cls), ev, dev in zip(ref, got, evs, devs):
+            for p, ((rss, idx, hc), (g_rss, g_idx)) in enumerate(zip(out, rs)):
+                assert np.array_equal(g_rss.cpu().numpy(), rss)
+                assert int(g_idx[0]) == idx
+                assert np.array_equal(cls[p, :ev.n_hits].cpu().numpy(), hc)
+            assert np.array_equal(dev.mask[:ev.n_hits].cpu().numpy(), mask)
+    finally:
+        pipe.close()
+
+
 def test_backward_partition_fp64_matches_oracle(ctx):
     """The exit-side (backward) scan of turn partition 0 — flipped charge and momentum — through the
     library against the oracle's pipeline, same bars as the forward scan."""
