@@ -230,6 +230,15 @@ def run_ours(args, rank, world):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     ctx = B.Context(local)
+    if args.only_legs:
+        # profiling: the two extra configurations alone
+        if rank == 0:
+            print(json.dumps({"legs": {
+                "single_event_fp64": leg_single_event_fp64(ctx, reps=args.fp64_reps),
+                "table_field_fp32": leg_table_field_fp32(ctx, 2, args.table_events, args.stride)},
+                "note": "profiling run (--only-legs)"}), flush=True)
+        ctx.close()
+        return
     field = B.DeviceField.from_synth(synth.uniform_field(1.0))
     dtype = torch.float32
     n_ev = args.warmup + args.steps
@@ -618,13 +627,14 @@ SURVEY_INSTR_PER_EVAL = 285
 FP64_PEAK_TFLOPS = 1.25
 
 # DRAM bytes (read + write) per launch of the two main kernels on this workload at stride 32, from a
-# one-pass ncu launch list of `python bench.py` (dram__bytes_read.sum + dram__bytes_write.sum, mean
-# over its 80 DCA launches and 108 propagate launches: the bench re-runs lattice + propagate once
-# per partition, untimed, to count the recorded states).
+# one-pass ncu launch list of `python bench.py --no-cpu --no-legs` (dram__bytes_read.sum +
+# dram__bytes_write.sum, mean over its 108 DCA launches and 136 propagate launches: warm-up, timed,
+# end-to-end and one-at-a-time passes, plus one untimed lattice + propagate per timed partition to
+# count the recorded states).
 # Valid only for the kernel sources they were measured on (SHA-1 of the package's csrc/ files);
 # reported as null once those change.
-NCU_TRAFFIC = {"csrc_sha1": "98b517e64c36932de778f78442187d9ccc6d7dc4", "stride": 32,
-               "dca": 206323827.2, "propagate": 402434688.0}
+NCU_TRAFFIC = {"csrc_sha1": "b479f8ea28cc5777c8998180c3b1914613e0d41d", "stride": 32,
+               "dca": 171.7e6, "propagate": 403.8e6}
 
 
 def csrc_sha1() -> str:
@@ -735,6 +745,8 @@ def main():
     ap.add_argument("--no-legs", action="store_true",
                     help="skip the single-event FP64 and table-field legs")
     ap.add_argument("--fp64-reps", type=int, default=20, help="timed events of the FP64 leg")
+    ap.add_argument("--only-legs", action="store_true",
+                    help="run only the FP64 single-event and table-field legs (profiling)")
     ap.add_argument("--table-events", type=int, default=3, help="timed events of the table-field leg")
     ap.add_argument("--sequential", action="store_true",
                     help="one partition at a time on one stream (no recording beside the DCA)")

@@ -187,7 +187,7 @@ comet_status comet_scan_batch_update(comet_ctx *ctx, comet_dtype dtype, const co
         cls[e + 1] = cls[e] + (W > 0 && S > 0 ? (W + 7) / 8 : 0);
         groups[e] = (S + 31) / 32;
         {
-            const int gpi = comet::dca_batch_groups(comet::dca_wire_chunks(W));
+            const int gpi = comet::dca_batch_groups(comet::dca_wire_chunks(W, S));
             dstart[e + 1] = dstart[e] + (groups[e] + gpi - 1) / gpi;
         }
         if (!S) continue;

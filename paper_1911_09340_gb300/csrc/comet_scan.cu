@@ -250,7 +250,7 @@ void fill_dca(comet_ctx *ctx, comet_dtype dtype, const comet_scan_params *p, con
     a->margin_f = (float)a->margin;
     a->bounds = bounds;
     a->exact_all = dca_out != nullptr;
-    a->n_chunks = comet::dca_wire_chunks(W);
+    a->n_chunks = comet::dca_wire_chunks(W, S);
     a->part = nullptr;
     a->arrive = nullptr;
 }
@@ -646,7 +646,7 @@ comet_status comet_scan_dca(comet_ctx *ctx, comet_dtype dtype, const comet_field
         // zeroed once here and left zero by every launch
         // sized at first for the chunks of max(W, 256) wires, so that events of up to 256 wires
         // never reallocate
-        const int nc_alloc = comet::dca_wire_chunks(W > 256 ? W : 256);
+        const int nc_alloc = comet::dca_wire_chunks(W > 256 ? W : 256, S);
         const size_t need = (size_t)(a.n_chunks > nc_alloc ? a.n_chunks : nc_alloc) * (size_t)S * (2 * esize(dtype) + 4);
         const size_t groups = (size_t)((S + 31) / 32);
         if (need > ctx->dca_part_bytes) {

@@ -84,7 +84,7 @@ struct DcaArgs {
     int G0;                // recorded states per super-segment
     int G1;                // recorded states per level-1 segment
     int exact_all;         // refine every wire (dca_out requested)
-    // The wires are cut into n_chunks chunks (dca_wire_chunks(W)); a seed's RSS is the sum of its
+    // The wires are cut into n_chunks chunks (dca_wire_chunks(W, S)); a seed's RSS is the sum of its
     // per-chunk compensated partial sums, added in chunk order.  With `part` and `arrive` given,
     // the persistent kernel schedules (group, chunk) items across warps: partial sums go to part
     // ([n_chunks][S] hi, [n_chunks][S] lo in T, then [n_chunks][S] int32 n_in) and the last warp
@@ -95,8 +95,11 @@ struct DcaArgs {
     uint32_t *arrive;
 };
 
-// Wire chunks of the DCA's per-seed sums for W wires (W <= 1024; 1 otherwise).
-int dca_wire_chunks(int W);
+// Wire chunks of the DCA's per-seed sums for W wires and S seeds (W <= 1024; 1 otherwise):
+// ceil(W / 32), or more, narrower chunks (at least 4 wires each, at most kDcaBatchSub) when
+// fewer than 4096 (32-seed group, chunk) items would result.  The same function serves the
+// single-event and the batched launches, so both sum in the same order.
+int dca_wire_chunks(int W, int64_t S);
 
 struct SelArgs {
     const void *rss;

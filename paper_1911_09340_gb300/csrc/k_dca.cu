@@ -939,10 +939,21 @@ static cudaError_t dca_dispatch(const comet_field &f, const DcaArgs &a, cudaStre
     }
 }
 
-int dca_wire_chunks(int W)
+int dca_wire_chunks(int W, int64_t S)
 {
     if (W <= 0 || W > kPersistMaxW) return 1;
-    return (W + COMET_DCA_CHUNK_W - 1) / COMET_DCA_CHUNK_W;
+    int nc = (W + COMET_DCA_CHUNK_W - 1) / COMET_DCA_CHUNK_W;
+    // few seeds: narrower chunks (at least 4 wires, at most kDcaBatchSub of them), so that the
+    // (32-seed group, chunk) work items occupy every SM
+    constexpr int64_t kTargetItems = 4096;
+    const int64_t groups = (S + 31) / 32;
+    if (groups > 0 && groups * nc < kTargetItems) {
+        const int64_t want = (kTargetItems + groups - 1) / groups;
+        int cap = W / 4;
+        cap = cap < kDcaBatchSub ? cap : kDcaBatchSub;
+        if (want > nc && cap > nc) nc = (int)(want < cap ? want : cap);
+    }
+    return nc;
 }
 
 void dca_segments(int n_rec, int *G0, int *G1)

@@ -453,9 +453,8 @@ cudaError_t launch_lattice_batch(comet_dtype dt, const BatchLaunch &L, cudaStrea
 
 template <typename T, class F, bool BATCH>
 static void prop_launch(const F &fld, const PropArgs &a, int stride, unsigned nb, const BatchLaunch &L,
-                        cudaStream_t st)
+                        cudaStream_t st, int nt = 128)
 {
-    const int nt = 128;
     switch (stride) {
     case 1: propagate_kernel<T, F, 1, BATCH><<<nb, nt, 0, st>>>(fld, a, L); break;
     case 2: propagate_kernel<T, F, 2, BATCH><<<nb, nt, 0, st>>>(fld, a, L); break;
@@ -467,31 +466,34 @@ static void prop_launch(const F &fld, const PropArgs &a, int stride, unsigned nb
 
 template <typename T, bool BATCH>
 static void prop_dispatch(const comet_field &f, const PropArgs &a, int stride, unsigned nb,
-                          const BatchLaunch &L, cudaStream_t st)
+                          const BatchLaunch &L, cudaStream_t st, int nt = 128)
 {
     switch (field_kind(f)) {
     case FieldKind::Axial:
-        prop_launch<T, FieldAxial<T>, BATCH>(FieldAxial<T>{(T)f.b[2]}, a, stride, nb, L, st);
+        prop_launch<T, FieldAxial<T>, BATCH>(FieldAxial<T>{(T)f.b[2]}, a, stride, nb, L, st, nt);
         break;
     case FieldKind::Uniform:
         prop_launch<T, FieldUniform<T>, BATCH>(FieldUniform<T>{(T)f.b[0], (T)f.b[1], (T)f.b[2]}, a,
-                                               stride, nb, L, st);
+                                               stride, nb, L, st, nt);
         break;
     case FieldKind::Table:
         prop_launch<T, FieldTable<T>, BATCH>(make_table<T>(f),
-                                             a, stride, nb, L, st);
+                                             a, stride, nb, L, st, nt);
         break;
     }
 }
 
 cudaError_t launch_propagate(comet_dtype dt, const comet_field &f, const PropArgs &a, cudaStream_t st)
 {
-    const unsigned nb = (unsigned)((a.S + 127) / 128);
+    // one seed per thread; with fewer seeds than 128 per SM, one warp per CTA, so that the seeds
+    // spread over as many SMs as possible (the search bounds are per warp either way)
+    const int nt = a.S < (int64_t)device_sm_count() * 128 ? 32 : 128;
+    const unsigned nb = (unsigned)((a.S + nt - 1) / nt);
     const BatchLaunch none{};
     if (dt == COMET_F32)
-        prop_dispatch<float, false>(f, a, a.stride, nb, none, st);
+        prop_dispatch<float, false>(f, a, a.stride, nb, none, st, nt);
     else
-        prop_dispatch<double, false>(f, a, a.stride, nb, none, st);
+        prop_dispatch<double, false>(f, a, a.stride, nb, none, st, nt);
     return cudaGetLastError();
 }
 
