@@ -381,8 +381,6 @@ def run_ours(args, rank, world):
         return
     # ---- roofline of the dominant kernel
     peaks = _peaks()
-    dom = max(kt, key=lambda k: kt[k][0])
-    dom_ms, dom_launches = kt[dom]
     dca_flops = (DCA_FLOPS_PER_WIRE * wire_pairs + DCA_FLOPS_PER_HIT * evals) / max(n_parts, 1)
     # states the timed propagate launches recorded (tracks leaving the target region stop early):
     # lattice + propagate of each timed partition once more, untimed, summing n_valid
@@ -395,8 +393,6 @@ def run_ours(args, rank, world):
             B.comet_scan_propagate(ctx, field, bp, seeds, charge, pts, nv)
             recorded += int(nv.sum().item())
     prop_bytes = (PROP_BYTES_PER_REC * recorded + 24 * S * n_parts) / max(n_parts, 1)
-    roof = roofline_entry(dom, dom_ms / dom_launches, prop_bytes, clocks, peaks, dca_flops,
-                          args.stride)
     survey = survey_count_entry(kt["dca"][0] / kt["dca"][1], evals / max(n_parts, 1), clocks, peaks)
     # the same kernels once more, one partition at a time on one stream (not part of `value`): the
     # DCA kernel's duration without the recording kernels of the next partition beside it
@@ -420,6 +416,12 @@ def run_ours(args, rank, world):
                     "kernel_ms": {k: round(v[0], 3) for k, v in skt.items()},
                     "note": "the timed events once more, one partition at a time on one stream, "
                             "a 256 MiB buffer written before each partition; not part of value"}
+    # the dominant kernel by device time, one partition at a time (in the pipelined region the
+    # recording's interval on its stream spans the DCA launch it runs beside)
+    share = skt if pipe is not None else kt
+    dom = max(share, key=lambda k: share[k][0])
+    roof = roofline_entry(dom, kt[dom][0] / kt[dom][1], prop_bytes, clocks, peaks, dca_flops,
+                          args.stride)
     second = "propagate" if dom != "propagate" else "dca"
     roof_prop = roofline_entry(second, kt[second][0] / kt[second][1], prop_bytes, clocks, peaks,
                                dca_flops, args.stride)

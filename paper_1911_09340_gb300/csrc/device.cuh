@@ -479,19 +479,17 @@ __device__ __forceinline__ float4 warp_sphere(bool has, T x, T y, T z, T reach)
     const T cx = T(0.5) * (__shfl_sync(0xffffffffu, x, l0) + __shfl_sync(0xffffffffu, x, l1));
     const T cy = T(0.5) * (__shfl_sync(0xffffffffu, y, l0) + __shfl_sync(0xffffffffu, y, l1));
     const T cz = T(0.5) * (__shfl_sync(0xffffffffu, z, l0) + __shfl_sync(0xffffffffu, z, l1));
-    T d;
-    if constexpr (sizeof(T) == 4) {
-        // d^2 >= 0: its bit pattern orders like its value, so one integer warp reduction finds the
-        // max; then one root by the hardware reciprocal square root (a few ulp, inside the 1e-6
-        // relative margin below)
-        const float d2 = has ? (x - cx) * (x - cx) + (y - cy) * (y - cy) + (z - cz) * (z - cz) : 0.f;
-        const float m2 = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(d2)));
-        d = m2 * rsqrtf(fmaxf(m2, 1e-30f));
-    } else {
-        d = has ? sqrt((x - cx) * (x - cx) + (y - cy) * (y - cy) + (z - cz) * (z - cz)) : T(0);
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) d = fmax(d, __shfl_xor_sync(0xffffffffu, d, off));
-    }
+    // d^2 >= 0 as a float (rounded up from double): its bit pattern orders like its value, so one
+    // integer warp reduction finds the max; then one root by the hardware reciprocal square root
+    // (a few ulp, inside the 1e-6 relative margin below).  The radius is a float either way, so the
+    // double path needs no double root or reductions (this part's FP64 rate is small).
+    float d2;
+    if constexpr (sizeof(T) == 4)
+        d2 = has ? (x - cx) * (x - cx) + (y - cy) * (y - cy) + (z - cz) * (z - cz) : 0.f;
+    else
+        d2 = has ? __double2float_ru((x - cx) * (x - cx) + (y - cy) * (y - cy) + (z - cz) * (z - cz)) : 0.f;
+    const float m2 = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(d2)));
+    const T d = (T)(m2 * rsqrtf(fmaxf(m2, 1e-30f)));
     const T extra = sizeof(T) == 8 ? T(2e-7) : T(0);
     return make_float4((float)cx, (float)cy, (float)cz, (float)((d + reach + extra) * T(1.000001)));
 }

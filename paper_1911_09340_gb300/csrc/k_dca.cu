@@ -38,7 +38,7 @@
 // Tuning constants (compile-time): minimum resident CTAs per SM requested from the register
 // allocator, and how many states are loaded together.
 #ifndef COMET_DCA_MINB
-#define COMET_DCA_MINB 8
+#define COMET_DCA_MINB 7
 #endif
 #ifndef COMET_DCA_U2
 #define COMET_DCA_U2 2
