@@ -135,6 +135,12 @@ typedef struct {
  *   per SM for comet_scan_dca's persistent launch with this context: leaves room on every SM for
  *   kernels of other streams (for example the next turn partition's track recording) to run beside
  *   it.  Results do not depend on it.  Host-side setting; takes effect for calls enqueued after it.
+ * comet_ctx_set_dca_chunk_wires: wires per chunk of comet_scan_dca's per-seed sums (and of the
+ *   batched launch) with this context: 0 (the default) takes chunks of at most 32 wires, narrower
+ *   when a call has few seeds; 4 .. 1024 fixes the width (at most 64 chunks).  The chunking is a
+ *   work split and a summation order (the sum within each chunk, then over chunks), so FP32 RSS
+ *   values change in their last bits with it; the batched and single-event launches of one
+ *   context use the same chunks.
  * comet_kernel_arch: writes to *sm_version (host pointer) the SM version the library's device code
  *   was compiled for, as major * 10 + minor (103 for sm_103a), read from a kernel's attributes on
  *   the current device.
@@ -144,6 +150,7 @@ void comet_ctx_destroy(comet_ctx *ctx);
 comet_status comet_ctx_status(comet_ctx *ctx, int32_t *flags);
 comet_status comet_ctx_set_copy_wait(comet_ctx *ctx, int64_t ns);
 comet_status comet_ctx_set_dca_ctas_per_sm(comet_ctx *ctx, int32_t n);
+comet_status comet_ctx_set_dca_chunk_wires(comet_ctx *ctx, int32_t wires);
 comet_status comet_kernel_arch(int32_t *sm_version);
 const char *comet_last_error(void);
 
@@ -351,6 +358,8 @@ typedef struct {
     int32_t max_wires;         /* wires of one event, <= 1024 */
     int32_t max_total_wires;   /* wires of all events of a batch */
     int32_t dca_ctas_per_sm;   /* resident CTAs per SM of the batched DCA launch; 0: as many as fit */
+    int32_t dca_item_groups;   /* 32-seed groups per item of the batched DCA launch, 0 .. 64;
+                                  0: 64 / (wire chunks of the event) */
 } comet_batch_caps;
 
 typedef struct {

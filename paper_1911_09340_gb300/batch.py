@@ -54,7 +54,8 @@ class BatchScanner:
                  slots: int = 128, max_seeds: int = 1 << 18, max_total_seeds: int = 1 << 24,
                  max_wires: int = 512, max_hits: int = 2048, max_n_steps: int = 2400,
                  graph: bool = True, field: Optional[synth.Field] = None, dca_ctas_per_sm: int = 0,
-                 solo_min_seeds: Optional[int] = None, solo_lanes: int = 1):
+                 solo_min_seeds: Optional[int] = None, solo_lanes: int = 1, chunk_wires: int = 0,
+                 item_groups: int = 0):
         self.ctx, self.dtype, self.stride, self.lam = ctx, dtype, stride, lam
         self.slots = self.slots_alloc = slots
         self.max_hits = max_hits
@@ -63,6 +64,9 @@ class BatchScanner:
                                    tol=1e-12 if dtype == torch.float64 else 1e-6, max_iter=16)
         self.max_seeds, self.max_total_seeds, self.max_wires = max_seeds, max_total_seeds, max_wires
         self.dca_ctas_per_sm = dca_ctas_per_sm
+        self.item_groups = item_groups        # 32-seed groups per batched DCA item (0: automatic)
+        self.chunk_wires = chunk_wires        # wires per chunk of the DCA's sums (0: automatic)
+        ctx.set_dca_chunk_wires(chunk_wires)
         self.caps = self._caps(slots, dca_ctas_per_sm)
         self.n_rec_max = max_n_steps // stride + 1
         dev = dict(device="cuda")
@@ -101,17 +105,26 @@ class BatchScanner:
 
     def _caps(self, slots: int, dca_ctas_per_sm: int) -> B.BatchCaps:
         return B.BatchCaps(slots, self.max_seeds, self.max_total_seeds, self.max_wires,
-                           slots * self.max_wires, dca_ctas_per_sm)
+                           slots * self.max_wires, dca_ctas_per_sm, self.item_groups)
 
     def configure(self, slots: Optional[int] = None, dca_ctas_per_sm: Optional[int] = None,
-                  graph: Optional[bool] = None, solo_min_seeds=-1, solo_lanes: Optional[int] = None):
+                  graph: Optional[bool] = None, solo_min_seeds=-1, solo_lanes: Optional[int] = None,
+                  chunk_wires: Optional[int] = None, item_groups: Optional[int] = None):
         """Events in flight (at most the slots allocated), DCA CTAs per SM, graph use, the solo
-        threshold (None: every partition batched) and the number of solo lanes of the next runs
-        (the knobs the autotuner turns)."""
+        threshold (None: every partition batched), the number of solo lanes, the DCA's wires per
+        chunk and the batched DCA's seed groups per item of the next runs (the knobs the autotuner
+        turns; 0 = automatic for the last two)."""
         if solo_min_seeds != -1:
             self.solo_min_seeds = solo_min_seeds
         if solo_lanes is not None:
             self.solo_lanes = max(1, int(solo_lanes))
+        if chunk_wires is not None:
+            self.chunk_wires = int(chunk_wires)
+            self.ctx.set_dca_chunk_wires(self.chunk_wires)
+            for c, _, _ in self._lanes[1:]:
+                c.set_dca_chunk_wires(self.chunk_wires)
+        if item_groups is not None:
+            self.item_groups = int(item_groups)
         if slots is not None:
             if slots > self.slots_alloc:
                 raise ValueError("more slots than allocated")
@@ -121,7 +134,8 @@ class BatchScanner:
         if graph is not None:
             self.use_graph = graph
         caps = self._caps(self.slots, self.dca_ctas_per_sm)
-        if (caps.max_events, caps.dca_ctas_per_sm) != (self.caps.max_events, self.caps.dca_ctas_per_sm):
+        if ((caps.max_events, caps.dca_ctas_per_sm, caps.dca_item_groups) !=
+                (self.caps.max_events, self.caps.dca_ctas_per_sm, self.caps.dca_item_groups)):
             # the next update reallocates the context's staging buffers that captured graphs copy
             # from: a graph captured before must never be replayed again
             self.graphs.clear()
@@ -182,6 +196,7 @@ class BatchScanner:
     def _lane(self, k: int):
         while len(self._lanes) <= k:
             c = self.ctx if not self._lanes else B.Context(self.ctx.device)
+            c.set_dca_chunk_wires(self.chunk_wires)
             self._lanes.append((c, torch.cuda.Stream(),
                                 scan.Workspace(self.max_seeds, self.n_rec_max, 1, self.dtype)))
         return self._lanes[k]
@@ -317,7 +332,8 @@ class BatchScanner:
             B.comet_scan_batch(self.ctx, self.dtype, self.field, self.params, self.caps,
                                stream=self.stream)
             return
-        key = (self.caps.max_events, self.caps.dca_ctas_per_sm)   # at most one entry (see configure)
+        key = (self.caps.max_events, self.caps.dca_ctas_per_sm,
+               self.caps.dca_item_groups)                         # at most one entry (see configure)
         g = self.graphs.get(key)
         if g is None:
             g = torch.cuda.CUDAGraph()
@@ -372,10 +388,12 @@ def run_interleaved(scanners, events, collect: bool = False, pinned=None) -> Dic
 
 
 def autotune(scanner: BatchScanner, events, slots_options=(32, 64, 128, 256), ctas_options=(0, 4, 2),
-             graph_options=(True, False), solo_options=(None,), lanes_options=(1,)):
+             graph_options=(True, False), solo_options=(None,), lanes_options=(1,),
+             chunk_options=(0,), item_options=(0,)):
     """Measures events/s of each (events in flight, DCA CTAs per SM, CUDA graph, solo threshold,
-    solo lanes) on ``events`` (a sample of the workload; one warm run and one timed run each) and
-    leaves the scanner configured with the fastest.  Returns (best, table)."""
+    solo lanes) on ``events`` (a sample of the workload; one warm run and one timed run each), then
+    from the best of those each (wires per chunk, seed groups per batched DCA item), and leaves the
+    scanner configured with the fastest.  Returns (best, table)."""
     table = []
     pinned = scanner.pin(events)
     for solo in solo_options:
@@ -391,9 +409,25 @@ def autotune(scanner: BatchScanner, events, slots_options=(32, 64, 128, 256), ct
                         r = scanner.run(events, pinned=pinned)
                         table.append({"slots": sl, "dca_ctas_per_sm": c, "graph": g,
                                       "solo_min_seeds": solo, "solo_lanes": nl,
+                                      "chunk_wires": scanner.chunk_wires,
+                                      "item_groups": scanner.item_groups,
                                       "events_per_s": len(events) / (r["gpu_ms"] * 1e-3),
                                       "gpu_ms": r["gpu_ms"]})
     best = max(table, key=lambda t: t["events_per_s"])
     scanner.configure(slots=best["slots"], dca_ctas_per_sm=best["dca_ctas_per_sm"], graph=best["graph"],
                       solo_min_seeds=best["solo_min_seeds"], solo_lanes=best["solo_lanes"])
+    # second stage, from the best of the first: the DCA's wires per chunk (the work item's hit tile)
+    # and the batched DCA's 32-seed groups per CTA item (its seeds per block); 0 = automatic
+    for cw in chunk_options:
+        for ig in item_options:
+            if (cw, ig) == (0, 0):
+                continue
+            scanner.configure(chunk_wires=cw, item_groups=ig)
+            scanner.run(events, pinned=pinned)
+            r = scanner.run(events, pinned=pinned)
+            row = dict(best, chunk_wires=cw, item_groups=ig,
+                       events_per_s=len(events) / (r["gpu_ms"] * 1e-3), gpu_ms=r["gpu_ms"])
+            table.append(row)
+    best = max(table, key=lambda t: t["events_per_s"])
+    scanner.configure(chunk_wires=best.get("chunk_wires", 0), item_groups=best.get("item_groups", 0))
     return best, table

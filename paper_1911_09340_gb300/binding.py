@@ -49,7 +49,8 @@ class _Lattice(C.Structure):
 class BatchCaps(C.Structure):
     """Mirror of comet_batch_caps."""
     _fields_ = [("max_events", C.c_int32), ("max_seeds", C.c_int64), ("max_total_seeds", C.c_int64),
-                ("max_wires", C.c_int32), ("max_total_wires", C.c_int32), ("dca_ctas_per_sm", C.c_int32)]
+                ("max_wires", C.c_int32), ("max_total_wires", C.c_int32), ("dca_ctas_per_sm", C.c_int32),
+                ("dca_item_groups", C.c_int32)]
 
 
 class BatchEvent(C.Structure):
@@ -74,6 +75,7 @@ SIGNATURES = {
     "comet_ctx_status": [_vp, C.POINTER(C.c_int32)],
     "comet_ctx_set_copy_wait": [_vp, _i64],
     "comet_ctx_set_dca_ctas_per_sm": [_vp, _i32],
+    "comet_ctx_set_dca_chunk_wires": [_vp, _i32],
     "comet_kernel_arch": [C.POINTER(C.c_int32)],
     "comet_last_error": [],
     "comet_scan_lattice": [_vp, C.c_int, C.POINTER(_Lattice), _vp, _vp, _i64, _vp],
@@ -227,6 +229,10 @@ class Context:
     def set_copy_wait(self, ns: int):
         """Limit (ns) of a kernel's wait for a staging bulk copy; 0 forces the plain-load path."""
         _check(lib().comet_ctx_set_copy_wait(self.handle, int(ns)))
+
+    def set_dca_chunk_wires(self, wires: int):
+        """Wires per chunk of the DCA's per-seed sums (0: automatic)."""
+        _check(lib().comet_ctx_set_dca_chunk_wires(self.handle, int(wires)))
 
     def set_dca_ctas_per_sm(self, n: int):
         """Cap of the persistent DCA launch's resident CTAs per SM (0: as many as fit)."""

@@ -73,7 +73,8 @@ bool same_caps(const comet_batch_caps &a, const comet_batch_caps &b)
 {
     return a.max_events == b.max_events && a.max_seeds == b.max_seeds &&
            a.max_total_seeds == b.max_total_seeds && a.max_wires == b.max_wires &&
-           a.max_total_wires == b.max_total_wires && a.dca_ctas_per_sm == b.dca_ctas_per_sm;
+           a.max_total_wires == b.max_total_wires && a.dca_ctas_per_sm == b.dca_ctas_per_sm &&
+           a.dca_item_groups == b.dca_item_groups;
 }
 
 } // namespace
@@ -105,6 +106,8 @@ comet_status comet_scan_batch_update(comet_ctx *ctx, comet_dtype dtype, const co
     int per_sm = comet::dca_persistent_ctas_per_sm(dtype, *field, caps->max_wires);
     if (per_sm < 1) return fail(COMET_ERR_CUDA, "no resident DCA CTA for %d wires", caps->max_wires);
     if (caps->dca_ctas_per_sm < 0) return fail(COMET_ERR_INVALID_ARG, "caps.dca_ctas_per_sm must be >= 0");
+    if (caps->dca_item_groups < 0 || caps->dca_item_groups > comet::kDcaBatchSub)
+        return fail(COMET_ERR_INVALID_ARG, "caps.dca_item_groups must be in 0 .. %d", comet::kDcaBatchSub);
     if (caps->dca_ctas_per_sm > 0 && caps->dca_ctas_per_sm < per_sm) per_sm = caps->dca_ctas_per_sm;
     const unsigned dca_ctas = (unsigned)(per_sm * comet::device_sm_count());
     const Layout L = make_layout(*caps, dtype, dca_ctas);
@@ -186,10 +189,10 @@ comet_status comet_scan_batch_update(comet_ctx *ctx, comet_dtype dtype, const co
         sel[e + 1] = sel[e] + (S + comet::select_chunk() - 1) / comet::select_chunk();
         cls[e + 1] = cls[e] + (W > 0 && S > 0 ? (W + 7) / 8 : 0);
         groups[e] = (S + 31) / 32;
-        {
-            const int gpi = comet::dca_batch_groups(comet::dca_wire_chunks(W, S));
-            dstart[e + 1] = dstart[e] + (groups[e] + gpi - 1) / gpi;
-        }
+        const int nc_e = comet::dca_wire_chunks(W, S, ctx->dca_chunk_wires);
+        int gpi = comet::dca_batch_groups(nc_e);
+        if (caps->dca_item_groups > 0 && caps->dca_item_groups < gpi) gpi = caps->dca_item_groups;
+        dstart[e + 1] = dstart[e] + (groups[e] + gpi - 1) / gpi;
         if (!S) continue;
 
         comet_scan_params p = *params;
@@ -204,6 +207,7 @@ comet_status comet_scan_batch_update(comet_ctx *ctx, comet_dtype dtype, const co
         // dca (the counter is set per CTA on the device)
         fill_dca(ctx, dtype, &p, sg, x->points, x->n_valid, x->charge, S, x->bounds, x->wires, W, x->ldw,
                  x->hit_offsets, x->drift, x->hit_mask, x->rss, x->n_in, nullptr, x->n_unconverged, &be.dca);
+        be.dca.batch_groups = gpi;
         // select (k = 1)
         be.sel.rss = x->rss;
         be.sel.S = S;

@@ -233,6 +233,7 @@ void fill_dca(comet_ctx *ctx, comet_dtype dtype, const comet_scan_params *p, con
     a->counter = ctx->status + 16;
     a->wait_ns = ctx->copy_wait_ns;
     a->max_ctas_per_sm = ctx->dca_ctas_per_sm;
+    a->batch_groups = 0;
     a->lambda = p->lambda;
     a->tol = p->tol;
     a->max_iter = p->max_iter;
@@ -250,7 +251,7 @@ void fill_dca(comet_ctx *ctx, comet_dtype dtype, const comet_scan_params *p, con
     a->margin_f = (float)a->margin;
     a->bounds = bounds;
     a->exact_all = dca_out != nullptr;
-    a->n_chunks = comet::dca_wire_chunks(W, S);
+    a->n_chunks = comet::dca_wire_chunks(W, S, ctx->dca_chunk_wires);
     a->part = nullptr;
     a->arrive = nullptr;
 }
@@ -360,6 +361,15 @@ comet_status comet_ctx_set_dca_ctas_per_sm(comet_ctx *ctx, int32_t n)
     if (!ctx) return fail(COMET_ERR_INVALID_ARG, "ctx is NULL");
     if (n < 0 || n > 64) return fail(COMET_ERR_INVALID_ARG, "CTAs per SM must be in 0 .. 64");
     ctx->dca_ctas_per_sm = n;
+    return COMET_OK;
+}
+
+comet_status comet_ctx_set_dca_chunk_wires(comet_ctx *ctx, int32_t wires)
+{
+    if (!ctx) return fail(COMET_ERR_INVALID_ARG, "ctx is NULL");
+    if (wires != 0 && (wires < 4 || wires > 1024))
+        return fail(COMET_ERR_INVALID_ARG, "wires per chunk must be 0 (automatic) or in 4 .. 1024");
+    ctx->dca_chunk_wires = wires;
     return COMET_OK;
 }
 
@@ -646,7 +656,7 @@ comet_status comet_scan_dca(comet_ctx *ctx, comet_dtype dtype, const comet_field
         // zeroed once here and left zero by every launch
         // sized at first for the chunks of max(W, 256) wires, so that events of up to 256 wires
         // never reallocate
-        const int nc_alloc = comet::dca_wire_chunks(W > 256 ? W : 256, S);
+        const int nc_alloc = comet::dca_wire_chunks(W > 256 ? W : 256, S, ctx->dca_chunk_wires);
         const size_t need = (size_t)(a.n_chunks > nc_alloc ? a.n_chunks : nc_alloc) * (size_t)S * (2 * esize(dtype) + 4);
         const size_t groups = (size_t)((S + 31) / 32);
         if (need > ctx->dca_part_bytes) {

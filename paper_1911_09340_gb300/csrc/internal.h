@@ -69,6 +69,7 @@ struct DcaArgs {
     int32_t *counter;      // device work counter (context-owned; zeroed before each launch)
     uint64_t wait_ns;      // limit of a wait for a staging bulk copy (0: give up at once)
     int max_ctas_per_sm;   // persistent launch: at most this many CTAs per SM (0: as many as fit)
+    int batch_groups;      // batched launch: 32-seed groups per CTA item (0: kDcaBatchSub / n_chunks)
     double lambda, tol;
     double R0;             // super-segment radius (m), margins included
     double R1;             // level-1 segment radius (m), margins included
@@ -97,9 +98,10 @@ struct DcaArgs {
 
 // Wire chunks of the DCA's per-seed sums for W wires and S seeds (W <= 1024; 1 otherwise):
 // ceil(W / 32), or more, narrower chunks (at least 4 wires each, at most kDcaBatchSub) when
-// fewer than 4096 (32-seed group, chunk) items would result.  The same function serves the
+// fewer than 4096 (32-seed group, chunk) items would result; chunk_wires > 0 (the context's
+// setting) fixes the width instead (at most kDcaBatchSub chunks).  The same function serves the
 // single-event and the batched launches, so both sum in the same order.
-int dca_wire_chunks(int W, int64_t S);
+int dca_wire_chunks(int W, int64_t S, int chunk_wires);
 
 struct SelArgs {
     const void *rss;

@@ -939,9 +939,14 @@ static cudaError_t dca_dispatch(const comet_field &f, const DcaArgs &a, cudaStre
     }
 }
 
-int dca_wire_chunks(int W, int64_t S)
+int dca_wire_chunks(int W, int64_t S, int chunk_wires)
 {
     if (W <= 0 || W > kPersistMaxW) return 1;
+    if (chunk_wires > 0) {
+        // a fixed width (the context's setting), at most kDcaBatchSub chunks
+        const int n = (W + chunk_wires - 1) / chunk_wires;
+        return n < kDcaBatchSub ? n : kDcaBatchSub;
+    }
     int nc = (W + COMET_DCA_CHUNK_W - 1) / COMET_DCA_CHUNK_W;
     // few seeds: narrower chunks (at least 4 wires, at most kDcaBatchSub of them), so that the
     // (32-seed group, chunk) work items occupy every SM
@@ -1112,8 +1117,9 @@ __global__ void __launch_bounds__(kThreads, COMET_DCA_BATCH_MINB) dca_batch_kern
         // the item's (group, wire chunk) sub-items, taken by the warps as they come free
         const int nc = a.n_chunks;
         const int64_t n_groups = (a.S + 31) / 32;
-        const int64_t g0 = lc * dca_batch_groups(nc);
-        const int ng = (int)min((int64_t)dca_batch_groups(nc), n_groups - g0);
+        const int gpi = a.batch_groups > 0 ? a.batch_groups : dca_batch_groups(nc);
+        const int64_t g0 = lc * gpi;
+        const int ng = (int)min((int64_t)gpi, n_groups - g0);
         const int n_sub = ng * nc;
         T *ph = (T *)((unsigned char *)BL.dca_part +
                       (size_t)blockIdx.x * kDcaBatchSub * 32 * (2 * sizeof(T) + 4));

@@ -84,6 +84,7 @@ struct comet_ctx {
     int32_t *status = nullptr;   // device status word (bit 0: bulk-copy timeout, bit 1: bad seed index)
     uint64_t copy_wait_ns = 2000000000ull;   // limit of a kernel's wait for a staging bulk copy
     int dca_ctas_per_sm = 0;                 // cap of the persistent DCA launch (0: as many as fit)
+    int dca_chunk_wires = 0;                 // wires per chunk of the DCA's sums (0: automatic)
     void *dca_part = nullptr;    // comet_scan_dca's per-chunk partial sums
     size_t dca_part_bytes = 0;
     uint32_t *dca_arrive = nullptr;   // per-group arrival counters (kept zero between launches)

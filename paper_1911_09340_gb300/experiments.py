@@ -401,7 +401,8 @@ def batch_study(n_events: int = 512, stride: int = 32, lam: float = 1e-2, tune_e
                          max_hits=max(2048, max(ev.n_hits for ev in events)))
     best, table = BT.autotune(sc, events[:tune_events], slots_options=(64, 128, 256), ctas_options=(0, 4),
                               graph_options=(True, False), solo_options=(None, 1 << 16, 1 << 17),
-                              lanes_options=(1, 2, 3, 4))
+                              lanes_options=(1, 2, 3, 4), chunk_options=(0, 16, 64),
+                              item_options=(0, 4, 16))
     pinned = sc.pin(events)
     sc.run(events[:tune_events], pinned=pinned[:tune_events])
     r = sc.run(events, pinned=pinned)
@@ -415,7 +416,8 @@ def batch_study(n_events: int = 512, stride: int = 32, lam: float = 1e-2, tune_e
                             max_wires=max(512, max(ev.n_wires for ev in events)),
                             max_hits=max(2048, max(ev.n_hits for ev in events)),
                             graph=best["graph"], dca_ctas_per_sm=best["dca_ctas_per_sm"],
-                            solo_min_seeds=best["solo_min_seeds"], solo_lanes=best["solo_lanes"])
+                            solo_min_seeds=best["solo_min_seeds"], solo_lanes=best["solo_lanes"],
+                            chunk_wires=best["chunk_wires"], item_groups=best["item_groups"])
             for c in (ctx, ctx2)]
     BT.run_interleaved(pair, events[:tune_events])
     r2 = BT.run_interleaved(pair, events)

@@ -76,6 +76,29 @@ def test_size_aware_rounds_equal_per_event_scan(ctx, dtype_name, solo_lanes):
         bs.close_lanes()
 
 
+@pytest.mark.parametrize("chunk_wires,item_groups", [(8, 2), (64, 0), (0, 5)])
+def test_chunk_and_item_knobs_equal_per_event_scan(ctx, chunk_wires, item_groups):
+    """The DCA's wires per chunk (a context setting, shared by both paths) and the batched DCA's
+    seed groups per item: batched results stay bit-identical to the per-event scan of the same
+    context setting."""
+    import torch
+    from paper_1911_09340_gb300 import batch
+    events = _events(6)
+    ctx.set_dca_chunk_wires(chunk_wires)
+    try:
+        ref = _reference(ctx, events, torch.float32, 16)
+        bs = batch.BatchScanner(ctx, torch.float32, stride=16, lam=1e-2, slots=3, max_seeds=4096,
+                                max_total_seeds=1 << 15, max_wires=512, max_hits=1024,
+                                chunk_wires=chunk_wires, item_groups=item_groups)
+        r = bs.run(events, collect=True)
+        for ev, rr, res in zip(events, ref, r["results"]):
+            for p, part in enumerate(rr):
+                assert res.best_idx[p] == part["idx"] and res.best_rss[p] == part["rss"]
+                assert np.array_equal(res.hit_class[p], part["hit_class"])
+    finally:
+        ctx.set_dca_chunk_wires(0)
+
+
 def test_autotune_then_run_matches_per_event_scan(ctx):
     """The autotuner cycles through configurations (new caps reallocate the context's staging, and
     graphs captured before must be dropped); the configured run afterwards still reproduces the
@@ -86,10 +109,16 @@ def test_autotune_then_run_matches_per_event_scan(ctx):
     ref = _reference(ctx, events, torch.float32, 16)
     bs = batch.BatchScanner(ctx, torch.float32, stride=16, lam=1e-2, slots=4, max_seeds=4096,
                             max_total_seeds=1 << 16, max_wires=512, max_hits=1024)
-    best, table = batch.autotune(bs, events[:3], slots_options=(2, 4), ctas_options=(0, 2),
-                                 graph_options=(True, False))
-    assert len(table) == 8 and best in table
-    r = bs.run(events, collect=True)
+    try:
+        best, table = batch.autotune(bs, events[:3], slots_options=(2, 4), ctas_options=(0, 2),
+                                     graph_options=(True, False), chunk_options=(0, 16),
+                                     item_options=(0, 8))
+        assert len(table) == 11 and best in table
+        # the per-event reference with the chunk width the autotuner left on the context
+        ref = _reference(ctx, events, torch.float32, 16)
+        r = bs.run(events, collect=True)
+    finally:
+        ctx.set_dca_chunk_wires(0)
     for rr, res in zip(ref, r["results"]):
         for p, part in enumerate(rr):
             assert res.best_idx[p] == part["idx"] and res.best_rss[p] == part["rss"]

@@ -249,6 +249,9 @@ def test_context_validation():
     _expect_invalid(L.comet_ctx_set_dca_ctas_per_sm(None, 1))
     _expect_invalid(L.comet_ctx_set_dca_ctas_per_sm(c.handle, -1))
     _expect_invalid(L.comet_ctx_set_dca_ctas_per_sm(c.handle, 65))
+    _expect_invalid(L.comet_ctx_set_dca_chunk_wires(None, 8))
+    for w in (-1, 1, 3, 1025):
+        _expect_invalid(L.comet_ctx_set_dca_chunk_wires(c.handle, w))
     _expect_invalid(L.comet_ctx_status(c.handle, None))
     _expect_invalid(L.comet_kernel_arch(None))
     c.close()

@@ -310,6 +310,34 @@ def test_wire_chunk_boundaries(ctx, n_wires):
     assert np.array_equal(a["rss"], b["rss"]) and np.array_equal(a["n_in"], b["n_in"])
 
 
+@pytest.mark.parametrize("chunk_wires", [4, 16, 100])
+def test_chunk_width_setting_keeps_the_oracle_sums(ctx, chunk_wires):
+    """The context's wires per chunk (4, 16 and 100; 200 wires, 586 seeds): FP64 RSS within the
+    bound of the 1e-9 m DCA bar and n_in identical away from the cutoff; FP32 RSS within the bound
+    of the 2 um bar."""
+    ev, wires, offs, drift, mask = _wires_case(200)
+    seeds = O.lattice(ev.partitions[0])[::7].astype(np.float32).astype(np.float64)
+    f = B.DeviceField.from_synth(UNIFORM)
+    lam = 0.01
+    c = B.Context(0)
+    try:
+        c.set_dca_chunk_wires(chunk_wires)
+        for dtype, delta in ((torch.float64, 1e-9), (torch.float32, FP32_DCA_TOL)):
+            op, bp = both_params(n_steps=ev.n_steps[0], stride=16, lam=lam,
+                                 tol=1e-12 if dtype == torch.float64 else 1e-6)
+            op.tol = 1e-12
+            r = O.scan(UNIFORM, op, seeds, -1, O.wires_aos(seen(wires, dtype)), offs,
+                       seen(drift, dtype), mask, want_dca=True)
+            e = per_wire_residual(r["dca"], offs, seen(drift, dtype), mask)
+            bound = rss_bound(e, lam, delta, fp32=dtype == torch.float32) + 1e-14 * r["rss"]
+            g = gpu_dca(c, f, bp, seeds, -1, wires, offs, drift, mask, dtype, want_dca=False)
+            assert (np.abs(g["rss"] - r["rss"]) <= bound + 1e-12).all()
+            edge = (np.abs(e - lam) < delta).any(1)
+            assert np.array_equal(g["n_in"][~edge], r["n_in"][~edge])
+    finally:
+        c.close()
+
+
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
 @pytest.mark.parametrize("n_wires", [200, 1025])
 def test_copy_wait_give_up_falls_back_to_plain_loads(ctx, dtype, n_wires):
