@@ -30,11 +30,13 @@
  *     launched; an invalid argument returns COMET_ERR_INVALID_ARG and launches nothing.  A failed
  *     launch returns COMET_ERR_CUDA.  No call aborts, throws or prints.  comet_last_error() returns
  *     a message for the last non-OK status of the calling thread.
- *   - The library allocates device memory only inside a comet_ctx: a status word at creation, and
- *     comet_scan_select's per-block partial results lazily on first need (grown when a larger S or
- *     k needs more), kept until comet_ctx_destroy.  A comet_scan_select call that grows the scratch
- *     synchronises the device and calls cudaMalloc; make the largest such call once before
- *     capturing a stream.
+ *   - The library allocates device memory only inside a comet_ctx (comet_scan_select_noalloc
+ *     aside): a status word at creation; lazily, on first need and grown when a larger call needs
+ *     more, comet_scan_select's per-block partial results, comet_scan_dca's per-chunk partial sums
+ *     and per-group arrival counters, and its selection slots (16 B per CTA, when best_idx_out is
+ *     given); the batch staging buffers; all kept until comet_ctx_destroy.  A call that grows
+ *     scratch calls cudaMalloc (comet_scan_select also synchronises the device first); make the
+ *     largest such call once before capturing a stream.
  */
 #ifndef COMET_SCAN_H
 #define COMET_SCAN_H
@@ -210,6 +212,12 @@ comet_status comet_scan_propagate(comet_ctx *ctx, comet_dtype dtype, const comet
  *                The caller zeroes it.  Non-convergence is reported only here, never through the
  *                return status: the count exists on the device once the kernel has run, and
  *                returning it would need a host synchronisation in every call.
+ *   best_idx_out optional out, device [1] int64 (NULL to skip): the seed of lowest RSS, exactly
+ *                as comet_scan_select with k = 1 gives it (ascending RSS, NaN after every number,
+ *                ties by lowest seed index), selected inside this launch (Sec. 2.1: the best seed of
+ *                the partition) -- no separate selection launches: each CTA folds its seeds into
+ *                a slot, and the last CTA to finish (an arrival counter in the status word) folds
+ *                the slots.  best_rss_out optional [1] T: its RSS (needs best_idx_out).
  * D_i: start from the recorded state closest to the wire line (ties: lowest index), then step along
  * the track by -d/|n| with one RK4 step, where n is the part of the unit direction perpendicular to
  * the wire and d the distance to the plane that contains the wire axis with normal n, until
@@ -224,7 +232,8 @@ comet_status comet_scan_dca(comet_ctx *ctx, comet_dtype dtype, const comet_field
                             const int32_t *n_valid, const int8_t *charge, int64_t S,
                             const void *bounds, const void *wires, int32_t W, int32_t ldw, const int32_t *hit_offsets,
                             const void *drift, const uint8_t *hit_mask, void *rss, int32_t *n_in,
-                            void *dca_out, int32_t *n_unconverged, comet_stream stream);
+                            void *dca_out, int32_t *n_unconverged, int64_t *best_idx_out,
+                            void *best_rss_out, comet_stream stream);
 
 /* ---- a7: selection (Sec. 2.1; top-k for Sec. 3.1's "10 seeds at each side") ------------------
  *   rss      [S] T.

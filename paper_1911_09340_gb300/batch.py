@@ -232,9 +232,8 @@ class BatchScanner:
         B.comet_scan_lattice(ctx, spec, seeds, charge, stream=st)
         B.comet_scan_propagate(ctx, self.field, bp, seeds, charge, pts, nv, bounds=bounds, stream=st)
         B.comet_scan_dca(ctx, self.field, bp, pts, nv, charge, wires, offs, drift, mask, rss, n_in,
-                         n_unconverged=self.s_unconv[slot:slot + 1], n_wires=W, bounds=bounds, stream=st)
-        B.comet_scan_select(ctx, rss, 1, self.s_best[slot:slot + 1], self.s_best_rss[slot:slot + 1],
-                            stream=st)
+                         n_unconverged=self.s_unconv[slot:slot + 1], n_wires=W, bounds=bounds, stream=st,
+                         best_idx=self.s_best[slot:slot + 1], best_rss=self.s_best_rss[slot:slot + 1])
         if W > 0:
             B.comet_scan_classify(ctx, self.field, bp, pts, nv, charge, self.s_best[slot:slot + 1],
                                   wires, offs, drift, mask, self.s_class[slot, : max(H, 1)],

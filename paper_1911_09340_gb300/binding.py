@@ -82,7 +82,7 @@ SIGNATURES = {
     "comet_scan_propagate": [_vp, C.c_int, C.POINTER(_Field), C.POINTER(_Params), _vp, _vp, _i64,
                              _vp, _vp, _vp, _vp],
     "comet_scan_dca": [_vp, C.c_int, C.POINTER(_Field), C.POINTER(_Params), _vp, _vp, _vp, _i64,
-                       _vp, _vp, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
+                       _vp, _vp, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "comet_scan_select": [_vp, C.c_int, _vp, _i64, _i32, _vp, _vp, _vp],
     "comet_scan_select_noalloc": [C.c_int, _vp, _i64, _i32, _vp, _vp, _vp],
     "comet_scan_refine_refs": [_vp, C.c_int, _vp, _i64, _vp, _i32, C.POINTER(C.c_double), _i32, _vp,
@@ -284,8 +284,10 @@ def comet_scan_propagate(ctx: Context, field: DeviceField, params: ScanParams, s
 
 def comet_scan_dca(ctx: Context, field: DeviceField, params: ScanParams, points, n_valid, charge,
                    wires, hit_offsets, drift, hit_mask, rss, n_in, dca_out=None, n_unconverged=None,
-                   n_wires: Optional[int] = None, bounds=None, stream=None):
-    """``wires`` is [6][ldw]; the first ``n_wires`` columns (default: all) are the wires."""
+                   n_wires: Optional[int] = None, bounds=None, stream=None, best_idx=None,
+                   best_rss=None):
+    """``wires`` is [6][ldw]; the first ``n_wires`` columns (default: all) are the wires.
+    ``best_idx`` ([1] int64) / ``best_rss`` ([1]): the seed of lowest RSS selected in the launch."""
     dt = _dtype_code(points)
     S = n_valid.shape[0]
     ldw = wires.shape[-1]
@@ -297,6 +299,7 @@ def comet_scan_dca(ctx: Context, field: DeviceField, params: ScanParams, points,
                                 _ptr(drift, points.dtype), _ptr(hit_mask, torch.uint8),
                                 _ptr(rss, points.dtype), _ptr(n_in, torch.int32),
                                 _ptr(dca_out, points.dtype), _ptr(n_unconverged, torch.int32),
+                                _ptr(best_idx, torch.int64), _ptr(best_rss, points.dtype),
                                 _stream(stream)))
 
 

@@ -234,6 +234,11 @@ void fill_dca(comet_ctx *ctx, comet_dtype dtype, const comet_scan_params *p, con
     a->wait_ns = ctx->copy_wait_ns;
     a->max_ctas_per_sm = ctx->dca_ctas_per_sm;
     a->batch_groups = 0;
+    a->best_idx_out = nullptr;
+    a->best_rss_out = nullptr;
+    a->best_slots = nullptr;
+    a->best_slots_cap = 0;
+    a->best_counter = nullptr;
     a->lambda = p->lambda;
     a->tol = p->tol;
     a->max_iter = p->max_iter;
@@ -331,7 +336,9 @@ void comet_ctx_destroy(comet_ctx *ctx)
         if (ctx->status) cudaFree(ctx->status);
         if (ctx->dca_part) cudaFree(ctx->dca_part);
         if (ctx->dca_arrive) cudaFree(ctx->dca_arrive);
+        if (ctx->dca_best) cudaFree(ctx->dca_best);
         ctx->batch.release();
+        cudaGetLastError();   // destroy reports nothing: leave no error behind for the next call
     }
     delete ctx;
 }
@@ -632,7 +639,8 @@ comet_status comet_scan_dca(comet_ctx *ctx, comet_dtype dtype, const comet_field
                             const int32_t *n_valid, const int8_t *charge, int64_t S,
                             const void *bounds, const void *wires, int32_t W, int32_t ldw, const int32_t *hit_offsets,
                             const void *drift, const uint8_t *hit_mask, void *rss, int32_t *n_in,
-                            void *dca_out, int32_t *n_unconverged, comet_stream stream)
+                            void *dca_out, int32_t *n_unconverged, int64_t *best_idx_out,
+                            void *best_rss_out, comet_stream stream)
 {
     if (!ctx) return fail(COMET_ERR_INVALID_ARG, "ctx is NULL");
     CHECK(check_dtype(dtype));
@@ -644,8 +652,10 @@ comet_status comet_scan_dca(comet_ctx *ctx, comet_dtype dtype, const comet_field
     if (!points || !n_valid || !charge || !rss || !n_in) return fail(COMET_ERR_INVALID_ARG, "points, n_valid, charge, rss and n_in are required");
     if (!aligned(points, esize(dtype)) || !aligned(rss, esize(dtype)) || !aligned(n_valid, 4) ||
         !aligned(n_in, 4) || (dca_out && !aligned(dca_out, esize(dtype))) ||
-        (n_unconverged && !aligned(n_unconverged, 4)) || !bounds_aligned(bounds))
+        (n_unconverged && !aligned(n_unconverged, 4)) || !bounds_aligned(bounds) ||
+        (best_idx_out && !aligned(best_idx_out, 8)) || (best_rss_out && !aligned(best_rss_out, esize(dtype))))
         return fail(COMET_ERR_INVALID_ARG, "an array is misaligned for its element type");
+    if (best_rss_out && !best_idx_out) return fail(COMET_ERR_INVALID_ARG, "best_rss_out needs best_idx_out");
     DeviceGuard g(ctx->device);
     if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
     comet::DcaArgs a;
@@ -684,6 +694,26 @@ comet_status comet_scan_dca(comet_ctx *ctx, comet_dtype dtype, const comet_field
         }
         a.part = ctx->dca_part;
         a.arrive = ctx->dca_arrive;
+    }
+    if (best_idx_out) {
+        // one slot per CTA: the persistent grid is at most 64 CTAs per SM, the tiled one S / 128
+        const int64_t cap_p = (int64_t)64 * comet::device_sm_count();
+        const int64_t cap_t = (S + 127) / 128;
+        const int64_t cap = cap_p > cap_t ? cap_p : cap_t;
+        if (cap > ctx->dca_best_cap) {
+            if (ctx->dca_best) cudaFree(ctx->dca_best);
+            ctx->dca_best = nullptr;
+            ctx->dca_best_cap = 0;
+            cudaError_t e = cudaMalloc(&ctx->dca_best, (size_t)cap * 16);
+            if (e != cudaSuccess)
+                return e == cudaErrorMemoryAllocation ? fail(COMET_ERR_NO_MEMORY, "cudaMalloc(dca selection slots)") : cuda_fail(e, "cudaMalloc");
+            ctx->dca_best_cap = cap;
+        }
+        a.best_idx_out = best_idx_out;
+        a.best_rss_out = best_rss_out;
+        a.best_slots = ctx->dca_best;
+        a.best_slots_cap = ctx->dca_best_cap;
+        a.best_counter = (uint32_t *)(ctx->status + 20);
     }
     cudaError_t e = comet::launch_dca(dtype, *field, a, (cudaStream_t)stream);
     return e == cudaSuccess ? COMET_OK : cuda_fail(e, "dca launch");

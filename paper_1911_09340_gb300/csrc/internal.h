@@ -70,6 +70,14 @@ struct DcaArgs {
     uint64_t wait_ns;      // limit of a wait for a staging bulk copy (0: give up at once)
     int max_ctas_per_sm;   // persistent launch: at most this many CTAs per SM (0: as many as fit)
     int batch_groups;      // batched launch: 32-seed groups per CTA item (0: kDcaBatchSub / n_chunks)
+    // optional k = 1 selection inside the launch: the seed of lowest RSS and its RSS, through
+    // per-CTA slots (int64 index [slots_cap], then T value [slots_cap]; slots_cap >= the grid) and
+    // a CTA arrival counter kept at zero between launches
+    int64_t *best_idx_out;
+    void *best_rss_out;
+    void *best_slots;
+    int64_t best_slots_cap;
+    uint32_t *best_counter;
     double lambda, tol;
     double R0;             // super-segment radius (m), margins included
     double R1;             // level-1 segment radius (m), margins included

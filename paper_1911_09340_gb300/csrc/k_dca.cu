@@ -563,6 +563,112 @@ __device__ __forceinline__ bool finish_stage(uint64_t *bar, uint32_t &parity, ui
 }
 
 // ------------------------------------------------------------------------------------------------
+// The seed of lowest RSS, selected inside the DCA launch (optional; the k = 1 case of
+// comet_scan_select, in its order: ascending RSS, NaN after every number, ties by lowest index).
+// The warp that finalises a group folds the group's best into its warp's best (shared memory); at
+// the end each CTA folds its warps into a slot, and the last CTA to finish folds the slots.
+// ------------------------------------------------------------------------------------------------
+
+template <typename T>
+struct Best {
+    T v;
+    int64_t i;
+};
+
+template <typename T>
+__device__ __forceinline__ T nan_value()
+{
+    if constexpr (sizeof(T) == 4)
+        return __int_as_float(0x7fc00000);
+    else
+        return __longlong_as_double(0x7ff8000000000000ll);
+}
+
+template <typename T>
+__device__ __forceinline__ Best<T> best_none()
+{
+    return Best<T>{nan_value<T>(), INT64_MAX};
+}
+
+// (v, i) before (b.v, b.i) in comet_scan_select's order
+template <typename T>
+__device__ __forceinline__ bool precedes(T v, int64_t i, const Best<T> &b)
+{
+    const bool vn = v != v, bn = b.v != b.v;
+    if (vn != bn) return bn;
+    if (!vn && v != b.v) return v < b.v;
+    return i < b.i;
+}
+
+template <typename T>
+__device__ __forceinline__ void best_fold(Best<T> &b, T v, int64_t i)
+{
+    if (precedes<T>(v, i, b)) {
+        b.v = v;
+        b.i = i;
+    }
+}
+
+// The best of the warp's 32 candidates, in every lane.
+template <typename T>
+__device__ __forceinline__ Best<T> warp_best(Best<T> b)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const T v = __shfl_xor_sync(0xffffffffu, b.v, off);
+        const int64_t i = __shfl_xor_sync(0xffffffffu, b.i, off);
+        best_fold<T>(b, v, i);
+    }
+    return b;
+}
+
+// A finalised group: the best of its valid seeds folded into this warp's best (s_warp[warp]).
+template <typename T>
+__device__ __forceinline__ void group_best_fold(Best<T> *s_warp, int warp, int lane, bool valid, T rss,
+                                                int64_t s)
+{
+    Best<T> b = valid ? Best<T>{rss, s} : best_none<T>();
+    b = warp_best<T>(b);
+    if (lane == 0) best_fold<T>(s_warp[warp], b.v, b.i);
+}
+
+// End of the launch (every thread of the CTA): the CTA's best into its slot; the last CTA to finish
+// folds every slot and writes the selection, then leaves the counter at zero for the next launch.
+template <typename T>
+__device__ __forceinline__ void finish_best(const DcaArgs &a, Best<T> *s_warp, int *s_last)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int64_t *slot_i = (int64_t *)a.best_slots;
+    T *slot_v = (T *)(slot_i + gridDim.x);
+    __syncthreads();
+    if (tid == 0) {
+        Best<T> b = s_warp[0];
+        for (int w = 1; w < kWarps; ++w) best_fold<T>(b, s_warp[w].v, s_warp[w].i);
+        slot_i[blockIdx.x] = b.i;
+        slot_v[blockIdx.x] = b.v;
+        __threadfence();
+        const unsigned int t = atomicAdd(a.best_counter, 1u);
+        *s_last = t == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (*s_last) {
+        __threadfence();
+        Best<T> b = best_none<T>();
+        for (unsigned int k = tid; k < gridDim.x; k += blockDim.x) best_fold<T>(b, __ldcg(slot_v + k), __ldcg(slot_i + k));
+        b = warp_best<T>(b);
+        if (lane == 0) s_warp[warp] = b;
+        __syncthreads();
+        if (tid == 0) {
+            Best<T> r = s_warp[0];
+            for (int w = 1; w < kWarps; ++w) best_fold<T>(r, s_warp[w].v, s_warp[w].i);
+            *a.best_idx_out = r.i;
+            if (a.best_rss_out) *(T *)a.best_rss_out = r.v;
+            *a.best_counter = 0u;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
 // Persistent kernel: all wires fit one shared-memory tile (the common case).  Each CTA stages the
 // wires and hits once; each warp then takes work items -- (32-seed group, wire chunk) pairs, or
 // whole groups when no partial-sum scratch is given -- from a device counter until none is left,
@@ -632,8 +738,11 @@ __global__ void __launch_bounds__(kThreads, COMET_DCA_MINB) dca_persistent_kerne
     const int W = a.W;
     const int H = W > 0 ? a.offs[W] : 0;
     const bool hits_sm = H <= kHitMax;
+    __shared__ Best<T> s_best[kWarps];
+    __shared__ int s_last;
 
     if (tid == 0) mbar_init(bar, 1);
+    if (lane == 0) s_best[warp] = best_none<T>();
     __syncthreads();
 
     // ---- stage wires, offsets and (when they fit) hits: one bulk-copy transaction (W > 0 only:
@@ -716,10 +825,12 @@ __global__ void __launch_bounds__(kThreads, COMET_DCA_MINB) dca_persistent_kerne
         int nin = 0;
         if (!split) {
             group_all_chunks<T, F>(f, a, gr, tl, s0, s1, lane, acc, nin, nunc);
+            const T v = acc.value();
             if (gr.valid) {
-                ((T *)a.rss)[gr.s] = acc.value();
+                ((T *)a.rss)[gr.s] = v;
                 a.n_in[gr.s] = nin;
             }
+            if (a.best_idx_out) group_best_fold<T>(s_best, warp, lane, gr.valid, v, gr.s);
         } else {
             const int2 r = chunk_range(W, nc, c);
             group_wires<T, F>(f, a, gr, tl, s0, s1, lane, acc, nin, nunc, r.x, r.y);
@@ -739,6 +850,7 @@ __global__ void __launch_bounds__(kThreads, COMET_DCA_MINB) dca_persistent_kerne
             if (done == (unsigned)(nc - 1)) {
                 // the group's last chunk: add the partial sums in chunk order
                 __threadfence();
+                T v = T(0);
                 if (gr.valid) {
                     Acc<T> tot;
                     int nt = 0;
@@ -747,9 +859,11 @@ __global__ void __launch_bounds__(kThreads, COMET_DCA_MINB) dca_persistent_kerne
                         tot.add_pair(__ldcg(ph + o), __ldcg(pl + o));
                         nt += __ldcg(pn + o);
                     }
-                    ((T *)a.rss)[gr.s] = tot.value();
+                    v = tot.value();
+                    ((T *)a.rss)[gr.s] = v;
                     a.n_in[gr.s] = nt;
                 }
+                if (a.best_idx_out) group_best_fold<T>(s_best, warp, lane, gr.valid, v, gr.s);
                 if (lane == 0) a.arrive[g] = 0u;   // left zero for the next launch
             }
         }
@@ -761,6 +875,7 @@ __global__ void __launch_bounds__(kThreads, COMET_DCA_MINB) dca_persistent_kerne
         for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
         if (lane == 0 && t) atomicAdd(a.n_unconv, t);
     }
+    if (a.best_idx_out) finish_best<T>(a, s_best, &s_last);
     if (any_timeout) {
         if (tid == 0 && a.status) atomicOr(a.status, 1);
         mbar_wait(bar, parity ^ 1u, kWaitNs);
@@ -868,8 +983,9 @@ __global__ void __launch_bounds__(kThreads, COMET_DCA_MINB) dca_tiled_kernel(F f
         if (w0 + kWireTile < W) __syncthreads();   // tile consumed before the next staging
     }
 
+    const T v = acc.value();
     if (gr.valid) {
-        ((T *)a.rss)[gr.s] = acc.value();
+        ((T *)a.rss)[gr.s] = v;
         a.n_in[gr.s] = nin;
     }
     if (a.n_unconv) {
@@ -877,6 +993,14 @@ __global__ void __launch_bounds__(kThreads, COMET_DCA_MINB) dca_tiled_kernel(F f
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
         if (lane == 0 && t) atomicAdd(a.n_unconv, t);
+    }
+    if (a.best_idx_out) {
+        __shared__ Best<T> s_best[kWarps];
+        __shared__ int s_last;
+        if (lane == 0) s_best[warp] = best_none<T>();
+        __syncwarp();
+        group_best_fold<T>(s_best, warp, lane, gr.valid, v, gr.s);
+        finish_best<T>(a, s_best, &s_last);
     }
     if (any_timeout && tid == 0 && a.status) atomicOr(a.status, 1);
 }
@@ -912,6 +1036,7 @@ static cudaError_t dca_launch(const F &fld, const DcaArgs &a, cudaStream_t st)
         nb = nb < cap ? nb : cap;
         e = cudaMemsetAsync(a.counter, 0, sizeof(int32_t), st);
         if (e != cudaSuccess) return e;
+        if (a.best_idx_out && nb > a.best_slots_cap) return cudaErrorInvalidValue;   // one slot per CTA
         dca_persistent_kernel<T, F><<<(unsigned)nb, kThreads, L.total, st>>>(fld, a);
         return cudaGetLastError();
     }
@@ -920,6 +1045,7 @@ static cudaError_t dca_launch(const F &fld, const DcaArgs &a, cudaStream_t st)
         dca_tiled_kernel<T, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::total);
     if (attr != cudaSuccess) return attr;
     const int64_t nb = (a.S + kThreads - 1) / kThreads;
+    if (a.best_idx_out && nb > a.best_slots_cap) return cudaErrorInvalidValue;   // one slot per CTA
     dca_tiled_kernel<T, F><<<(unsigned)nb, kThreads, L::total, st>>>(fld, a);
     return cudaGetLastError();
 }

@@ -88,6 +88,8 @@ struct comet_ctx {
     void *dca_part = nullptr;    // comet_scan_dca's per-chunk partial sums
     size_t dca_part_bytes = 0;
     uint32_t *dca_arrive = nullptr;   // per-group arrival counters (kept zero between launches)
+    void *dca_best = nullptr;         // per-CTA slots of comet_scan_dca's fused selection
+    int64_t dca_best_cap = 0;         // slots
     size_t dca_arrive_n = 0;
     comet::detail::BatchState batch;
 };

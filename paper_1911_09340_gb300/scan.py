@@ -102,11 +102,15 @@ def scan_partition(ctx: B.Context, field: B.DeviceField, params: B.ScanParams, s
     bounds = ws.bounds[: (S + 31) // 32]
     B.comet_scan_propagate(ctx, field, params, seeds, charge, pts, nv, bounds=bounds)
     mark("dca")
+    # k = 1: the seed of lowest RSS is selected inside the DCA launch; top-k takes comet_scan_select
+    fused = k == 1
     B.comet_scan_dca(ctx, field, params, pts, nv, charge, ev.wires, ev.hit_offsets, ev.drift,
                      ev.mask, rss, n_in, dca_out=want_dca, n_unconverged=ws.n_unconv, n_wires=ev.W,
-                     bounds=bounds)
-    mark("select")
-    B.comet_scan_select(ctx, rss, k, ws.idx[:k], ws.best[:k])
+                     bounds=bounds, best_idx=ws.idx[:1] if fused else None,
+                     best_rss=ws.best[:1] if fused else None)
+    if not fused:
+        mark("select")
+        B.comet_scan_select(ctx, rss, k, ws.idx[:k], ws.best[:k])
     mark("classify")
     hc = ws.hit_class[: max(ev.H, 1)] if hit_class is None else hit_class
     B.comet_scan_classify(ctx, field, params, pts, nv, charge, ws.idx, ev.wires, ev.hit_offsets,
@@ -116,8 +120,9 @@ def scan_partition(ctx: B.Context, field: B.DeviceField, params: B.ScanParams, s
     return ws
 
 
-# kernel launches of one scan_partition call: lattice, propagate, dca, select (2 passes), classify
-LAUNCHES_PER_PARTITION = 6
+# kernel launches of one scan_partition call (k = 1): lattice, propagate, dca (with the selection),
+# classify
+LAUNCHES_PER_PARTITION = 4
 
 
 class KernelTimer:
@@ -163,7 +168,8 @@ class PipelinedScanner:
     """Scans turn partitions with the track recording of the next partition (lattice, propagate:
     they do not read the hit mask) on a second stream, beside the current partition's DCA,
     selection and classification (which read and update the mask, in partition order on the
-    caller's stream).  Two workspaces alternate: a partition's recording waits only until the
+    caller's stream; the seed of lowest RSS is selected inside the DCA launch).  Two workspaces
+    alternate: a partition's recording waits only until the
     partition two back has been classified.  Every kernel is the single-event path's; the results
     are identical to scan_partition's.  With ``dca_ctas_per_sm`` the context's DCA launches leave
     room on each SM for the recording kernels to run beside them."""
@@ -205,9 +211,7 @@ class PipelinedScanner:
         mark("dca")
         B.comet_scan_dca(self.ctx, self.field, params, pts, nv, charge, ev.wires, ev.hit_offsets,
                          ev.drift, ev.mask, rss, n_in, n_unconverged=ws.n_unconv, n_wires=ev.W,
-                         bounds=bounds)
-        mark("select")
-        B.comet_scan_select(self.ctx, rss, 1, ws.idx[:1], ws.best[:1])
+                         bounds=bounds, best_idx=ws.idx[:1], best_rss=ws.best[:1])
         mark("classify")
         hc = ws.hit_class[: max(ev.H, 1)] if hit_class is None else hit_class
         B.comet_scan_classify(self.ctx, self.field, params, pts, nv, charge, ws.idx, ev.wires,

@@ -108,7 +108,7 @@ def test_dca_validation(ctx, bufs):
     P = lambda **kw: C.byref(_params(**kw))
     good = [ctx.handle, 0, C.byref(_field()), P(), _p(b["points"]), _p(b["n_valid"]), _p(b["charge"]), S,
             None, _p(b["wires"]), W, W, _p(b["offs"]), _p(b["drift"]), _p(b["mask"]), _p(b["rss"]),
-            _p(b["n_in"]), None, None, None]
+            _p(b["n_in"]), None, None, None, None, None]
     bad = {
         0: [None], 1: [2], 2: [None],
         3: [None, P(lam=0.0), P(lam=-1.0), P(tol=0.0), P(max_iter=-1), P(n_steps=0), P(stride=0)],
@@ -116,7 +116,8 @@ def test_dca_validation(ctx, bufs):
         8: [C.c_void_p(b["bounds"].data_ptr() + 8)],
         9: [None, _odd(b["wires"])], 10: [-1], 11: [W - 1], 12: [None, _odd(b["offs"])],
         13: [None, _odd(b["drift"])], 14: [None], 15: [None, _odd(b["rss"])], 16: [None, _odd(b["n_in"])],
-        17: [_odd(b["rss"])], 18: [_odd(b["n_in"])],
+        17: [_odd(b["rss"])], 18: [_odd(b["n_in"])], 19: [_odd(b["idx"])],
+        20: [_odd(b["rss"]), _p(b["val"])],     # misaligned; an RSS output without the index output
     }
     for i, vals in bad.items():
         for v in vals:

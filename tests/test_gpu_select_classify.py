@@ -35,6 +35,59 @@ def test_select_matches_oracle(ctx, dtype, S):
         assert np.array_equal(val.double().cpu().numpy(), rv, equal_nan=True)
 
 
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+@pytest.mark.parametrize("case", ["event", "ties", "ragged", "no_wires", "tiled"])
+def test_selection_inside_the_dca_launch_equals_select(ctx, dtype, case):
+    """comet_scan_dca's optional best_idx / best_rss (the k = 1 selection folded into the DCA
+    launch: per warp, per CTA, then the last CTA) equal comet_scan_select(k = 1) on the RSS the same
+    launch wrote, bit for bit: an event's partition (persistent kernel), seeds duplicated so that
+    equal RSS values tie (lowest index wins), a ragged seed count, no wires (every RSS 0: seed 0),
+    and more than 1024 wires (tiled kernel, one CTA per 128 seeds)."""
+    from gpu_util import gpu_propagate
+    ev = synth.multi_turn_event(1, counts=(4, 8, 8, 16))
+    seeds = O.lattice(ev.partitions[0])
+    wires, offs, drift = ev.wires, ev.hit_offsets, ev.drift
+    if case == "ties":
+        seeds = np.concatenate([seeds[::2], seeds[::2], seeds[4:5]])   # every seed twice, in order
+    elif case == "ragged":
+        seeds = seeds[:3001]
+    elif case == "no_wires":
+        wires, offs, drift = np.zeros((6, 0)), np.zeros(1, np.int32), np.zeros(0)
+    elif case == "tiled":
+        ch = synth.make_chamber()
+        ids = np.arange(1100) * 3
+        wires = np.concatenate([ch.a[:, ids], ch.u[:, ids]], axis=0)
+        offs = np.arange(1101, dtype=np.int32)
+        drift = np.random.default_rng(2).uniform(0, 8e-3, size=1100)
+    _, bp = both_params(n_steps=ev.n_steps[0], stride=32, lam=0.01,
+                        tol=1e-12 if dtype == torch.float64 else 1e-6)
+    f = B.DeviceField.from_synth(UNIFORM)
+    _, charge, pts, nv = gpu_propagate(ctx, f, bp, seeds, -1, dtype)
+    S, W = seeds.shape[0], wires.shape[1]
+    w = dev_wires(wires, dtype)
+    o = torch.as_tensor(np.asarray(offs, np.int32), device="cuda")
+    d = torch.as_tensor(np.asarray(drift), dtype=dtype, device="cuda")
+    m = torch.zeros(max(int(offs[-1]), 1), dtype=torch.uint8, device="cuda")
+    rss = torch.empty(S, dtype=dtype, device="cuda")
+    n_in = torch.empty(S, dtype=torch.int32, device="cuda")
+    for rep in range(2):                  # twice: the arrival counter is left at zero
+        bi = torch.full((1,), -5, dtype=torch.int64, device="cuda")
+        bv = torch.full((1,), -5.0, dtype=dtype, device="cuda")
+        B.comet_scan_dca(ctx, f, bp, pts, nv, charge, w, o, d, m, rss, n_in, n_wires=W,
+                         best_idx=bi, best_rss=bv)
+        ri = torch.full((1,), -7, dtype=torch.int64, device="cuda")
+        rv = torch.zeros(1, dtype=dtype, device="cuda")
+        B.comet_scan_select(ctx, rss, 1, ri, rv)
+        torch.cuda.synchronize()
+        assert int(bi[0]) == int(ri[0]) and bv.cpu().numpy()[0] == rv.cpu().numpy()[0]
+        r = rss.double().cpu().numpy()
+        assert int(bi[0]) == int(np.flatnonzero(r == r.min())[0])
+    if case == "ties":
+        assert int(bi[0]) < S // 2 + 1 and r[int(bi[0])] == r[int(bi[0]) + (S - 1) // 2]
+    if case == "no_wires":
+        assert int(bi[0]) == 0 and float(bv[0]) == 0.0
+
+
 def test_select_rejects_bad_k(ctx):
     rss = torch.zeros(10, dtype=torch.float32, device="cuda")
     idx = torch.zeros(65, dtype=torch.int64, device="cuda")
