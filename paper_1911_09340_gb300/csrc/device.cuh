@@ -32,6 +32,11 @@ struct FieldAxial {
         by = T(0);
         bz_ = bz;
     }
+    struct Cell {};
+    __device__ __forceinline__ void at_cell(Cell &, T x, T y, T z, T &bx, T &by, T &bz_) const
+    {
+        at(x, y, z, bx, by, bz_);
+    }
 };
 
 // Uniform field of any direction.
@@ -44,6 +49,11 @@ struct FieldUniform {
         bx = b0;
         by = b1;
         bz = b2;
+    }
+    struct Cell {};
+    __device__ __forceinline__ void at_cell(Cell &, T x, T y, T z, T &bx, T &by, T &bz_) const
+    {
+        at(x, y, z, bx, by, bz_);
     }
 };
 
@@ -64,6 +74,87 @@ struct FieldTable {
         i = (int)fl;
         i = i > n - 2 ? n - 2 : i;
         t = g - T(i);
+    }
+
+    // The eight corner nodes of the grid cell a lane used last (base: index of its node 000; none
+    // at first).  Lookups in the same cell take them from registers: the RK4 stages 2 and 3 of a
+    // step are microns apart, and so are stage 4 and the next step's stage 1, so about half of the
+    // recording's lookups need no node load.  The interpolation is the same arithmetic on the same
+    // node values as at(), so results are bit-identical.
+    struct Cell {
+        int64_t base = -1;
+        T fx = T(-1e30), fy = T(-1e30), fz = T(-1e30);   // its node 000 in grid units
+        // per x edge e = (z bit, y bit) and component c: the node at x = 0 and the difference to
+        // the node at x = 1, both as the interpolation rounds them
+        T v0[4][3], dx[4][3];
+    };
+
+    __device__ __forceinline__ static T lerp3(const Cell &cc, int c, T tx, T ty, T tz)
+    {
+        const T a00 = cc.v0[0][c] + tx * cc.dx[0][c];
+        const T a01 = cc.v0[1][c] + tx * cc.dx[1][c];
+        const T a10 = cc.v0[2][c] + tx * cc.dx[2][c];
+        const T a11 = cc.v0[3][c] + tx * cc.dx[3][c];
+        const T b0 = a00 + ty * (a01 - a00);
+        const T b1 = a10 + ty * (a11 - a10);
+        return b0 + tz * (b1 - b0);
+    }
+
+    __device__ __forceinline__ void at_cell(Cell &cc, T x, T y, T z, T &bx, T &by, T &bz) const
+    {
+        const T gx = (x - ox) * inv_sp, gy = (y - oy) * inv_sp, gz = (z - oz) * inv_sp;
+        // inside the cached cell, 0 <= g - i < 1 in every dimension: g needs no clamping there,
+        // floor(g) = i, and g - i is exact (Sterbenz), so these are the fractions cell() gives
+        T tx = gx - cc.fx, ty = gy - cc.fy, tz = gz - cc.fz;
+        if (!(tx >= T(0) && tx < T(1) && ty >= T(0) && ty < T(1) && tz >= T(0) && tz < T(1)))
+            enter(cc, gx, gy, gz, tx, ty, tz);
+        bx = lerp3(cc, 0, tx, ty, tz);
+        by = lerp3(cc, 1, tx, ty, tz);
+        bz = lerp3(cc, 2, tx, ty, tz);
+    }
+
+    // A lookup outside the cached cell: the cell of (gx, gy, gz) as at() finds it, its fractions,
+    // and its corner nodes unless it is the cached one after all (clamped at the grid's edges).
+    __device__ __forceinline__ void enter(Cell &cc, T gx, T gy, T gz, T &tx, T &ty, T &tz) const
+    {
+        int ix, iy, iz;
+        cell(gx, nx, ix, tx);
+        cell(gy, ny, iy, ty);
+        cell(gz, nz, iz, tz);
+        cc.fx = T(ix);
+        cc.fy = T(iy);
+        cc.fz = T(iz);
+        const int64_t base = ((int64_t)iz * ny + iy) * nx + ix;
+        if (base != cc.base) {
+            cc.base = base;
+            const int64_t sy = nx, sz = (int64_t)nx * ny;
+            // corner j = (z bit, y bit, x bit), x fastest
+            const int64_t off[8] = {0, 1, sy, sy + 1, sz, sz + 1, sz + sy, sz + sy + 1};
+            float v[8][3];
+            if (il) {
+                const float4 *q = (const float4 *)tab + base;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const float4 n = __ldg(q + off[j]);
+                    v[j][0] = n.x;
+                    v[j][1] = n.y;
+                    v[j][2] = n.z;
+                }
+            } else {
+                const int64_t plane = (int64_t)nz * ny * nx;
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) v[j][c] = __ldg(tab + c * plane + base + off[j]);
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    cc.v0[e][c] = (T)v[2 * e][c];
+                    cc.dx[e][c] = (T)v[2 * e + 1][c] - (T)v[2 * e][c];
+                }
+        }
     }
 
     __device__ __forceinline__ void at(T x, T y, T z, T &bx, T &by, T &bz) const
@@ -166,6 +257,38 @@ __device__ __forceinline__ void axial_increment(const AxialStep<T> &k, const T y
     inc[5] = T(0);
 }
 
+// The four stages of one classic RK4 step of length h from state y, the field from look(x, y, z,
+// bx, by, bz): inc = h/6 (k1 + 2 k2 + 2 k3 + k4).  c = KAPPA q / P0, ip = 1 / P0.
+template <typename T, class Look>
+__device__ __forceinline__ void rk4_stages(Look look, T c, T ip, const T y[6], T h, T inc[6])
+{
+    const T hh = T(0.5) * h;
+    const T h6 = h / T(6);
+    T k[4][6];
+    T t[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) t[i] = y[i];
+#pragma unroll
+    for (int st = 0; st < 4; ++st) {
+        T bx, by, bz;
+        look(t[0], t[1], t[2], bx, by, bz);
+        k[st][0] = t[3] * ip;
+        k[st][1] = t[4] * ip;
+        k[st][2] = t[5] * ip;
+        k[st][3] = c * (t[4] * bz - t[5] * by);
+        k[st][4] = c * (t[5] * bx - t[3] * bz);
+        k[st][5] = c * (t[3] * by - t[4] * bx);
+        if (st < 3) {
+            const T a = st < 2 ? hh : h;
+#pragma unroll
+            for (int i = 0; i < 6; ++i) t[i] = y[i] + a * k[st][i];
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+        inc[i] = h6 * ((k[0][i] + T(2) * (k[1][i] + k[2][i])) + k[3][i]);
+}
+
 // Increment of one classic RK4 step of length h from state y: inc = h/6 (k1 + 2 k2 + 2 k3 + k4).
 // c = KAPPA q / P0, ip = 1 / P0.
 template <typename T, class F>
@@ -174,32 +297,19 @@ __device__ __forceinline__ void rk4_increment(const F &f, T c, T ip, const T y[6
     if constexpr (F::kAxial) {
         axial_increment<T>(axial_step_coeffs<T>(c * f.bz, ip, y[5], h), y, inc);
     } else {
-        const T hh = T(0.5) * h;
-        const T h6 = h / T(6);
-        T k[4][6];
-        T t[6];
-#pragma unroll
-        for (int i = 0; i < 6; ++i) t[i] = y[i];
-#pragma unroll
-        for (int st = 0; st < 4; ++st) {
-            T bx, by, bz;
-            f.at(t[0], t[1], t[2], bx, by, bz);
-            k[st][0] = t[3] * ip;
-            k[st][1] = t[4] * ip;
-            k[st][2] = t[5] * ip;
-            k[st][3] = c * (t[4] * bz - t[5] * by);
-            k[st][4] = c * (t[5] * bx - t[3] * bz);
-            k[st][5] = c * (t[3] * by - t[4] * bx);
-            if (st < 3) {
-                const T a = st < 2 ? hh : h;
-#pragma unroll
-                for (int i = 0; i < 6; ++i) t[i] = y[i] + a * k[st][i];
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < 6; ++i)
-            inc[i] = h6 * ((k[0][i] + T(2) * (k[1][i] + k[2][i])) + k[3][i]);
+        rk4_stages<T>([&](T x0, T x1, T x2, T &bx, T &by, T &bz) { f.at(x0, x1, x2, bx, by, bz); },
+                      c, ip, y, h, inc);
     }
+}
+
+// The same step with the lane's field cell carried from lookup to lookup (F::at_cell): for the
+// recording, whose consecutive lookups mostly fall in the cell of the one before.
+template <typename T, class F>
+__device__ __forceinline__ void rk4_increment_cell(const F &f, typename F::Cell &cell, T c, T ip,
+                                                   const T y[6], T h, T inc[6])
+{
+    rk4_stages<T>([&](T x0, T x1, T x2, T &bx, T &by, T &bz) { f.at_cell(cell, x0, x1, x2, bx, by, bz); },
+                  c, ip, y, h, inc);
 }
 
 template <typename T, class F>

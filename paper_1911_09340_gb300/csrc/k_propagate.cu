@@ -244,7 +244,8 @@ __device__ __forceinline__ AxialStep<float> axial_interval_ff(float px, float py
 // number of steps at compile time; 0 takes a.stride.
 template <typename T, class F, int STRIDE>
 __device__ __forceinline__ void advance_interval(const F &f, const PropArgs &a, const AxialStep<T> &ks,
-                                                 T c, T ip, T h, T y[6], float lo[6])
+                                                 T c, T ip, T h, T y[6], float lo[6],
+                                                 typename F::Cell &cell)
 {
     const int stride = STRIDE > 0 ? STRIDE : a.stride;
     if constexpr (sizeof(T) == 4 && F::kAxial) {
@@ -262,14 +263,14 @@ __device__ __forceinline__ void advance_interval(const F &f, const PropArgs &a, 
     } else if constexpr (sizeof(T) == 4) {
         for (int st = 0; st < stride; ++st) {
             float inc[6];
-            rk4_increment<float, F>(f, c, ip, y, h, inc);
+            rk4_increment_cell<float, F>(f, cell, c, ip, y, h, inc);
 #pragma unroll
             for (int i = 0; i < 6; ++i) two_sum_add(y[i], lo[i], inc[i]);
         }
     } else {
         for (int st = 0; st < stride; ++st) {
             T inc[6];
-            rk4_increment<T, F>(f, c, ip, y, h, inc);
+            rk4_increment_cell<T, F>(f, cell, c, ip, y, h, inc);
 #pragma unroll
             for (int i = 0; i < 6; ++i) y[i] += inc[i];
         }
@@ -339,6 +340,7 @@ __global__ void __launch_bounds__(128) propagate_kernel(F f, PropArgs a, BatchLa
         ks.dz = (T)m[4];
     }
     float lo[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // FP32: low words of the compensated state
+    typename F::Cell cell;                          // tabulated field: the cell of the last lookup
 
     // Bounding spheres of the segments whose centre is the state just recorded (see device.cuh);
     // lanes that stopped earlier contribute their last recorded state if the segment holds it.
@@ -363,7 +365,7 @@ __global__ void __launch_bounds__(128) propagate_kernel(F f, PropArgs a, BatchLa
     bool active = valid && !outside_region<T>(y[0], y[1], y[2], zmin, zmax, rmax2);
     for (int r = 0; r < n_rec; ++r) {
         if (r > 0 && active) {
-            advance_interval<T, F, STRIDE>(f, a, ks, c, ip, h, y, lo);
+            advance_interval<T, F, STRIDE>(f, a, ks, c, ip, h, y, lo, cell);
             const int64_t o = (int64_t)r * S + s;
 #pragma unroll
             for (int cc = 0; cc < 6; ++cc) pts[cc * plane + o] = y[cc];
