@@ -13,10 +13,11 @@ round replays it after comet_scan_batch_update has packed the round's descriptor
 depend on the caps only).
 
 Size-aware rounds (``solo_min_seeds``): a partition of that many seeds or more fills the GPU by
-itself, so it runs through the single-event calls (lattice, propagate, dca, select, classify on the
-slot's resident buffers) on a second stream, while the round's smaller partitions run as one batch
-on the first stream -- the big partitions keep the single-event kernels' efficiency, the small ones
-share launches, and each fills the other's kernel tails.  Both streams join at the end of a round.
+itself, so it runs through the single-event calls (lattice, propagate, dca with the selection,
+classify on the slot's resident buffers) on one of ``solo_lanes`` lanes (each its own context,
+stream and workspace), while the round's smaller partitions run as one batch on the scanner's
+stream -- the big partitions keep the single-event kernels' efficiency, the small ones share
+launches, and each fills the others' kernel tails.  All streams join at the end of a round.
 
 The host work per round is descriptor packing; every step of the scan runs in the library's
 kernels.

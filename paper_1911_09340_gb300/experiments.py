@@ -363,8 +363,9 @@ def generate_batch_events(n: int, workers: int = 0):
 def batch_study(n_events: int = 512, stride: int = 32, lam: float = 1e-2, tune_events: int = 128,
                 dtype=torch.float32, max_total_seeds: int = 1 << 25):
     """Events/s and per-event latency of the batching workload (1-6 turns, 2^12-2^18 seeds per
-    partition by turn count, uneven hit counts): the per-event path (one partition at a time, six
-    launches each) against continuous batching (comet_scan_batch rounds replayed from a CUDA graph,
+    partition by turn count, uneven hit counts): the per-event path (one partition at a time, four
+    launches each; and with each partition's recording beside the previous partition's DCA)
+    against continuous batching (comet_scan_batch rounds replayed from a CUDA graph,
     configured by the autotuner on the first ``tune_events`` events)."""
     from . import batch as BT
     events = generate_batch_events(n_events)
@@ -393,7 +394,33 @@ def batch_study(n_events: int = 512, stride: int = 32, lam: float = 1e-2, tune_e
     torch.cuda.synchronize()
     seq_ms = t_all0.elapsed_time(t_all1)
     seq_lat = np.array([a.elapsed_time(b) for a, b in lat])
-    del ws, devs
+    del ws
+    torch.cuda.empty_cache()
+    # per-event path with each partition's recording beside the previous partition's DCA
+    # (PipelinedScanner, the benchmark's driver): the same kernels, events back to back
+    ps = scan.PipelinedScanner(ctx, field, S, n_rec, max(ev.n_hits for ev in events), dtype)
+    params = [scan.event_params(ev, dtype, stride, lam) for ev in events]
+    for i in range(8):
+        devs[i].mask.zero_()
+        ps.event(events[i], devs[i], params[i])
+    torch.cuda.synchronize()
+    lat = []
+    t_all0 = torch.cuda.Event(enable_timing=True)
+    t_all0.record()
+    for ev, dev, prm in zip(events, devs, params):
+        dev.mask.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        ps.event(ev, dev, prm)
+        b.record()
+        lat.append((a, b))
+    t_all1 = torch.cuda.Event(enable_timing=True)
+    t_all1.record()
+    torch.cuda.synchronize()
+    pipe_ms = t_all0.elapsed_time(t_all1)
+    pipe_lat = np.array([a.elapsed_time(b) for a, b in lat])
+    ps.close()
+    del ps, devs
     torch.cuda.empty_cache()
     # batched path
     sc = BT.BatchScanner(ctx, dtype, stride, lam, slots=256, max_total_seeds=max_total_seeds,
@@ -433,6 +460,7 @@ def batch_study(n_events: int = 512, stride: int = 32, lam: float = 1e-2, tune_e
              "turns_1_to_6": turns.tolist(), "wires_min_median_max": [int(wires.min()), int(np.median(wires)),
                                                                       int(wires.max())],
              "per_event_path": {"events_per_s": n_events / (seq_ms * 1e-3), "latency_ms": pct(seq_lat)},
+             "per_event_pipelined": {"events_per_s": n_events / (pipe_ms * 1e-3), "latency_ms": pct(pipe_lat)},
              "batched": {"events_per_s": n_events / (r["gpu_ms"] * 1e-3), "latency_ms": pct(r["latency_ms"]),
                          "rounds": r["rounds"], "host_wall_ms": r["wall_ms"], "gpu_ms": r["gpu_ms"],
                          "config": best},
