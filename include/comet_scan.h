@@ -143,6 +143,14 @@ typedef struct {
  *   work split and a summation order (the sum within each chunk, then over chunks), so FP32 RSS
  *   values change in their last bits with it; the batched and single-event launches of one
  *   context use the same chunks.
+ * comet_ctx_set_record_blocks: 1 (the default) lets comet_scan_propagate record FP64 tracks in a
+ *   uniform axial field with fewer than four 32-seed groups per SM one super-segment per warp, each
+ *   started from the composed interval map of Algorithm 1's fixed RK4 step (the track recording
+ *   otherwise runs one warp per 32 seeds from the first state to the last, and a few seeds leave
+ *   most of the part idle); 0 always takes the one-warp-per-32-seeds recording.  The states agree
+ *   to rounding (about 1e-13 m over 2,000 steps), not bit for bit; comet_scan_batch always records
+ *   one warp per 32 seeds, so a context whose single-event results must equal its batched ones bit
+ *   for bit sets 0.  Host-side setting; takes effect for calls enqueued after it.
  * comet_kernel_arch: writes to *sm_version (host pointer) the SM version the library's device code
  *   was compiled for, as major * 10 + minor (103 for sm_103a), read from a kernel's attributes on
  *   the current device.
@@ -153,6 +161,7 @@ comet_status comet_ctx_status(comet_ctx *ctx, int32_t *flags);
 comet_status comet_ctx_set_copy_wait(comet_ctx *ctx, int64_t ns);
 comet_status comet_ctx_set_dca_ctas_per_sm(comet_ctx *ctx, int32_t n);
 comet_status comet_ctx_set_dca_chunk_wires(comet_ctx *ctx, int32_t wires);
+comet_status comet_ctx_set_record_blocks(comet_ctx *ctx, int32_t on);
 comet_status comet_kernel_arch(int32_t *sm_version);
 const char *comet_last_error(void);
 

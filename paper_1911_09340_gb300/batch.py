@@ -198,6 +198,7 @@ class BatchScanner:
         while len(self._lanes) <= k:
             c = self.ctx if not self._lanes else B.Context(self.ctx.device)
             c.set_dca_chunk_wires(self.chunk_wires)
+            c.set_record_blocks(self.ctx.record_blocks)
             self._lanes.append((c, torch.cuda.Stream(),
                                 scan.Workspace(self.max_seeds, self.n_rec_max, 1, self.dtype)))
         return self._lanes[k]

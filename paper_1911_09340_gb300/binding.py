@@ -76,6 +76,7 @@ SIGNATURES = {
     "comet_ctx_set_copy_wait": [_vp, _i64],
     "comet_ctx_set_dca_ctas_per_sm": [_vp, _i32],
     "comet_ctx_set_dca_chunk_wires": [_vp, _i32],
+    "comet_ctx_set_record_blocks": [_vp, _i32],
     "comet_kernel_arch": [C.POINTER(C.c_int32)],
     "comet_last_error": [],
     "comet_scan_lattice": [_vp, C.c_int, C.POINTER(_Lattice), _vp, _vp, _i64, _vp],
@@ -220,6 +221,7 @@ class Context:
         _check(lib().comet_ctx_create(int(device), C.byref(h)))
         self.handle = h
         self.device = device
+        self.record_blocks = 1
 
     def status(self) -> int:
         v = C.c_int32(0)
@@ -233,6 +235,12 @@ class Context:
     def set_dca_chunk_wires(self, wires: int):
         """Wires per chunk of the DCA's per-seed sums (0: automatic)."""
         _check(lib().comet_ctx_set_dca_chunk_wires(self.handle, int(wires)))
+
+    def set_record_blocks(self, on: int):
+        """1 (default): FP64 axial-field recording of few seeds one super-segment per warp; 0: one
+        warp per 32 seeds always (bit-identical to the batched recording)."""
+        _check(lib().comet_ctx_set_record_blocks(self.handle, int(on)))
+        self.record_blocks = int(on)
 
     def set_dca_ctas_per_sm(self, n: int):
         """Cap of the persistent DCA launch's resident CTAs per SM (0: as many as fit)."""

@@ -380,6 +380,14 @@ comet_status comet_ctx_set_dca_chunk_wires(comet_ctx *ctx, int32_t wires)
     return COMET_OK;
 }
 
+comet_status comet_ctx_set_record_blocks(comet_ctx *ctx, int32_t on)
+{
+    if (!ctx) return fail(COMET_ERR_INVALID_ARG, "ctx is NULL");
+    if (on != 0 && on != 1) return fail(COMET_ERR_INVALID_ARG, "record_blocks must be 0 or 1");
+    ctx->record_blocks = on;
+    return COMET_OK;
+}
+
 comet_status comet_kernel_arch(int32_t *sm_version)
 {
     if (!sm_version) return fail(COMET_ERR_INVALID_ARG, "sm_version is NULL");
@@ -630,7 +638,7 @@ comet_status comet_scan_propagate(comet_ctx *ctx, comet_dtype dtype, const comet
     const SearchGeometry sg = search_geometry(dtype, params);
     comet::PropArgs a;
     fill_prop(dtype, params, sg, seeds, charge, S, points, n_valid, bounds, &a);
-    cudaError_t e = comet::launch_propagate(dtype, *field, a, (cudaStream_t)stream);
+    cudaError_t e = comet::launch_propagate(dtype, *field, a, ctx->record_blocks != 0, (cudaStream_t)stream);
     return e == cudaSuccess ? COMET_OK : cuda_fail(e, "propagate launch");
 }
 

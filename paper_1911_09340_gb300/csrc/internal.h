@@ -263,7 +263,8 @@ int select_chunk();   // RSS entries per select pass-1 block
 
 cudaError_t launch_gn_step(double *theta, int64_t S, const double *jtj, const double *jtr, double mu,
                            cudaStream_t st);
-cudaError_t launch_propagate(comet_dtype dt, const comet_field &f, const PropArgs &a, cudaStream_t st);
+cudaError_t launch_propagate(comet_dtype dt, const comet_field &f, const PropArgs &a, bool blocks,
+                             cudaStream_t st);
 cudaError_t launch_dca(comet_dtype dt, const comet_field &f, const DcaArgs &a, cudaStream_t st);
 void dca_segments(int n_rec, int *G0, int *G1);   // segment sizes of the closest-state search
 cudaError_t launch_select(comet_dtype dt, const SelArgs &a, cudaStream_t st);

@@ -409,6 +409,116 @@ __global__ void __launch_bounds__(128) propagate_kernel(F f, PropArgs a, BatchLa
     if (valid) a.n_valid[s] = n;
 }
 
+// Few seeds, uniform axial field, FP64: one warp per (32-seed group, super-segment).  A track's
+// recorded states are the powers of one interval map (see axial_interval), so each super-segment
+// [r0, r1) starts from the seed mapped over r0 intervals at once and then steps interval by
+// interval as propagate_kernel does: with 4,096 seeds the sequential kernel has one warp per SM,
+// one of its four schedulers issuing FP64 work; here each SM gets up to G0-fold more warps.  The
+// states are those of the sequential recording up to rounding (the map of r0 intervals against r0
+// applications of the one-interval map).  n_valid: the caller's array is set to a large value
+// first (a byte memset), then each block lowers it to its first state outside the target region
+// plus one, and the last block to n_rec.  Spheres: a lane whose track left the region in an earlier
+// block still contributes its (extrapolated) states, which only makes the sphere larger; within
+// the block a lane stops contributing to segments after its exit, as in propagate_kernel.
+template <int STRIDE>
+__global__ void __launch_bounds__(32) propagate_blocks_kernel(FieldAxial<double> f, PropArgs a)
+{
+    const int n_rec = a.n_rec, G0 = a.G0, G1 = a.G1;
+    const int n0 = (n_rec + G0 - 1) / G0;
+    const int64_t g = blockIdx.x / n0;
+    const int j = (int)(blockIdx.x % n0);
+    const int lane = threadIdx.x;
+    const int64_t S = a.S;
+    const int64_t s = g * 32 + lane;
+    const bool valid = s < S;
+    const double *__restrict__ seeds = (const double *)a.seeds;
+    double *__restrict__ pts = (double *)a.points;
+    const int64_t plane = (int64_t)n_rec * S;
+
+    double y[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    int q = 0;
+    if (valid) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) y[c] = seeds[c * S + s];
+        q = a.charge[s];
+    }
+    // the one-step coefficients and the interval map exactly as propagate_kernel forms them
+    const double pd = valid ? sqrt((double)y[3] * y[3] + (double)y[4] * y[4] + (double)y[5] * y[5]) : 1.0;
+    const double ipd = 1.0 / pd;
+    const double w = kKappa * q * (double)f.bz * ipd;
+    const double t = a.h * w, t2 = t * t, hp = a.h * ipd;
+    const double s_am1 = t2 * (-0.5 + t2 / 24.0), s_b = t * (1.0 - t2 / 6.0), s_c = hp * (1.0 - t2 / 6.0),
+                 s_d = hp * t * (0.5 - t2 / 24.0), s_dz = hp * (double)y[5];
+    const int stride = STRIDE > 0 ? STRIDE : a.stride;
+    double m[5];
+    axial_interval(s_am1, s_b, s_c, s_d, s_dz, stride, m);
+    const AxialStep<double> ks{m[0], m[1], m[2], m[3], m[4]};
+    const int r0 = j * G0, r1 = min(r0 + G0, n_rec);
+    if (r0 > 0) {
+        // the state after r0 intervals: the map of r0 * stride steps applied once
+        axial_interval(s_am1, s_b, s_c, s_d, s_dz, r0 * stride, m);
+        const AxialStep<double> k0{m[0], m[1], m[2], m[3], m[4]};
+        double inc[6];
+        axial_increment<double>(k0, y, inc);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) y[i] += inc[i];
+    }
+
+    const double zmin = a.zmin, zmax = a.zmax, rmax2 = a.rmax * a.rmax;
+    const bool wb = a.bounds != nullptr;
+    float4 *tab = wb ? (float4 *)a.bounds + g * kBoundsPerGroup : nullptr;
+    const int N1 = (r1 - r0 + G1 - 1) / G1;   // level-1 segments of this super-segment
+    if (wb) {
+        // entries no segment of this block fills; block 0 also clears the unused super-segments
+        for (int mm = N1 + lane; mm < kN1Max; mm += 32)
+            tab[kN0Max + j * kN1Max + mm] = make_float4(0.f, 0.f, 0.f, -1.f);
+        if (j == 0)
+            for (int i = lane; i < (kN0Max - n0) * (kN1Max + 1); i += 32) {
+                const int jj = n0 + i / (kN1Max + 1), mm = i % (kN1Max + 1);
+                if (mm == kN1Max)
+                    tab[jj] = make_float4(0.f, 0.f, 0.f, -1.f);
+                else
+                    tab[kN0Max + jj * kN1Max + mm] = make_float4(0.f, 0.f, 0.f, -1.f);
+            }
+    }
+    int exit_k = 0x7fffffff;                  // this lane's first state outside the region
+    int m1 = 0, st1 = r0;
+    int c1 = segment_centre(r0, G1, r1);
+    const int c0 = segment_centre(r0, G0, r1);
+    for (int r = r0; r < r1; ++r) {
+        if (r > r0) {
+            double inc[6];
+            axial_increment<double>(ks, y, inc);
+#pragma unroll
+            for (int i = 0; i < 6; ++i) y[i] += inc[i];
+        }
+        if (valid) {
+            const int64_t o = (int64_t)r * S + s;
+#pragma unroll
+            for (int cc = 0; cc < 6; ++cc) pts[cc * plane + o] = y[cc];
+            if (exit_k == 0x7fffffff && outside_region<double>(y[0], y[1], y[2], zmin, zmax, rmax2))
+                exit_k = r;
+        }
+        if (wb) {
+            if (r == c1) {
+                const float4 sp = warp_sphere<double>(valid && exit_k >= st1, y[0], y[1], y[2], a.R1);
+                if (lane == 0) tab[kN0Max + j * kN1Max + m1] = sp;
+                ++m1;
+                st1 += G1;
+                c1 = st1 < r1 ? segment_centre(st1, G1, r1) : 0x7fffffff;
+            }
+            if (r == c0) {
+                const float4 sp = warp_sphere<double>(valid, y[0], y[1], y[2], a.R0);
+                if (lane == 0) tab[j] = sp;
+            }
+        }
+    }
+    if (valid) {
+        if (exit_k != 0x7fffffff) atomicMin(a.n_valid + s, exit_k + 1);
+        if (j == n0 - 1) atomicMin(a.n_valid + s, n_rec);
+    }
+}
+
 static cudaError_t lattice_launch(comet_dtype dt, const LatArgs &a, const LatTable &t,
                                   const double *refs, const int32_t *n_refs, int K, void *seeds,
                                   int64_t S, cudaStream_t st)
@@ -485,8 +595,28 @@ static void prop_dispatch(const comet_field &f, const PropArgs &a, int stride, u
     }
 }
 
-cudaError_t launch_propagate(comet_dtype dt, const comet_field &f, const PropArgs &a, cudaStream_t st)
+cudaError_t launch_propagate(comet_dtype dt, const comet_field &f, const PropArgs &a, bool blocks,
+                             cudaStream_t st)
 {
+    // FP64 in a uniform axial field with fewer than four 32-seed groups per SM (when the context
+    // allows it): one warp per (group, super-segment), each started from the composed interval map
+    const int64_t groups = (a.S + 31) / 32;
+    const int n0 = a.G0 > 0 ? (a.n_rec + a.G0 - 1) / a.G0 : 1;
+    if (blocks && dt == COMET_F64 && field_kind(f) == FieldKind::Axial && n0 > 1 &&
+        groups < (int64_t)device_sm_count() * 4) {
+        cudaError_t e = cudaMemsetAsync(a.n_valid, 0x7f, (size_t)a.S * sizeof(int32_t), st);
+        if (e != cudaSuccess) return e;
+        const unsigned nb = (unsigned)(groups * n0);
+        const FieldAxial<double> fa{f.b[2]};
+        switch (a.stride) {
+        case 1: propagate_blocks_kernel<1><<<nb, 32, 0, st>>>(fa, a); break;
+        case 2: propagate_blocks_kernel<2><<<nb, 32, 0, st>>>(fa, a); break;
+        case 4: propagate_blocks_kernel<4><<<nb, 32, 0, st>>>(fa, a); break;
+        case 8: propagate_blocks_kernel<8><<<nb, 32, 0, st>>>(fa, a); break;
+        default: propagate_blocks_kernel<0><<<nb, 32, 0, st>>>(fa, a); break;
+        }
+        return cudaGetLastError();
+    }
     // one seed per thread; with fewer seeds than 128 per SM, one warp per CTA, so that the seeds
     // spread over as many SMs as possible (the search bounds are per warp either way)
     const int nt = a.S < (int64_t)device_sm_count() * 128 ? 32 : 128;

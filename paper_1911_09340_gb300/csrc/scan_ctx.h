@@ -85,6 +85,7 @@ struct comet_ctx {
     uint64_t copy_wait_ns = 2000000000ull;   // limit of a kernel's wait for a staging bulk copy
     int dca_ctas_per_sm = 0;                 // cap of the persistent DCA launch (0: as many as fit)
     int dca_chunk_wires = 0;                 // wires per chunk of the DCA's sums (0: automatic)
+    int record_blocks = 1;                   // FP64 axial recording of few seeds by super-segment
     void *dca_part = nullptr;    // comet_scan_dca's per-chunk partial sums
     size_t dca_part_bytes = 0;
     uint32_t *dca_arrive = nullptr;   // per-group arrival counters (kept zero between launches)

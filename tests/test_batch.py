@@ -10,6 +10,15 @@ from paper_1911_09340_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 
+@pytest.fixture(autouse=True)
+def _one_warp_per_32_seeds(ctx):
+    """The batched launches record one warp per 32 seeds; the per-event reference records the same
+    way here (comet_ctx_set_record_blocks(0)), so that the two agree bit for bit in FP64 too."""
+    ctx.set_record_blocks(0)
+    yield
+    ctx.set_record_blocks(1)
+
+
 def _events(n):
     return [synth.batch_event(i, counts_scale=3) for i in range(n)]
 

@@ -253,6 +253,9 @@ def test_context_validation():
     _expect_invalid(L.comet_ctx_set_dca_chunk_wires(None, 8))
     for w in (-1, 1, 3, 1025):
         _expect_invalid(L.comet_ctx_set_dca_chunk_wires(c.handle, w))
+    _expect_invalid(L.comet_ctx_set_record_blocks(None, 1))
+    for v in (-1, 2):
+        _expect_invalid(L.comet_ctx_set_record_blocks(c.handle, v))
     _expect_invalid(L.comet_ctx_status(c.handle, None))
     _expect_invalid(L.comet_kernel_arch(None))
     c.close()

@@ -58,6 +58,42 @@ def test_fp64_points_match_oracle_single_event(ctx):
         assert np.abs(got[s, :n, 3:] - ref[s, :n, 3:]).max() <= 1e-9 * 105
 
 
+@pytest.mark.parametrize("stride", [1, 3, 16])
+def test_fp64_block_recording_equals_sequential(ctx, stride):
+    """FP64 in an axial field with fewer than four 32-seed groups per SM records each super-segment
+    in its own warp, started from the composed interval map (comet_ctx_set_record_blocks(1), the
+    default); with the setting at 0 the same seeds take the one-warp-per-32-seeds kernel.  Both
+    record the same states (to rounding: the map of r0 intervals against r0 applications of one)
+    and the same counts, both match the oracle, and both sets of spheres contain every recorded
+    state (the containment test covers the bounds with the default)."""
+    ev, seeds = _cfg1_seeds(8)
+    seeds = seeds[:200]
+    op, bp = both_params(n_steps=ev.n_steps[0] // stride * stride, stride=stride, rmax=0.67)
+    field = B.DeviceField.from_synth(synth.uniform_field(1.0))
+    _, _, p_blk, nv_blk = gpu_propagate(ctx, field, bp, seeds, -1, torch.float64)
+    ctx.set_record_blocks(0)
+    try:
+        _, _, p_seq, nv_seq = gpu_propagate(ctx, field, bp, seeds, -1, torch.float64)
+    finally:
+        ctx.set_record_blocks(1)
+    nb, ns = nv_blk.cpu().numpy(), nv_seq.cpu().numpy()
+    assert np.array_equal(nb, ns)
+    assert (nb < bp.n_rec).any() and (nb == bp.n_rec).any()   # some tracks leave through rmax
+    gb, gs = to_aos_points(p_blk), to_aos_points(p_seq)
+    ref, rnv = O.propagate(synth.uniform_field(1.0), op, seeds, -1)
+    assert np.array_equal(nb, rnv)
+    worst = 0.0
+    for s in range(seeds.shape[0]):
+        n = nb[s]
+        worst = max(worst, np.abs(gb[s, :n, :3] - gs[s, :n, :3]).max())
+        assert np.abs(gb[s, :n, 3:] - gs[s, :n, 3:]).max() <= 1e-11 * 105
+        assert np.abs(gb[s, :n, :3] - ref[s, :n, :3]).max() <= 1e-9
+        assert np.abs(gs[s, :n, :3] - ref[s, :n, :3]).max() <= 1e-9
+    # the two recordings differ in rounding (the block starts are formed differently): the block
+    # path ran, and the batched path's bit-for-bit tests need the setting
+    assert 0.0 < worst <= 1e-11, worst
+
+
 @pytest.mark.parametrize("stride", [1, 16, 24])
 def test_fp32_points_within_1um_over_three_turns(ctx, stride):
     """The compensated FP32 state (and, in an axial field, the per-seed interval map formed in
