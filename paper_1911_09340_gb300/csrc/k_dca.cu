@@ -40,6 +40,11 @@
 #ifndef COMET_DCA_MINB
 #define COMET_DCA_MINB 7
 #endif
+// FP64: bound by the FP64 pipe rather than by resident warps; fewer CTAs per SM buy registers (at
+// 72 the FP64 kernels spill ~300 B per thread)
+#ifndef COMET_DCA_MINB_F64
+#define COMET_DCA_MINB_F64 4
+#endif
 #ifndef COMET_DCA_U2
 #define COMET_DCA_U2 2
 #endif
@@ -716,7 +721,7 @@ __host__ __device__ inline PLayout p_layout(int W, int es, int nsph)
 constexpr int kPersistMaxW = 1024;
 
 template <typename T, class F>
-__global__ void __launch_bounds__(kThreads, COMET_DCA_MINB) dca_persistent_kernel(F f, DcaArgs a)
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 8 ? COMET_DCA_MINB_F64 : COMET_DCA_MINB) dca_persistent_kernel(F f, DcaArgs a)
 {
     const bool sph_smem = a.bounds == nullptr && !a.exact_all;
     const PLayout L = p_layout(a.W, (int)sizeof(T), p_sph_entries(a));
@@ -887,7 +892,7 @@ __global__ void __launch_bounds__(kThreads, COMET_DCA_MINB) dca_persistent_kerne
 // ------------------------------------------------------------------------------------------------
 
 template <typename T, class F>
-__global__ void __launch_bounds__(kThreads, COMET_DCA_MINB) dca_tiled_kernel(F f, DcaArgs a)
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 8 ? COMET_DCA_MINB_F64 : COMET_DCA_MINB) dca_tiled_kernel(F f, DcaArgs a)
 {
     using L = Smem<T>;
     extern __shared__ __align__(128) unsigned char sm[];
