@@ -1,10 +1,14 @@
 // Hit classification of the selected seed (Sec. 2.1) and the hit mask of the next turn partition
 // (Sec. 3.1: hits classified earlier are excluded from later seed scans).
 //
-// One warp per wire: the 32 lanes split the selected seed's recorded states for an exhaustive
-// closest-state search, reduce the lexicographic (distance, index) minimum with warp shuffles, and
-// lane 0 refines the DCA on the virtual plane exactly as comet_scan_dca does (same device functions,
-// same inputs, hence the same D), then classifies the closest unmasked hit if |D - r| < lambda.
+// WPW warps per wire: their lanes split the selected seed's recorded states for an exhaustive
+// closest-state search and reduce the lexicographic (distance, index) minimum with warp shuffles
+// (then, with WPW > 1, across the warps in shared memory); one lane refines the DCA on the virtual
+// plane exactly as comet_scan_dca does (same device functions, same inputs, hence the same D), then
+// classifies the closest unmasked hit if |D - r| < lambda.  The minimum does not depend on how the
+// states are split, so every WPW gives the same results.  The batched launch packs 8 wires into a
+// block (WPW 1); a single-event launch has a few hundred wires at most and gives each its own block
+// of 4 warps, so that a partition with few wires still spreads over the SMs.
 #include <float.h>
 
 #include "device.cuh"
@@ -14,7 +18,7 @@ namespace comet {
 
 // BATCH: one launch for a batch of events; block b belongs to the event that batch_find gives
 // (8 wires per block).
-template <typename T, class F, bool BATCH>
+template <typename T, class F, bool BATCH, int WPW>
 __global__ void __launch_bounds__(256) classify_kernel(F f, ClsArgs a, BatchLaunch L)
 {
     int64_t bx = blockIdx.x;
@@ -26,13 +30,16 @@ __global__ void __launch_bounds__(256) classify_kernel(F f, ClsArgs a, BatchLaun
         bx = lb;
     }
     const int lane = threadIdx.x & 31;
-    const int i = (int)((bx * blockDim.x + threadIdx.x) >> 5);
-    if (i >= a.W) return;   // whole warps
+    const int warp = WPW > 1 ? (int)(threadIdx.x >> 5) : 0;
+    const int i = WPW > 1 ? (int)bx : (int)((bx * blockDim.x + threadIdx.x) >> 5);
+    if (i >= a.W) return;   // whole warps (whole blocks when WPW > 1)
     const int hb = a.offs[i], he = a.offs[i + 1];
     const int64_t s = *a.seed_index;
-    if (s < 0 || s >= a.S) {
-        for (int j = hb + lane; j < he; j += 32) a.hit_class[j] = 0;
-        if (lane == 0 && a.status) atomicOr(a.status, 2);
+    if (s < 0 || s >= a.S) {   // the same for every thread of the block
+        if (warp == 0) {
+            for (int j = hb + lane; j < he; j += 32) a.hit_class[j] = 0;
+            if (lane == 0 && a.status) atomicOr(a.status, 2);
+        }
         return;
     }
     const int64_t S = a.S;
@@ -48,7 +55,7 @@ __global__ void __launch_bounds__(256) classify_kernel(F f, ClsArgs a, BatchLaun
     [[maybe_unused]] const WireFrame<T> fr = wire_frame<T>(ax, ay, az, ux, uy, uz);
     T bd = T(INFINITY);
     int bk = 0x7fffffff;
-    for (int k = lane; k < nv; k += 32) {
+    for (int k = warp * 32 + lane; k < nv; k += 32 * WPW) {
         const int64_t o = (int64_t)k * S + s;
 #if COMET_SEARCH_FRAME
         lex_min<T>(bd, bk,
@@ -66,7 +73,19 @@ __global__ void __launch_bounds__(256) classify_kernel(F f, ClsArgs a, BatchLaun
         const int ok = __shfl_xor_sync(0xffffffffu, bk, off);
         lex_min<T>(bd, bk, od, ok);
     }
-    if (lane != 0) return;
+    if constexpr (WPW > 1) {
+        __shared__ T s_bd[WPW];
+        __shared__ int s_bk[WPW];
+        if (lane == 0) {
+            s_bd[warp] = bd;
+            s_bk[warp] = bk;
+        }
+        __syncthreads();
+        if (threadIdx.x != 0) return;
+        for (int w = 1; w < WPW; ++w) lex_min<T>(bd, bk, s_bd[w], s_bk[w]);
+    } else {
+        if (lane != 0) return;
+    }
 
     T c, ip;
     seed_kinematics<T>(P[3 * plane + s], P[4 * plane + s], P[5 * plane + s], a.charge[s], c, ip);
@@ -97,23 +116,21 @@ __global__ void __launch_bounds__(256) classify_kernel(F f, ClsArgs a, BatchLaun
     }
 }
 
-template <typename T, bool BATCH>
+template <typename T, bool BATCH, int WPW>
 static void cls_dispatch(const comet_field &f, const ClsArgs &a, unsigned nb, const BatchLaunch &L,
                          cudaStream_t st)
 {
-    const int nt = 256;
+    const int nt = WPW > 1 ? 32 * WPW : 256;
     switch (field_kind(f)) {
     case FieldKind::Axial:
-        classify_kernel<T, FieldAxial<T>, BATCH><<<nb, nt, 0, st>>>(FieldAxial<T>{(T)f.b[2]}, a, L);
+        classify_kernel<T, FieldAxial<T>, BATCH, WPW><<<nb, nt, 0, st>>>(FieldAxial<T>{(T)f.b[2]}, a, L);
         break;
     case FieldKind::Uniform:
-        classify_kernel<T, FieldUniform<T>, BATCH><<<nb, nt, 0, st>>>(
+        classify_kernel<T, FieldUniform<T>, BATCH, WPW><<<nb, nt, 0, st>>>(
             FieldUniform<T>{(T)f.b[0], (T)f.b[1], (T)f.b[2]}, a, L);
         break;
     case FieldKind::Table:
-        classify_kernel<T, FieldTable<T>, BATCH><<<nb, nt, 0, st>>>(
-            make_table<T>(f),
-            a, L);
+        classify_kernel<T, FieldTable<T>, BATCH, WPW><<<nb, nt, 0, st>>>(make_table<T>(f), a, L);
         break;
     }
 }
@@ -121,11 +138,11 @@ static void cls_dispatch(const comet_field &f, const ClsArgs &a, unsigned nb, co
 cudaError_t launch_classify(comet_dtype dt, const comet_field &f, const ClsArgs &a, cudaStream_t st)
 {
     if (a.W == 0) return cudaSuccess;
-    const unsigned nb = (unsigned)(((int64_t)a.W * 32 + 255) / 256);
+    const unsigned nb = (unsigned)a.W;   // one block of 4 warps per wire
     if (dt == COMET_F32)
-        cls_dispatch<float, false>(f, a, nb, BatchLaunch{}, st);
+        cls_dispatch<float, false, 4>(f, a, nb, BatchLaunch{}, st);
     else
-        cls_dispatch<double, false>(f, a, nb, BatchLaunch{}, st);
+        cls_dispatch<double, false, 4>(f, a, nb, BatchLaunch{}, st);
     return cudaGetLastError();
 }
 
@@ -134,9 +151,9 @@ cudaError_t launch_classify_batch(comet_dtype dt, const comet_field &f, const Ba
 {
     if (L.cls_blocks == 0) return cudaSuccess;
     if (dt == COMET_F32)
-        cls_dispatch<float, true>(f, ClsArgs{}, L.cls_blocks, L, st);
+        cls_dispatch<float, true, 1>(f, ClsArgs{}, L.cls_blocks, L, st);
     else
-        cls_dispatch<double, true>(f, ClsArgs{}, L.cls_blocks, L, st);
+        cls_dispatch<double, true, 1>(f, ClsArgs{}, L.cls_blocks, L, st);
     return cudaGetLastError();
 }
 
