@@ -37,6 +37,10 @@ struct FieldAxial {
     {
         at(x, y, z, bx, by, bz_);
     }
+    __device__ __forceinline__ void at_enter(Cell &, T x, T y, T z, T &bx, T &by, T &bz_) const
+    {
+        at(x, y, z, bx, by, bz_);
+    }
 };
 
 // Uniform field of any direction.
@@ -52,6 +56,10 @@ struct FieldUniform {
     }
     struct Cell {};
     __device__ __forceinline__ void at_cell(Cell &, T x, T y, T z, T &bx, T &by, T &bz_) const
+    {
+        at(x, y, z, bx, by, bz_);
+    }
+    __device__ __forceinline__ void at_enter(Cell &, T x, T y, T z, T &bx, T &by, T &bz_) const
     {
         at(x, y, z, bx, by, bz_);
     }
@@ -108,6 +116,16 @@ struct FieldTable {
         T tx = gx - cc.fx, ty = gy - cc.fy, tz = gz - cc.fz;
         if (!(tx >= T(0) && tx < T(1) && ty >= T(0) && ty < T(1) && tz >= T(0) && tz < T(1)))
             enter(cc, gx, gy, gz, tx, ty, tz);
+        bx = lerp3(cc, 0, tx, ty, tz);
+        by = lerp3(cc, 1, tx, ty, tz);
+        bz = lerp3(cc, 2, tx, ty, tz);
+    }
+
+    // The lookup through enter() without the in-cell test (for a lookup that has probably moved).
+    __device__ __forceinline__ void at_enter(Cell &cc, T x, T y, T z, T &bx, T &by, T &bz) const
+    {
+        T tx, ty, tz;
+        enter(cc, (x - ox) * inv_sp, (y - oy) * inv_sp, (z - oz) * inv_sp, tx, ty, tz);
         bx = lerp3(cc, 0, tx, ty, tz);
         by = lerp3(cc, 1, tx, ty, tz);
         bz = lerp3(cc, 2, tx, ty, tz);
@@ -271,7 +289,7 @@ __device__ __forceinline__ void rk4_stages(Look look, T c, T ip, const T y[6], T
 #pragma unroll
     for (int st = 0; st < 4; ++st) {
         T bx, by, bz;
-        look(t[0], t[1], t[2], bx, by, bz);
+        look(st, t[0], t[1], t[2], bx, by, bz);
         k[st][0] = t[3] * ip;
         k[st][1] = t[4] * ip;
         k[st][2] = t[5] * ip;
@@ -297,19 +315,28 @@ __device__ __forceinline__ void rk4_increment(const F &f, T c, T ip, const T y[6
     if constexpr (F::kAxial) {
         axial_increment<T>(axial_step_coeffs<T>(c * f.bz, ip, y[5], h), y, inc);
     } else {
-        rk4_stages<T>([&](T x0, T x1, T x2, T &bx, T &by, T &bz) { f.at(x0, x1, x2, bx, by, bz); },
+        rk4_stages<T>([&](int, T x0, T x1, T x2, T &bx, T &by, T &bz) { f.at(x0, x1, x2, bx, by, bz); },
                       c, ip, y, h, inc);
     }
 }
 
 // The same step with the lane's field cell carried from lookup to lookup (F::at_cell): for the
-// recording, whose consecutive lookups mostly fall in the cell of the one before.
+// recording, whose consecutive lookups mostly fall in the cell of the one before.  Stages 1 and 3
+// lie microns from the lookup before them and test the cached cell; stages 2 and 4 move half a
+// step, so some lane of nearly every warp enters a new cell there, and they enter it without the
+// test (F::at_enter: the same cell, fractions and values).
 template <typename T, class F>
 __device__ __forceinline__ void rk4_increment_cell(const F &f, typename F::Cell &cell, T c, T ip,
                                                    const T y[6], T h, T inc[6])
 {
-    rk4_stages<T>([&](T x0, T x1, T x2, T &bx, T &by, T &bz) { f.at_cell(cell, x0, x1, x2, bx, by, bz); },
-                  c, ip, y, h, inc);
+    rk4_stages<T>(
+        [&](int st, T x0, T x1, T x2, T &bx, T &by, T &bz) {
+            if (st & 1)
+                f.at_enter(cell, x0, x1, x2, bx, by, bz);
+            else
+                f.at_cell(cell, x0, x1, x2, bx, by, bz);
+        },
+        c, ip, y, h, inc);
 }
 
 template <typename T, class F>

@@ -45,6 +45,11 @@
 #ifndef COMET_DCA_MINB_F64
 #define COMET_DCA_MINB_F64 4
 #endif
+// FP32 in a non-axial field (tabulated or general uniform): RK4 stages in the refinement; at 72
+// registers the tabulated-field kernel spilled ~200 B per thread
+#ifndef COMET_DCA_MINB_FIELD
+#define COMET_DCA_MINB_FIELD 5
+#endif
 #ifndef COMET_DCA_U2
 #define COMET_DCA_U2 2
 #endif
@@ -721,7 +726,7 @@ __host__ __device__ inline PLayout p_layout(int W, int es, int nsph)
 constexpr int kPersistMaxW = 1024;
 
 template <typename T, class F>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 8 ? COMET_DCA_MINB_F64 : COMET_DCA_MINB) dca_persistent_kernel(F f, DcaArgs a)
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 8 ? COMET_DCA_MINB_F64 : (F::kAxial ? COMET_DCA_MINB : COMET_DCA_MINB_FIELD)) dca_persistent_kernel(F f, DcaArgs a)
 {
     const bool sph_smem = a.bounds == nullptr && !a.exact_all;
     const PLayout L = p_layout(a.W, (int)sizeof(T), p_sph_entries(a));
@@ -892,7 +897,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 8 ? COMET_DCA_MINB_F64 
 // ------------------------------------------------------------------------------------------------
 
 template <typename T, class F>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 8 ? COMET_DCA_MINB_F64 : COMET_DCA_MINB) dca_tiled_kernel(F f, DcaArgs a)
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 8 ? COMET_DCA_MINB_F64 : (F::kAxial ? COMET_DCA_MINB : COMET_DCA_MINB_FIELD)) dca_tiled_kernel(F f, DcaArgs a)
 {
     using L = Smem<T>;
     extern __shared__ __align__(128) unsigned char sm[];
