@@ -625,7 +625,7 @@ DCA_FLOPS_PER_WIRE = 201
 DCA_FLOPS_PER_HIT = 8
 PROP_BYTES_PER_REC = 24
 TABLE_FLOPS_PER_STEP = 438
-SURVEY_INSTR_PER_EVAL = 285
+INSTR_PER_EVAL_ESTIMATE = 285
 FP64_PEAK_TFLOPS = 1.25
 
 # DRAM bytes (read + write) per launch of the two main kernels on this workload at stride 32, from a
@@ -660,15 +660,15 @@ def measured_traffic(kernel: str, stride: int):
 
 
 def survey_count_entry(avg_ms, evals_per_launch, clocks, peaks):
-    """The DCA kernel against the FP32 instruction peak by the scope table's own count: 285 FP32
-    instructions (the middle of its 250-320 estimate: 2-3 Newton iterations of an RK4 partial step
-    and the plane and distance arithmetic, plus min / cap / square) per DCA evaluation, i.e. per
-    (seed, unmasked hit) pair, against 152 SMs x 128 FP32 lanes x the maximum SM clock."""
-    instr = SURVEY_INSTR_PER_EVAL * evals_per_launch
+    """The DCA kernel against the FP32 instruction peak by an a-priori instruction count: 285 FP32
+    instructions (the middle of a 250-320 estimate: 2-3 Newton iterations of an RK4 partial step and
+    the plane and distance arithmetic, plus min / cap / square) per DCA evaluation, i.e. per (seed,
+    unmasked hit) pair, against 152 SMs x 128 FP32 lanes x the maximum SM clock."""
+    instr = INSTR_PER_EVAL_ESTIMATE * evals_per_launch
     rate = instr / (avg_ms * 1e-3)
     peak = 152 * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6
     return {"kernel": "dca", "bound": "alu", "achieved": rate / 1e12, "peak": peak / 1e12,
-            "unit": "T FP32 instr/s", "frac": rate / peak, "instr_per_eval": SURVEY_INSTR_PER_EVAL,
+            "unit": "T FP32 instr/s", "frac": rate / peak, "instr_per_eval": INSTR_PER_EVAL_ESTIMATE,
             "evals_per_launch": evals_per_launch, "avg_launch_ms": avg_ms,
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x max SM clock"}
 
