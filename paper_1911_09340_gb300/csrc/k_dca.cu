@@ -154,6 +154,15 @@ struct Acc<double> {
 
 } // namespace
 
+// Extra reach (m) when an FP64 kernel tests a sphere in FP32: float rounding of the wire frame (unit
+// vectors and the offsets av = a.v, aw = a.w) and of the distance arithmetic moves the distance by
+// a few ulp of the coordinates involved, ~1e-7 m per metre of |av| + |aw| + reach; 2 um plus 1 um
+// per metre is a generous bound (the FP64 test it stands in for then never rejects more).
+__device__ __forceinline__ float sph_margin_f32(double av, double aw)
+{
+    return 2e-6f + 1e-6f * (float)(fabs(av) + fabs(aw));
+}
+
 template <typename T>
 __device__ __forceinline__ bool sphere_within(const float4 &sp, T fvx, T fvy, T fvz, T fav, T fwx,
                                               T fwy, T fwz, T faw, T ax, T ay, T az, T ux, T uy,
@@ -349,10 +358,24 @@ __device__ __forceinline__ void group_wires(const F &f, const DcaArgs &a, const 
                 const T lim = capw + half_rec;
                 const Q4<T> r0 = rec[4 * iw + 0], r1 = rec[4 * iw + 1], r2 = rec[4 * iw + 2],
                             r3 = rec[4 * iw + 3];
-                for (int j = 0; j < gr.n0w; ++j)
-                    if (sphere_within<T>(sph0[j], r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w, r2.x,
-                                         r2.y, r2.z, r3.x, r3.y, r3.z, lim))
-                        mask0 |= 1u << j;
+                if constexpr (sizeof(T) == 8) {
+                    // FP64 kernels test the (float) spheres in FP32: the part's FP64 rate is the
+                    // limit there.  The reach grows by sph_margin_f32 so that the test stays a
+                    // superset of the FP64 one.
+                    const float l = (float)lim + sph_margin_f32(r0.w, r1.w);
+                    const float v0 = (float)r0.x, v1 = (float)r0.y, v2 = (float)r0.z, va = (float)r0.w;
+                    const float w0 = (float)r1.x, w1 = (float)r1.y, w2 = (float)r1.z, wa = (float)r1.w;
+                    for (int j = 0; j < gr.n0w; ++j)
+                        if (sphere_within<float>(sph0[j], v0, v1, v2, va, w0, w1, w2, wa, (float)r2.x,
+                                                 (float)r2.y, (float)r2.z, (float)r3.x, (float)r3.y,
+                                                 (float)r3.z, l))
+                            mask0 |= 1u << j;
+                } else {
+                    for (int j = 0; j < gr.n0w; ++j)
+                        if (sphere_within<T>(sph0[j], r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w,
+                                             r2.x, r2.y, r2.z, r3.x, r3.y, r3.z, lim))
+                            mask0 |= 1u << j;
+                }
             }
         }
         for (int t = 0; t < clen; ++t) {
@@ -465,10 +488,18 @@ __device__ __forceinline__ void group_wires(const F &f, const DcaArgs &a, const 
                     const bool end1 = G1 == 1 && (k1 == 0 || (k1 >= gr.elo && k1 <= gr.ehi));
                     // one-state segments away from the track ends need only the interior reach
                     const T lim1 = G1 == 1 ? (end1 ? capth + half_rec : thin) : capth;
-                    const bool hit1 = lane < N1 &&
-                                      sphere_within<T>(sph1[j * kN1Max + lane], fvx, fvy, fvz, fav,
-                                                       fwx, fwy, fwz, faw, ax, ay, az, ux, uy, uz,
-                                                       lim1);
+                    bool hit1;
+                    if constexpr (sizeof(T) == 8)
+                        hit1 = lane < N1 &&
+                               sphere_within<float>(sph1[j * kN1Max + lane], (float)fvx, (float)fvy,
+                                                    (float)fvz, (float)fav, (float)fwx, (float)fwy,
+                                                    (float)fwz, (float)faw, (float)ax, (float)ay,
+                                                    (float)az, (float)ux, (float)uy, (float)uz,
+                                                    (float)lim1 + sph_margin_f32(fav, faw));
+                    else
+                        hit1 = lane < N1 &&
+                               sphere_within<T>(sph1[j * kN1Max + lane], fvx, fvy, fvz, fav, fwx, fwy,
+                                                fwz, faw, ax, ay, az, ux, uy, uz, lim1);
                     const uint32_t u1 = __ballot_sync(0xffffffffu, hit1);
                     if (u1) {
                         // one contiguous range from the first to the last candidate level-1
