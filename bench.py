@@ -161,7 +161,7 @@ def pairs_of(ev, classes):
 def oracle_rate(ev, target_s: float = 10.0, nthreads=None, stride: int = 16):
     """Times the oracle's RSS scan of partition 0 on a strided sample of its seeds, sized for
     ~target_s of CPU time, recording every stride-th state like the GPU arm; returns (evals/s,
-    threads, sample description)."""
+    threads, sample description, wall seconds of the timed sample)."""
     import oracle as O
     from paper_1911_09340_gb300 import synth
     nthreads = nthreads or O.default_threads()
@@ -183,7 +183,7 @@ def oracle_rate(ev, target_s: float = 10.0, nthreads=None, stride: int = 16):
     dt, n = run(n2)
     evals = n * ev.n_hits
     return evals / dt, nthreads, f"{n} of {spec.n_seeds} seeds (strided) of turn partition 0 of event 0, " \
-                                f"{ev.n_hits} hits, stride {stride}, FP64 oracle, {dt:.1f} s"
+                                f"{ev.n_hits} hits, stride {stride}, FP64 oracle, {dt:.1f} s", dt
 
 
 def workload_config(args, arithmetic: str):
@@ -200,15 +200,17 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     ev = make_events([0])[0]
-    steps = []
+    steps, walls = [], []
     for i in range(args.warmup + args.steps):
-        rate, cores, sample = oracle_rate(ev, target_s=args.ref_seconds, stride=args.stride)
+        rate, cores, sample, wall = oracle_rate(ev, target_s=args.ref_seconds, stride=args.stride)
         if i >= args.warmup:
             steps.append(rate)
+            walls.append(wall)
     value = statistics.median(steps)
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+        "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+        "ms_per_step": 1e3 * statistics.mean(walls),   # a step: one bounded sample (see cpu_baseline)
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": dict(workload_config(args, "FP64 CPU oracle"), parallelism=f"host threads ({cores})"),
         "cpu_baseline": {"value": value, "unit": "evals/s", "cores": cores, "kind": "oracle",
