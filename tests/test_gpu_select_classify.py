@@ -36,13 +36,14 @@ def test_select_matches_oracle(ctx, dtype, S):
 
 
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
-@pytest.mark.parametrize("case", ["event", "ties", "ragged", "no_wires", "tiled"])
+@pytest.mark.parametrize("case", ["event", "ties", "ragged", "no_wires", "tiled", "exact"])
 def test_selection_inside_the_dca_launch_equals_select(ctx, dtype, case):
     """comet_scan_dca's optional best_idx / best_rss (the k = 1 selection folded into the DCA
     launch: per warp, per CTA, then the last CTA) equal comet_scan_select(k = 1) on the RSS the same
     launch wrote, bit for bit: an event's partition (persistent kernel), seeds duplicated so that
     equal RSS values tie (lowest index wins), a ragged seed count, no wires (every RSS 0: seed 0),
-    and more than 1024 wires (tiled kernel, one CTA per 128 seeds)."""
+    and more than 1024 wires (tiled kernel, one CTA per 128 seeds), and the exhaustive path that a
+    requested dca_out takes (every wire refined from the closest of all states)."""
     from gpu_util import gpu_propagate
     ev = synth.multi_turn_event(1, counts=(4, 8, 8, 16))
     seeds = O.lattice(ev.partitions[0])
@@ -73,7 +74,8 @@ def test_selection_inside_the_dca_launch_equals_select(ctx, dtype, case):
     for rep in range(2):                  # twice: the arrival counter is left at zero
         bi = torch.full((1,), -5, dtype=torch.int64, device="cuda")
         bv = torch.full((1,), -5.0, dtype=dtype, device="cuda")
-        B.comet_scan_dca(ctx, f, bp, pts, nv, charge, w, o, d, m, rss, n_in, n_wires=W,
+        dca = torch.empty((max(W, 1), S), dtype=dtype, device="cuda") if case == "exact" else None
+        B.comet_scan_dca(ctx, f, bp, pts, nv, charge, w, o, d, m, rss, n_in, n_wires=W, dca_out=dca,
                          best_idx=bi, best_rss=bv)
         ri = torch.full((1,), -7, dtype=torch.int64, device="cuda")
         rv = torch.zeros(1, dtype=dtype, device="cuda")
