@@ -90,9 +90,12 @@ def params_for(spec, n_steps: int, dtype=torch.float32, stride: int = 1, lam: fl
 def scan_partition(ctx: B.Context, field: B.DeviceField, params: B.ScanParams, spec,
                    ev: DeviceEvent, ws: Workspace, k: int = 1, update_mask: bool = True,
                    want_dca: Optional[torch.Tensor] = None, dca_wire: Optional[torch.Tensor] = None,
-                   hit_class: Optional[torch.Tensor] = None, timer=None):
-    """One turn partition: lattice -> propagate -> dca -> select -> classify.  Results stay on the
-    device in ``ws`` (idx, best, rss, n_in, hit_class) and ``ev.mask`` (updated in place)."""
+                   hit_class: Optional[torch.Tensor] = None, timer=None,
+                   best_idx: Optional[torch.Tensor] = None, best_rss: Optional[torch.Tensor] = None):
+    """One turn partition: lattice -> propagate -> dca (with the selection when k = 1, else a
+    select launch) -> classify.  Results stay on the device in ``ws`` (idx, best, rss, n_in,
+    hit_class) and ``ev.mask`` (updated in place); with k = 1, ``best_idx`` / ``best_rss`` ([1]
+    device tensors) take the selected seed and its RSS instead of ws.idx / ws.best."""
     S = spec.n_seeds
     seeds, charge, pts, nv, rss, n_in = ws.views(S, params.n_rec)
     mark = timer.mark if timer is not None else (lambda name: None)
@@ -104,16 +107,17 @@ def scan_partition(ctx: B.Context, field: B.DeviceField, params: B.ScanParams, s
     mark("dca")
     # k = 1: the seed of lowest RSS is selected inside the DCA launch; top-k takes comet_scan_select
     fused = k == 1
+    bi = (ws.idx[:1] if best_idx is None else best_idx) if fused else ws.idx
+    br = (ws.best[:1] if best_rss is None else best_rss) if fused else None
     B.comet_scan_dca(ctx, field, params, pts, nv, charge, ev.wires, ev.hit_offsets, ev.drift,
                      ev.mask, rss, n_in, dca_out=want_dca, n_unconverged=ws.n_unconv, n_wires=ev.W,
-                     bounds=bounds, best_idx=ws.idx[:1] if fused else None,
-                     best_rss=ws.best[:1] if fused else None)
+                     bounds=bounds, best_idx=bi if fused else None, best_rss=br)
     if not fused:
         mark("select")
         B.comet_scan_select(ctx, rss, k, ws.idx[:k], ws.best[:k])
     mark("classify")
     hc = ws.hit_class[: max(ev.H, 1)] if hit_class is None else hit_class
-    B.comet_scan_classify(ctx, field, params, pts, nv, charge, ws.idx, ev.wires, ev.hit_offsets,
+    B.comet_scan_classify(ctx, field, params, pts, nv, charge, bi, ev.wires, ev.hit_offsets,
                           ev.drift, ev.mask, hc, dca_wire=dca_wire, update_mask=update_mask,
                           n_wires=ev.W)
     mark(None)
@@ -184,10 +188,11 @@ class PipelinedScanner:
         ctx.set_dca_ctas_per_sm(dca_ctas_per_sm)
 
     def partition(self, params: B.ScanParams, spec, ev: DeviceEvent, hit_class=None,
-                  rec_timer=None, timer=None, update_mask: bool = True):
+                  rec_timer=None, timer=None, update_mask: bool = True, best_idx=None, best_rss=None):
         """Enqueues one partition (recording on the second stream, the rest on the current
         stream); returns its workspace (idx, best, rss, n_in, hit_class valid once the current
-        stream reaches them)."""
+        stream reaches them).  ``best_idx`` / ``best_rss`` ([1] device tensors) take the selected
+        seed and its RSS instead of the workspace's idx / best."""
         b = self.k
         self.k ^= 1
         ws = self.ws[b]
@@ -209,12 +214,14 @@ class PipelinedScanner:
         main.wait_event(ready)
         mark = timer.mark if timer is not None else (lambda name: None)
         mark("dca")
+        bi = ws.idx[:1] if best_idx is None else best_idx
+        br = ws.best[:1] if best_rss is None else best_rss
         B.comet_scan_dca(self.ctx, self.field, params, pts, nv, charge, ev.wires, ev.hit_offsets,
                          ev.drift, ev.mask, rss, n_in, n_unconverged=ws.n_unconv, n_wires=ev.W,
-                         bounds=bounds, best_idx=ws.idx[:1], best_rss=ws.best[:1])
+                         bounds=bounds, best_idx=bi, best_rss=br)
         mark("classify")
         hc = ws.hit_class[: max(ev.H, 1)] if hit_class is None else hit_class
-        B.comet_scan_classify(self.ctx, self.field, params, pts, nv, charge, ws.idx, ev.wires,
+        B.comet_scan_classify(self.ctx, self.field, params, pts, nv, charge, bi, ev.wires,
                               ev.hit_offsets, ev.drift, ev.mask, hc, update_mask=update_mask,
                               n_wires=ev.W)
         mark(None)
@@ -283,12 +290,12 @@ class HostEventRunner:
             pinned["d"].numel() * pinned["d"].element_size()
         n = len(ev.partitions)
         for i, (spec, p) in enumerate(zip(ev.partitions, event_params(ev, self.dtype, stride, lam))):
+            # the DCA launch writes the selected seed and its RSS straight into the result arrays
+            bi, br = self.res_idx[i:i + 1], self.res_rss[i:i + 1]
             if self.pipeline is not None:
-                ws = self.pipeline.partition(p, spec, dev)
+                self.pipeline.partition(p, spec, dev, best_idx=bi, best_rss=br)
             else:
-                ws = scan_partition(self.ctx, self.field, p, spec, dev, self.ws)
-            self.res_idx[i:i + 1].copy_(ws.idx[:1])
-            self.res_rss[i:i + 1].copy_(ws.best[:1])
+                scan_partition(self.ctx, self.field, p, spec, dev, self.ws, best_idx=bi, best_rss=br)
         h_idx, h_rss, h_mask = out if out is not None else (self.h_idx, self.h_rss, self.h_mask)
         h_idx[:n].copy_(self.res_idx[:n], non_blocking=True)
         h_rss[:n].copy_(self.res_rss[:n], non_blocking=True)

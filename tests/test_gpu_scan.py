@@ -320,3 +320,41 @@ def test_sixteen_million_seed_partition_needs_64bit_offsets(ctx):
     assert excess.max() <= 1e-12, (int((excess > 1e-12).sum()), sample[int(np.argmax(excess))])
     r_best = r["rss"][np.searchsorted(sample, g_idx)]
     assert r_best <= r["rss"].min() * (1 + 1e-5)
+
+
+@pytest.mark.parametrize("pipelined", [False, True])
+def test_host_event_runner_equals_device_scan(ctx, pipelined):
+    """The end-to-end path from pinned host buffers (copies in, every partition, the selected seed
+    and RSS written by the DCA launch straight into the result arrays, copies out) gives the same
+    best seed and RSS per partition and the same final hit mask as the device-resident scan, one
+    partition at a time and with the next partition's recording beside the DCA."""
+    events = [synth.multi_turn_event(i, counts=(4, 8, 8, 16)) for i in range(3)]
+    dtype, stride, lam = torch.float32, 32, 1e-2
+    field = B.DeviceField.from_synth(UNIFORM)
+    S = max(sp.n_seeds for ev in events for sp in ev.partitions)
+    n_rec = max(n // stride + 1 for ev in events for n in ev.n_steps)
+    H = max(ev.n_hits for ev in events)
+    ws = scan.Workspace(S, n_rec, H, dtype)
+    ref = []
+    for ev in events:
+        dev = scan.DeviceEvent.from_event(ev, dtype)
+        parts = scan.scan_event(ctx, field, ev, dev, ws, dtype, stride, lam, collect=True)
+        ref.append((parts, dev.mask[: ev.n_hits].cpu().numpy().copy()))
+    pipe = scan.PipelinedScanner(ctx, field, S, n_rec, H, dtype) if pipelined else None
+    runner = scan.HostEventRunner(ctx, field, ws, max(ev.n_wires for ev in events), H, dtype,
+                                  pipeline=pipe)
+    try:
+        outs = []
+        for ev in events:           # enqueued back to back, results read once at the end
+            out = runner.result_slots()
+            runner.run(ev, runner.pin(ev, dtype), stride, lam, out=out)
+            outs.append(out)
+        torch.cuda.synchronize()
+    finally:
+        if pipe is not None:
+            pipe.close()
+    for ev, (parts, mask), (h_idx, h_rss, h_mask) in zip(events, ref, outs):
+        n = len(ev.partitions)
+        assert [int(v) for v in h_idx[:n]] == [p["idx"] for p in parts]
+        assert [float(v) for v in h_rss[:n]] == [p["rss"] for p in parts]
+        assert np.array_equal(h_mask[: ev.n_hits].numpy(), mask)
