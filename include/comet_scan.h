@@ -177,7 +177,8 @@ comet_status comet_scan_lattice(comet_ctx *ctx, comet_dtype dtype, const comet_l
  *   seeds    SoA [6][S] T: (x, y, z, px, py, pz) of each seed.
  *   charge   [S] int8: particle charge in units of e (the electron is -1); 0 gives a straight line.
  *   points   out, SoA [6][n_rec][S] T: recorded state k of seed s is points[c][k][s].  Entries past
- *            n_valid[s] are left unwritten.
+ *            n_valid[s] are unspecified (left unwritten, or states extrapolated past the target
+ *            region by the FP64 block recording below); no call reads them.
  *   n_valid  out, [S] int32: number of recorded states of each seed (1 .. n_rec).
  *   bounds   optional out (NULL to skip), [ceil(S/32)][200][4] float32, 16-byte aligned: search
  *            bounds for comet_scan_dca with the same params -- for each group of 32 consecutive
@@ -186,7 +187,9 @@ comet_status comet_scan_lattice(comet_ctx *ctx, comet_dtype dtype, const comet_l
  *            comet_scan_dca from rebuilding them.
  * One thread extrapolates one seed with fixed-step RK4.  The FP32 path carries each state component
  * as an unevaluated float pair (a compensated sum), so that 6,500 steps stay within a few um of FP64;
- * the recorded value is the leading float. */
+ * the recorded value is the leading float.  FP64 in a uniform axial field with fewer than four
+ * 32-seed groups per SM records one super-segment per warp instead (comet_ctx_set_record_blocks);
+ * it then also sets n_valid with a byte memset before its kernel. */
 comet_status comet_scan_propagate(comet_ctx *ctx, comet_dtype dtype, const comet_field *field,
                                   const comet_scan_params *params, const void *seeds,
                                   const int8_t *charge, int64_t S, void *points, int32_t *n_valid,
