@@ -58,8 +58,8 @@ def test_fp64_points_match_oracle_single_event(ctx):
         assert np.abs(got[s, :n, 3:] - ref[s, :n, 3:]).max() <= 1e-9 * 105
 
 
-@pytest.mark.parametrize("stride", [1, 3, 16])
-def test_fp64_block_recording_equals_sequential(ctx, stride):
+@pytest.mark.parametrize("stride,n_seeds", [(1, 200), (3, 200), (16, 200), (1, 1), (16, 33)])
+def test_fp64_block_recording_equals_sequential(ctx, stride, n_seeds):
     """FP64 in an axial field with fewer than four 32-seed groups per SM records each super-segment
     in its own warp, started from the composed interval map (comet_ctx_set_record_blocks(1), the
     default); with the setting at 0 the same seeds take the one-warp-per-32-seeds kernel.  Both
@@ -67,7 +67,7 @@ def test_fp64_block_recording_equals_sequential(ctx, stride):
     and the same counts, both match the oracle, and both sets of spheres contain every recorded
     state (the containment test covers the bounds with the default)."""
     ev, seeds = _cfg1_seeds(8)
-    seeds = seeds[:200]
+    seeds = seeds[:n_seeds]
     op, bp = both_params(n_steps=ev.n_steps[0] // stride * stride, stride=stride, rmax=0.67)
     field = B.DeviceField.from_synth(synth.uniform_field(1.0))
     _, _, p_blk, nv_blk = gpu_propagate(ctx, field, bp, seeds, -1, torch.float64)
@@ -78,7 +78,8 @@ def test_fp64_block_recording_equals_sequential(ctx, stride):
         ctx.set_record_blocks(1)
     nb, ns = nv_blk.cpu().numpy(), nv_seq.cpu().numpy()
     assert np.array_equal(nb, ns)
-    assert (nb < bp.n_rec).any() and (nb == bp.n_rec).any()   # some tracks leave through rmax
+    if n_seeds >= 33:
+        assert (nb < bp.n_rec).any() and (nb == bp.n_rec).any()   # some tracks leave through rmax
     gb, gs = to_aos_points(p_blk), to_aos_points(p_seq)
     ref, rnv = O.propagate(synth.uniform_field(1.0), op, seeds, -1)
     assert np.array_equal(nb, rnv)

@@ -36,12 +36,13 @@ def test_select_matches_oracle(ctx, dtype, S):
 
 
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
-@pytest.mark.parametrize("case", ["event", "ties", "ragged", "no_wires", "tiled", "exact"])
+@pytest.mark.parametrize("case", ["event", "ties", "ragged", "single", "no_wires", "tiled", "exact"])
 def test_selection_inside_the_dca_launch_equals_select(ctx, dtype, case):
     """comet_scan_dca's optional best_idx / best_rss (the k = 1 selection folded into the DCA
     launch: per warp, per CTA, then the last CTA) equal comet_scan_select(k = 1) on the RSS the same
     launch wrote, bit for bit: an event's partition (persistent kernel), seeds duplicated so that
-    equal RSS values tie (lowest index wins), a ragged seed count, no wires (every RSS 0: seed 0),
+    equal RSS values tie (lowest index wins), a ragged seed count, one seed, no wires (every RSS 0:
+    seed 0),
     and more than 1024 wires (tiled kernel, one CTA per 128 seeds), and the exhaustive path that a
     requested dca_out takes (every wire refined from the closest of all states)."""
     from gpu_util import gpu_propagate
@@ -52,6 +53,8 @@ def test_selection_inside_the_dca_launch_equals_select(ctx, dtype, case):
         seeds = np.concatenate([seeds[::2], seeds[::2], seeds[4:5]])   # every seed twice, in order
     elif case == "ragged":
         seeds = seeds[:3001]
+    elif case == "single":
+        seeds = seeds[1000:1001]
     elif case == "no_wires":
         wires, offs, drift = np.zeros((6, 0)), np.zeros(1, np.int32), np.zeros(0)
     elif case == "tiled":
