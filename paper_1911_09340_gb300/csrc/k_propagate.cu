@@ -413,13 +413,14 @@ __global__ void __launch_bounds__(128) propagate_kernel(F f, PropArgs a, BatchLa
 // recorded states are the powers of one interval map (see axial_interval), so each super-segment
 // [r0, r1) starts from the seed mapped over r0 intervals at once and then steps interval by
 // interval as propagate_kernel does: with 4,096 seeds the sequential kernel has one warp per SM,
-// one of its four schedulers issuing FP64 work; here each SM gets up to G0-fold more warps.  The
-// states are those of the sequential recording up to rounding (the map of r0 intervals against r0
-// applications of the one-interval map).  n_valid: the caller's array is set to a large value
-// first (a byte memset), then each block lowers it to its first state outside the target region
-// plus one, and the last block to n_rec.  Spheres: a lane whose track left the region in an earlier
-// block still contributes its (extrapolated) states, which only makes the sphere larger; within
-// the block a lane stops contributing to segments after its exit, as in propagate_kernel.
+// one of its four schedulers issuing FP64 work; here each group has one warp per super-segment
+// (up to 8).  The states are those of the sequential recording up to rounding (the map of r0
+// intervals against r0 applications of the one-interval map).  n_valid: the caller's array is set
+// to a large value first (a byte memset), then each block lowers it to its first state outside the
+// target region plus one, and the last block to n_rec.  Spheres: a lane whose track left the region
+// in an earlier block still contributes its (extrapolated) states, which only makes the sphere
+// larger; within the block a lane stops contributing to segments after its exit, as in
+// propagate_kernel.
 template <int STRIDE>
 __global__ void __launch_bounds__(32) propagate_blocks_kernel(FieldAxial<double> f, PropArgs a)
 {
