@@ -637,7 +637,7 @@ FP64_PEAK_TFLOPS = 1.25
 # count the recorded states).
 # Valid only for the kernel sources they were measured on (SHA-1 of the package's csrc/ files);
 # reported as null once those change.
-NCU_TRAFFIC = {"csrc_sha1": "cf2a90a059654e2e4599c0585a3c4a544e9e30b0", "stride": 32,
+NCU_TRAFFIC = {"csrc_sha1": "4e3dd4393e52b4d843f8a1d7b3ca6aaa9c6a8301", "stride": 32,
                "dca": 171.5e6, "propagate": 403.7e6}
 
 

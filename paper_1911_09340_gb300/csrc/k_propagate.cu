@@ -466,6 +466,22 @@ __global__ void __launch_bounds__(32) propagate_blocks_kernel(FieldAxial<double>
     }
 
     const double zmin = a.zmin, zmax = a.zmax, rmax2 = a.rmax * a.rmax;
+    // A lane whose states in [r0, r1) provably stay inside the target region skips the per-state
+    // test: in this field the track is a circle of radius R = pT / |P0 w| about
+    // C = (x, y) + (py, -px) / (P0 w) (in the transverse plane) and z moves by ks.dz per interval,
+    // so all its states lie within |C| + R of the axis and between the z of the first and the last
+    // state.  The 1 um margin is far above the RK4 map's drift from that circle (~1e-13 m per turn)
+    // and the rounding; lanes near the boundary keep the per-state test.
+    bool safe = false;
+    if (valid && w != 0.0) {
+        const double pw = pd * w;
+        const double cx = y[0] + y[4] / pw, cy = y[1] - y[3] / pw;
+        const double rr = sqrt(y[3] * y[3] + y[4] * y[4]) / fabs(pw);
+        const double rout = sqrt(cx * cx + cy * cy) + rr + 1e-6;
+        const double z_end = y[2] + (double)(r1 - 1 - r0) * ks.dz;
+        const double zlo = fmin(y[2], z_end) - 1e-6, zhi = fmax(y[2], z_end) + 1e-6;
+        safe = rout * rout < rmax2 && zlo > zmin && zhi < zmax;
+    }
     const bool wb = a.bounds != nullptr;
     float4 *tab = wb ? (float4 *)a.bounds + g * kBoundsPerGroup : nullptr;
     const int N1 = (r1 - r0 + G1 - 1) / G1;   // level-1 segments of this super-segment
@@ -497,7 +513,8 @@ __global__ void __launch_bounds__(32) propagate_blocks_kernel(FieldAxial<double>
             const int64_t o = (int64_t)r * S + s;
 #pragma unroll
             for (int cc = 0; cc < 6; ++cc) pts[cc * plane + o] = y[cc];
-            if (exit_k == 0x7fffffff && outside_region<double>(y[0], y[1], y[2], zmin, zmax, rmax2))
+            if (!safe && exit_k == 0x7fffffff &&
+                outside_region<double>(y[0], y[1], y[2], zmin, zmax, rmax2))
                 exit_k = r;
         }
         if (wb) {
